@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""AIREBO MD throughput on one GB300: atom-steps/s on 1,044,480-atom polyethylene.
+
+A step is one velocity-Verlet NVE step of the whole hot path: half kick and
+drift, the displacement check that triggers a list rebuild (binning, LJ half
+list, REBO intermediate list) when an atom moved more than skin/2, the exact
+REBO list, REBO bonds with the bond order, torsion, the connectivity map, the
+LJ pairs, the deferred b* pairs, and the second half kick.  `value` is the
+FP64 path; the mixed path (FP32 geometry/splines/bond order, FP64
+accumulation) is reported beside it with its max |dF| against FP64.
+
+Timing: W untimed warm-up steps, then K steps bracketed by a barrier and
+torch.cuda.synchronize(), timed with CUDA events on the library's stream; the
+working set (~3 GB of lists, 50 MB of positions and forces) is larger than the
+L2, so no flush is needed.  Per-kernel times come from CUDA events the library
+records around each launch during the same timed region.
+
+--impl reference times the CPU oracle (the reference arm of this build) on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import platform
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1810_07026_gb300 import inputs  # noqa: E402
+
+METRIC = "AIREBO atom-steps/s (1M-atom PE) FP64 vs mixed on GB300; max |dF| vs FP64 oracle"
+UNIT = "atom-steps/s"
+WORKLOAD = "pe1m"
+DT = 0.5
+TEMP = 300.0
+
+# Algorithmic FP64 work per unit, in flops (FMA = 2); see the roofline notes in the design doc.
+FLOPS_LJ_PAIR = 44        # displacement with image (9), r^2 (5), sqrt, 1/r, (s/r)^6, V, dV/dr, force, sums (30)
+FLOPS_LJ_TEST = 14        # displacement and r^2 of a pair that is tested but not evaluated (C = 0, or queued for b*)
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+FP64_FMA_PER_SM_CLK = 2   # 1.25 TFLOP/s nominal FP64 = 152 SMs x 2 FMA x 2 flop x 2.07 GHz
+FP32_FMA_PER_SM_CLK = 128
+
+
+def peaks_nominal():
+    f64 = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    f32 = SM_COUNT * FP32_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    return f64, f32
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def oracle_sample(pos, types, box, target_s, threads=None):
+    """Time the CPU oracle on a sphere of anchor atoms of the workload, sized
+    to take about target_s seconds.  Returns (atom-steps/s, threads, sample text, counters per anchor)."""
+    from oracle import oracle as O
+    if threads:
+        O.set_threads(threads)
+    o = O.Oracle(inputs.params_text(inputs.make_params(0)))
+    center = int(np.argmin(np.abs(pos - (box / 2)[:, None]).sum(axis=0)))
+    r = 12.0
+    t0 = time.perf_counter()
+    _, _, c, na = o.evaluate_sphere(pos, types, box, center, r)
+    dt = time.perf_counter() - t0
+    rate = na / dt
+    if dt < target_s * 0.5:
+        want = rate * target_s
+        r = max(r, (want / (0.1295 * 4.0 / 3.0 * math.pi)) ** (1.0 / 3.0))
+        t0 = time.perf_counter()
+        _, _, c, na = o.evaluate_sphere(pos, types, box, center, r)
+        dt = time.perf_counter() - t0
+    nth = O.threads()
+    per = {k: v / na for k, v in c.items()}
+    sample = f"all terms anchored at the {na} atoms within {r:.1f} A of the box centre of the 1,044,480-atom PE, one force evaluation"
+    return na / dt, nth, sample, per, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    pos, types, box = inputs.workload(WORKLOAD)
+    rates = []
+    nth = None
+    sample = ""
+    for k in range(args.warmup + args.steps):
+        target = max(2.0, min(8.0, 150.0 / max(1, args.warmup + args.steps)))
+        rate, nth, sample, _, _ = oracle_sample(pos, types, box, target)
+        if k >= args.warmup:
+            rates.append(rate)
+    v = float(np.median(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * len(types) / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "polyethylene 34x40x64 cells, 1,044,480 atoms, 300 K, dt 0.5 fs",
+                       "global_batch": len(types), "parallelism": "cpu"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": nth, "kind": "oracle",
+                             "sample": sample + " per step; value is the median over the steps",
+                             "cpu": cpu_model()},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    from paper_1810_07026_gb300 import build, airebo
+    build.build()
+    A = airebo
+    params = inputs.params_text(inputs.make_params(0))
+    pos0, types, box = inputs.workload(WORKLOAD)
+    vel0 = inputs.velocities(types, TEMP, seed=2)
+    n = len(types)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream()
+    results = {}
+    forces = {}
+    for prec, name in ((A.FP64, "fp64"), (A.MIXED, "mixed")):
+        with torch.cuda.stream(stream):
+            ev = A.Airebo(params, precision=prec, stream=stream)
+            pos = torch.tensor(pos0, device=dev)
+            vel = torch.tensor(vel0, device=dev)
+            t = torch.tensor(types, device=dev)
+            ev.neighbor(pos, t, box)
+            f, e4, _ = ev.compute(pos)
+            forces[name] = f.clone()
+            e_start = ev.nve(pos, vel, f, DT, 1)
+            for _ in range(max(0, args.warmup - 1)):
+                ev.nve(pos, vel, f, DT, 1)
+            builds0 = ev.counters()["list_builds"]
+            stream.synchronize()
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            clocks = Clocks(local) if name == "fp64" else None
+            if clocks:
+                clocks.start()
+            ev.set_timing(True)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                ev.nve(pos, vel, f, DT, 1)
+            e1.record(stream)
+            e1.synchronize()
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            ck = clocks.stop() if clocks else None
+            kt = ev.kernel_times()
+            ev.set_timing(False)
+            builds = ev.counters()["list_builds"] - builds0
+            e_end = ev.nve(pos, vel, f, DT, 1).cpu().numpy()
+            e_beg = e_start.cpu().numpy()
+            if dist:
+                tt = torch.tensor([ms], device=dev)
+                dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+                ms = tt.item()
+            results[name] = dict(ms=ms, kt=kt, clocks=ck, builds=builds, counters=ev.counters(),
+                                 drift=(e_end[2] - e_beg[2]) / (args.steps + args.warmup + 1) / n,
+                                 etot=float(e_end[2]))
+            ev.close()
+    # mixed against FP64 at the same (initial) positions
+    df = (forces["mixed"] - forces["fp64"]).abs().max().item()
+    fscale = forces["fp64"].abs().max().item()
+
+    # e2e through the host-buffer API (FP64): copy in, one step, copy out, every step
+    e2e = None
+    with torch.cuda.stream(stream):
+        ev = A.Airebo(params, precision=A.FP64, stream=stream)
+        hp = torch.tensor(pos0).pin_memory()
+        hv = torch.tensor(vel0).pin_memory()
+        hf = torch.zeros_like(hp).pin_memory()
+        fh, _, _ = ev.compute_host(hp.numpy(), types, box)
+        hf.copy_(torch.from_numpy(fh))
+        for _ in range(args.warmup):
+            ev.nve_host(hp, hv, hf, DT, 1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ev.nve_host(hp, hv, hf, DT, 1)
+        dt_e2e = time.perf_counter() - t0
+        ev.close()
+        e2e = {"value": n * args.steps / dt_e2e, "unit": UNIT, "h2d_bytes_per_step": 3 * 24 * n,
+               "d2h_bytes_per_step": 3 * 24 * n + 32}
+
+    r64 = results["fp64"]
+    value = ws * n * args.steps / (r64["ms"] * 1e-3)
+    mixed_value = ws * n * args.steps / (results["mixed"]["ms"] * 1e-3)
+    # roofline of the dominant kernel (FP64 path)
+    kt = r64["kt"]
+    dom = max((k for k in kt if k not in ("neighbor",)), key=lambda k: kt[k][0])
+    peak64_nom, peak32_nom = peaks_nominal()
+    peak64_meas = A.alu_peak(A.FP64)
+    peak32_meas = A.alu_peak(A.MIXED)
+
+    line = None
+    if rank == 0:
+        # algorithmic work from the oracle's term counters on a bounded sample
+        cpu_rate, nth, sample, per, cpu_dt = oracle_sample(pos0, types, box, target_s=12.0)
+        pairs_eval = per["lj_in_cutoff"] - per["lj_c_zero"] - per["bstar"]
+        pairs_test = per["lj_c_zero"] + per["bstar"]
+        flops_lj = n * (FLOPS_LJ_PAIR * pairs_eval + FLOPS_LJ_TEST * pairs_test)
+        lj_ms, lj_n = kt["lj"]
+        lj_avg_s = lj_ms * 1e-3 / max(1, lj_n)
+        achieved = flops_lj / lj_avg_s / 1e12 if dom == "lj" else None
+        mix_kt = results["mixed"]["kt"]
+        mlj_ms, mlj_n = mix_kt["lj"]
+        roof = {"kernel": "k_lj<double>", "bound": "alu", "achieved": achieved, "peak": peak64_nom,
+                "unit": "TFLOP/s", "frac": (achieved / peak64_nom) if achieved else None, "traffic": None,
+                "peak_kind": "FP64 nominal from SM count x FMA units x max clock; measured FMA probe beside it",
+                "peak_measured": peak64_meas,
+                "flops_per_launch": flops_lj, "avg_launch_ms": lj_avg_s * 1e3,
+                "dominant_kernel": dom}
+        launches = 0
+        for k, (ms_k, nl) in kt.items():
+            launches += nl
+        launches += args.steps   # the counter-finishing kernel of each compute
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r64["ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "polyethylene 34x40x64 cells, 1,044,480 atoms, 300 K, dt 0.5 fs, skin 1 A",
+                       "global_batch": n * ws, "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                       "l2": "working set > L2 (lists ~3 GB), no flush"},
+            "mixed": {"value": mixed_value, "unit": UNIT, "ms_per_step": results["mixed"]["ms"] / args.steps,
+                      "max_abs_dF_vs_fp64": df, "max_rel_dF_vs_fp64": df / fscale,
+                      "drift_eV_per_atom_step": results["mixed"]["drift"],
+                      "kernel_ms": {k: v[0] / max(1, v[1]) for k, v in mix_kt.items()},
+                      "lj_achieved_fp32_frac": None if not mlj_n else
+                      (flops_lj / (mlj_ms * 1e-3 / mlj_n) / 1e12) / peak32_nom},
+            "drift_eV_per_atom_step": r64["drift"],
+            "list_builds_in_timed_region": r64["builds"],
+            "kernel_ms": {k: v[0] / max(1, v[1]) for k, v in kt.items()},
+            "kernel_share": {k: v[0] / max(1e-9, sum(x[0] for x in kt.values())) for k, v in kt.items()},
+            "roofline": roof,
+            "peaks_TFLOPs": {"fp64_nominal": peak64_nom, "fp64_measured": peak64_meas,
+                             "fp32_nominal": peak32_nom, "fp32_measured": peak32_meas},
+            "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": nth, "kind": "oracle", "sample": sample,
+                             "cpu": cpu_model(), "seconds": cpu_dt},
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": r64["clocks"],
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

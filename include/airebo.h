@@ -1,0 +1,181 @@
+/*
+ * airebo.h -- C ABI of the GB300 AIREBO energy/force library (libairebo.so).
+ *
+ * The library evaluates the AIREBO potential of Hoehnerbach & Bientinesi,
+ * "Optimizing AIREBO" (Sec. 2.1): the REBO term E = f_R + b_ij f_A with the
+ * bond order b_ij (Alg. 1, Sec. 2.1.3), the torsion term (Alg. 2) and the
+ * bond-order- and connectivity-switched Lennard-Jones term (Alg. 3,
+ * Sec. 2.1.2), on one GPU.  The problem statement follows Sec. 2: positions
+ * in, forces F_i = -grad_i V out; a long neighbour list with a skin, rebuilt
+ * only when an atom has moved more than half the skin; a short REBO list
+ * rebuilt every step from an intermediate list (Sec. 4.1).
+ *
+ * Conventions shared by every call:
+ *  - Units: Angstrom, eV, eV/Angstrom, fs, amu ("metal" units).
+ *  - Atom arrays are structure-of-arrays: x[3][n] (all x, then all y, then
+ *    all z), double.  Types are int8: 0 = carbon, 1 = hydrogen.
+ *  - The box is orthorhombic and periodic in all three directions; each edge
+ *    must exceed 4 x the largest REBO cut-off (8 A with the usual values), so
+ *    that a path of three bonds never meets two images of one atom.
+ *    Positions may lie outside the box; at a neighbour build they must lie
+ *    within 127 box lengths of it.
+ *  - Forces are -dE/dx.  The virial is W_ab = -sum_terms sum_atoms
+ *    x_a * dE/dx_b with positions unwrapped within each term, i.e.
+ *    W = -dE/d(strain); order xx, yy, zz, xy, xz, yz.
+ *  - Energies are reported as four doubles: total, REBO, LJ, torsion.
+ *  - Device pointers ("d_") are owned by the caller, must stay valid for the
+ *    duration of the call, and are used on the handle's stream.  Host
+ *    pointers ("h_") are plain host memory.  The library owns its lists and
+ *    scratch buffers and frees them in airebo_destroy.
+ *  - Every call returns an airebo_status and never aborts the process;
+ *    airebo_last_error() gives a text for the last failure on a handle.
+ *  - Calls that return results to the host synchronise the handle's stream.
+ */
+#ifndef AIREBO_H
+#define AIREBO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct airebo_ctx* airebo_handle;
+
+typedef enum {
+    AIREBO_OK = 0,
+    AIREBO_ERR_ARG = 1,        /* bad argument: null pointer, size, box too small, bad parameter text */
+    AIREBO_ERR_CUDA = 2,       /* a CUDA runtime call failed (text in airebo_last_error) */
+    AIREBO_ERR_CAPACITY = 3,   /* more than 8 REBO neighbours on an atom (the bound of Sec. 4.3) */
+    AIREBO_ERR_TIMEOUT = 4,    /* reserved: a bounded device-side wait gave up */
+    AIREBO_ERR_NONFINITE = 5,  /* a position is NaN or infinite */
+    AIREBO_ERR_STATE = 6       /* call out of order, e.g. compute before neighbor */
+} airebo_status;
+
+enum { AIREBO_FP64 = 0, AIREBO_MIXED = 1 };
+
+typedef struct {
+    double skin;          /* neighbour-list skin, Angstrom (default 1.0) */
+    int precision;        /* AIREBO_FP64, or AIREBO_MIXED: FP32 geometry, splines and bond
+                             order; FP64 positions, displacements, accumulation and integrator */
+    int enable_rebo;      /* 1: REBO term (Alg. 1) */
+    int enable_lj;        /* 1: LJ term (Alg. 3) */
+    int enable_torsion;   /* 1: torsion term (Alg. 2) */
+    int max_lj_nbrs;      /* initial long-list capacity per atom; 0 = from the density */
+} airebo_options;
+
+/* Fill opts with the defaults: skin 1.0 A, FP64, all three terms on, auto capacity. */
+void airebo_default_options(airebo_options* opts);
+
+/*
+ * Create a handle.  params: the parameter set as text, one entry per line
+ * "name count v1 ... vcount" (scalars of f_R, f_A, the switches, LJ and
+ * torsion, and the knot data of the g, P, pi^rc and T splines); the handle
+ * keeps its own copy.  stream: a cudaStream_t (NULL = default stream) on which
+ * every later call enqueues its work.  The current CUDA device at creation is
+ * the handle's device.  Returns AIREBO_ERR_ARG for unparsable or incomplete
+ * text.
+ */
+airebo_status airebo_create(const char* params, const airebo_options* opts, void* stream, airebo_handle* out);
+
+/* Free every buffer of the handle.  NULL is accepted. */
+void airebo_destroy(airebo_handle h);
+
+/* Text of the last error on the handle ("" if none). */
+const char* airebo_last_error(airebo_handle h);
+
+/*
+ * Build the neighbour lists (Sec. 2, Sec. 4.1): bin atoms into cells, then a
+ * half list of pairs with r < 3 sigma_ij + skin for the LJ term and a full
+ * intermediate list with r < Dmax_ij + skin for the REBO term, with explicit
+ * periodic images.  d_pos: device double[3][n]; d_types: device int8[n]
+ * (copied); box: host double[3].  Grows its capacities as needed (one stream
+ * synchronisation).  n may be 0.
+ */
+airebo_status airebo_neighbor(airebo_handle h, const double* d_pos, const int8_t* d_types, int64_t n,
+                              const double* box);
+
+/*
+ * Energy and forces at d_pos (same atoms as the last airebo_neighbor; the
+ * lists stay valid while no atom has moved more than skin/2 since it).
+ * d_force: device double[3][n], overwritten.  d_energy4 (device double[4])
+ * and d_virial6 (device double[6]) may be NULL; the virial is only computed
+ * when d_virial6 is given.  Synchronises the stream once to check capacity
+ * flags, and regrows and recomputes when a scratch capacity was exceeded.
+ */
+airebo_status airebo_compute(airebo_handle h, const double* d_pos, double* d_force, double* d_energy4,
+                             double* d_virial6);
+
+/*
+ * Same as airebo_compute with host buffers: copies h_pos to the device, runs
+ * the neighbour build when needed (first call, new n or box, or an atom moved
+ * more than skin/2), computes, and copies forces, energies and virial back.
+ * h_types/box are read on the first call and whenever n changes.
+ */
+airebo_status airebo_compute_host(airebo_handle h, const double* h_pos, const int8_t* h_types, int64_t n,
+                                  const double* box, double* h_force, double* h_energy4, double* h_virial6);
+
+/* *out_flag = 1 if some atom moved more than skin/2 since the last neighbour build. */
+airebo_status airebo_needs_rebuild(airebo_handle h, const double* d_pos, int* out_flag);
+
+/*
+ * Velocity-Verlet NVE (the MD step of Sec. 2): nsteps steps of dt fs on
+ * d_pos/d_vel (device double[3][n], Angstrom, Angstrom/fs, updated in place),
+ * d_force holds the forces on return.  Rebuilds the lists when an atom moved
+ * more than skin/2 (checked every step).  Masses are 12.011 (C) and 1.008 (H)
+ * amu.  On entry d_force must hold the forces at d_pos (from airebo_compute
+ * or the previous airebo_nve call).  d_energy4 (nullable, device double[4])
+ * receives potential energy total, kinetic energy, their sum, and the number
+ * of list builds of the handle so far, after the last step.  The lists must
+ * have been built for these atoms.
+ */
+airebo_status airebo_nve(airebo_handle h, double* d_pos, double* d_vel, double* d_force, double dt, int nsteps,
+                         double* d_energy4);
+
+/* The NVE step with host buffers: copy in, nsteps steps, copy positions,
+ * velocities, forces and d_energy4's four values back. */
+airebo_status airebo_nve_host(airebo_handle h, double* h_pos, double* h_vel, double* h_force, double dt,
+                              int nsteps, double* h_energy4);
+
+/*
+ * Counters of the last compute (int64[8]): bonds, b* pairs, b* pairs with a
+ * nonzero S_b derivative, LJ pairs within the cut-off evaluated in the pair
+ * kernel, connectivity-map entries, list rebuilds, LJ list capacity, bond
+ * order evaluations.  Synchronises.
+ */
+airebo_status airebo_counters(airebo_handle h, int64_t* out8);
+
+
+/*
+ * Copy a neighbour list to the host (for checks).  which: 0 = LJ half list
+ * (pairs i<j, or i==j with a positive image, r < 3 sigma + skin), 1 = REBO
+ * intermediate list (r < Dmax + skin, full), 2 = exact REBO list of the last
+ * compute (r < Dmax, full, at most 8 per atom).  h_cnt: int32[n];
+ * h_j: int32[n * cap]; h_img: int8[n * cap * 3] (image S, x_j + S L - x_i).
+ * Entries beyond cap per atom are dropped (*h_cnt still counts them).
+ */
+airebo_status airebo_export_lists(airebo_handle h, int which, int32_t* h_cnt, int32_t* h_j, int8_t* h_img, int64_t cap);
+
+/*
+ * Per-kernel timing with CUDA events recorded on the handle's stream around
+ * each launch.  airebo_set_timing(h, 1) starts (and zeroes) the record;
+ * airebo_kernel_times fills ms[k] (total milliseconds) and launches[k] for
+ * k = 0 short list, 1 REBO bonds, 2 torsion, 3 connectivity map, 4 LJ pairs,
+ * 5 b* pairs, 6 neighbour build, 7 NVE half steps.  out arrays: 8 entries.
+ */
+airebo_status airebo_set_timing(airebo_handle h, int on);
+airebo_status airebo_kernel_times(airebo_handle h, double* ms, int64_t* launches);
+
+/*
+ * Measure the FMA throughput of the current device with a register-resident
+ * loop (precision AIREBO_FP64 or AIREBO_MIXED for FP32); *tflops receives
+ * the achieved TFLOP/s (an FMA counts 2).  A roofline denominator for the
+ * ALU-bound kernels; it runs for a few tens of milliseconds.
+ */
+airebo_status airebo_alu_peak(int precision, double* tflops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AIREBO_H */

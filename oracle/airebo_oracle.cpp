@@ -266,7 +266,8 @@ struct System {
 
 // all (j, S) != (i, 0) with |x_j + S L - x_i| < cutoff(ti, tj), by binning (Sec. 2)
 template <class Cut>
-void find_pairs(const System& sys, double rmax, Cut cutoff, std::vector<std::vector<Nbr>>& out) {
+void find_pairs(const System& sys, double rmax, Cut cutoff, std::vector<std::vector<Nbr>>& out,
+                const char* only = nullptr) {
     int64_t n = sys.n;
     out.assign(n, {});
     int nc[3], m[3];
@@ -290,6 +291,7 @@ void find_pairs(const System& sys, double rmax, Cut cutoff, std::vector<std::vec
     }
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t i = 0; i < n; i++) {
+        if (only && !only[i]) continue;
         int ci[3] = {cell[i] / (nc[1] * nc[2]), (cell[i] / nc[2]) % nc[1], cell[i] % nc[2]};
         for (int dx = -m[0]; dx <= m[0]; dx++)
             for (int dy = -m[1]; dy <= m[1]; dy++)
@@ -382,12 +384,14 @@ struct Oracle {
 
     int pt(int64_t a, int64_t b) const { return pair_index(sys.t[a], sys.t[b]); }
 
-    void neighbours() {
+    // need (nullable): atoms whose REBO neighbours are built; anchor (nullable):
+    // atoms whose LJ pairs are built
+    void neighbours(const char* need = nullptr, const char* anchor = nullptr) {
         double dmx = 0, rlj = 0;
         for (int p = 0; p < 3; p++) { dmx = std::max(dmx, P.Dmax[p]); rlj = std::max(rlj, P.ljcut * P.sigma[p]); }
-        find_pairs(sys, dmx, [&](int a, int b) { return P.Dmax[pair_index(a, b)]; }, rebo);
+        find_pairs(sys, dmx, [&](int a, int b) { return P.Dmax[pair_index(a, b)]; }, rebo, need);
         std::vector<std::vector<Nbr>> full;
-        find_pairs(sys, rlj, [&](int a, int b) { return P.ljcut * P.sigma[pair_index(a, b)]; }, full);
+        find_pairs(sys, rlj, [&](int a, int b) { return P.ljcut * P.sigma[pair_index(a, b)]; }, full, anchor);
         lj.assign(sys.n, {});
         for (int64_t i = 0; i < sys.n; i++)
             for (auto& nb : full[i])
@@ -688,6 +692,14 @@ void* oracle_create(const char* param_text) {
 
 void oracle_destroy(void* h) { delete (Oracle*)h; }
 
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 int oracle_threads() {
 #ifdef _OPENMP
     return omp_get_max_threads();
@@ -700,13 +712,15 @@ int oracle_threads() {
 // sel (nullable): per-atom 0/1 mask.  With a mask only the terms anchored at
 // atoms flagged in `anchor` are evaluated and only selected atoms get forces.
 // energy4 = total, REBO, LJ, torsion (over the evaluated terms).
+// need (nullable): atoms whose REBO neighbour sets are needed by the anchored
+// terms (all atoms when null).
 int oracle_compute_masked(void* h, int64_t n, const double* pos, const int8_t* types, const double* box,
-                          int flags, const char* anchor, const char* sel, double* force, double* energy4,
-                          double* virial6, int64_t* counters) {
+                          int flags, const char* anchor, const char* sel, const char* need, double* force,
+                          double* energy4, double* virial6, int64_t* counters) {
     Oracle* o = (Oracle*)h;
     o->sys.n = n; o->sys.x = pos; o->sys.t = types;
     for (int d = 0; d < 3; d++) o->sys.L[d] = box[d];
-    o->neighbours();
+    o->neighbours(need, anchor);
     std::vector<char> selv;
     if (sel) selv.assign(sel, sel + n);
     if (force) std::fill(force, force + 3 * n, 0.0);
@@ -770,7 +784,7 @@ int oracle_compute_masked(void* h, int64_t n, const double* pos, const int8_t* t
 
 int oracle_compute(void* h, int64_t n, const double* pos, const int8_t* types, const double* box, int flags,
                    double* force, double* energy4, double* virial6, int64_t* counters) {
-    return oracle_compute_masked(h, n, pos, types, box, flags, nullptr, nullptr, force, energy4, virial6, counters);
+    return oracle_compute_masked(h, n, pos, types, box, flags, nullptr, nullptr, nullptr, force, energy4, virial6, counters);
 }
 
 // REBO neighbour sets (r < Dmax) as flat arrays; returns the total count, or

@@ -41,8 +41,9 @@ def lib():
         L.oracle_create.argtypes = [C.c_char_p]
         L.oracle_destroy.argtypes = [P]
         L.oracle_threads.restype = C.c_int
+        L.oracle_set_threads.argtypes = [C.c_int]
         L.oracle_compute_masked.restype = C.c_int
-        L.oracle_compute_masked.argtypes = [P, C.c_int64, P, P, P, C.c_int, P, P, P, P, P, P]
+        L.oracle_compute_masked.argtypes = [P, C.c_int64, P, P, P, C.c_int, P, P, P, P, P, P, P]
         L.oracle_compute.restype = C.c_int
         L.oracle_compute.argtypes = [P, C.c_int64, P, P, P, C.c_int, P, P, P, P]
         for f in (L.oracle_rebo_neighbors, L.oracle_lj_pairs):
@@ -95,12 +96,13 @@ class Oracle:
     def energy(self, pos, types, box, flags=FLAG_ALL):
         return self.compute(pos, types, box, flags, forces=False)[0][0]
 
-    def forces_subset(self, pos, types, box, atoms, flags=FLAG_ALL, radius=None):
+    def forces_subset(self, pos, types, box, atoms, flags=FLAG_ALL, radius=None, counters=False):
         """Forces on the listed atoms only, from the terms anchored near them.
 
         Every term that can touch an atom is anchored at an atom within
         `radius` of it (default: the LJ cut-off plus four REBO bond lengths),
-        so the forces are complete for the selected atoms."""
+        so the forces are complete for the selected atoms.  Neighbour sets
+        are built only where those terms look."""
         pos, types, box = self._sys(pos, types, box)
         n = types.shape[0]
         atoms = np.asarray(atoms, dtype=np.int64)
@@ -109,14 +111,38 @@ class Oracle:
         sel = np.zeros(n, dtype=np.int8)
         sel[atoms] = 1
         anchor = np.zeros(n, dtype=np.int8)
+        need = np.zeros(n, dtype=np.int8)
         for a in atoms:
             d = pos - pos[:, a:a + 1]
             d -= box[:, None] * np.round(d / box[:, None])
-            anchor[np.einsum("ij,ij->j", d, d) < radius * radius] = 1
+            r2 = np.einsum("ij,ij->j", d, d)
+            anchor[r2 < radius * radius] = 1
+            need[r2 < (radius + 8.5) ** 2] = 1
         f = np.zeros((3, n))
+        c = np.zeros(16, dtype=np.int64)
         lib().oracle_compute_masked(self._h, n, _ptr(pos), _ptr(types), _ptr(box), flags, _ptr(anchor), _ptr(sel),
-                                    _ptr(f), None, None, None)
+                                    _ptr(need), _ptr(f), None, None, _ptr(c))
+        if counters:
+            return f[:, atoms], dict(zip(COUNTERS, c.tolist()))
         return f[:, atoms]
+
+    def evaluate_sphere(self, pos, types, box, center, radius, flags=FLAG_ALL):
+        """Energy, forces and counters of all terms anchored at the atoms within
+        `radius` of atom `center` (minimum image): a bounded sample of a large
+        system.  Returns (energy4, forces on all atoms, counters, anchor count)."""
+        pos, types, box = self._sys(pos, types, box)
+        n = types.shape[0]
+        d = pos - pos[:, center:center + 1]
+        d -= box[:, None] * np.round(d / box[:, None])
+        r2 = np.einsum("ij,ij->j", d, d)
+        anchor = (r2 < radius * radius).astype(np.int8)
+        need = (r2 < (radius + 20.0) ** 2).astype(np.int8)
+        f = np.zeros((3, n))
+        e = np.zeros(4)
+        c = np.zeros(16, dtype=np.int64)
+        lib().oracle_compute_masked(self._h, n, _ptr(pos), _ptr(types), _ptr(box), flags, _ptr(anchor), None,
+                                    _ptr(need), _ptr(f), _ptr(e), None, _ptr(c))
+        return e, f, dict(zip(COUNTERS, c.tolist())), int(anchor.sum())
 
     def _pairs(self, fn, pos, types, box, cap=None):
         pos, types, box = self._sys(pos, types, box)
@@ -151,3 +177,7 @@ class Oracle:
 
 def threads() -> int:
     return int(lib().oracle_threads())
+
+
+def set_threads(n: int) -> None:
+    lib().oracle_set_threads(int(n))

@@ -1,0 +1,218 @@
+"""Python binding of libairebo (ctypes): argument marshalling only.
+
+Every step of the evaluation runs in the CUDA library declared in
+``include/airebo.h``; this module passes torch device pointers and the
+current CUDA stream through.  It raises if the library is missing -- there is
+no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import inputs
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libairebo.so")
+
+OK, ERR_ARG, ERR_CUDA, ERR_CAPACITY, ERR_TIMEOUT, ERR_NONFINITE, ERR_STATE = range(7)
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_CAPACITY", 4: "ERR_TIMEOUT", 5: "ERR_NONFINITE", 6: "ERR_STATE"}
+FP64, MIXED = 0, 1
+KERNELS = ("short_list", "rebo", "torsion", "path_map", "lj", "bstar", "neighbor", "nve")
+
+
+class AireboError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(C.Structure):
+    _fields_ = [("skin", C.c_double), ("precision", C.c_int), ("enable_rebo", C.c_int),
+                ("enable_lj", C.c_int), ("enable_torsion", C.c_int), ("max_lj_nbrs", C.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libairebo.so; raises when it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libairebo.so is not built ({LIB_PATH}); run paper_1810_07026_gb300/build.py")
+        L = C.CDLL(LIB_PATH)
+        P, I64, D, I = C.c_void_p, C.c_int64, C.c_double, C.c_int
+        sig = {
+            "airebo_default_options": (None, [P]),
+            "airebo_create": (I, [C.c_char_p, P, P, P]),
+            "airebo_destroy": (None, [P]),
+            "airebo_last_error": (C.c_char_p, [P]),
+            "airebo_neighbor": (I, [P, P, P, I64, P]),
+            "airebo_compute": (I, [P, P, P, P, P]),
+            "airebo_compute_host": (I, [P, P, P, I64, P, P, P, P]),
+            "airebo_needs_rebuild": (I, [P, P, P]),
+            "airebo_nve": (I, [P, P, P, P, D, I, P]),
+            "airebo_nve_host": (I, [P, P, P, P, D, I, P]),
+            "airebo_counters": (I, [P, P]),
+            "airebo_export_lists": (I, [P, I, P, P, P, I64]),
+            "airebo_set_timing": (I, [P, I]),
+            "airebo_kernel_times": (I, [P, P, P]),
+            "airebo_alu_peak": (I, [I, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _np(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+def alu_peak(precision: int = FP64) -> float:
+    """Measured FMA TFLOP/s of the current device (FP64 or FP32)."""
+    out = C.c_double(0)
+    st = lib().airebo_alu_peak(precision, C.byref(out))
+    if st:
+        raise AireboError(st, "alu peak probe failed")
+    return out.value
+
+
+class Airebo:
+    """One AIREBO evaluator on the current CUDA device and stream.
+
+    Positions, forces and velocities are torch float64 tensors of shape
+    (3, N) on the device (structure of arrays), types int8 (N,)."""
+
+    def __init__(self, params: str | dict | None = None, precision: int = FP64, skin: float = 1.0,
+                 rebo: bool = True, lj: bool = True, torsion: bool = True, max_lj_nbrs: int = 0, stream=None):
+        import torch
+        self._torch = torch
+        if params is None:
+            params = inputs.make_params(0)
+        if isinstance(params, dict):
+            params = inputs.params_text(params)
+        opt = Options(skin, precision, int(rebo), int(lj), int(torsion), int(max_lj_nbrs))
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.device = stream.device
+        h = C.c_void_p()
+        st = lib().airebo_create(params.encode(), C.byref(opt), C.c_void_p(stream.cuda_stream), C.byref(h))
+        if st:
+            raise AireboError(st, "airebo_create failed")
+        self._h = h
+        self.n = None
+        self.precision = precision
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().airebo_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st:
+            raise AireboError(st, lib().airebo_last_error(self._h).decode())
+
+    def _dev(self, t, dtype):
+        t = t.to(device=self.device, dtype=dtype)
+        return t.contiguous()
+
+    def neighbor(self, pos, types, box):
+        torch = self._torch
+        pos = self._dev(pos, torch.float64)
+        types = self._dev(types, torch.int8)
+        assert pos.dim() == 2 and pos.shape[0] == 3 and pos.shape[1] == types.shape[0]
+        b = np.ascontiguousarray(np.asarray(box, dtype=np.float64).reshape(3))
+        self._check(lib().airebo_neighbor(self._h, _ptr(pos), _ptr(types), pos.shape[1], _np(b)))
+        self.n = pos.shape[1]
+        self._types = types
+        self.box = b
+
+    def compute(self, pos, force=None, virial=False):
+        """Forces (3, N), energies (total, REBO, LJ, torsion) and the virial (or None)."""
+        torch = self._torch
+        pos = self._dev(pos, torch.float64)
+        if force is None:
+            force = torch.empty_like(pos)
+        e4 = torch.empty(4, dtype=torch.float64, device=self.device)
+        w6 = torch.empty(6, dtype=torch.float64, device=self.device) if virial else None
+        self._check(lib().airebo_compute(self._h, _ptr(pos), _ptr(force), _ptr(e4), _ptr(w6)))
+        return force, e4, w6
+
+    def needs_rebuild(self, pos) -> bool:
+        flag = C.c_int(0)
+        self._check(lib().airebo_needs_rebuild(self._h, _ptr(pos), C.byref(flag)))
+        return bool(flag.value)
+
+    def nve(self, pos, vel, force, dt: float, nsteps: int):
+        """nsteps velocity-Verlet steps in place; returns (PE, KE, total, list builds)."""
+        e4 = self._torch.empty(4, dtype=self._torch.float64, device=self.device)
+        self._check(lib().airebo_nve(self._h, _ptr(pos), _ptr(vel), _ptr(force), dt, nsteps, _ptr(e4)))
+        return e4
+
+    def compute_host(self, pos, types, box, virial=False):
+        pos = np.ascontiguousarray(pos, dtype=np.float64)
+        types = np.ascontiguousarray(types, dtype=np.int8)
+        b = np.ascontiguousarray(np.asarray(box, dtype=np.float64).reshape(3))
+        n = types.shape[0]
+        f = np.zeros((3, n))
+        e4 = np.zeros(4)
+        w6 = np.zeros(6) if virial else None
+        self._check(lib().airebo_compute_host(self._h, _np(pos), _np(types), n, _np(b), _np(f), _np(e4), _np(w6)))
+        self.n = n
+        return f, e4, w6
+
+    def nve_host(self, pos, vel, force, dt: float, nsteps: int):
+        """In-place NVE on host arrays (3, N) float64 (pinned or pageable)."""
+        e4 = np.zeros(4)
+        self._check(lib().airebo_nve_host(self._h, C.c_void_p(_addr(pos)), C.c_void_p(_addr(vel)),
+                                          C.c_void_p(_addr(force)), dt, nsteps, _np(e4)))
+        return e4
+
+    def counters(self) -> dict:
+        out = np.zeros(8, dtype=np.int64)
+        self._check(lib().airebo_counters(self._h, _np(out)))
+        names = ("bonds", "bstar", "bstar_dsb", "lj_in_cutoff", "map_cap", "list_builds", "lj_cap", "reserved")
+        return dict(zip(names, out.tolist()))
+
+    def export_lists(self, which: int, cap: int | None = None):
+        """(counts, j, image) of list `which` (0 LJ half, 1 REBO intermediate, 2 exact REBO)."""
+        n = self.n
+        if cap is None:
+            cap = {0: 2048, 1: 128, 2: 8}[which]
+        cnt = np.zeros(n, dtype=np.int32)
+        j = np.zeros((n, cap), dtype=np.int32)
+        img = np.zeros((n, cap, 3), dtype=np.int8)
+        self._check(lib().airebo_export_lists(self._h, which, _np(cnt), _np(j), _np(img), cap))
+        return cnt, j, img
+
+    def set_timing(self, on: bool = True):
+        self._check(lib().airebo_set_timing(self._h, int(on)))
+
+    def kernel_times(self) -> dict:
+        ms = np.zeros(8)
+        nl = np.zeros(8, dtype=np.int64)
+        self._check(lib().airebo_kernel_times(self._h, _np(ms), _np(nl)))
+        return {k: (float(ms[i]), int(nl[i])) for i, k in enumerate(KERNELS)}
+
+
+def _addr(a):
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data

@@ -1,0 +1,874 @@
+// Host side of libairebo: the C ABI of include/airebo.h.
+//
+// Parses the parameter text, builds the power-basis coefficients of every
+// spline (quintic per interval for g, bicubic for P, tricubic for pi^rc and
+// T -- the Hermite interpolants of the knot data), owns every device buffer,
+// and sequences the kernels of a step on the handle's stream.
+#include <cuda_runtime.h>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <sstream>
+#include <string>
+#include <vector>
+#include <algorithm>
+
+#include "../../include/airebo.h"
+#include "internal.h"
+
+using namespace airebo;
+
+namespace {
+
+// ------------------------------------------------------------------ parameters
+struct HostParams {
+    std::map<std::string, std::vector<double>> v;
+    bool get(const char* k, size_t n, std::vector<double>& out, std::string& err) const {
+        auto it = v.find(k);
+        if (it == v.end() || it->second.size() != n) {
+            err = std::string("parameter ") + k + " missing or of wrong size";
+            return false;
+        }
+        out = it->second;
+        return true;
+    }
+};
+
+bool parse_text(const char* text, HostParams& hp, std::string& err) {
+    std::istringstream in(text);
+    std::string line;
+    int nlines = 0;
+    while (std::getline(in, line)) {
+        if (line.empty() || line[0] == '#') continue;
+        std::istringstream ls(line);
+        std::string name;
+        long long n;
+        if (!(ls >> name >> n) || n < 0 || n > 100000) { err = "bad parameter line: " + line.substr(0, 60); return false; }
+        std::vector<double> vals((size_t)n);
+        for (long long k = 0; k < n; k++)
+            if (!(ls >> vals[k])) { err = "too few values for " + name; return false; }
+        hp.v[name] = vals;
+        nlines++;
+    }
+    if (!nlines) { err = "empty parameter text"; return false; }
+    return true;
+}
+
+// cubic Hermite basis on [0,1] in powers of t: [kind][end][power];
+// kind 0 = value basis, 1 = slope basis; end 0 = t=0, 1 = t=1
+const double HB[2][2][4] = {
+    {{1, 0, -3, 2}, {0, 0, 3, -2}},
+    {{0, 1, -2, 1}, {0, 0, -1, 1}},
+};
+
+// knot data (5 x 5 grid, f fx fy fxy) -> 16 cells x 16 coefficients a[p*4+q]
+void bicubic_coeffs(const std::vector<double>& d, double* out) {
+    const int comp[2][2] = {{0, 2}, {1, 3}};   // [dx][dy]
+    for (int ix = 0; ix < 4; ix++)
+        for (int iy = 0; iy < 4; iy++) {
+            double* a = out + (ix * 4 + iy) * 16;
+            for (int k = 0; k < 16; k++) a[k] = 0;
+            for (int ex = 0; ex < 2; ex++)
+                for (int ey = 0; ey < 2; ey++)
+                    for (int dx = 0; dx < 2; dx++)
+                        for (int dy = 0; dy < 2; dy++) {
+                            double val = d[((ix + ex) * 5 + (iy + ey)) * 4 + comp[dx][dy]];
+                            if (val == 0.0) continue;
+                            for (int p = 0; p < 4; p++)
+                                for (int q = 0; q < 4; q++)
+                                    a[p * 4 + q] += val * HB[dx][ex][p] * HB[dy][ey][q];
+                        }
+        }
+}
+
+// knot data (5 x 5 x 9 grid, f fx fy fz fxy fxz fyz fxyz) -> 128 cells x 64 a[(p*4+q)*4+r]
+void tricubic_coeffs(const std::vector<double>& d, double* out, unsigned char* nz) {
+    int comp[2][2][2];
+    comp[0][0][0] = 0; comp[1][0][0] = 1; comp[0][1][0] = 2; comp[0][0][1] = 3;
+    comp[1][1][0] = 4; comp[1][0][1] = 5; comp[0][1][1] = 6; comp[1][1][1] = 7;
+    for (int ix = 0; ix < 4; ix++)
+        for (int iy = 0; iy < 4; iy++)
+            for (int iz = 0; iz < 8; iz++) {
+                int cell = (ix * 4 + iy) * 8 + iz;
+                double* a = out + cell * 64;
+                for (int k = 0; k < 64; k++) a[k] = 0;
+                bool any = false;
+                for (int ex = 0; ex < 2; ex++)
+                    for (int ey = 0; ey < 2; ey++)
+                        for (int ez = 0; ez < 2; ez++)
+                            for (int dx = 0; dx < 2; dx++)
+                                for (int dy = 0; dy < 2; dy++)
+                                    for (int dz = 0; dz < 2; dz++) {
+                                        double val = d[(((ix + ex) * 5 + (iy + ey)) * 9 + (iz + ez)) * 8 + comp[dx][dy][dz]];
+                                        if (val == 0.0) continue;
+                                        any = true;
+                                        for (int p = 0; p < 4; p++)
+                                            for (int q = 0; q < 4; q++)
+                                                for (int r = 0; r < 4; r++)
+                                                    a[(p * 4 + q) * 4 + r] += val * HB[dx][ex][p] * HB[dy][ey][q] * HB[dz][ez][r];
+                                    }
+                if (nz) nz[cell] = any ? 1 : 0;
+            }
+}
+
+// quintic Hermite basis in powers of t: value, slope, curvature at t=0, then curvature, slope, value at t=1
+const double QB[6][6] = {
+    {1, 0, 0, -10, 15, -6},
+    {0, 1, 0, -6, 8, -3},
+    {0, 0, 0.5, -1.5, 1.5, -0.5},
+    {0, 0, 0, 0.5, -1, 0.5},
+    {0, 0, 0, -4, 7, -3},
+    {0, 0, 0, 10, -15, 6},
+};
+
+template <class R>
+bool quintic_coeffs(const std::vector<double>& kn, const std::vector<double>& d, Quintic<R>& q, std::string& err) {
+    int n = (int)kn.size() - 1;
+    if (n < 1 || n > 5 || d.size() != kn.size() * 3) { err = "bad angular spline"; return false; }
+    q.n = n;
+    for (int m = 0; m <= n; m++) q.k[m] = (R)kn[m];
+    for (int m = n + 1; m < 6; m++) q.k[m] = (R)kn[n];
+    for (int m = 0; m < 5; m++) { q.invh[m] = 0; for (int p = 0; p < 6; p++) q.a[m][p] = 0; }
+    for (int m = 0; m < n; m++) {
+        double h = kn[m + 1] - kn[m];
+        if (!(h > 0)) { err = "angular spline knots not increasing"; return false; }
+        q.invh[m] = (R)(1.0 / h);
+        double w[6] = {d[3 * m], h * d[3 * m + 1], h * h * d[3 * m + 2],
+                       h * h * d[3 * (m + 1) + 2], h * d[3 * (m + 1) + 1], d[3 * (m + 1)]};
+        for (int p = 0; p < 6; p++) {
+            double s = 0;
+            for (int b = 0; b < 6; b++) s += w[b] * QB[b][p];
+            q.a[m][p] = (R)s;
+        }
+    }
+    return true;
+}
+
+struct Scalars {
+    double Dmin[3], Dmax[3], Q[3], alpha[3], A[3], B[3][3], beta[3][3], rho[3];
+    double lam, gN[2], Fx[2], guard[2], sigma[3], eps[3], ljcut, ljsw, Sr[2], bmin[3], bmax[3], rstar[3], teps[3];
+    std::vector<double> gC1k, gC1d, gC2k, gC2d, gHk, gHd;
+    std::vector<double> P[3], F[3], T;
+};
+
+bool load_scalars(const HostParams& hp, Scalars& s, std::string& err) {
+    std::vector<double> t;
+    auto g3 = [&](const char* k, double* dst) { if (!hp.get(k, 3, t, err)) return false; for (int i = 0; i < 3; i++) dst[i] = t[i]; return true; };
+    double b1[3], b2[3], b3[3], e1[3], e2[3], e3[3];
+    if (!(g3("Dmin", s.Dmin) && g3("Dmax", s.Dmax) && g3("Q", s.Q) && g3("alpha", s.alpha) && g3("A", s.A) &&
+          g3("B1", b1) && g3("B2", b2) && g3("B3", b3) && g3("beta1", e1) && g3("beta2", e2) && g3("beta3", e3) &&
+          g3("rho", s.rho) && g3("lj.sigma", s.sigma) && g3("lj.epsilon", s.eps) && g3("bstar.bmin", s.bmin) &&
+          g3("bstar.bmax", s.bmax) && g3("bstar.rstar", s.rstar) && g3("tors.epsilon", s.teps)))
+        return false;
+    for (int i = 0; i < 3; i++) {
+        s.B[i][0] = b1[i]; s.B[i][1] = b2[i]; s.B[i][2] = b3[i];
+        s.beta[i][0] = e1[i]; s.beta[i][1] = e2[i]; s.beta[i][2] = e3[i];
+    }
+    auto g1 = [&](const char* k, double& dst) { if (!hp.get(k, 1, t, err)) return false; dst = t[0]; return true; };
+    auto g2 = [&](const char* k, double* dst) { if (!hp.get(k, 2, t, err)) return false; dst[0] = t[0]; dst[1] = t[1]; return true; };
+    if (!(g1("lambda_coef", s.lam) && g2("gC_Nswitch", s.gN) && g2("Fconj_x", s.Fx) && g2("dihedral_guard", s.guard) &&
+          g1("lj.cut", s.ljcut) && g1("lj.switch_start", s.ljsw) && g2("lj.Sr_range", s.Sr)))
+        return false;
+    if (!(hp.get("gC1.knots", 6, s.gC1k, err) && hp.get("gC1.data", 18, s.gC1d, err) &&
+          hp.get("gC2.knots", 6, s.gC2k, err) && hp.get("gC2.data", 18, s.gC2d, err) &&
+          hp.get("gH.knots", 4, s.gHk, err) && hp.get("gH.data", 12, s.gHd, err) &&
+          hp.get("P.CC", 100, s.P[0], err) && hp.get("P.CH", 100, s.P[1], err) && hp.get("P.HC", 100, s.P[2], err) &&
+          hp.get("piRC.CC", 1800, s.F[0], err) && hp.get("piRC.CH", 1800, s.F[1], err) &&
+          hp.get("piRC.HH", 1800, s.F[2], err) && hp.get("Tij.CC", 1800, s.T, err)))
+        return false;
+    for (int p = 0; p < 3; p++) {
+        if (!(s.Dmax[p] > s.Dmin[p] && s.Dmin[p] > 0)) { err = "Dmax must exceed Dmin > 0"; return false; }
+        if (!(s.sigma[p] > 0 && s.bmax[p] > s.bmin[p] && s.rstar[p] > 0)) { err = "bad LJ/b* parameter"; return false; }
+    }
+    if (!(s.ljcut > s.ljsw && s.ljsw > 0 && s.Sr[1] > s.Sr[0] && s.gN[1] > s.gN[0] && s.Fx[1] > s.Fx[0] && s.guard[1] > 0)) {
+        err = "bad switch parameter";
+        return false;
+    }
+    return true;
+}
+
+template <class R>
+bool fill_params(const Scalars& s, DevParams<R>& P, std::vector<R>& tables, std::vector<unsigned char>& Tnz, std::string& err) {
+    for (int p = 0; p < 3; p++) {
+        P.Dmin[p] = (R)s.Dmin[p]; P.Dmax[p] = (R)s.Dmax[p]; P.Dinv[p] = (R)(1.0 / (s.Dmax[p] - s.Dmin[p]));
+        P.Q[p] = (R)s.Q[p]; P.alpha[p] = (R)s.alpha[p]; P.A[p] = (R)s.A[p];
+        int nb = 0;
+        for (int m = 0; m < 3; m++) {
+            P.B[p][m] = 0; P.beta[p][m] = 0;
+            if (s.B[p][m] != 0.0) { P.B[p][nb] = (R)s.B[p][m]; P.beta[p][nb] = (R)s.beta[p][m]; nb++; }
+        }
+        P.nB[p] = nb;
+        double sg = s.sigma[p];
+        P.sigma[p] = (R)sg;
+        P.eps4[p] = (R)(4.0 * s.eps[p]);
+        P.rc2[p] = (R)(s.ljcut * sg * s.ljcut * sg);
+        P.swlo[p] = (R)(s.ljsw * sg);
+        P.swinv[p] = (R)(1.0 / ((s.ljcut - s.ljsw) * sg));
+        P.Srlo[p] = (R)(s.Sr[0] * sg);
+        P.Srhi[p] = (R)(s.Sr[1] * sg);
+        P.Srinv[p] = (R)(1.0 / ((s.Sr[1] - s.Sr[0]) * sg));
+        P.bmin[p] = (R)s.bmin[p];
+        P.binv[p] = (R)(1.0 / (s.bmax[p] - s.bmin[p]));
+        P.rstar[p] = (R)s.rstar[p];
+        P.teps[p] = (R)s.teps[p];
+    }
+    P.rhoH[0] = (R)s.rho[1];   // H centre, C neighbour: rho_CH
+    P.rhoH[1] = (R)s.rho[2];   // H centre, H neighbour: rho_HH
+    P.lam = (R)s.lam;
+    P.gN0 = (R)s.gN[0]; P.gNinv = (R)(1.0 / (s.gN[1] - s.gN[0]));
+    P.Fx0 = (R)s.Fx[0]; P.Fxinv = (R)(1.0 / (s.Fx[1] - s.Fx[0]));
+    P.guard0 = (R)s.guard[0]; P.guardinv = (R)(1.0 / s.guard[1]);
+    double dm = std::max(s.Dmax[0], std::max(s.Dmax[1], s.Dmax[2]));
+    P.rpath2 = (R)(9.0 * dm * dm * (1.0 + 1e-6));
+    if (!quintic_coeffs<R>(s.gC1k, s.gC1d, P.gC1, err) || !quintic_coeffs<R>(s.gC2k, s.gC2d, P.gC2, err) ||
+        !quintic_coeffs<R>(s.gHk, s.gHd, P.gH, err))
+        return false;
+    // tables: P (3 x 256), pi^rc (3 x 8192), T (8192)
+    std::vector<double> buf(3 * 256 + 4 * NTRI_CELLS * 64);
+    for (int t = 0; t < 3; t++) bicubic_coeffs(s.P[t], buf.data() + t * 256);
+    for (int t = 0; t < 3; t++) tricubic_coeffs(s.F[t], buf.data() + 3 * 256 + t * NTRI_CELLS * 64, nullptr);
+    Tnz.assign(NTRI_CELLS, 0);
+    tricubic_coeffs(s.T, buf.data() + 3 * 256 + 3 * NTRI_CELLS * 64, Tnz.data());
+    tables.resize(buf.size());
+    for (size_t k = 0; k < buf.size(); k++) tables[k] = (R)buf[k];
+    return true;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ handle
+template <class R> struct Precision {
+    DevParams<R> hp;                 // host copy, table pointers already device pointers
+    StepBuffers<R> b;
+    std::vector<R> tables;
+    std::vector<unsigned char> Tnz;
+};
+
+struct airebo_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 1;
+    airebo_options opt{};
+    std::string err;
+    Scalars sc;
+    Precision<double> p64;
+    Precision<float> p32;
+    // system
+    int n = 0, n_alloc = 0;
+    double L[3] = {0, 0, 0};
+    int8_t* types = nullptr;
+    bool built = false;
+    // cells
+    int nc[3] = {0, 0, 0}, reach[3] = {0, 0, 0}, ncell_alloc = 0;
+    double cell_w[3] = {0, 0, 0};
+    int *cell_of = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cell_fill = nullptr;
+    float4* spos = nullptr;
+    char4* swrap = nullptr;
+    // lists
+    int2* lj = nullptr; int* lj_cnt = nullptr; int lj_cap = 0; size_t lj_alloc = 0;
+    int2* im = nullptr; int* im_cnt = nullptr; int im_cap = 32; size_t im_alloc = 0;
+    double* xref = nullptr;
+    // step scratch
+    int2* bonds = nullptr; int bond_cap = 0;
+    int4* bq = nullptr; int bq_cap = 0;
+    int* counts = nullptr;               // [0] bonds [1] queue
+    double* acc = nullptr;               // 9 doubles
+    unsigned long long* counters = nullptr;   // 8
+    int* derr = nullptr;                 // 8 ints
+    unsigned long long* maxd2 = nullptr;
+    double* ke = nullptr;
+    // pinned mirrors
+    int* h_err = nullptr;
+    unsigned long long* h_u64 = nullptr;
+    double* h_acc = nullptr;
+    // host-API staging
+    double *hpos = nullptr, *hvel = nullptr, *hforce = nullptr, *he4 = nullptr, *hw6 = nullptr;
+    int host_n = -1;
+    long long rebuilds = 0;
+    // per-kernel timing
+    bool timing = false;
+    cudaEvent_t ev[11] = {};
+    double kt_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long kt_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
+namespace {
+
+airebo_status fail(airebo_handle h, airebo_status st, const std::string& msg) {
+    if (h) h->err = msg;
+    return st;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(h, AIREBO_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <class T> cudaError_t realloc_dev(T*& p, size_t count) {
+    if (p) cudaFree(p);
+    p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void**)&p, sizeof(T) * count);
+}
+
+template <class R> airebo_status upload_params(airebo_handle h, Precision<R>& pr) {
+    std::string e;
+    if (!fill_params<R>(h->sc, pr.hp, pr.tables, pr.Tnz, e)) return fail(h, AIREBO_ERR_ARG, e);
+    CK(realloc_dev(pr.b.tables, pr.tables.size()));
+    CK(realloc_dev(pr.b.Tnz, pr.Tnz.size()));
+    CK(realloc_dev(pr.b.P, 1));
+    CK(cudaMemcpy(pr.b.tables, pr.tables.data(), sizeof(R) * pr.tables.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(pr.b.Tnz, pr.Tnz.data(), pr.Tnz.size(), cudaMemcpyHostToDevice));
+    pr.hp.Ptab = pr.b.tables;
+    pr.hp.Ftab = pr.b.tables + 3 * 256;
+    pr.hp.Ttab = pr.b.tables + 3 * 256 + 3 * NTRI_CELLS * 64;
+    pr.hp.Tnz = pr.b.Tnz;
+    CK(cudaMemcpy(pr.b.P, &pr.hp, sizeof(DevParams<R>), cudaMemcpyHostToDevice));
+    return AIREBO_OK;
+}
+
+template <class R> airebo_status alloc_step(airebo_handle h, Precision<R>& pr, int n) {
+    StepBuffers<R>& b = pr.b;
+    size_t m = (size_t)n * MAXN;
+    CK(realloc_dev(b.cnt, n)); CK(realloc_dev(b.nj, m)); CK(realloc_dev(b.nimg, m));
+    CK(realloc_dev(b.dx, m)); CK(realloc_dev(b.dy, m)); CK(realloc_dev(b.dz, m));
+    CK(realloc_dev(b.r, m)); CK(realloc_dev(b.w, m)); CK(realloc_dev(b.dw, m));
+    CK(realloc_dev(b.nC, n)); CK(realloc_dev(b.nH, n));
+    if (b.map_cap == 0) b.map_cap = 32;
+    size_t mm = (size_t)n * b.map_cap;
+    CK(realloc_dev(b.map_cnt, n)); CK(realloc_dev(b.map_key, mm)); CK(realloc_dev(b.map_wt, mm)); CK(realloc_dev(b.map_path, mm));
+    return AIREBO_OK;
+}
+
+template <class R> airebo_status grow_map(airebo_handle h, Precision<R>& pr, int need) {
+    StepBuffers<R>& b = pr.b;
+    b.map_cap = std::max(need + 8, b.map_cap * 2);
+    size_t mm = (size_t)h->n_alloc * b.map_cap;
+    CK(realloc_dev(b.map_key, mm)); CK(realloc_dev(b.map_wt, mm)); CK(realloc_dev(b.map_path, mm));
+    return AIREBO_OK;
+}
+
+template <class R> void free_prec(Precision<R>& pr) {
+    StepBuffers<R>& b = pr.b;
+    void* ps[] = {b.P, b.tables, b.Tnz, b.cnt, b.nj, b.nimg, b.dx, b.dy, b.dz, b.r, b.w, b.dw, b.nC, b.nH,
+                  b.map_cnt, b.map_key, b.map_wt, b.map_path};
+    for (void* p : ps) if (p) cudaFree(p);
+    b = StepBuffers<R>();
+}
+
+double max3(const double* v) { return std::max(v[0], std::max(v[1], v[2])); }
+
+airebo_status alloc_atoms(airebo_handle h, int n) {
+    if (n <= h->n_alloc && h->n_alloc > 0) return AIREBO_OK;
+    int na = std::max(n, 1);
+    CK(realloc_dev(h->types, na));
+    CK(realloc_dev(h->cell_of, na));
+    CK(realloc_dev(h->spos, na));
+    CK(realloc_dev(h->swrap, na));
+    CK(realloc_dev(h->lj_cnt, na));
+    CK(realloc_dev(h->im_cnt, na));
+    CK(realloc_dev(h->xref, 3 * (size_t)na));
+    h->bond_cap = na * MAXN / 2 + 64;
+    CK(realloc_dev(h->bonds, h->bond_cap));
+    h->bq_cap = std::max(h->bq_cap, na * 8 + 1024);
+    CK(realloc_dev(h->bq, h->bq_cap));
+    h->n_alloc = na;
+    airebo_status st = h->opt.precision == AIREBO_MIXED ? alloc_step<float>(h, h->p32, na) : alloc_step<double>(h, h->p64, na);
+    if (st) return st;
+    h->lj_alloc = 0;
+    h->im_alloc = 0;
+    return AIREBO_OK;
+}
+
+airebo_status ensure_lists(airebo_handle h) {
+    size_t need_lj = (size_t)h->n_alloc * h->lj_cap, need_im = (size_t)h->n_alloc * h->im_cap;
+    if (need_lj > h->lj_alloc) { CK(realloc_dev(h->lj, need_lj)); h->lj_alloc = need_lj; }
+    if (need_im > h->im_alloc) { CK(realloc_dev(h->im, need_im)); h->im_alloc = need_im; }
+    return AIREBO_OK;
+}
+
+airebo_status do_neighbor(airebo_handle h, const double* d_pos) {
+    const Scalars& s = h->sc;
+    double rlj = 0, rim = 0;
+    NeighborArgs a{};
+    for (int p = 0; p < 3; p++) {
+        double rc = s.ljcut * s.sigma[p] + h->opt.skin;
+        double ri = s.Dmax[p] + h->opt.skin;
+        rlj = std::max(rlj, rc);
+        rim = std::max(rim, ri);
+        a.lj_rc[p] = (float)(rc + 2e-3);
+        a.im_rc[p] = (float)(ri + 2e-3);
+    }
+    rlj += 2e-3;
+    int ncell = 1;
+    for (int d = 0; d < 3; d++) {
+        h->nc[d] = std::max(1, (int)std::floor(h->L[d] / rlj));
+        h->cell_w[d] = h->L[d] / h->nc[d];
+        h->reach[d] = (int)std::ceil(rlj / h->cell_w[d]);
+        ncell *= h->nc[d];
+    }
+    if (ncell > h->ncell_alloc) {
+        CK(realloc_dev(h->cell_count, ncell));
+        CK(realloc_dev(h->cell_start, ncell + 1));
+        CK(realloc_dev(h->cell_fill, ncell));
+        h->ncell_alloc = ncell;
+    }
+    if (h->lj_cap == 0) {
+        double vol = h->L[0] * h->L[1] * h->L[2];
+        double rho = h->n / vol;
+        double est = 0.5 * 4.0 / 3.0 * M_PI * rlj * rlj * rlj * rho;
+        h->lj_cap = h->opt.max_lj_nbrs > 0 ? h->opt.max_lj_nbrs : ((int)(1.2 * est + 32) + 31) / 32 * 32;
+    }
+    for (int attempt = 0; attempt < 4; attempt++) {
+        airebo_status st = ensure_lists(h);
+        if (st) return st;
+        a.n = h->n; a.pos = d_pos; a.type = h->types;
+        for (int d = 0; d < 3; d++) { a.L[d] = h->L[d]; a.nc[d] = h->nc[d]; a.reach[d] = h->reach[d]; a.cell_w[d] = h->cell_w[d]; }
+        a.cell_of = h->cell_of; a.cell_count = h->cell_count; a.cell_start = h->cell_start; a.cell_fill = h->cell_fill;
+        a.spos = h->spos; a.swrap = h->swrap;
+        a.lj = h->lj; a.lj_cnt = h->lj_cnt; a.lj_cap = h->lj_cap;
+        a.im = h->im; a.im_cnt = h->im_cnt; a.im_cap = h->im_cap;
+        a.err = h->derr; a.xref = h->xref;
+        CK(cudaMemsetAsync(h->derr, 0, sizeof(int) * 8, h->stream));
+        if (h->timing) CK(cudaEventRecord(h->ev[7], h->stream));
+        launch_neighbor(a, h->stream);
+        CK(cudaGetLastError());
+        if (h->timing) CK(cudaEventRecord(h->ev[8], h->stream));
+        CK(cudaMemcpyAsync(h->h_err, h->derr, sizeof(int) * 8, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        if (h->timing && h->n) {
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, h->ev[7], h->ev[8]));
+            h->kt_ms[6] += ms;
+            h->kt_n[6] += 1;
+        }
+        if (h->h_err[2] == 1) { h->built = false; return fail(h, AIREBO_ERR_NONFINITE, "non-finite position"); }
+        if (h->h_err[2] == 2) return fail(h, AIREBO_ERR_ARG, "position more than 120 box lengths outside the box");
+        if (h->h_err[3]) { h->built = false; return fail(h, AIREBO_ERR_ARG, "atom type other than 0 (C) or 1 (H)"); }
+        bool again = false;
+        if (h->h_err[0] > h->lj_cap) { h->lj_cap = ((int)(h->h_err[0] * 1.1) + 32) / 32 * 32; again = true; }
+        if (h->h_err[1] > h->im_cap) { h->im_cap = ((int)(h->h_err[1] * 1.2) + 8); again = true; }
+        if (!again) {
+            if (h->n) CK(cudaMemcpyAsync(h->xref, d_pos, sizeof(double) * 3 * h->n, cudaMemcpyDeviceToDevice, h->stream));
+            h->built = true;
+            h->rebuilds++;
+            return AIREBO_OK;
+        }
+    }
+    return fail(h, AIREBO_ERR_CAPACITY, "neighbour list capacity did not converge");
+}
+
+__global__ void k_finalize(const double* acc, double* e4, double* w6) {
+    int t = threadIdx.x;
+    if (e4 && t < 4) e4[t] = t == 0 ? acc[0] + acc[1] + acc[2] : acc[t - 1];
+    if (w6 && t < 6) w6[t] = acc[3 + t];
+}
+
+template <class R> StepArgs<R> make_args(airebo_handle h, Precision<R>& pr, const double* d_pos, double* d_force, bool virial) {
+    StepArgs<R> a{};
+    StepBuffers<R>& b = pr.b;
+    a.n = h->n;
+    a.P = b.P;
+    a.G.n = h->n; a.G.type = h->types; a.G.cnt = b.cnt; a.G.nj = b.nj; a.G.nimg = b.nimg;
+    a.G.dx = b.dx; a.G.dy = b.dy; a.G.dz = b.dz; a.G.r = b.r; a.G.w = b.w; a.G.dw = b.dw; a.G.nC = b.nC; a.G.nH = b.nH;
+    a.g_cnt = b.cnt; a.g_nj = b.nj; a.g_nimg = b.nimg; a.g_dx = b.dx; a.g_dy = b.dy; a.g_dz = b.dz;
+    a.g_r = b.r; a.g_w = b.w; a.g_dw = b.dw; a.g_nC = b.nC; a.g_nH = b.nH;
+    a.M.cap = b.map_cap; a.M.cnt = b.map_cnt; a.M.key = b.map_key; a.M.wt = b.map_wt; a.M.path = b.map_path;
+    a.pos = d_pos;
+    for (int d = 0; d < 3; d++) a.L[d] = h->L[d];
+    a.lj = h->lj; a.lj_cnt = h->lj_cnt; a.lj_cap = h->lj_cap;
+    a.im = h->im; a.im_cnt = h->im_cnt; a.im_cap = h->im_cap;
+    a.bonds = h->bonds; a.nbonds = h->counts; a.bond_cap = h->bond_cap;
+    a.bq = h->bq; a.nbq = h->counts + 1; a.bq_cap = h->bq_cap;
+    a.f = d_force; a.acc = h->acc; a.counters = h->counters; a.err = h->derr;
+    a.virial = virial;
+    a.rebo = h->opt.enable_rebo != 0;
+    a.lj_on = h->opt.enable_lj != 0;
+    a.torsion = h->opt.enable_torsion != 0;
+    return a;
+}
+
+template <class R>
+airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos, double* d_force, double* d_e4,
+                         double* d_w6) {
+    for (int attempt = 0; attempt < 4; attempt++) {
+        cudaStream_t s = h->stream;
+        if (h->n) CK(cudaMemsetAsync(d_force, 0, sizeof(double) * 3 * h->n, s));
+        CK(cudaMemsetAsync(h->acc, 0, sizeof(double) * 9, s));
+        CK(cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * 8, s));
+        CK(cudaMemsetAsync(h->counts, 0, sizeof(int) * 2, s));
+        CK(cudaMemsetAsync(h->derr, 0, sizeof(int) * 8, s));
+        StepArgs<R> a = make_args<R>(h, pr, d_pos, d_force, d_w6 != nullptr);
+        launch_compute<R>(a, s, h->num_sms, h->timing ? h->ev : nullptr);
+        CK(cudaGetLastError());
+        if (d_e4 || d_w6) k_finalize<<<1, 32, 0, s>>>(h->acc, d_e4, d_w6);
+        CK(cudaMemcpyAsync(h->h_err, h->derr, sizeof(int) * 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(h->h_u64, h->counts, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (h->timing && h->n) {
+            bool ran[6] = {true, a.rebo, a.torsion, a.lj_on, a.lj_on, a.lj_on};
+            for (int k = 0; k < 6; k++) {
+                float ms = 0;
+                CK(cudaEventElapsedTime(&ms, h->ev[k], h->ev[k + 1]));
+                if (ran[k]) { h->kt_ms[k] += ms; h->kt_n[k] += 1; }
+            }
+        }
+        if (h->h_err[ERR_NONFINITE]) return fail(h, AIREBO_ERR_NONFINITE, "non-finite position");
+        if (h->h_err[ERR_SHORT] > MAXN)
+            return fail(h, AIREBO_ERR_CAPACITY, "an atom has more than 8 REBO neighbours (" + std::to_string(h->h_err[ERR_SHORT]) + ")");
+        bool again = false;
+        if (h->h_err[ERR_MAP]) {
+            airebo_status st = grow_map<R>(h, pr, h->h_err[ERR_MAP]);
+            if (st) return st;
+            again = true;
+        }
+        int nq = ((int*)h->h_u64)[1];
+        if (nq > h->bq_cap) {
+            h->bq_cap = nq + nq / 4 + 1024;
+            CK(realloc_dev(h->bq, h->bq_cap));
+            again = true;
+        }
+        if (!again) return AIREBO_OK;
+    }
+    return fail(h, AIREBO_ERR_CAPACITY, "scratch capacity did not converge");
+}
+
+airebo_status compute_any(airebo_handle h, const double* d_pos, double* d_force, double* d_e4, double* d_w6) {
+    if (!h->built) return fail(h, AIREBO_ERR_STATE, "airebo_compute before airebo_neighbor");
+    CK(cudaSetDevice(h->device));
+    if (h->opt.precision == AIREBO_MIXED) return do_compute<float>(h, h->p32, d_pos, d_force, d_e4, d_w6);
+    return do_compute<double>(h, h->p64, d_pos, d_force, d_e4, d_w6);
+}
+
+airebo_status check_rebuild(airebo_handle h, const double* d_pos, int* flag) {
+    CK(cudaMemsetAsync(h->maxd2, 0, sizeof(unsigned long long), h->stream));
+    launch_max_disp(d_pos, h->xref, h->n, h->maxd2, h->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->h_u64, h->maxd2, sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    double d2;
+    memcpy(&d2, h->h_u64, sizeof(double));
+    double half = 0.5 * h->opt.skin;
+    *flag = d2 > half * half ? 1 : 0;
+    return AIREBO_OK;
+}
+
+airebo_status set_system(airebo_handle h, const int8_t* d_types, int64_t n, const double* box, bool types_on_host) {
+    if (n < 0 || n > (1LL << 30)) return fail(h, AIREBO_ERR_ARG, "atom count out of range");
+    if (!box) return fail(h, AIREBO_ERR_ARG, "box is null");
+    double dm = max3(h->sc.Dmax);
+    for (int d = 0; d < 3; d++)
+        if (!(box[d] > 4.0 * dm)) return fail(h, AIREBO_ERR_ARG, "box edge must exceed 4 x the largest REBO cut-off");
+    airebo_status st = alloc_atoms(h, (int)n);
+    if (st) return st;
+    h->n = (int)n;
+    for (int d = 0; d < 3; d++) h->L[d] = box[d];
+    if (n) CK(cudaMemcpyAsync(h->types, d_types, n, types_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->stream));
+    return AIREBO_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+void airebo_default_options(airebo_options* o) {
+    if (!o) return;
+    o->skin = 1.0;
+    o->precision = AIREBO_FP64;
+    o->enable_rebo = 1;
+    o->enable_lj = 1;
+    o->enable_torsion = 1;
+    o->max_lj_nbrs = 0;
+}
+
+airebo_status airebo_create(const char* params, const airebo_options* opts, void* stream, airebo_handle* out) {
+    if (!params || !out) return AIREBO_ERR_ARG;
+    *out = nullptr;
+    airebo_handle h = new airebo_ctx();
+    if (opts) h->opt = *opts; else airebo_default_options(&h->opt);
+    if (!(h->opt.skin >= 0.0) || (h->opt.precision != AIREBO_FP64 && h->opt.precision != AIREBO_MIXED)) {
+        delete h;
+        return AIREBO_ERR_ARG;
+    }
+    h->stream = (cudaStream_t)stream;
+    HostParams hp;
+    std::string e;
+    if (!parse_text(params, hp, e) || !load_scalars(hp, h->sc, e)) {
+        delete h;
+        return AIREBO_ERR_ARG;
+    }
+    airebo_status st = AIREBO_OK;
+    cudaError_t ce = cudaGetDevice(&h->device);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (ce != cudaSuccess) { delete h; return AIREBO_ERR_CUDA; }
+    st = h->opt.precision == AIREBO_MIXED ? upload_params<float>(h, h->p32) : upload_params<double>(h, h->p64);
+    if (!st) {
+        if (realloc_dev(h->counts, 2) || realloc_dev(h->acc, 9) || realloc_dev(h->counters, 8) ||
+            realloc_dev(h->derr, 8) || realloc_dev(h->maxd2, 1) || realloc_dev(h->ke, 1) ||
+            cudaMallocHost((void**)&h->h_err, sizeof(int) * 8) || cudaMallocHost((void**)&h->h_u64, sizeof(unsigned long long) * 8) ||
+            cudaMallocHost((void**)&h->h_acc, sizeof(double) * 16))
+            st = AIREBO_ERR_CUDA;
+    }
+    if (st) { airebo_destroy(h); return st; }
+    *out = h;
+    return AIREBO_OK;
+}
+
+void airebo_destroy(airebo_handle h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
+    free_prec(h->p64);
+    free_prec(h->p32);
+    void* ps[] = {h->types, h->cell_of, h->cell_count, h->cell_start, h->cell_fill, h->spos, h->swrap, h->lj, h->lj_cnt,
+                  h->im, h->im_cnt, h->xref, h->bonds, h->bq, h->counts, h->acc, h->counters, h->derr, h->maxd2, h->ke,
+                  h->hpos, h->hvel, h->hforce, h->he4, h->hw6};
+    for (void* p : ps) if (p) cudaFree(p);
+    for (int k = 0; k < 11; k++) if (h->ev[k]) cudaEventDestroy(h->ev[k]);
+    if (h->h_err) cudaFreeHost(h->h_err);
+    if (h->h_u64) cudaFreeHost(h->h_u64);
+    if (h->h_acc) cudaFreeHost(h->h_acc);
+    delete h;
+}
+
+const char* airebo_last_error(airebo_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+airebo_status airebo_neighbor(airebo_handle h, const double* d_pos, const int8_t* d_types, int64_t n, const double* box) {
+    if (!h) return AIREBO_ERR_ARG;
+    if (n > 0 && (!d_pos || !d_types)) return fail(h, AIREBO_ERR_ARG, "null position or type pointer");
+    CK(cudaSetDevice(h->device));
+    airebo_status st = set_system(h, d_types, n, box, false);
+    if (st) return st;
+    return do_neighbor(h, d_pos);
+}
+
+airebo_status airebo_compute(airebo_handle h, const double* d_pos, double* d_force, double* d_energy4, double* d_virial6) {
+    if (!h) return AIREBO_ERR_ARG;
+    if (h->n > 0 && (!d_pos || !d_force)) return fail(h, AIREBO_ERR_ARG, "null position or force pointer");
+    return compute_any(h, d_pos, d_force, d_energy4, d_virial6);
+}
+
+airebo_status airebo_needs_rebuild(airebo_handle h, const double* d_pos, int* out_flag) {
+    if (!h || !out_flag) return AIREBO_ERR_ARG;
+    if (!h->built) return fail(h, AIREBO_ERR_STATE, "no neighbour list yet");
+    CK(cudaSetDevice(h->device));
+    return check_rebuild(h, d_pos, out_flag);
+}
+
+static airebo_status stage_host(airebo_handle h, int n) {
+    if (h->host_n == n && h->hpos) return AIREBO_OK;
+    size_t m = 3 * (size_t)std::max(n, 1);
+    CK(realloc_dev(h->hpos, m)); CK(realloc_dev(h->hvel, m)); CK(realloc_dev(h->hforce, m));
+    CK(realloc_dev(h->he4, 4)); CK(realloc_dev(h->hw6, 6));
+    h->host_n = n;
+    return AIREBO_OK;
+}
+
+airebo_status airebo_compute_host(airebo_handle h, const double* h_pos, const int8_t* h_types, int64_t n,
+                                  const double* box, double* h_force, double* h_energy4, double* h_virial6) {
+    if (!h) return AIREBO_ERR_ARG;
+    if (n > 0 && (!h_pos || !h_types || !h_force)) return fail(h, AIREBO_ERR_ARG, "null host pointer");
+    CK(cudaSetDevice(h->device));
+    airebo_status st = stage_host(h, (int)n);
+    if (st) return st;
+    if (n) CK(cudaMemcpyAsync(h->hpos, h_pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+    bool rebuild = !h->built || n != h->n || !box || box[0] != h->L[0] || box[1] != h->L[1] || box[2] != h->L[2];
+    if (rebuild) {
+        st = set_system(h, h_types, n, box, true);
+        if (st) return st;
+        st = do_neighbor(h, h->hpos);
+        if (st) return st;
+    } else {
+        int flag = 0;
+        st = check_rebuild(h, h->hpos, &flag);
+        if (st) return st;
+        if (flag) { st = do_neighbor(h, h->hpos); if (st) return st; }
+    }
+    st = compute_any(h, h->hpos, h->hforce, h->he4, h_virial6 ? h->hw6 : nullptr);
+    if (st) return st;
+    if (n) CK(cudaMemcpyAsync(h_force, h->hforce, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+    if (h_energy4) CK(cudaMemcpyAsync(h_energy4, h->he4, sizeof(double) * 4, cudaMemcpyDeviceToHost, h->stream));
+    if (h_virial6) CK(cudaMemcpyAsync(h_virial6, h->hw6, sizeof(double) * 6, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return AIREBO_OK;
+}
+
+__global__ void k_nve_energy(const double* acc, const double* ke, double* e4, long long rebuilds) {
+    if (threadIdx.x == 0) {
+        double pe = acc[0] + acc[1] + acc[2];
+        e4[0] = pe; e4[1] = *ke; e4[2] = pe + *ke; e4[3] = (double)rebuilds;
+    }
+}
+
+airebo_status airebo_nve(airebo_handle h, double* d_pos, double* d_vel, double* d_force, double dt, int nsteps,
+                         double* d_energy4) {
+    if (!h) return AIREBO_ERR_ARG;
+    if (!h->built) return fail(h, AIREBO_ERR_STATE, "airebo_nve before airebo_neighbor");
+    if (nsteps < 0 || !(dt > 0)) return fail(h, AIREBO_ERR_ARG, "bad dt or step count");
+    CK(cudaSetDevice(h->device));
+    cudaStream_t s = h->stream;
+    bool pending = false;      // second half step timed but not yet read
+    auto read_pending = [&]() -> airebo_status {
+        if (pending) {
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, h->ev[9], h->ev[10]));
+            h->kt_ms[7] += ms;
+            h->kt_n[7] += 1;
+            pending = false;
+        }
+        return AIREBO_OK;
+    };
+    for (int step = 0; step < nsteps; step++) {
+        CK(cudaMemsetAsync(h->maxd2, 0, sizeof(unsigned long long), s));
+        if (h->timing) CK(cudaEventRecord(h->ev[7], s));
+        launch_nve_half(d_pos, d_vel, d_force, h->types, h->n, dt, true, h->xref, h->maxd2, nullptr, s);
+        CK(cudaGetLastError());
+        if (h->timing) CK(cudaEventRecord(h->ev[8], s));
+        CK(cudaMemcpyAsync(h->h_u64, h->maxd2, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (h->timing) {
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, h->ev[7], h->ev[8]));
+            h->kt_ms[7] += ms;
+            h->kt_n[7] += 1;
+            airebo_status st = read_pending();
+            if (st) return st;
+        }
+        double d2;
+        memcpy(&d2, h->h_u64, sizeof(double));
+        double half = 0.5 * h->opt.skin;
+        if (d2 > half * half) {
+            airebo_status st = do_neighbor(h, d_pos);
+            if (st) return st;
+        }
+        bool last = step == nsteps - 1;
+        airebo_status st = compute_any(h, d_pos, d_force, nullptr, nullptr);
+        if (st) return st;
+        if (last) CK(cudaMemsetAsync(h->ke, 0, sizeof(double), s));
+        if (h->timing) CK(cudaEventRecord(h->ev[9], s));
+        launch_nve_half(d_pos, d_vel, d_force, h->types, h->n, dt, false, nullptr, nullptr, last ? h->ke : nullptr, s);
+        CK(cudaGetLastError());
+        if (h->timing) { CK(cudaEventRecord(h->ev[10], s)); pending = true; }
+        if (last && d_energy4) k_nve_energy<<<1, 32, 0, s>>>(h->acc, h->ke, d_energy4, h->rebuilds);
+    }
+    CK(cudaGetLastError());
+    if (pending) {
+        CK(cudaEventSynchronize(h->ev[10]));
+        airebo_status st = read_pending();
+        if (st) return st;
+    }
+    return AIREBO_OK;
+}
+
+airebo_status airebo_nve_host(airebo_handle h, double* h_pos, double* h_vel, double* h_force, double dt, int nsteps,
+                              double* h_energy4) {
+    if (!h) return AIREBO_ERR_ARG;
+    if (!h->built) return fail(h, AIREBO_ERR_STATE, "airebo_nve_host before a neighbour build");
+    int n = h->n;
+    if (n > 0 && (!h_pos || !h_vel || !h_force)) return fail(h, AIREBO_ERR_ARG, "null host pointer");
+    CK(cudaSetDevice(h->device));
+    airebo_status st = stage_host(h, n);
+    if (st) return st;
+    size_t bytes = sizeof(double) * 3 * n;
+    cudaStream_t s = h->stream;
+    if (n) {
+        CK(cudaMemcpyAsync(h->hpos, h_pos, bytes, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(h->hvel, h_vel, bytes, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(h->hforce, h_force, bytes, cudaMemcpyHostToDevice, s));
+    }
+    st = airebo_nve(h, h->hpos, h->hvel, h->hforce, dt, nsteps, h->he4);
+    if (st) return st;
+    if (n) {
+        CK(cudaMemcpyAsync(h_pos, h->hpos, bytes, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(h_vel, h->hvel, bytes, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(h_force, h->hforce, bytes, cudaMemcpyDeviceToHost, s));
+    }
+    if (h_energy4) CK(cudaMemcpyAsync(h_energy4, h->he4, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return AIREBO_OK;
+}
+
+airebo_status airebo_counters(airebo_handle h, int64_t* out8) {
+    if (!h || !out8) return AIREBO_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    CK(cudaMemcpyAsync(h->h_u64, h->counters, sizeof(unsigned long long) * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < 8; k++) out8[k] = (int64_t)h->h_u64[k];
+    out8[5] = h->rebuilds;
+    out8[6] = h->lj_cap;
+    int mc = h->opt.precision == AIREBO_MIXED ? h->p32.b.map_cap : h->p64.b.map_cap;
+    out8[4] = mc;
+    return AIREBO_OK;
+}
+
+airebo_status airebo_export_lists(airebo_handle h, int which, int32_t* h_cnt, int32_t* h_j, int8_t* h_img, int64_t cap) {
+    if (!h || !h_cnt || !h_j || !h_img || cap < 0 || which < 0 || which > 2) return AIREBO_ERR_ARG;
+    if (!h->built) return fail(h, AIREBO_ERR_STATE, "no neighbour list yet");
+    CK(cudaSetDevice(h->device));
+    CK(cudaStreamSynchronize(h->stream));
+    int n = h->n;
+    std::vector<int> cnt(n);
+    std::vector<int2> ent;
+    int rowcap = 0;
+    if (which == 2) {
+        const int* dcnt = h->opt.precision == AIREBO_MIXED ? h->p32.b.cnt : h->p64.b.cnt;
+        const int* dnj = h->opt.precision == AIREBO_MIXED ? h->p32.b.nj : h->p64.b.nj;
+        const int* dimg = h->opt.precision == AIREBO_MIXED ? h->p32.b.nimg : h->p64.b.nimg;
+        rowcap = MAXN;
+        std::vector<int> nj((size_t)n * MAXN), im((size_t)n * MAXN);
+        if (n) {
+            CK(cudaMemcpy(cnt.data(), dcnt, sizeof(int) * n, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(nj.data(), dnj, sizeof(int) * nj.size(), cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(im.data(), dimg, sizeof(int) * im.size(), cudaMemcpyDeviceToHost));
+        }
+        ent.resize(nj.size());
+        for (size_t k = 0; k < nj.size(); k++) ent[k] = make_int2(nj[k], im[k]);
+    } else {
+        rowcap = which == 0 ? h->lj_cap : h->im_cap;
+        ent.resize((size_t)n * rowcap);
+        if (n) {
+            CK(cudaMemcpy(cnt.data(), which == 0 ? h->lj_cnt : h->im_cnt, sizeof(int) * n, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(ent.data(), which == 0 ? h->lj : h->im, sizeof(int2) * ent.size(), cudaMemcpyDeviceToHost));
+        }
+    }
+    for (int i = 0; i < n; i++) {
+        h_cnt[i] = cnt[i];
+        for (int e = 0; e < cnt[i] && e < cap; e++) {
+            int2 v = ent[(size_t)i * rowcap + e];
+            h_j[(size_t)i * cap + e] = v.x;
+            h_img[((size_t)i * cap + e) * 3 + 0] = (int8_t)img_x(v.y);
+            h_img[((size_t)i * cap + e) * 3 + 1] = (int8_t)img_y(v.y);
+            h_img[((size_t)i * cap + e) * 3 + 2] = (int8_t)img_z(v.y);
+        }
+    }
+    return AIREBO_OK;
+}
+
+airebo_status airebo_set_timing(airebo_handle h, int on) {
+    if (!h) return AIREBO_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    if (on && !h->ev[0])
+        for (int k = 0; k < 11; k++) CK(cudaEventCreate(&h->ev[k]));
+    h->timing = on != 0;
+    for (int k = 0; k < 8; k++) { h->kt_ms[k] = 0; h->kt_n[k] = 0; }
+    return AIREBO_OK;
+}
+
+airebo_status airebo_kernel_times(airebo_handle h, double* ms, int64_t* launches) {
+    if (!h || !ms || !launches) return AIREBO_ERR_ARG;
+    for (int k = 0; k < 8; k++) { ms[k] = h->kt_ms[k]; launches[k] = h->kt_n[k]; }
+    return AIREBO_OK;
+}
+
+airebo_status airebo_alu_peak(int precision, double* tflops) {
+    if (!tflops || (precision != AIREBO_FP64 && precision != AIREBO_MIXED)) return AIREBO_ERR_ARG;
+    double t = alu_peak(precision == AIREBO_FP64 ? 1 : 0);
+    *tflops = t;
+    return t > 0 ? AIREBO_OK : AIREBO_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,78 @@
+// Declarations shared by the translation units of libairebo (not public).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include "terms.cuh"
+
+namespace airebo {
+
+// per-step device data of one precision R, all owned by the handle
+template <class R> struct StepBuffers {
+    DevParams<R>* P = nullptr;        // device copy of the parameter struct
+    R* tables = nullptr;              // P, pi^rc and T coefficients
+    unsigned char* Tnz = nullptr;
+    // short list
+    int* cnt = nullptr; int* nj = nullptr; int* nimg = nullptr;
+    R* dx = nullptr; R* dy = nullptr; R* dz = nullptr; R* r = nullptr; R* w = nullptr; R* dw = nullptr;
+    R* nC = nullptr; R* nH = nullptr;
+    // connectivity map
+    int map_cap = 0;
+    int* map_cnt = nullptr; long long* map_key = nullptr; R* map_wt = nullptr; int* map_path = nullptr;
+};
+
+// everything the compute kernels read, passed by value
+template <class R> struct StepArgs {
+    int n;
+    const DevParams<R>* P;
+    Graph<R> G;
+    int* g_cnt; int* g_nj; int* g_nimg;
+    R* g_dx; R* g_dy; R* g_dz; R* g_r; R* g_w; R* g_dw; R* g_nC; R* g_nH;
+    PathMap<R> M;
+    const double* pos;
+    double L[3];
+    const int2* lj; const int* lj_cnt; int lj_cap;
+    const int2* im; const int* im_cnt; int im_cap;
+    int2* bonds; int* nbonds; int bond_cap;
+    int4* bq; int* nbq; int bq_cap;
+    double* f;
+    double* acc;          // E_rebo, E_lj, E_tors, W[6]
+    unsigned long long* counters;   // [8]
+    int* err;             // [4]: max short-list count, map overflow, queue overflow, nonfinite
+    bool virial;
+    bool rebo, lj_on, torsion;
+};
+
+enum { ERR_SHORT = 0, ERR_MAP = 1, ERR_QUEUE = 2, ERR_NONFINITE = 3 };
+enum { CNT_BONDS = 0, CNT_BSTAR = 1, CNT_DSB = 2, CNT_LJ = 3, CNT_MAP = 4, CNT_BO = 7 };
+
+// launchers, one instantiation per precision (kernels_f64.cu, kernels_f32.cu)
+// ev (nullable): 7 events recorded before each of the 6 kernels and after the last
+template <class R> void launch_compute(const StepArgs<R>& a, cudaStream_t s, int num_sms, cudaEvent_t* ev);
+
+// neighbour build (neighbor.cu)
+struct NeighborArgs {
+    int n;
+    const double* pos;
+    const int8_t* type;
+    double L[3];
+    int nc[3], reach[3];
+    double cell_w[3];
+    float lj_rc[3];       // (3 sigma + skin + margin) per pair, squared below
+    float im_rc[3];       // (Dmax + skin + margin)
+    int* cell_of; int* cell_count; int* cell_start; int* cell_fill;
+    float4* spos; char4* swrap;
+    int2* lj; int* lj_cnt; int lj_cap;
+    int2* im; int* im_cnt; int im_cap;
+    int* err;             // [0] max lj count, [1] max im count, [2] nonfinite / out of range, [3] bad type
+    double* xref;         // copy of positions at the build (rebuild trigger)
+};
+void launch_neighbor(NeighborArgs& a, cudaStream_t s);
+
+// NVE helpers (neighbor.cu)
+void launch_nve_half(double* pos, double* vel, const double* f, const int8_t* type, int n, double dt,
+                     bool drift, const double* xref, unsigned long long* maxdisp2_bits, double* ke, cudaStream_t s);
+double alu_peak(int fp64);
+void launch_max_disp(const double* pos, const double* xref, int n, unsigned long long* maxdisp2_bits, cudaStream_t s);
+
+}  // namespace airebo

@@ -1,0 +1,8 @@
+// FP64 instantiation of the compute kernels.
+#include "kernels.cuh"
+
+namespace airebo {
+template <> void launch_compute<double>(const StepArgs<double>& a, cudaStream_t s, int num_sms, cudaEvent_t* ev) {
+    launch_compute_impl<double>(a, s, num_sms, ev);
+}
+}  // namespace airebo

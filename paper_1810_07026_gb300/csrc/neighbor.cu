@@ -1,0 +1,211 @@
+// Neighbour lists by binning (Sec. 2) and the velocity-Verlet step.
+//
+// Atoms are binned into cells at least one long cut-off wide and counting-
+// sorted by cell.  One thread per sorted atom then scans the cells of the
+// stencil, with explicit periodic images (boxes may be smaller than twice the
+// cut-off), and writes
+//   - a half list of pairs with r < 3 sigma_ij + skin for the LJ term, and
+//   - a full intermediate list with r < Dmax_ij + skin, from which the exact
+//     REBO list is filtered every step (Sec. 4.1).
+// The distance test runs in FP32 on wrapped coordinates with a small safety
+// margin: the lists are supersets, every compute kernel applies the exact
+// cut-off in FP64.  Each entry stores the neighbour and its image S relative
+// to the caller's (unwrapped) positions: x_j + S L - x_i.
+#include "internal.h"
+
+namespace airebo {
+
+__global__ void k_bin(NeighborArgs a) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    int c[3];
+    for (int d = 0; d < 3; d++) {
+        double x = a.pos[d * a.n + i];
+        if (!isfinite(x)) { atomicMax(a.err + 2, 1); x = 0.0; }
+        double w = floor(x / a.L[d]);
+        if (w < -120.0 || w > 120.0) { atomicMax(a.err + 2, 2); w = 0.0; }
+        double xw = x - w * a.L[d];
+        int cd = (int)(xw / a.cell_w[d]);
+        c[d] = cd < 0 ? 0 : (cd >= a.nc[d] ? a.nc[d] - 1 : cd);
+    }
+    int cell = (c[0] * a.nc[1] + c[1]) * a.nc[2] + c[2];
+    if (a.type[i] != 0 && a.type[i] != 1) atomicMax(a.err + 3, 1);
+    a.cell_of[i] = cell;
+    atomicAdd(a.cell_count + cell, 1);
+}
+
+// exclusive scan of the cell counts, one block
+__global__ void k_scan(const int* count, int* start, int* fill, int ncell) {
+    __shared__ int part[1024];
+    int t = threadIdx.x;
+    int per = (ncell + 1023) / 1024;
+    int lo = t * per, hi = min(lo + per, ncell);
+    int s = 0;
+    for (int c = lo; c < hi; c++) s += count[c];
+    part[t] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        int v = t >= o ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int run = part[t] - s;
+    for (int c = lo; c < hi; c++) {
+        start[c] = run;
+        fill[c] = run;
+        run += count[c];
+    }
+    if (t == 1023) start[ncell] = part[1023];
+}
+
+__global__ void k_scatter(NeighborArgs a) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    int slot = atomicAdd(a.cell_fill + a.cell_of[i], 1);
+    float xw[3];
+    int wr[3];
+    for (int d = 0; d < 3; d++) {
+        double x = a.pos[d * a.n + i];
+        if (!isfinite(x)) x = 0.0;
+        double w = floor(x / a.L[d]);
+        if (w < -120.0 || w > 120.0) w = 0.0;
+        xw[d] = (float)(x - w * a.L[d]);
+        wr[d] = (int)w;
+    }
+    a.spos[slot] = make_float4(xw[0], xw[1], xw[2], __int_as_float(i));
+    a.swrap[slot] = make_char4((char)wr[0], (char)wr[1], (char)wr[2], (char)(a.type[i] == 1 ? 1 : 0));
+}
+
+__global__ void __launch_bounds__(128) k_build(NeighborArgs a, const int* cell_start) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.n) return;
+    float4 pi = a.spos[s];
+    char4 wi = a.swrap[s];
+    int i = __float_as_int(pi.w);
+    int ti = wi.w;
+    int cell = a.cell_of[i];
+    int ci[3] = {cell / (a.nc[1] * a.nc[2]), (cell / a.nc[2]) % a.nc[1], cell % a.nc[2]};
+    float lj2[2], im2[2];
+    for (int t = 0; t < 2; t++) {
+        lj2[t] = a.lj_rc[ti + t] * a.lj_rc[ti + t];
+        im2[t] = a.im_rc[ti + t] * a.im_rc[ti + t];
+    }
+    float Lf[3] = {(float)a.L[0], (float)a.L[1], (float)a.L[2]};
+    int nlj = 0, nim = 0;
+    int2* ljrow = a.lj + (size_t)i * a.lj_cap;
+    int2* imrow = a.im + (size_t)i * a.im_cap;
+    for (int ox = -a.reach[0]; ox <= a.reach[0]; ox++) {
+        int qx = ci[0] + ox;
+        int sx = qx >= 0 ? qx / a.nc[0] : -((-qx + a.nc[0] - 1) / a.nc[0]);
+        int cx = qx - sx * a.nc[0];
+        for (int oy = -a.reach[1]; oy <= a.reach[1]; oy++) {
+            int qy = ci[1] + oy;
+            int sy = qy >= 0 ? qy / a.nc[1] : -((-qy + a.nc[1] - 1) / a.nc[1]);
+            int cy = qy - sy * a.nc[1];
+            for (int oz = -a.reach[2]; oz <= a.reach[2]; oz++) {
+                int qz = ci[2] + oz;
+                int sz = qz >= 0 ? qz / a.nc[2] : -((-qz + a.nc[2] - 1) / a.nc[2]);
+                int cz = qz - sz * a.nc[2];
+                int c = (cx * a.nc[1] + cy) * a.nc[2] + cz;
+                float shx = sx * Lf[0] - pi.x, shy = sy * Lf[1] - pi.y, shz = sz * Lf[2] - pi.z;
+                int e1 = cell_start[c + 1];
+                for (int t = cell_start[c]; t < e1; t++) {
+                    float4 pj = a.spos[t];
+                    float dx = pj.x + shx, dy = pj.y + shy, dz = pj.z + shz;
+                    float r2 = dx * dx + dy * dy + dz * dz;
+                    char4 wj = a.swrap[t];
+                    int tj = wj.w;
+                    if (r2 >= lj2[tj]) continue;
+                    int j = __float_as_int(pj.w);
+                    int Sx = sx - wj.x + wi.x, Sy = sy - wj.y + wi.y, Sz = sz - wj.z + wi.z;
+                    bool self = (j == i);
+                    if (self && Sx == 0 && Sy == 0 && Sz == 0) continue;
+                    int img = pack_img(Sx, Sy, Sz);
+                    if (r2 < im2[tj]) {
+                        if (nim < a.im_cap) imrow[nim] = make_int2(j, img);
+                        nim++;
+                    }
+                    bool pos = Sx > 0 || (Sx == 0 && (Sy > 0 || (Sy == 0 && Sz > 0)));
+                    if (j > i || (self && pos)) {
+                        if (nlj < a.lj_cap) ljrow[nlj] = make_int2(j, img);
+                        nlj++;
+                    }
+                }
+            }
+        }
+    }
+    a.lj_cnt[i] = nlj < a.lj_cap ? nlj : a.lj_cap;
+    a.im_cnt[i] = nim < a.im_cap ? nim : a.im_cap;
+    if (nlj > a.lj_cap) atomicMax(a.err + 0, nlj);
+    if (nim > a.im_cap) atomicMax(a.err + 1, nim);
+}
+
+void launch_neighbor(NeighborArgs& a, cudaStream_t s) {
+    if (a.n == 0) return;
+    int ncell = a.nc[0] * a.nc[1] * a.nc[2];
+    cudaMemsetAsync(a.cell_count, 0, sizeof(int) * ncell, s);
+    int nb = (a.n + 127) / 128;
+    k_bin<<<nb, 128, 0, s>>>(a);
+    k_scan<<<1, 1024, 0, s>>>(a.cell_count, a.cell_start, a.cell_fill, ncell);
+    k_scatter<<<nb, 128, 0, s>>>(a);
+    k_build<<<nb, 128, 0, s>>>(a, a.cell_start);
+}
+
+// ------------------------------------------------------------------ NVE
+constexpr double MVV2E = 103.642697;          // amu A^2 / fs^2 in eV
+
+__global__ void k_nve_half(double* pos, double* vel, const double* f, const int8_t* type, int n, double dt,
+                           bool drift, const double* xref, unsigned long long* maxd2, double* ke) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double k = 0, d2 = 0;
+    if (i < n) {
+        double m = type[i] == 0 ? 12.011 : 1.008;
+        double c = 0.5 * dt / (m * MVV2E);
+        double vx = vel[i] + c * f[i];
+        double vy = vel[n + i] + c * f[n + i];
+        double vz = vel[2 * n + i] + c * f[2 * n + i];
+        vel[i] = vx; vel[n + i] = vy; vel[2 * n + i] = vz;
+        if (drift) {
+            double x = pos[i] + dt * vx, y = pos[n + i] + dt * vy, z = pos[2 * n + i] + dt * vz;
+            pos[i] = x; pos[n + i] = y; pos[2 * n + i] = z;
+            double ex = x - xref[i], ey = y - xref[n + i], ez = z - xref[2 * n + i];
+            d2 = ex * ex + ey * ey + ez * ez;
+            if (!(d2 == d2)) d2 = 1e300;
+        }
+        k = 0.5 * m * MVV2E * (vx * vx + vy * vy + vz * vz);
+    }
+    if (drift && maxd2) {
+        for (int o = 16; o > 0; o >>= 1) d2 = fmax(d2, __shfl_xor_sync(0xffffffffu, d2, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(maxd2, (unsigned long long)__double_as_longlong(d2));
+    }
+    if (ke) {
+        for (int o = 16; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(ke, k);
+    }
+}
+
+__global__ void k_max_disp(const double* pos, const double* xref, int n, unsigned long long* maxd2) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double d2 = 0;
+    if (i < n) {
+        double ex = pos[i] - xref[i], ey = pos[n + i] - xref[n + i], ez = pos[2 * n + i] - xref[2 * n + i];
+        d2 = ex * ex + ey * ey + ez * ez;
+        if (!(d2 == d2)) d2 = 1e300;
+    }
+    for (int o = 16; o > 0; o >>= 1) d2 = fmax(d2, __shfl_xor_sync(0xffffffffu, d2, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(maxd2, (unsigned long long)__double_as_longlong(d2));
+}
+
+void launch_nve_half(double* pos, double* vel, const double* f, const int8_t* type, int n, double dt, bool drift,
+                     const double* xref, unsigned long long* maxd2, double* ke, cudaStream_t s) {
+    if (n == 0) return;
+    k_nve_half<<<(n + 255) / 256, 256, 0, s>>>(pos, vel, f, type, n, dt, drift, xref, maxd2, ke);
+}
+
+void launch_max_disp(const double* pos, const double* xref, int n, unsigned long long* maxd2, cudaStream_t s) {
+    if (n == 0) return;
+    k_max_disp<<<(n + 255) / 256, 256, 0, s>>>(pos, xref, n, maxd2);
+}
+
+}  // namespace airebo

@@ -1,0 +1,853 @@
+// AIREBO term arithmetic for the CUDA path: switches, splines, bond order
+// (forward and reverse), REBO bond, torsion, LJ pair with C_ij, b* pair.
+//
+// Every function here works on one interaction (one bond, one pair) and is
+// written for one GPU thread; the kernels in kernels.cuh map threads and warps
+// onto interactions.  Energies follow Sec. 2.1 of Hoehnerbach & Bientinesi:
+//   E^REBO_ij = f_R(r_ij) + b_ij f_A(r_ij)                             (Alg. 1)
+//   b_ij = 1/2 (p_ij + p_ji) + pi^rc_ij + pi^dh_ij                      (Sec. 2.1.3)
+//   p_ij = [1 + sum_k w_ik g_i(cos theta_jik) e^lambda_jik + P_ij]^-1/2  (Sec. 2.1.3)
+//   E^tors = sum w_ki w_ij w_jl V^tors(omega_kijl)                      (Alg. 2)
+//   E^LJ_ij = (S_r S_b(b*_ij) + 1 - S_r) C_ij V^LJ(r_ij)                (Alg. 3, Sec. 2.1.2)
+// Forces use the forward/reverse pattern of Sec. 2: a forward pass forms the
+// sums, the reverse pass pushes dE/d(sum) back onto every bond vector.
+// Each gradient with respect to a bond vector v = x_b - x_a is applied as
+// F_b -= g, F_a += g and adds -v (x) g to the virial.
+//
+// R is the arithmetic type of the geometry, splines and bond order (double
+// for the FP64 path, float for the mixed path); forces, energies and virial
+// are always accumulated in double.
+#pragma once
+
+#include <cstdint>
+#include <cmath>
+
+#ifdef __CUDACC__
+#define HD __host__ __device__ __forceinline__
+#else
+#define HD inline
+#endif
+
+namespace airebo {
+
+constexpr int MAXN = 8;            // REBO neighbours per atom (the bound of Sec. 4.3)
+constexpr int NTRI_CELLS = 4 * 4 * 8;
+
+// ------------------------------------------------------------------ images
+HD int pack_img(int sx, int sy, int sz) { return (sx & 0xff) | ((sy & 0xff) << 8) | ((sz & 0xff) << 16); }
+HD int img_x(int p) { return (int)(int8_t)(p & 0xff); }
+HD int img_y(int p) { return (int)(int8_t)((p >> 8) & 0xff); }
+HD int img_z(int p) { return (int)(int8_t)((p >> 16) & 0xff); }
+HD int img_add(int a, int b) { return pack_img(img_x(a) + img_x(b), img_y(a) + img_y(b), img_z(a) + img_z(b)); }
+
+// ------------------------------------------------------------------ atomics
+HD void atomic_add(double* p, double v) {
+#ifdef __CUDA_ARCH__
+    atomicAdd(p, v);
+#else
+    *p += v;
+#endif
+}
+
+// ------------------------------------------------------------------ math wrappers
+HD double rsqrt_(double x) {
+#ifdef __CUDA_ARCH__
+    return rsqrt(x);
+#else
+    return 1.0 / std::sqrt(x);
+#endif
+}
+HD float rsqrt_(float x) {
+#ifdef __CUDA_ARCH__
+    return rsqrtf(x);
+#else
+    return 1.0f / std::sqrt(x);
+#endif
+}
+HD double sqrt_(double x) { return sqrt(x); }
+HD float sqrt_(float x) { return sqrtf(x); }
+HD double exp_(double x) { return exp(x); }
+HD float exp_(float x) { return expf(x); }
+HD void sincospi_(double t, double* s, double* c) {
+#ifdef __CUDA_ARCH__
+    sincospi(t, s, c);
+#else
+    *s = std::sin(M_PI * t); *c = std::cos(M_PI * t);
+#endif
+}
+HD void sincospi_(float t, float* s, float* c) {
+#ifdef __CUDA_ARCH__
+    sincospif(t, s, c);
+#else
+    *s = (float)std::sin(M_PI * (double)t); *c = (float)std::cos(M_PI * (double)t);
+#endif
+}
+
+// ------------------------------------------------------------------ parameters
+template <class R> struct Quintic {
+    int n;             // number of intervals
+    R k[6];            // knots
+    R invh[5];         // 1 / interval width
+    R a[5][6];         // power-basis coefficients in t = (x - k_m) / h_m
+};
+
+// Device copy of the parameter set; pair-indexed arrays use 0 = CC, 1 = CH, 2 = HH.
+template <class R> struct DevParams {
+    R Dmin[3], Dmax[3], Dinv[3];
+    R Q[3], alpha[3], A[3], B[3][3], beta[3][3];
+    int nB[3];
+    R rhoH[2];                      // rho between an H centre and a neighbour of type t
+    R lam;
+    R gN0, gNinv, Fx0, Fxinv;
+    Quintic<R> gC1, gC2, gH;
+    R guard0, guardinv;
+    R sigma[3], eps4[3], rc2[3], swlo[3], swinv[3], Srlo[3], Srhi[3], Srinv[3];
+    R bmin[3], binv[3], rstar[3];
+    R teps[3];
+    R rpath2;                        // no C_ij path reaches beyond sqrt(rpath2)
+    const R* Ptab;                   // 3 tables (CC, CH, HC) x 16 cells x 16 coefficients
+    const R* Ftab;                   // 3 tables (CC, CH, HH) x 128 cells x 64 coefficients
+    const R* Ttab;                   // T_CC: 128 cells x 64 coefficients
+    const unsigned char* Tnz;        // 1 where a T_CC cell has a nonzero coefficient
+};
+
+HD int pidx(int ti, int tj) { return ti + tj; }
+
+// ------------------------------------------------------------------ switches
+// S(t) = 1 for t <= 0, 0 for t >= 1, (1 + cos pi t)/2 between; dS = dS/dt
+template <class R> HD R Sw(R t, R& dS) {
+    if (t <= R(0)) { dS = R(0); return R(1); }
+    if (t >= R(1)) { dS = R(0); return R(0); }
+    R s, c;
+    sincospi_(t, &s, &c);
+    dS = R(-0.5 * M_PI) * s;
+    return R(0.5) * (R(1) + c);
+}
+// bond weight w(r) and dw/dr
+template <class R> HD R wfun(const DevParams<R>& P, int p, R r, R& dw) {
+    R dS;
+    R w = Sw<R>((r - P.Dmin[p]) * P.Dinv[p], dS);
+    dw = dS * P.Dinv[p];
+    return w;
+}
+
+// ------------------------------------------------------------------ splines
+template <class R> HD R quintic(const Quintic<R>& q, R x, R& dfdx) {
+    bool cl = false;
+    if (x < q.k[0]) { x = q.k[0]; cl = true; }
+    if (x > q.k[q.n]) { x = q.k[q.n]; cl = true; }
+    if (!(x == x)) { x = q.k[0]; cl = true; }
+    int m = 0;
+    while (m + 1 < q.n && x > q.k[m + 1]) m++;
+    R t = (x - q.k[m]) * q.invh[m];
+    const R* a = q.a[m];
+    R f = a[5], d = R(5) * a[5];
+    f = f * t + a[4]; d = d * t + R(4) * a[4];
+    f = f * t + a[3]; d = d * t + R(3) * a[3];
+    f = f * t + a[2]; d = d * t + R(2) * a[2];
+    f = f * t + a[1]; d = d * t + a[1];
+    f = f * t + a[0];
+    dfdx = cl ? R(0) : d * q.invh[m];
+    return f;
+}
+
+template <class R> HD void clamp_arg(R& x, R lo, R hi, bool& cl) {
+    cl = false;
+    if (x < lo) { x = lo; cl = true; }
+    if (x > hi) { x = hi; cl = true; }
+    if (!(x == x)) { x = lo; cl = true; }      // NaN: keep every table index in range
+}
+HD int clamp_cell(int c, int hi) { return c < 0 ? 0 : (c > hi ? hi : c); }
+
+// bicubic on the integer grid [0,4]^2, 16 power-basis coefficients per cell
+template <class R> HD R bicubic(const R* tab, R x, R y, R& fx, R& fy) {
+    bool cx, cy;
+    clamp_arg<R>(x, R(0), R(4), cx);
+    clamp_arg<R>(y, R(0), R(4), cy);
+    int ix = clamp_cell((int)floor(x), 3);
+    int iy = clamp_cell((int)floor(y), 3);
+    R tx = x - R(ix), ty = y - R(iy);
+    const R* a = tab + (ix * 4 + iy) * 16;
+    R f = 0, dx = 0, dy = 0;
+    for (int p = 3; p >= 0; p--) {
+        const R* c = a + p * 4;
+        R cp = ((c[3] * ty + c[2]) * ty + c[1]) * ty + c[0];
+        R dcp = (R(3) * c[3] * ty + R(2) * c[2]) * ty + c[1];
+        dx = dx * tx + f;
+        f = f * tx + cp;
+        dy = dy * tx + dcp;
+    }
+    fx = cx ? R(0) : dx;
+    fy = cy ? R(0) : dy;
+    return f;
+}
+
+// tricubic on [0,4]x[0,4]x[1,9], 64 power-basis coefficients per cell
+template <class R> HD int tri_cell_index(R& x, R& y, R& z, bool* cl, R& tx, R& ty, R& tz) {
+    clamp_arg<R>(x, R(0), R(4), cl[0]);
+    clamp_arg<R>(y, R(0), R(4), cl[1]);
+    clamp_arg<R>(z, R(1), R(9), cl[2]);
+    int ix = clamp_cell((int)floor(x), 3);
+    int iy = clamp_cell((int)floor(y), 3);
+    int iz = clamp_cell((int)floor(z - R(1)), 7);
+    tx = x - R(ix); ty = y - R(iy); tz = z - R(1) - R(iz);
+    return (ix * 4 + iy) * 8 + iz;
+}
+template <class R> HD R tricubic_cell(const R* a, R tx, R ty, R tz, const bool* cl, R& fx, R& fy, R& fz) {
+    R f = 0, dx = 0, dy = 0, dz = 0;
+    for (int p = 3; p >= 0; p--) {
+        R cp = 0, cpy = 0, cpz = 0;
+        for (int q = 3; q >= 0; q--) {
+            const R* c = a + (p * 4 + q) * 4;
+            R cq = ((c[3] * tz + c[2]) * tz + c[1]) * tz + c[0];
+            R dcq = (R(3) * c[3] * tz + R(2) * c[2]) * tz + c[1];
+            cpy = cpy * ty + cp;
+            cp = cp * ty + cq;
+            cpz = cpz * ty + dcq;
+        }
+        dx = dx * tx + f;
+        f = f * tx + cp;
+        dy = dy * tx + cpy;
+        dz = dz * tx + cpz;
+    }
+    fx = cl[0] ? R(0) : dx;
+    fy = cl[1] ? R(0) : dy;
+    fz = cl[2] ? R(0) : dz;
+    return f;
+}
+
+// ------------------------------------------------------------------ neighbour data
+// Short REBO list of one step: slot s of atom i at index i * MAXN + s.
+template <class R> struct Graph {
+    int n;
+    const int8_t* type;
+    const int* cnt;          // neighbours per atom
+    const int* nj;           // neighbour atom
+    const int* nimg;         // packed image of the neighbour relative to i
+    const R* dx; const R* dy; const R* dz;   // x_j + S L - x_i
+    const R* r; const R* w; const R* dw;
+    const R* nC; const R* nH;                // sum of w over C / H neighbours
+};
+
+// accumulation of forces (atomics) and the virial of one thread
+struct Sink {
+    double* f;          // 3 x n, SoA
+    int n;
+    bool virial;
+    double W[6];
+    HD void pair(int a, int b, double vx, double vy, double vz, double gx, double gy, double gz) {
+        atomic_add(f + b, -gx); atomic_add(f + n + b, -gy); atomic_add(f + 2 * n + b, -gz);
+        atomic_add(f + a, gx); atomic_add(f + n + a, gy); atomic_add(f + 2 * n + a, gz);
+        if (virial) {
+            W[0] -= vx * gx; W[1] -= vy * gy; W[2] -= vz * gz;
+            W[3] -= vx * gy; W[4] -= vx * gz; W[5] -= vy * gz;
+        }
+    }
+    // gradient on the vector from a to b, where the force on a is kept by the caller
+    HD void half(int b, double vx, double vy, double vz, double gx, double gy, double gz,
+                 double& fax, double& fay, double& faz) {
+        atomic_add(f + b, -gx); atomic_add(f + n + b, -gy); atomic_add(f + 2 * n + b, -gz);
+        fax += gx; fay += gy; faz += gz;
+        if (virial) {
+            W[0] -= vx * gx; W[1] -= vy * gy; W[2] -= vz * gz;
+            W[3] -= vx * gy; W[4] -= vx * gz; W[5] -= vy * gz;
+        }
+    }
+};
+
+// ------------------------------------------------------------------ bond order
+// One side of b_ij: centre c, partner o.  The forward pass fills it.
+template <class R> struct Side {
+    R NC, NH, N;        // coordination of c without o, by neighbour species
+    R conj;             // sum over C neighbours k != o of w_ck F(x_ck)
+    R sum;              // sum_k w g e^lambda
+    R dsum_dN;          // d sum / d N (through the g_C mixing)
+    R P, dPdNC, dPdNH;
+    R p;                // p^{sigma pi}
+};
+
+// angular function g_c(cos) (with the g_C mixing in N for a carbon centre)
+template <class R> HD R gfun(const DevParams<R>& P, int tc, R cs, R N, R& dg_dcos, R& dg_dN) {
+    if (tc == 0) {
+        R d1, d2, dQ;
+        R G = quintic<R>(P.gC1, cs, d1);
+        R gam = quintic<R>(P.gC2, cs, d2);
+        R Qn = Sw<R>((N - P.gN0) * P.gNinv, dQ);
+        dg_dcos = d1 + Qn * (d2 - d1);
+        dg_dN = dQ * P.gNinv * (gam - G);
+        return G + Qn * (gam - G);
+    }
+    dg_dN = R(0);
+    return quintic<R>(P.gH, cs, dg_dcos);
+}
+
+// lambda_jik = lam [(rho_kH - r_ik) - (rho_jH - r_ij)] for an H centre, else 0
+template <class R> HD R lambda(const DevParams<R>& P, int tc, int tk, int to, R rck, R umag) {
+    if (tc == 0) return R(0);
+    return P.lam * ((P.rhoH[tk] - rck) - (P.rhoH[to] - umag));
+}
+
+template <class R>
+HD void side_forward(const DevParams<R>& P, const Graph<R>& G, int c, int o, R ux, R uy, R uz, R umag, Side<R>& s) {
+    int tc = G.type[c], to = G.type[o];
+    int nc = G.cnt[c];
+    s.NC = 0; s.NH = 0; s.conj = 0;
+    for (int a = 0; a < nc; a++) {
+        int q = c * MAXN + a;
+        int k = G.nj[q];
+        if (k == o) continue;
+        R w = G.w[q];
+        if (G.type[k] == 0) {
+            s.NC += w;
+            R x = G.nC[k] + G.nH[k] - w;
+            R dF;
+            s.conj += w * Sw<R>((x - P.Fx0) * P.Fxinv, dF);
+        } else {
+            s.NH += w;
+        }
+    }
+    s.N = s.NC + s.NH;
+    s.sum = 0; s.dsum_dN = 0;
+    R inv_u = R(1) / umag;
+    for (int a = 0; a < nc; a++) {
+        int q = c * MAXN + a;
+        int k = G.nj[q];
+        if (k == o) continue;
+        R rck = G.r[q];
+        R cs = (ux * G.dx[q] + uy * G.dy[q] + uz * G.dz[q]) * inv_u / rck;
+        cs = cs < R(-1) ? R(-1) : (cs > R(1) ? R(1) : cs);
+        R dgc, dgN;
+        R g = gfun<R>(P, tc, cs, s.N, dgc, dgN);
+        R e = exp_(lambda<R>(P, tc, G.type[k], to, rck, umag));
+        s.sum += G.w[q] * g * e;
+        s.dsum_dN += G.w[q] * dgN * e;
+    }
+    s.P = 0; s.dPdNC = 0; s.dPdNH = 0;
+    if (!(tc == 1 && to == 1)) {
+        int tab = (tc == 0 && to == 0) ? 0 : (tc == 0 ? 1 : 2);
+        s.P = bicubic<R>(P.Ptab + tab * 256, s.NC, s.NH, s.dPdNC, s.dPdNH);
+    }
+    s.p = R(1) / sqrt_(R(1) + s.sum + s.P);
+}
+
+// Reverse of one side.  dEdp: adjoint of p; dEdN_direct: adjoint of N_co
+// from pi^rc / pi^dh; dEdconj: adjoint of the conjugation sum.  Accumulates
+// the gradient with respect to the partner vector u (sign as given) and to
+// its length; applies the forces on the neighbours of c.
+template <class R>
+HD void side_reverse(const DevParams<R>& P, const Graph<R>& G, int c, int o, R ux, R uy, R uz, R umag,
+                     const Side<R>& s, R dEdp, R dEdN_direct, R dEdconj, Sink& sink,
+                     R& gux, R& guy, R& guz, R& gumag, double& fcx, double& fcy, double& fcz) {
+    int tc = G.type[c], to = G.type[o];
+    int nc = G.cnt[c];
+    R ac = R(-0.5) * s.p * s.p * s.p * dEdp;       // dE/dsum = dE/dP
+    R dEdN = dEdN_direct + ac * s.dsum_dN;
+    R dEdNC = dEdN + ac * s.dPdNC;
+    R dEdNH = dEdN + ac * s.dPdNH;
+    R inv_u = R(1) / umag;
+    for (int a = 0; a < nc; a++) {
+        int q = c * MAXN + a;
+        int k = G.nj[q];
+        if (k == o) continue;
+        int tk = G.type[k];
+        R dxk = G.dx[q], dyk = G.dy[q], dzk = G.dz[q];
+        R rck = G.r[q], w = G.w[q], dw = G.dw[q];
+        R inv_r = R(1) / rck;
+        R cs_raw = (ux * dxk + uy * dyk + uz * dzk) * inv_u * inv_r;
+        bool cl = cs_raw < R(-1) || cs_raw > R(1);
+        R cs = cs_raw < R(-1) ? R(-1) : (cs_raw > R(1) ? R(1) : cs_raw);
+        R dgc, dgN;
+        R g = gfun<R>(P, tc, cs, s.N, dgc, dgN);
+        R lam = lambda<R>(P, tc, tk, to, rck, umag);
+        R e = exp_(lam);
+        // d E / d w_ck
+        R dEdw = (tk == 0 ? dEdNC : dEdNH) + ac * g * e;
+        R x = R(0), Fx = R(0), dFx = R(0);
+        if (tk == 0) {
+            x = G.nC[k] + G.nH[k] - w;
+            Fx = Sw<R>((x - P.Fx0) * P.Fxinv, dFx);
+            dFx *= P.Fxinv;
+            dEdw += dEdconj * Fx;
+        }
+        R dEdr = dEdw * dw;
+        if (tc == 1) {           // lambda depends on r_ck (-lam) and on |u| (+lam)
+            R t = ac * w * g * e * P.lam;
+            dEdr -= t;
+            gumag += t;
+        }
+        R dEdcs = cl ? R(0) : ac * w * e * dgc;
+        // cos = u.d / (|u| |d|)
+        R gxk = dEdr * dxk * inv_r + dEdcs * (ux * inv_u * inv_r - cs * dxk * inv_r * inv_r);
+        R gyk = dEdr * dyk * inv_r + dEdcs * (uy * inv_u * inv_r - cs * dyk * inv_r * inv_r);
+        R gzk = dEdr * dzk * inv_r + dEdcs * (uz * inv_u * inv_r - cs * dzk * inv_r * inv_r);
+        gux += dEdcs * (dxk * inv_u * inv_r - cs * ux * inv_u * inv_u);
+        guy += dEdcs * (dyk * inv_u * inv_r - cs * uy * inv_u * inv_u);
+        guz += dEdcs * (dzk * inv_u * inv_r - cs * uz * inv_u * inv_u);
+        sink.half(k, dxk, dyk, dzk, gxk, gyk, gzk, fcx, fcy, fcz);
+        // conjugation: x_ck = sum_{m in N(k), m != c} w_km
+        if (tk == 0 && dFx != R(0) && dEdconj != R(0)) {
+            R coef = dEdconj * w * dFx;
+            int nk = G.cnt[k];
+            for (int b = 0; b < nk; b++) {
+                int qq = k * MAXN + b;
+                int m = G.nj[qq];
+                if (m == c) continue;
+                R dwm = G.dw[qq];
+                if (dwm == R(0)) continue;
+                R t = coef * dwm / G.r[qq];
+                sink.pair(k, m, G.dx[qq], G.dy[qq], G.dz[qq], t * G.dx[qq], t * G.dy[qq], t * G.dz[qq]);
+            }
+        }
+    }
+}
+
+// angle guard of the dihedral sums: 1 unless |cos| is within the guard band of 1
+template <class R> HD R guardf(const DevParams<R>& P, R cs, R& dgd) {
+    R a = cs < R(0) ? -cs : cs;
+    R dS;
+    R g = Sw<R>((a - P.guard0) * P.guardinv, dS);
+    dgd = dS * P.guardinv * (cs < R(0) ? R(-1) : R(1));
+    return g;
+}
+
+// sum over k in N(i)\j, l in N(j)\{i,k} of (1 - cos^2 w) w_ik w_jl s_i s_j, and
+// (reverse) its gradient times dEdD.  u = vector standing for r_ij.
+template <class R>
+HD R dihedral_sum(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, R uy, R uz, R umag,
+                  bool reverse, R dEdD, Sink& sink, R& gux, R& guy, R& guz,
+                  double& fix, double& fiy, double& fiz, double& fjx, double& fjy, double& fjz) {
+    R D = 0;
+    int ni = G.cnt[i], nj = G.cnt[j];
+    R inv_u = R(1) / umag;
+    for (int a = 0; a < ni; a++) {
+        int qa = i * MAXN + a;
+        int k = G.nj[qa];
+        if (k == j) continue;
+        R ax = G.dx[qa], ay = G.dy[qa], az = G.dz[qa];
+        R ra = G.r[qa], wik = G.w[qa], dwik = G.dw[qa];
+        R csi = (ux * ax + uy * ay + uz * az) * inv_u / ra;
+        R dsi;
+        R si = guardf<R>(P, csi, dsi);
+        if (si == R(0)) continue;
+        // n1 = u x a
+        R n1x = uy * az - uz * ay, n1y = uz * ax - ux * az, n1z = ux * ay - uy * ax;
+        R n1 = sqrt_(n1x * n1x + n1y * n1y + n1z * n1z);
+        for (int b = 0; b < nj; b++) {
+            int qb = j * MAXN + b;
+            int l = G.nj[qb];
+            if (l == i || l == k) continue;
+            R bx = G.dx[qb], by = G.dy[qb], bz = G.dz[qb];
+            R rb = G.r[qb], wjl = G.w[qb], dwjl = G.dw[qb];
+            R csj = -(ux * bx + uy * by + uz * bz) * inv_u / rb;
+            R dsj;
+            R sj = guardf<R>(P, csj, dsj);
+            if (sj == R(0)) continue;
+            R n2x = uy * bz - uz * by, n2y = uz * bx - ux * bz, n2z = ux * by - uy * bx;
+            R n2 = sqrt_(n2x * n2x + n2y * n2y + n2z * n2z);
+            R inv12 = R(1) / (n1 * n2);
+            R cw = (n1x * n2x + n1y * n2y + n1z * n2z) * inv12;
+            R one_m = R(1) - cw * cw;
+            D += one_m * wik * wjl * si * sj;
+            if (!reverse) continue;
+            R dcw = dEdD * R(-2) * cw * wik * wjl * si * sj;
+            R dwi = dEdD * one_m * wjl * si * sj;
+            R dwj = dEdD * one_m * wik * si * sj;
+            R dci = dEdD * one_m * wik * wjl * sj * dsi;   // dE/dcos theta_jik
+            R dcj = dEdD * one_m * wik * wjl * si * dsj;   // dE/dcos theta_ijl
+            // gradient of cw with respect to n1, n2
+            R g1x = dcw * (n2x * inv12 - cw * n1x / (n1 * n1));
+            R g1y = dcw * (n2y * inv12 - cw * n1y / (n1 * n1));
+            R g1z = dcw * (n2z * inv12 - cw * n1z / (n1 * n1));
+            R g2x = dcw * (n1x * inv12 - cw * n2x / (n2 * n2));
+            R g2y = dcw * (n1y * inv12 - cw * n2y / (n2 * n2));
+            R g2z = dcw * (n1z * inv12 - cw * n2z / (n2 * n2));
+            // n1 = u x a: d/du = a x g1, d/da = g1 x u ; n2 = u x b likewise
+            gux += ay * g1z - az * g1y + by * g2z - bz * g2y;
+            guy += az * g1x - ax * g1z + bz * g2x - bx * g2z;
+            guz += ax * g1y - ay * g1x + bx * g2y - by * g2x;
+            R gax = g1y * uz - g1z * uy, gay = g1z * ux - g1x * uz, gaz = g1x * uy - g1y * ux;
+            R gbx = g2y * uz - g2z * uy, gby = g2z * ux - g2x * uz, gbz = g2x * uy - g2y * ux;
+            // weights
+            R inv_ra = R(1) / ra, inv_rb = R(1) / rb;
+            gax += dwi * dwik * ax * inv_ra; gay += dwi * dwik * ay * inv_ra; gaz += dwi * dwik * az * inv_ra;
+            gbx += dwj * dwjl * bx * inv_rb; gby += dwj * dwjl * by * inv_rb; gbz += dwj * dwjl * bz * inv_rb;
+            // guards: csi = u.a/(|u||a|), csj = -u.b/(|u||b|)
+            gax += dci * (ux * inv_u * inv_ra - csi * ax * inv_ra * inv_ra);
+            gay += dci * (uy * inv_u * inv_ra - csi * ay * inv_ra * inv_ra);
+            gaz += dci * (uz * inv_u * inv_ra - csi * az * inv_ra * inv_ra);
+            gux += dci * (ax * inv_u * inv_ra - csi * ux * inv_u * inv_u);
+            guy += dci * (ay * inv_u * inv_ra - csi * uy * inv_u * inv_u);
+            guz += dci * (az * inv_u * inv_ra - csi * uz * inv_u * inv_u);
+            gbx += dcj * (-ux * inv_u * inv_rb - csj * bx * inv_rb * inv_rb);
+            gby += dcj * (-uy * inv_u * inv_rb - csj * by * inv_rb * inv_rb);
+            gbz += dcj * (-uz * inv_u * inv_rb - csj * bz * inv_rb * inv_rb);
+            gux += dcj * (-bx * inv_u * inv_rb - csj * ux * inv_u * inv_u);
+            guy += dcj * (-by * inv_u * inv_rb - csj * uy * inv_u * inv_u);
+            guz += dcj * (-bz * inv_u * inv_rb - csj * uz * inv_u * inv_u);
+            sink.half(k, ax, ay, az, gax, gay, gaz, fix, fiy, fiz);
+            sink.half(l, bx, by, bz, gbx, gby, gbz, fjx, fjy, fjz);
+        }
+    }
+    return D;
+}
+
+// b_ij with u standing for r_ij.  In reverse mode (eps = dE/db != 0) it applies
+// the forces on all neighbours and returns the gradient with respect to u and
+// its length in gu*, gumag, and the forces on i and j themselves in fi*, fj*
+// (excluding the u gradient, which the caller applies).
+template <class R>
+HD R bond_order(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, R uy, R uz, R umag,
+                bool reverse, R eps, Sink& sink, R& gux, R& guy, R& guz, R& gumag,
+                double& fix, double& fiy, double& fiz, double& fjx, double& fjy, double& fjz) {
+    Side<R> si, sj;
+    side_forward<R>(P, G, i, j, ux, uy, uz, umag, si);
+    side_forward<R>(P, G, j, i, -ux, -uy, -uz, umag, sj);
+    int ti = G.type[i], tj = G.type[j];
+    R Nconj = R(1) + si.conj * si.conj + sj.conj * sj.conj;
+    // pi^rc: the carbon side's coordination first for a C-H bond
+    int tab = (ti == tj) ? (ti == 0 ? 0 : 2) : 1;
+    bool swap = (ti == 1 && tj == 0);
+    R xa = swap ? sj.N : si.N, xb = swap ? si.N : sj.N, xc = Nconj;
+    bool cl[3];
+    R tx, ty, tz;
+    int cell = tri_cell_index<R>(xa, xb, xc, cl, tx, ty, tz);
+    R Fa, Fb, Fc;
+    R pirc = tricubic_cell<R>(P.Ftab + (tab * NTRI_CELLS + cell) * 64, tx, ty, tz, cl, Fa, Fb, Fc);
+    R dFdNi = swap ? Fb : Fa, dFdNj = swap ? Fa : Fb;
+    // pi^dh (C-C only), skipped where the T_CC cell is identically zero
+    R pidh = 0, D = 0, Tv = 0, Ta = 0, Tb = 0, Tc = 0;
+    bool dih = (ti == 0 && tj == 0) && P.Tnz[cell];
+    if (dih) {
+        Tv = tricubic_cell<R>(P.Ttab + cell * 64, tx, ty, tz, cl, Ta, Tb, Tc);
+        R dummy = 0;
+        D = dihedral_sum<R>(P, G, i, j, ux, uy, uz, umag, false, R(0), sink, dummy, dummy, dummy,
+                            fix, fiy, fiz, fjx, fjy, fjz);
+        pidh = Tv * D;
+    }
+    R b = R(0.5) * (si.p + sj.p) + pirc + pidh;
+    if (!reverse) return b;
+    R dEdNi = eps * (dFdNi + D * Ta);
+    R dEdNj = eps * (dFdNj + D * Tb);
+    R dEdNconj = eps * (Fc + D * Tc);
+    R half = R(0.5) * eps;
+    R gvx = 0, gvy = 0, gvz = 0;     // side j works on -u
+    side_reverse<R>(P, G, i, j, ux, uy, uz, umag, si, half, dEdNi, dEdNconj * R(2) * si.conj, sink,
+                    gux, guy, guz, gumag, fix, fiy, fiz);
+    side_reverse<R>(P, G, j, i, -ux, -uy, -uz, umag, sj, half, dEdNj, dEdNconj * R(2) * sj.conj, sink,
+                    gvx, gvy, gvz, gumag, fjx, fjy, fjz);
+    gux -= gvx; guy -= gvy; guz -= gvz;
+    if (dih) {
+        dihedral_sum<R>(P, G, i, j, ux, uy, uz, umag, true, eps * Tv, sink, gux, guy, guz,
+                        fix, fiy, fiz, fjx, fjy, fjz);
+    }
+    return b;
+}
+
+// ------------------------------------------------------------------ REBO bond (Alg. 1)
+template <class R>
+HD double rebo_bond(const DevParams<R>& P, const Graph<R>& G, int i, int slot, Sink& sink) {
+    int q = i * MAXN + slot;
+    int j = G.nj[q];
+    int p = pidx(G.type[i], G.type[j]);
+    R ux = G.dx[q], uy = G.dy[q], uz = G.dz[q], r = G.r[q];
+    R w = G.w[q], dw = G.dw[q];
+    R eR = exp_(-P.alpha[p] * r);
+    R qr = R(1) + P.Q[p] / r;
+    R fR = w * qr * P.A[p] * eR;
+    R dfR = dw * qr * P.A[p] * eR + w * (-P.Q[p] / (r * r)) * P.A[p] * eR - P.alpha[p] * fR;
+    R sB = 0, dsB = 0;
+    for (int m = 0; m < P.nB[p]; m++) {
+        R e = P.B[p][m] * exp_(-P.beta[p][m] * r);
+        sB += e;
+        dsB -= P.beta[p][m] * e;
+    }
+    R fA = -w * sB;
+    R dfA = -dw * sB - w * dsB;
+    R gux = 0, guy = 0, guz = 0, gumag = 0;
+    double fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
+    R b = bond_order<R>(P, G, i, j, ux, uy, uz, r, true, fA, sink, gux, guy, guz, gumag,
+                        fix, fiy, fiz, fjx, fjy, fjz);
+    R dEdr = dfR + b * dfA + gumag;
+    R inv_r = R(1) / r;
+    gux += dEdr * ux * inv_r; guy += dEdr * uy * inv_r; guz += dEdr * uz * inv_r;
+    // vector u runs from i to j
+    double gx = gux, gy = guy, gz = guz;
+    atomic_add(sink.f + i, fix + gx); atomic_add(sink.f + sink.n + i, fiy + gy); atomic_add(sink.f + 2 * sink.n + i, fiz + gz);
+    atomic_add(sink.f + j, fjx - gx); atomic_add(sink.f + sink.n + j, fjy - gy); atomic_add(sink.f + 2 * sink.n + j, fjz - gz);
+    if (sink.virial) {
+        sink.W[0] -= (double)ux * gx; sink.W[1] -= (double)uy * gy; sink.W[2] -= (double)uz * gz;
+        sink.W[3] -= (double)ux * gy; sink.W[4] -= (double)ux * gz; sink.W[5] -= (double)uy * gz;
+    }
+    return (double)(fR + b * fA);
+}
+
+// ------------------------------------------------------------------ torsion (Alg. 2)
+// omega is the dihedral angle with trans = pi; cos^2(omega/2) = (1 + cos omega)/2
+template <class R>
+HD double torsion_bond(const DevParams<R>& P, const Graph<R>& G, int i, int slot, Sink& sink) {
+    int q = i * MAXN + slot;
+    int j = G.nj[q];
+    R ux = G.dx[q], uy = G.dy[q], uz = G.dz[q], r = G.r[q];
+    R wij = G.w[q], dwij = G.dw[q];
+    R inv_u = R(1) / r;
+    double E = 0;
+    R gux = 0, guy = 0, guz = 0;
+    double fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
+    int ni = G.cnt[i], nj = G.cnt[j];
+    for (int a = 0; a < ni; a++) {
+        int qa = i * MAXN + a;
+        int k = G.nj[qa];
+        if (k == j) continue;
+        R ax = G.dx[qa], ay = G.dy[qa], az = G.dz[qa];
+        R ra = G.r[qa], wik = G.w[qa], dwik = G.dw[qa];
+        R inv_ra = R(1) / ra;
+        R csi = (ux * ax + uy * ay + uz * az) * inv_u * inv_ra;
+        R dsi;
+        R si = guardf<R>(P, csi, dsi);
+        if (si == R(0)) continue;
+        R n1x = uy * az - uz * ay, n1y = uz * ax - ux * az, n1z = ux * ay - uy * ax;
+        R n1s = n1x * n1x + n1y * n1y + n1z * n1z;
+        for (int b = 0; b < nj; b++) {
+            int qb = j * MAXN + b;
+            int l = G.nj[qb];
+            if (l == i || l == k) continue;
+            R bx = G.dx[qb], by = G.dy[qb], bz = G.dz[qb];
+            R rb = G.r[qb], wjl = G.w[qb], dwjl = G.dw[qb];
+            R inv_rb = R(1) / rb;
+            R csj = -(ux * bx + uy * by + uz * bz) * inv_u * inv_rb;
+            R dsj;
+            R sj = guardf<R>(P, csj, dsj);
+            if (sj == R(0)) continue;
+            R n2x = uy * bz - uz * by, n2y = uz * bx - ux * bz, n2z = ux * by - uy * bx;
+            R n2s = n2x * n2x + n2y * n2y + n2z * n2z;
+            R inv12 = rsqrt_(n1s * n2s);
+            R cw = (n1x * n2x + n1y * n2y + n1z * n2z) * inv12;
+            R h = R(0.5) * (R(1) + cw);
+            R h2 = h * h, h4 = h2 * h2;
+            R eps = P.teps[(G.type[k] == 1) + (G.type[l] == 1)];
+            R Vt = eps * (R(256.0 / 405.0) * h4 * h - R(0.1));
+            R dVdcw = eps * R(256.0 / 405.0) * R(2.5) * h4;
+            R wprod = wik * wij * wjl;
+            R ss = si * sj;
+            E += (double)(wprod * ss * Vt);
+            R dcw = wprod * ss * dVdcw;
+            R dwi = dwik * wij * wjl * ss * Vt;
+            R dwj = wik * wij * dwjl * ss * Vt;
+            R dwm = wik * dwij * wjl * ss * Vt;
+            R dci = wprod * sj * dsi * Vt;
+            R dcj = wprod * si * dsj * Vt;
+            R g1x = dcw * (n2x * inv12 - cw * n1x / n1s);
+            R g1y = dcw * (n2y * inv12 - cw * n1y / n1s);
+            R g1z = dcw * (n2z * inv12 - cw * n1z / n1s);
+            R g2x = dcw * (n1x * inv12 - cw * n2x / n2s);
+            R g2y = dcw * (n1y * inv12 - cw * n2y / n2s);
+            R g2z = dcw * (n1z * inv12 - cw * n2z / n2s);
+            gux += ay * g1z - az * g1y + by * g2z - bz * g2y;
+            guy += az * g1x - ax * g1z + bz * g2x - bx * g2z;
+            guz += ax * g1y - ay * g1x + bx * g2y - by * g2x;
+            R gax = g1y * uz - g1z * uy, gay = g1z * ux - g1x * uz, gaz = g1x * uy - g1y * ux;
+            R gbx = g2y * uz - g2z * uy, gby = g2z * ux - g2x * uz, gbz = g2x * uy - g2y * ux;
+            gax += dwi * ax * inv_ra; gay += dwi * ay * inv_ra; gaz += dwi * az * inv_ra;
+            gbx += dwj * bx * inv_rb; gby += dwj * by * inv_rb; gbz += dwj * bz * inv_rb;
+            gux += dwm * ux * inv_u; guy += dwm * uy * inv_u; guz += dwm * uz * inv_u;
+            gax += dci * (ux * inv_u * inv_ra - csi * ax * inv_ra * inv_ra);
+            gay += dci * (uy * inv_u * inv_ra - csi * ay * inv_ra * inv_ra);
+            gaz += dci * (uz * inv_u * inv_ra - csi * az * inv_ra * inv_ra);
+            gux += dci * (ax * inv_u * inv_ra - csi * ux * inv_u * inv_u);
+            guy += dci * (ay * inv_u * inv_ra - csi * uy * inv_u * inv_u);
+            guz += dci * (az * inv_u * inv_ra - csi * uz * inv_u * inv_u);
+            gbx += dcj * (-ux * inv_u * inv_rb - csj * bx * inv_rb * inv_rb);
+            gby += dcj * (-uy * inv_u * inv_rb - csj * by * inv_rb * inv_rb);
+            gbz += dcj * (-uz * inv_u * inv_rb - csj * bz * inv_rb * inv_rb);
+            gux += dcj * (-bx * inv_u * inv_rb - csj * ux * inv_u * inv_u);
+            guy += dcj * (-by * inv_u * inv_rb - csj * uy * inv_u * inv_u);
+            guz += dcj * (-bz * inv_u * inv_rb - csj * uz * inv_u * inv_u);
+            sink.half(k, ax, ay, az, gax, gay, gaz, fix, fiy, fiz);
+            sink.half(l, bx, by, bz, gbx, gby, gbz, fjx, fjy, fjz);
+        }
+    }
+    if (E == 0.0 && gux == R(0) && guy == R(0) && guz == R(0) && fix == 0.0 && fjx == 0.0 && fiy == 0.0 && fjy == 0.0)
+        return 0.0;
+    double gx = gux, gy = guy, gz = guz;
+    atomic_add(sink.f + i, fix + gx); atomic_add(sink.f + sink.n + i, fiy + gy); atomic_add(sink.f + 2 * sink.n + i, fiz + gz);
+    atomic_add(sink.f + j, fjx - gx); atomic_add(sink.f + sink.n + j, fjy - gy); atomic_add(sink.f + 2 * sink.n + j, fjz - gz);
+    if (sink.virial) {
+        sink.W[0] -= (double)ux * gx; sink.W[1] -= (double)uy * gy; sink.W[2] -= (double)uz * gz;
+        sink.W[3] -= (double)ux * gy; sink.W[4] -= (double)ux * gz; sink.W[5] -= (double)uy * gz;
+    }
+    return E;
+}
+
+// ------------------------------------------------------------------ C_ij paths (Sec. 2.1.2, 4.3)
+// A connectivity map of atom i holds, for every atom reachable over at most
+// three REBO bonds (keyed by atom and periodic image), the largest path
+// weight and the path realising it (slots of the bonds along the path).
+HD long long map_key(int j, int img) { return ((long long)j << 24) | (long long)(img & 0xffffff); }
+HD int path_pack(int len, int a, int b, int c) { return len | (a << 4) | (b << 8) | (c << 12); }
+HD int path_len(int p) { return p & 15; }
+HD int path_a(int p) { return (p >> 4) & 15; }
+HD int path_b(int p) { return (p >> 8) & 15; }
+HD int path_c(int p) { return (p >> 12) & 15; }
+
+template <class R> struct PathMap {
+    int cap;
+    int* cnt;            // entries per atom
+    long long* key;      // [n * cap]
+    R* wt;
+    int* path;
+};
+
+// Ties: larger weight, then the shorter path, then the smaller k, then the smaller l.
+HD bool path_better(double w, int len, int k, int l, double w0, int len0, int k0, int l0) {
+    if (w != w0) return w > w0;
+    if (len != len0) return len < len0;
+    if (k != k0) return k < k0;
+    return l < l0;
+}
+
+template <class R>
+HD int build_path_map(const Graph<R>& G, PathMap<R>& M, int i) {
+    int base = i * M.cap;
+    int count = 0, overflow = 0;
+    auto insert = [&](int atom, int img, R w, int len, int k, int l, int code) {
+        long long key = map_key(atom, img);
+        for (int e = 0; e < count; e++) {
+            if (M.key[base + e] == key) {
+                int p0 = M.path[base + e];
+                int k0 = path_len(p0) >= 2 ? G.nj[i * MAXN + path_a(p0)] : -1;
+                int l0 = -1;
+                if (path_len(p0) == 3) l0 = G.nj[G.nj[i * MAXN + path_a(p0)] * MAXN + path_b(p0)];
+                if (path_better((double)w, len, k, l, (double)M.wt[base + e], path_len(p0), k0, l0)) {
+                    M.wt[base + e] = w;
+                    M.path[base + e] = code;
+                }
+                return;
+            }
+        }
+        if (count < M.cap) {
+            M.key[base + count] = key;
+            M.wt[base + count] = w;
+            M.path[base + count] = code;
+            count++;
+        } else {
+            overflow++;
+        }
+    };
+    int ni = G.cnt[i];
+    for (int a = 0; a < ni; a++) {
+        int qa = i * MAXN + a;
+        int k = G.nj[qa];
+        int Sk = G.nimg[qa];
+        R w1 = G.w[qa];
+        insert(k, Sk, w1, 1, -1, -1, path_pack(1, a, 0, 0));
+        int nk = G.cnt[k];
+        for (int b = 0; b < nk; b++) {
+            int qb = k * MAXN + b;
+            int l = G.nj[qb];
+            if (l == i) continue;
+            int Sl = img_add(Sk, G.nimg[qb]);
+            R w2 = w1 * G.w[qb];
+            insert(l, Sl, w2, 2, k, -1, path_pack(2, a, b, 0));
+            int nl = G.cnt[l];
+            for (int c = 0; c < nl; c++) {
+                int qc = l * MAXN + c;
+                int m = G.nj[qc];
+                if (m == i || m == k) continue;
+                int Sm = img_add(Sl, G.nimg[qc]);
+                insert(m, Sm, w2 * G.w[qc], 3, k, l, path_pack(3, a, b, c));
+            }
+        }
+    }
+    M.cnt[i] = count;
+    return overflow;
+}
+
+// forces of dE/dwmax on the bonds of the path stored for atom i
+template <class R>
+HD void path_forces(const Graph<R>& G, int i, int code, R dEdw, Sink& sink, double& fix, double& fiy, double& fiz) {
+    int len = path_len(code);
+    int q[3], from[3];
+    q[0] = i * MAXN + path_a(code); from[0] = i;
+    int k = G.nj[q[0]];
+    if (len >= 2) { q[1] = k * MAXN + path_b(code); from[1] = k; }
+    if (len == 3) { int l = G.nj[q[1]]; q[2] = l * MAXN + path_c(code); from[2] = l; }
+    R w[3], dw[3];
+    for (int s = 0; s < len; s++) { w[s] = G.w[q[s]]; dw[s] = G.dw[q[s]]; }
+    for (int s = 0; s < len; s++) {
+        if (dw[s] == R(0)) continue;
+        R other = R(1);
+        for (int t = 0; t < len; t++) if (t != s) other *= w[t];
+        R c = dEdw * other * dw[s] / G.r[q[s]];
+        R gx = c * G.dx[q[s]], gy = c * G.dy[q[s]], gz = c * G.dz[q[s]];
+        if (from[s] == i) sink.half(G.nj[q[s]], G.dx[q[s]], G.dy[q[s]], G.dz[q[s]], gx, gy, gz, fix, fiy, fiz);
+        else sink.pair(from[s], G.nj[q[s]], G.dx[q[s]], G.dy[q[s]], G.dz[q[s]], gx, gy, gz);
+    }
+}
+
+// ------------------------------------------------------------------ LJ (Alg. 3)
+// V^LJ(r) 4 eps [(s/r)^12 - (s/r)^6] times the C^1 cubic cut-off; returns dV/dr
+template <class R> HD R vlj(const DevParams<R>& P, int p, R r, R inv_r2, R& dV) {
+    R s2 = P.sigma[p] * P.sigma[p] * inv_r2;
+    R s6 = s2 * s2 * s2;
+    R v = P.eps4[p] * (s6 * s6 - s6);
+    R dv = P.eps4[p] * (R(-12) * s6 * s6 + R(6) * s6) / r;
+    R t = (r - P.swlo[p]) * P.swinv[p];
+    if (t > R(0)) {
+        R so = R(1) - t * t * (R(3) - R(2) * t);
+        R dso = R(-6) * t * (R(1) - t) * P.swinv[p];
+        dV = dv * so + v * dso;
+        return v * so;
+    }
+    dV = dv;
+    return v;
+}
+
+// b* pair: (S_r S_b + 1 - S_r) C V for the pair i -> (j, image) with
+// displacement d (FP64 in, R for the arithmetic); C and its path given.
+template <class R>
+HD double bstar_pair(const DevParams<R>& P, const Graph<R>& G, int i, int j, R dx, R dy, R dz, R r,
+                     R C, int path_code, Sink& sink, unsigned* dsb_count) {
+    int p = pidx(G.type[i], G.type[j]);
+    R inv_r = R(1) / r;
+    R dV;
+    R V = vlj<R>(P, p, r, inv_r * inv_r, dV);
+    R dSr;
+    R Sr = Sw<R>((r - P.Srlo[p]) * P.Srinv[p], dSr);
+    dSr *= P.Srinv[p];
+    R rs = P.rstar[p];
+    R ux = dx * inv_r * rs, uy = dy * inv_r * rs, uz = dz * inv_r * rs;
+    R gux = 0, guy = 0, guz = 0, gumag = 0;
+    double fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
+    R bs = bond_order<R>(P, G, i, j, ux, uy, uz, rs, false, R(0), sink, gux, guy, guz, gumag,
+                         fix, fiy, fiz, fjx, fjy, fjz);
+    R dSb;
+    R Sb = Sw<R>((bs - P.bmin[p]) * P.binv[p], dSb);
+    dSb *= P.binv[p];
+    R factor = Sr * Sb + R(1) - Sr;
+    R E = factor * C * V;
+    R dEdr = (dSr * (Sb - R(1))) * C * V + factor * C * dV;
+    R gx = dEdr * dx * inv_r, gy = dEdr * dy * inv_r, gz = dEdr * dz * inv_r;
+    if (dSb != R(0)) {
+        if (dsb_count) *dsb_count += 1;
+        R eps = Sr * C * V * dSb;
+        bond_order<R>(P, G, i, j, ux, uy, uz, rs, true, eps, sink, gux, guy, guz, gumag,
+                      fix, fiy, fiz, fjx, fjy, fjz);
+        // u = r* d/|d|: only the direction of d carries a gradient
+        R ud = (gux * dx + guy * dy + guz * dz) * inv_r;
+        R sc = rs * inv_r;
+        gx += sc * (gux - ud * dx * inv_r);
+        gy += sc * (guy - ud * dy * inv_r);
+        gz += sc * (guz - ud * dz * inv_r);
+    }
+    if (path_code >= 0) path_forces<R>(G, i, path_code, -factor * V, sink, fix, fiy, fiz);
+    double g3[3] = {gx, gy, gz};
+    atomic_add(sink.f + i, fix + g3[0]); atomic_add(sink.f + sink.n + i, fiy + g3[1]); atomic_add(sink.f + 2 * sink.n + i, fiz + g3[2]);
+    atomic_add(sink.f + j, fjx - g3[0]); atomic_add(sink.f + sink.n + j, fjy - g3[1]); atomic_add(sink.f + 2 * sink.n + j, fjz - g3[2]);
+    if (sink.virial) {
+        sink.W[0] -= (double)dx * g3[0]; sink.W[1] -= (double)dy * g3[1]; sink.W[2] -= (double)dz * g3[2];
+        sink.W[3] -= (double)dx * g3[1]; sink.W[4] -= (double)dx * g3[2]; sink.W[5] -= (double)dy * g3[2];
+    }
+    return (double)E;
+}
+
+}  // namespace airebo

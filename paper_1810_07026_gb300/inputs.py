@@ -204,22 +204,25 @@ def polyethylene(nx: int, ny: int, nz: int, noise: float = 0.03, seed: int = 1,
     half = 0.5 * c
     lateral = math.sqrt(r_cc * r_cc - half * half)     # zig-zag amplitude
     th = math.radians(109.4712206 / 2.0)
-    atoms, types = [], []
+    # the 12 atoms of one cell, relative to the cell corner
+    motif, mtypes = [], []
     chains = [((0.0, 0.0), +setting_deg), ((0.5 * a, 0.5 * b), -setting_deg)]
-    for ix in range(nx):
-        for iy in range(ny):
-            for iz in range(nz):
-                for (cx, cy), phi in chains:
-                    u = np.array([math.cos(math.radians(phi)), math.sin(math.radians(phi)), 0.0])
-                    v = np.array([-u[1], u[0], 0.0])
-                    for s, zoff in ((+1, 0.0), (-1, half)):
-                        C = np.array([ix * a + cx, iy * b + cy, iz * c + zoff]) + s * 0.5 * lateral * u
-                        atoms.append(C); types.append(0)
-                        out = s * u
-                        for sv in (+1, -1):
-                            atoms.append(C + r_ch * (math.cos(th) * out + sv * math.sin(th) * v))
-                            types.append(1)
-    pos = np.array(atoms)
+    for (cx, cy), phi in chains:
+        u = np.array([math.cos(math.radians(phi)), math.sin(math.radians(phi)), 0.0])
+        v = np.array([-u[1], u[0], 0.0])
+        for s, zoff in ((+1, 0.0), (-1, half)):
+            C = np.array([cx, cy, zoff]) + s * 0.5 * lateral * u
+            motif.append(C); mtypes.append(0)
+            out = s * u
+            for sv in (+1, -1):
+                motif.append(C + r_ch * (math.cos(th) * out + sv * math.sin(th) * v))
+                mtypes.append(1)
+    motif = np.array(motif)
+    ix, iy, iz = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    corners = np.stack([ix.ravel() * a, iy.ravel() * b, iz.ravel() * c], axis=1)
+    atoms = (corners[:, None, :] + motif[None, :, :]).reshape(-1, 3)
+    types = np.tile(np.array(mtypes), len(corners))
+    pos = atoms
     box = np.array([nx * a, ny * b, nz * c])
     pos = np.mod(pos, box)
     rng = np.random.default_rng(seed)

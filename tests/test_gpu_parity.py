@@ -1,0 +1,262 @@
+"""GPU path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances (FP64 path): |dE| <= 1e-10 |E|, max|dF| <= 1e-8 max|F|,
+max|dW| <= 1e-8 max|W| -- the bar of the north star for a potential whose
+every term is evaluated in double precision (differences come only from the
+order of floating-point sums and from FP64 atomics).  Mixed path: FP32
+geometry/splines/bond order against FP64 gives about 1e-6 relative per term;
+the test allows |dE| <= 1e-5 |E| and max|dF| <= 1e-4 max|F|.
+"""
+import numpy as np
+import pytest
+
+from paper_1810_07026_gb300 import inputs
+from oracle.oracle import FLAG_REBO, FLAG_LJ, FLAG_TORSION, FLAG_ALL
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def A():
+    from paper_1810_07026_gb300 import build, airebo
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return airebo
+
+
+CASES = {
+    "diamond216": lambda: inputs.diamond(),
+    "pe1152": lambda: inputs.polyethylene(3, 4, 8, noise=0.05),
+    "hot160": lambda: inputs.amorphous(160, 1.0, 1.0, seed=11),
+    "hot300": lambda: inputs.amorphous(300, 0.5, 0.9, seed=5),
+    "hot1000": lambda: inputs.amorphous(1000, 1.5, 0.9, seed=7),
+}
+FLAGS = {"all": FLAG_ALL, "rebo": FLAG_REBO, "lj": FLAG_LJ, "torsion": FLAG_TORSION}
+
+
+def gpu_eval(A, params, pos, types, box, flags=FLAG_ALL, precision=0, virial=True, **kw):
+    ev = A.Airebo(params, precision=precision, rebo=bool(flags & 1), lj=bool(flags & 2),
+                  torsion=bool(flags & 4), **kw)
+    p = torch.tensor(pos, device="cuda")
+    ev.neighbor(p, torch.tensor(types, device="cuda"), box)
+    f, e4, w6 = ev.compute(p, virial=virial)
+    torch.cuda.synchronize()
+    out = (e4.cpu().numpy(), f.cpu().numpy(), w6.cpu().numpy() if virial else None)
+    return out, ev
+
+
+def assert_close(got, want, etol, ftol, wtol=None):
+    eg, fg, wg = got
+    ew, fw, ww = want
+    assert abs(eg[0] - ew[0]) <= etol * max(abs(ew[0]), 1e-12), (eg, ew)
+    for k in (1, 2, 3):
+        assert abs(eg[k] - ew[k]) <= etol * max(abs(ew[0]), 1e-12) + 1e-12, (k, eg, ew)
+    fs = max(np.abs(fw).max(), 1e-12)
+    assert np.abs(fg - fw).max() <= ftol * fs, np.abs(fg - fw).max() / fs
+    if wtol is not None and wg is not None:
+        assert np.abs(wg - ww).max() <= wtol * max(np.abs(ww).max(), 1e-12)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("term", list(FLAGS))
+def test_fp64_parity(A, oracle, param_text, case, term):
+    pos, types, box = CASES[case]()
+    flags = FLAGS[term]
+    e, f, w, _ = oracle.compute(pos, types, box, flags)
+    got, _ = gpu_eval(A, param_text, pos, types, box, flags)
+    assert_close(got, (e, f, w), 1e-10, 1e-8, 1e-8)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_mixed_parity(A, oracle, param_text, case):
+    pos, types, box = CASES[case]()
+    e, f, w, _ = oracle.compute(pos, types, box)
+    got, _ = gpu_eval(A, param_text, pos, types, box, precision=A.MIXED)
+    assert_close(got, (e, f, w), 1e-5, 1e-4, 1e-4)
+
+
+def test_counters_match_oracle(A, oracle, param_text):
+    pos, types, box = CASES["hot1000"]()
+    _, _, _, c = oracle.compute(pos, types, box)
+    _, ev = gpu_eval(A, param_text, pos, types, box)
+    g = ev.counters()
+    assert g["bonds"] == c["bonds"]
+    assert g["bstar"] == c["bstar"]
+    assert g["bstar_dsb"] == c["bstar_dsb_nonzero"]
+    assert g["lj_in_cutoff"] == c["lj_in_cutoff"]
+
+
+def as_set(cnt, j, img):
+    out = set()
+    for i in range(len(cnt)):
+        for e in range(cnt[i]):
+            out.add((i, int(j[i, e]), tuple(int(s) for s in img[i, e])))
+    return out
+
+
+@pytest.mark.parametrize("case", ["diamond216", "hot300", "pe1152"])
+def test_lists(A, oracle, params, param_text, case):
+    """Index work: the exact REBO list equals the oracle's set bit for bit; the
+    skin lists contain every pair within cut-off + skin, and nothing beyond it
+    by more than the FP32 margin."""
+    pos, types, box = CASES[case]()
+    _, ev = gpu_eval(A, param_text, pos, types, box)
+    off, jj, img = oracle.rebo_neighbors(pos, types, box)
+    want = {(i, int(jj[k]), tuple(int(s) for s in img[k])) for i in range(len(types)) for k in range(off[i], off[i + 1])}
+    assert as_set(*ev.export_lists(2)) == want
+    skin = 1.0
+    for which, cut in ((0, lambda a, b: 3.0 * params["lj.sigma"][a + b]), (1, lambda a, b: params["Dmax"][a + b])):
+        got = as_set(*ev.export_lists(which))
+        for (i, j, S) in got:
+            d = pos[:, j] + np.array(S) * box - pos[:, i]
+            assert np.sqrt(d @ d) < cut(types[i], types[j]) + skin + 3e-3
+            if which == 0:
+                assert j > i or (j == i and S > (0, 0, 0))
+        # every pair within cut + skin - margin is present
+        rc = np.array([[cut(a, b) for b in (0, 1)] for a in (0, 1)])
+        for i in range(0, len(types), 7):
+            for S in np.ndindex(5, 5, 5):
+                S = tuple(int(s) - 2 for s in S)
+                d = pos + (np.array(S) * box)[:, None] - pos[:, i:i + 1]
+                r = np.sqrt(np.einsum("ij,ij->j", d, d))
+                hit = np.nonzero(r < rc[types[i], types] + skin - 3e-3)[0]
+                for j in hit:
+                    j = int(j)
+                    if j == i and S == (0, 0, 0):
+                        continue
+                    if which == 1 or j > i or (j == i and S > (0, 0, 0)):
+                        assert (i, j, S) in got
+
+
+def test_pe32k_full_parity(A, oracle, param_text):
+    pos, types, box = inputs.workload("pe32k")
+    e, f, w, _ = oracle.compute(pos, types, box)
+    got, _ = gpu_eval(A, param_text, pos, types, box)
+    assert_close(got, (e, f, w), 1e-10, 1e-8, 1e-8)
+    got, _ = gpu_eval(A, param_text, pos, types, box, precision=A.MIXED)
+    assert_close(got, (e, f, w), 1e-5, 1e-4, 1e-4)
+
+
+def test_pe1m_sampled_parity(A, oracle, param_text):
+    """The bench's 1,044,480-atom polyethylene: sampled forces against the
+    oracle's one-atom-at-a-time evaluation, plus zero net force."""
+    pos, types, box = inputs.workload("pe1m")
+    for prec, tol in ((0, 1e-8), (A.MIXED, 1e-4)):
+        (e4, f, _), _ = gpu_eval(A, param_text, pos, types, box, precision=prec, virial=False)
+        rng = np.random.default_rng(3)
+        atoms = np.concatenate([[0, len(types) - 1], rng.choice(len(types), 4, replace=False)])
+        if prec == 0:
+            fo = oracle.forces_subset(pos, types, box, atoms)
+        scale = np.abs(f).max()
+        assert np.abs(f[:, atoms] - fo).max() <= tol * scale
+        assert np.abs(f.sum(axis=1)).max() <= 1e-9 * scale * len(types) ** 0.5
+        assert np.isfinite(e4).all() and -4.2 < e4[0] / len(types) < -3.7
+
+
+def test_empty_system(A, param_text):
+    ev = A.Airebo(param_text)
+    p = torch.zeros((3, 0), dtype=torch.float64, device="cuda")
+    ev.neighbor(p, torch.zeros(0, dtype=torch.int8, device="cuda"), [20.0, 20.0, 20.0])
+    f, e4, w6 = ev.compute(p, virial=True)
+    torch.cuda.synchronize()
+    assert f.shape == (3, 0) and e4.abs().max().item() == 0.0 and w6.abs().max().item() == 0.0
+
+
+def test_errors(A, param_text):
+    ev = A.Airebo(param_text)
+    pos, types, box = inputs.diamond()
+    p = torch.tensor(pos, device="cuda")
+    t = torch.tensor(types, device="cuda")
+    with pytest.raises(A.AireboError) as ex:
+        ev.compute(p)
+    assert ex.value.status == A.ERR_STATE
+    with pytest.raises(A.AireboError) as ex:
+        ev.neighbor(p, t, [7.5, 20.0, 20.0])
+    assert ex.value.status == A.ERR_ARG
+    bad = p.clone()
+    bad[1, 5] = float("nan")
+    with pytest.raises(A.AireboError) as ex:
+        ev.neighbor(bad, t, box)
+    assert ex.value.status == A.ERR_NONFINITE
+    ev.neighbor(p, t, box)
+    with pytest.raises(A.AireboError) as ex:
+        ev.compute(bad)
+    assert ex.value.status == A.ERR_NONFINITE
+    # more than 8 REBO neighbours: a tight cluster of 12 carbons
+    rng = np.random.default_rng(0)
+    cl = rng.uniform(-0.7, 0.7, (3, 12)) + 10.0
+    ev2 = A.Airebo(param_text)
+    pc = torch.tensor(cl, device="cuda")
+    ev2.neighbor(pc, torch.zeros(12, dtype=torch.int8, device="cuda"), [20.0, 20.0, 20.0])
+    with pytest.raises(A.AireboError) as ex:
+        ev2.compute(pc)
+    assert ex.value.status == A.ERR_CAPACITY
+    with pytest.raises(A.AireboError):
+        A.Airebo("not a parameter file")
+
+
+def test_capacity_regrow(A, oracle, param_text):
+    """A long-list capacity far too small is grown, and the result is exact."""
+    pos, types, box = CASES["hot300"]()
+    e, f, w, _ = oracle.compute(pos, types, box)
+    got, ev = gpu_eval(A, param_text, pos, types, box, max_lj_nbrs=8)
+    assert ev.counters()["lj_cap"] > 8
+    assert_close(got, (e, f, w), 1e-10, 1e-8, 1e-8)
+
+
+def test_host_api_matches_device(A, param_text):
+    pos, types, box = CASES["hot300"]()
+    (e4, f, w), _ = gpu_eval(A, param_text, pos, types, box)
+    ev = A.Airebo(param_text)
+    fh, eh, wh = ev.compute_host(pos, types, box, virial=True)
+    assert np.abs(fh - f).max() <= 1e-12 * np.abs(f).max()
+    assert abs(eh[0] - e4[0]) <= 1e-12 * abs(e4[0])
+
+
+def oracle_nve(oracle, pos, vel, types, box, dt, nsteps):
+    m = inputs.masses(types)
+    e, f, _, _ = oracle.compute(pos, types, box)
+    x, v = pos.copy(), vel.copy()
+    for _ in range(nsteps):
+        v += 0.5 * dt * f / m / inputs.MVV2E
+        x += dt * v
+        e, f, _, _ = oracle.compute(x, types, box)
+        v += 0.5 * dt * f / m / inputs.MVV2E
+    ke = 0.5 * inputs.MVV2E * (m * v * v).sum()
+    return x, v, e[0], ke
+
+
+@pytest.mark.parametrize("precision,xtol,etol", [(0, 1e-8, 1e-9), (1, 1e-3, 1e-4)])
+def test_nve_against_oracle_trajectory(A, oracle, param_text, precision, xtol, etol):
+    """Velocity Verlet on the GPU follows the oracle-driven trajectory, with
+    list rebuilds on the way (small skin)."""
+    pos, types, box = CASES["hot300"]()
+    vel = inputs.velocities(types, 2000.0, seed=4)
+    x_o, v_o, pe_o, ke_o = oracle_nve(oracle, pos, vel, types, box, 0.5, 20)
+    ev = A.Airebo(param_text, precision=precision, skin=0.15)
+    p = torch.tensor(pos, device="cuda")
+    v = torch.tensor(vel, device="cuda")
+    ev.neighbor(p, torch.tensor(types, device="cuda"), box)
+    f, _, _ = ev.compute(p)
+    e4 = ev.nve(p, v, f, 0.5, 20).cpu().numpy()
+    assert e4[3] > 1                      # the lists were rebuilt on the way
+    assert np.abs(p.cpu().numpy() - x_o).max() < xtol
+    assert abs(e4[0] - pe_o) <= etol * abs(pe_o)
+    assert abs(e4[1] - ke_o) <= etol * 10 * abs(ke_o)
+
+
+def test_nve_energy_conservation(A, param_text):
+    pos, types, box = inputs.diamond()
+    vel = inputs.velocities(types, 1000.0, seed=3)
+    ev = A.Airebo(param_text)
+    p = torch.tensor(pos, device="cuda")
+    v = torch.tensor(vel, device="cuda")
+    ev.neighbor(p, torch.tensor(types, device="cuda"), box)
+    f, _, _ = ev.compute(p)
+    tot = []
+    for _ in range(20):
+        tot.append(ev.nve(p, v, f, 0.5, 5)[2].item())
+    tot = np.array(tot)
+    assert (tot.max() - tot.min()) < 3e-4 * abs(tot[0])
