@@ -280,6 +280,7 @@ WORKLOADS = {
     "diamond216": dict(kind="diamond", ncell=3, noise=0.05, seed=1),
     "pe32k": dict(kind="pe", cells=(17, 20, 8), noise=0.03, seed=1),
     "pe1m": dict(kind="pe", cells=(34, 40, 64), noise=0.05, seed=1),
+    "pe261k": dict(kind="pe", cells=(34, 40, 16), noise=0.05, seed=1),
 }
 
 
