@@ -174,6 +174,25 @@ airebo_status airebo_kernel_times(airebo_handle h, double* ms, int64_t* launches
  */
 airebo_status airebo_alu_peak(int precision, double* tflops);
 
+/*
+ * Rebuild check that allocates no device memory (the paper has no
+ * counterpart: it is a service for callers that cannot call cudaMalloc, such
+ * as code running inside a framework that owns all device memory, or code
+ * that must not allocate after its set-up).  Same test as
+ * airebo_needs_rebuild -- *h_flag = 1 if max_i |x_i - x_ref,i| > skin/2 --
+ * but it needs no handle: d_pos and d_ref are device double[3][n] given by
+ * the caller, stream is a cudaStream_t (NULL = default stream); *h_max_disp
+ * (nullable) receives max |x - x_ref| in Angstrom.  Synchronises the stream.
+ * Its scratch is a fixed 64 KB array inside the library image, held by every
+ * GPU that loads the library until exit, so n is limited to 2,097,152 atoms
+ * (larger n returns AIREBO_ERR_ARG).  The first call on a device looks up the
+ * array's device address (set-up); make that first call before any stream
+ * capture.  All calls share the array: calls whose kernels overlap on the GPU
+ * race and must be serialised by the caller.
+ */
+airebo_status airebo_needs_rebuild_noalloc(const double* d_pos, const double* d_ref, int64_t n, double skin,
+                                           void* stream, int* h_flag, double* h_max_disp);
+
 #ifdef __cplusplus
 }
 #endif

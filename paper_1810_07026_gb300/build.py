@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libairebo.so")
-SOURCES = ("api.cu", "neighbor.cu", "kernels_f64.cu", "kernels_f32.cu", "peak.cu")
+SOURCES = ("api.cu", "neighbor.cu", "kernels_f64.cu", "kernels_f32.cu", "peak.cu", "noalloc.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
