@@ -201,12 +201,15 @@ bool fill_params(const Scalars& s, DevParams<R>& P, std::vector<R>& tables, std:
         P.nB[p] = nb;
         double sg = s.sigma[p];
         P.sigma[p] = (R)sg;
+        P.sig2[p] = (R)(sg * sg);
         P.eps4[p] = (R)(4.0 * s.eps[p]);
         P.rc2[p] = (R)(s.ljcut * sg * s.ljcut * sg);
         P.swlo[p] = (R)(s.ljsw * sg);
+        P.swlo2[p] = (R)(s.ljsw * sg * s.ljsw * sg);
         P.swinv[p] = (R)(1.0 / ((s.ljcut - s.ljsw) * sg));
         P.Srlo[p] = (R)(s.Sr[0] * sg);
         P.Srhi[p] = (R)(s.Sr[1] * sg);
+        P.Srhi2[p] = (R)(s.Sr[1] * sg * s.Sr[1] * sg);
         P.Srinv[p] = (R)(1.0 / ((s.Sr[1] - s.Sr[0]) * sg));
         P.bmin[p] = (R)s.bmin[p];
         P.binv[p] = (R)(1.0 / (s.bmax[p] - s.bmin[p]));
@@ -270,9 +273,10 @@ struct airebo_ctx {
     int2* im = nullptr; int* im_cnt = nullptr; int im_cap = 32; size_t im_alloc = 0;
     double* xref = nullptr;
     // step scratch
-    int2* bonds = nullptr; int bond_cap = 0;
+    int2* bonds = nullptr; int2* ccbonds = nullptr; int bond_cap = 0;
     int4* bq = nullptr; int bq_cap = 0;
-    int* counts = nullptr;               // [0] bonds [1] queue
+    int* bq2 = nullptr; double* bq2_eps = nullptr;
+    int* counts = nullptr;               // [0] non-C-C bonds [2] C-C bonds [3] b* reverse queue [4..6] b* queue per species pair [7] LJ work counter
     double* acc = nullptr;               // 9 doubles
     unsigned long long* counters = nullptr;   // 8
     int* derr = nullptr;                 // 8 ints
@@ -335,7 +339,7 @@ template <class R> airebo_status alloc_step(airebo_handle h, Precision<R>& pr, i
     size_t m = (size_t)n * MAXN;
     CK(realloc_dev(b.cnt, n)); CK(realloc_dev(b.nj, m)); CK(realloc_dev(b.nimg, m));
     CK(realloc_dev(b.dx, m)); CK(realloc_dev(b.dy, m)); CK(realloc_dev(b.dz, m));
-    CK(realloc_dev(b.r, m)); CK(realloc_dev(b.w, m)); CK(realloc_dev(b.dw, m));
+    CK(realloc_dev(b.r, m)); CK(realloc_dev(b.ir, m)); CK(realloc_dev(b.w, m)); CK(realloc_dev(b.dw, m)); CK(realloc_dev(b.omw, m));
     CK(realloc_dev(b.nC, n)); CK(realloc_dev(b.nH, n));
     if (b.map_cap == 0) b.map_cap = 32;
     size_t mm = (size_t)n * b.map_cap;
@@ -353,7 +357,7 @@ template <class R> airebo_status grow_map(airebo_handle h, Precision<R>& pr, int
 
 template <class R> void free_prec(Precision<R>& pr) {
     StepBuffers<R>& b = pr.b;
-    void* ps[] = {b.P, b.tables, b.Tnz, b.cnt, b.nj, b.nimg, b.dx, b.dy, b.dz, b.r, b.w, b.dw, b.nC, b.nH,
+    void* ps[] = {b.P, b.tables, b.Tnz, b.cnt, b.nj, b.nimg, b.dx, b.dy, b.dz, b.r, b.ir, b.w, b.dw, b.omw, b.nC, b.nH,
                   b.map_cnt, b.map_key, b.map_wt, b.map_path};
     for (void* p : ps) if (p) cudaFree(p);
     b = StepBuffers<R>();
@@ -373,8 +377,11 @@ airebo_status alloc_atoms(airebo_handle h, int n) {
     CK(realloc_dev(h->xref, 3 * (size_t)na));
     h->bond_cap = na * MAXN / 2 + 64;
     CK(realloc_dev(h->bonds, h->bond_cap));
-    h->bq_cap = std::max(h->bq_cap, na * 8 + 1024);
-    CK(realloc_dev(h->bq, h->bq_cap));
+    CK(realloc_dev(h->ccbonds, h->bond_cap));
+    h->bq_cap = std::max(h->bq_cap, na * 4 + 1024);
+    CK(realloc_dev(h->bq, 3 * (size_t)h->bq_cap));
+    CK(realloc_dev(h->bq2, 3 * (size_t)h->bq_cap));
+    CK(realloc_dev(h->bq2_eps, 3 * (size_t)h->bq_cap));
     h->n_alloc = na;
     airebo_status st = h->opt.precision == AIREBO_MIXED ? alloc_step<float>(h, h->p32, na) : alloc_step<double>(h, h->p64, na);
     if (st) return st;
@@ -473,16 +480,19 @@ template <class R> StepArgs<R> make_args(airebo_handle h, Precision<R>& pr, cons
     a.n = h->n;
     a.P = b.P;
     a.G.n = h->n; a.G.type = h->types; a.G.cnt = b.cnt; a.G.nj = b.nj; a.G.nimg = b.nimg;
-    a.G.dx = b.dx; a.G.dy = b.dy; a.G.dz = b.dz; a.G.r = b.r; a.G.w = b.w; a.G.dw = b.dw; a.G.nC = b.nC; a.G.nH = b.nH;
+    a.G.dx = b.dx; a.G.dy = b.dy; a.G.dz = b.dz; a.G.r = b.r; a.G.ir = b.ir; a.G.w = b.w; a.G.dw = b.dw; a.G.omw = b.omw; a.G.nC = b.nC; a.G.nH = b.nH;
     a.g_cnt = b.cnt; a.g_nj = b.nj; a.g_nimg = b.nimg; a.g_dx = b.dx; a.g_dy = b.dy; a.g_dz = b.dz;
-    a.g_r = b.r; a.g_w = b.w; a.g_dw = b.dw; a.g_nC = b.nC; a.g_nH = b.nH;
+    a.g_r = b.r; a.g_ir = b.ir; a.g_w = b.w; a.g_dw = b.dw; a.g_omw = b.omw; a.g_nC = b.nC; a.g_nH = b.nH;
     a.M.cap = b.map_cap; a.M.cnt = b.map_cnt; a.M.key = b.map_key; a.M.wt = b.map_wt; a.M.path = b.map_path;
     a.pos = d_pos;
     for (int d = 0; d < 3; d++) a.L[d] = h->L[d];
     a.lj = h->lj; a.lj_cnt = h->lj_cnt; a.lj_cap = h->lj_cap;
     a.im = h->im; a.im_cnt = h->im_cnt; a.im_cap = h->im_cap;
     a.bonds = h->bonds; a.nbonds = h->counts; a.bond_cap = h->bond_cap;
-    a.bq = h->bq; a.nbq = h->counts + 1; a.bq_cap = h->bq_cap;
+    a.ccbonds = h->ccbonds; a.nccbonds = h->counts + 2;
+    a.bq = h->bq; a.nbq = h->counts + 4; a.bq_cap = h->bq_cap;
+    a.bq2 = h->bq2; a.bq2_eps = h->bq2_eps; a.nbq2 = h->counts + 3;
+    a.lj_next = h->counts + 7;
     a.f = d_force; a.acc = h->acc; a.counters = h->counters; a.err = h->derr;
     a.virial = virial;
     a.rebo = h->opt.enable_rebo != 0;
@@ -499,14 +509,14 @@ airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos,
         if (h->n) CK(cudaMemsetAsync(d_force, 0, sizeof(double) * 3 * h->n, s));
         CK(cudaMemsetAsync(h->acc, 0, sizeof(double) * 9, s));
         CK(cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * 8, s));
-        CK(cudaMemsetAsync(h->counts, 0, sizeof(int) * 2, s));
+        CK(cudaMemsetAsync(h->counts, 0, sizeof(int) * 8, s));
         CK(cudaMemsetAsync(h->derr, 0, sizeof(int) * 8, s));
         StepArgs<R> a = make_args<R>(h, pr, d_pos, d_force, d_w6 != nullptr);
         launch_compute<R>(a, s, h->num_sms, h->timing ? h->ev : nullptr);
         CK(cudaGetLastError());
         if (d_e4 || d_w6) k_finalize<<<1, 32, 0, s>>>(h->acc, d_e4, d_w6);
         CK(cudaMemcpyAsync(h->h_err, h->derr, sizeof(int) * 8, cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(h->h_u64, h->counts, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(h->h_u64, h->counts, sizeof(int) * 8, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (h->timing && h->n) {
             bool ran[6] = {true, a.rebo, a.torsion, a.lj_on, a.lj_on, a.lj_on};
@@ -525,10 +535,13 @@ airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos,
             if (st) return st;
             again = true;
         }
-        int nq = ((int*)h->h_u64)[1];
+        const int* cn = (const int*)h->h_u64;
+        int nq = std::max(cn[4], std::max(cn[5], cn[6]));
         if (nq > h->bq_cap) {
             h->bq_cap = nq + nq / 4 + 1024;
-            CK(realloc_dev(h->bq, h->bq_cap));
+            CK(realloc_dev(h->bq, 3 * (size_t)h->bq_cap));
+            CK(realloc_dev(h->bq2, 3 * (size_t)h->bq_cap));
+            CK(realloc_dev(h->bq2_eps, 3 * (size_t)h->bq_cap));
             again = true;
         }
         if (!again) return AIREBO_OK;
@@ -607,7 +620,7 @@ airebo_status airebo_create(const char* params, const airebo_options* opts, void
     if (ce != cudaSuccess) { delete h; return AIREBO_ERR_CUDA; }
     st = h->opt.precision == AIREBO_MIXED ? upload_params<float>(h, h->p32) : upload_params<double>(h, h->p64);
     if (!st) {
-        if (realloc_dev(h->counts, 2) || realloc_dev(h->acc, 9) || realloc_dev(h->counters, 8) ||
+        if (realloc_dev(h->counts, 8) || realloc_dev(h->acc, 9) || realloc_dev(h->counters, 8) ||
             realloc_dev(h->derr, 8) || realloc_dev(h->maxd2, 1) || realloc_dev(h->ke, 1) ||
             cudaMallocHost((void**)&h->h_err, sizeof(int) * 8) || cudaMallocHost((void**)&h->h_u64, sizeof(unsigned long long) * 8) ||
             cudaMallocHost((void**)&h->h_acc, sizeof(double) * 16))
@@ -625,7 +638,7 @@ void airebo_destroy(airebo_handle h) {
     free_prec(h->p64);
     free_prec(h->p32);
     void* ps[] = {h->types, h->cell_of, h->cell_count, h->cell_start, h->cell_fill, h->spos, h->swrap, h->lj, h->lj_cnt,
-                  h->im, h->im_cnt, h->xref, h->bonds, h->bq, h->counts, h->acc, h->counters, h->derr, h->maxd2, h->ke,
+                  h->im, h->im_cnt, h->xref, h->bonds, h->ccbonds, h->bq, h->bq2, h->bq2_eps, h->counts, h->acc, h->counters, h->derr, h->maxd2, h->ke,
                   h->hpos, h->hvel, h->hforce, h->he4, h->hw6};
     for (void* p : ps) if (p) cudaFree(p);
     for (int k = 0; k < 11; k++) if (h->ev[k]) cudaEventDestroy(h->ev[k]);

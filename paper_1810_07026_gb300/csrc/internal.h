@@ -14,7 +14,7 @@ template <class R> struct StepBuffers {
     unsigned char* Tnz = nullptr;
     // short list
     int* cnt = nullptr; int* nj = nullptr; int* nimg = nullptr;
-    R* dx = nullptr; R* dy = nullptr; R* dz = nullptr; R* r = nullptr; R* w = nullptr; R* dw = nullptr;
+    R* dx = nullptr; R* dy = nullptr; R* dz = nullptr; R* r = nullptr; R* ir = nullptr; R* w = nullptr; R* dw = nullptr; R* omw = nullptr;
     R* nC = nullptr; R* nH = nullptr;
     // connectivity map
     int map_cap = 0;
@@ -27,14 +27,17 @@ template <class R> struct StepArgs {
     const DevParams<R>* P;
     Graph<R> G;
     int* g_cnt; int* g_nj; int* g_nimg;
-    R* g_dx; R* g_dy; R* g_dz; R* g_r; R* g_w; R* g_dw; R* g_nC; R* g_nH;
+    R* g_dx; R* g_dy; R* g_dz; R* g_r; R* g_ir; R* g_w; R* g_dw; R* g_omw; R* g_nC; R* g_nH;
     PathMap<R> M;
     const double* pos;
     double L[3];
     const int2* lj; const int* lj_cnt; int lj_cap;
     const int2* im; const int* im_cnt; int im_cap;
-    int2* bonds; int* nbonds; int bond_cap;
+    int2* bonds; int* nbonds; int bond_cap;   // bonds i<j that are not C-C
+    int2* ccbonds; int* nccbonds;             // C-C bonds i<j, same capacity
     int4* bq; int* nbq; int bq_cap;
+    int* bq2; double* bq2_eps; int* nbq2;  // b* pairs whose S_b is in its transition, and dE/db*
+    int* lj_next;                          // work counter of the LJ kernel's warps
     double* f;
     double* acc;          // E_rebo, E_lj, E_tors, W[6]
     unsigned long long* counters;   // [8]
@@ -47,7 +50,7 @@ enum { ERR_SHORT = 0, ERR_MAP = 1, ERR_QUEUE = 2, ERR_NONFINITE = 3 };
 enum { CNT_BONDS = 0, CNT_BSTAR = 1, CNT_DSB = 2, CNT_LJ = 3, CNT_MAP = 4, CNT_BO = 7 };
 
 // launchers, one instantiation per precision (kernels_f64.cu, kernels_f32.cu)
-// ev (nullable): 7 events recorded before each of the 6 kernels and after the last
+// ev (nullable): 7 events recorded before each of the 6 stages and after the last
 template <class R> void launch_compute(const StepArgs<R>& a, cudaStream_t s, int num_sms, cudaEvent_t* ev);
 
 // neighbour build (neighbor.cu)

@@ -75,17 +75,26 @@ __global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
         int p = pidx(ti, tj);
         double dmax = (double)P.Dmax[p];
         if (!(r2 < dmax * dmax)) continue;
-        double r = sqrt(r2);
-        R dw;
-        R w = wfun<R>(P, p, (R)r, dw);
+        double ir = rsqrt(r2);
+        double r = r2 * ir;
+        R dw, omw;
+        R w = wfun_c<R>(P, p, (R)r, dw, omw);
         if (cnt < MAXN) {
             int q = i * MAXN + cnt;
             a.g_nj[q] = j; a.g_nimg[q] = img;
             a.g_dx[q] = (R)dx; a.g_dy[q] = (R)dy; a.g_dz[q] = (R)dz;
-            a.g_r[q] = (R)r; a.g_w[q] = w; a.g_dw[q] = dw;
-            if (j > i) {
-                int b = atomicAdd(a.nbonds, 1);
-                if (b < a.bond_cap) a.bonds[b] = make_int2(i, cnt);
+            a.g_r[q] = (R)r; a.g_ir[q] = (R)ir; a.g_w[q] = w; a.g_dw[q] = dw; a.g_omw[q] = omw;
+            // each bond once: i < j between like species, from the carbon for C-H,
+            // so that the threads of a warp run the same code (species batches, Sec. 4.2)
+            bool mine = (ti == tj) ? (j > i) : (ti == 0);
+            if (mine) {
+                if (ti == 0 && tj == 0) {
+                    int c = atomicAdd(a.nccbonds, 1);
+                    if (c < a.bond_cap) a.ccbonds[c] = make_int2(i, cnt);
+                } else {
+                    int b = atomicAdd(a.nbonds, 1);
+                    if (b < a.bond_cap) a.bonds[b] = make_int2(i, cnt);
+                }
             }
         }
         cnt++;
@@ -103,10 +112,10 @@ __global__ void __launch_bounds__(128) k_rebo(StepArgs<R> a) {
     const DevParams<R>& P = *a.P;
     Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}};
     double E = 0;
-    int nb = *a.nbonds;
-    if (nb > a.bond_cap) nb = a.bond_cap;
+    int ncc = min(*a.nccbonds, a.bond_cap);
+    int nb = ncc + min(*a.nbonds, a.bond_cap);
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
-        int2 bd = a.bonds[b];
+        int2 bd = b < ncc ? a.ccbonds[b] : a.bonds[b - ncc];
         E += rebo_bond<R>(P, a.G, bd.x, bd.y, sink);
     }
     block_accumulate<128>(E, sink.W, a.virial, a.acc + 0, a.acc + 3);
@@ -118,12 +127,10 @@ __global__ void __launch_bounds__(128) k_torsion(StepArgs<R> a) {
     const DevParams<R>& P = *a.P;
     Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}};
     double E = 0;
-    int nb = *a.nbonds;
+    int nb = *a.nccbonds;
     if (nb > a.bond_cap) nb = a.bond_cap;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
-        int2 bd = a.bonds[b];
-        int j = a.G.nj[bd.x * MAXN + bd.y];
-        if (a.G.type[bd.x] != 0 || a.G.type[j] != 0) continue;
+        int2 bd = a.ccbonds[b];
         E += torsion_bond<R>(P, a.G, bd.x, bd.y, sink);
     }
     block_accumulate<128>(E, sink.W, a.virial, a.acc + 2, a.acc + 3);
@@ -139,69 +146,121 @@ __global__ void __launch_bounds__(128) k_path_map(StepArgs<R> a) {
     if (ov) atomicMax(a.err + ERR_MAP, M.cnt[i] + ov);
 }
 
+// ------------------------------------------------------------------ LJ
+// Persistent warps stride over atoms i.  For each chunk of 32 entries of i's
+// half list, every lane forms the FP64 displacement and tests its pair (cut-off,
+// C_ij lookup, S_r); the pairs that need the full pair term are compacted with
+// a ballot into a per-warp buffer in shared memory (the "compress" of Sec. 4.3),
+// and the FP64 pair arithmetic runs only on full batches of 32 compacted pairs,
+// so no lane idles through it.  Pairs with S_r != 0 go to the b* queue.
+constexpr int LJ_THREADS = 256;
+constexpr int LJ_WARPS = LJ_THREADS / 32;
+constexpr int LJ_CHUNK = 8;
+
+// two compaction buffers per warp: 0 = inner pairs, 1 = pairs in the cut-off switch
+struct LjBuf {
+    double dx[2][64], dy[2][64], dz[2][64];
+    int jp[2][64];          // j | species pair << 30
+};
+
 template <class R>
-__device__ __forceinline__ int map_find(const PathMap<R>& M, int i, long long key) {
-    int c = M.cnt[i];
-    const long long* k = M.key + (size_t)i * M.cap;
-    for (int e = 0; e < c; e++)
-        if (k[e] == key) return e;
-    return -1;
+__device__ __forceinline__ void lj_batch(const DevParams<R>& P, LjBuf& B, int b, int lane, Sink& sink,
+                                         double& fix, double& fiy, double& fiz, double& E) {
+    int jp = B.jp[b][lane];
+    int j = jp & 0x3fffffff, p = (unsigned)jp >> 30;
+    if (b == 0) lj_eval_inner<R>(P, p, j, B.dx[b][lane], B.dy[b][lane], B.dz[b][lane], sink, fix, fiy, fiz, E);
+    else lj_eval_switch<R>(P, p, j, B.dx[b][lane], B.dy[b][lane], B.dz[b][lane], sink, fix, fiy, fiz, E);
 }
 
-// ------------------------------------------------------------------ LJ
 template <class R>
-__global__ void __launch_bounds__(256) k_lj(StepArgs<R> a) {
+__global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
     const DevParams<R>& P = *a.P;
+    __shared__ double shift[3][9];                // image shifts S L for S in [-4, 4]
+    __shared__ LjBuf bufs[LJ_WARPS];
+    if (threadIdx.x < 27) shift[threadIdx.x / 9][threadIdx.x % 9] = (double)((int)(threadIdx.x % 9) - 4) * a.L[threadIdx.x / 9];
+    __syncthreads();
     int lane = threadIdx.x & 31;
-    int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    LjBuf& B = bufs[threadIdx.x >> 5];
+    unsigned lt = (1u << lane) - 1u;
     Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}};
     double E = 0;
     unsigned evaluated = 0;
-    if (i < a.n) {
-        int n = a.n;
+    int n = a.n;
+    // warps take chunks of LJ_CHUNK consecutive atoms from a global counter,
+    // which balances C and H atoms (different list lengths) across warps
+    int chunk_end = 0;
+    for (int i = 0;; i++) {
+        if (i >= chunk_end) {
+            int c = 0;
+            if (lane == 0) c = atomicAdd(a.lj_next, LJ_CHUNK);
+            c = __shfl_sync(0xffffffffu, c, 0);
+            if (c >= n) break;
+            chunk_end = min(c + LJ_CHUNK, n);
+            i = c;
+        }
         double xi = a.pos[i], yi = a.pos[n + i], zi = a.pos[2 * n + i];
         int ti = a.G.type[i];
         double fix = 0, fiy = 0, fiz = 0;
         int ne = a.lj_cnt[i];
         const int2* row = a.lj + (size_t)i * a.lj_cap;
-        for (int e = lane; e < ne; e += 32) {
-            int2 ent = row[e];
-            int j = ent.x, img = ent.y;
-            // displacement in FP64 (minimum-image arithmetic stays double)
-            double dx = a.pos[j] + img_x(img) * a.L[0] - xi;
-            double dy = a.pos[n + j] + img_y(img) * a.L[1] - yi;
-            double dz = a.pos[2 * n + j] + img_z(img) * a.L[2] - zi;
-            R rx = (R)dx, ry = (R)dy, rz = (R)dz;
-            R r2 = rx * rx + ry * ry + rz * rz;
-            int p = pidx(ti, a.G.type[j]);
-            if (!(r2 < P.rc2[p])) continue;
-            evaluated++;
-            R C = R(1);
-            int mi = -1, code = -1;
-            if (r2 < P.rpath2) {
-                mi = map_find<R>(a.M, i, map_key(j, img));
-                if (mi >= 0) {
-                    R wm = a.M.wt[(size_t)i * a.M.cap + mi];
-                    if (wm >= R(1)) continue;
-                    C = R(1) - wm;
-                    code = a.M.path[(size_t)i * a.M.cap + mi];
+        int cnt[2] = {0, 0};
+        for (int base = 0; base < ne; base += 32) {
+            int e = base + lane;
+            int st = 0, j = 0, p = 0;
+            double dx = 0, dy = 0, dz = 0;
+            if (e < ne) {
+                int2 ent = row[e];
+                j = ent.x;
+                int img = ent.y;
+                // displacement in FP64 (minimum-image arithmetic stays double)
+                dx = a.pos[j] - xi; dy = a.pos[n + j] - yi; dz = a.pos[2 * n + j] - zi;
+                if (img != 0) {
+                    int sx = img_x(img), sy = img_y(img), sz = img_z(img);
+                    if (sx < -4 || sx > 4 || sy < -4 || sy > 4 || sz < -4 || sz > 4) {
+                        dx += sx * a.L[0]; dy += sy * a.L[1]; dz += sz * a.L[2];
+                    } else {
+                        dx += shift[0][sx + 4]; dy += shift[1][sy + 4]; dz += shift[2][sz + 4];
+                    }
+                }
+                R rx = (R)dx, ry = (R)dy, rz = (R)dz;
+                R r2 = rx * rx + ry * ry + rz * rz;
+                p = pidx(ti, a.G.type[j]);
+                evaluated += lt_nonneg(r2, P.rc2[p]);
+                R C;
+                int code, mi;
+                st = lj_classify<R>(P, a.M, i, p, j, img, r2, C, code, mi);
+                if (st == 2) {
+                    int q = atomicAdd(a.nbq + p, 1);
+                    if (q < a.bq_cap) a.bq[(size_t)p * a.bq_cap + q] = make_int4(i, e, mi, 0);
+                } else if (st == 4) {     // rare: 0 < C < 1 along a path
+                    lj_eval<R>(P, a.G, i, p, j, dx, dy, dz, C, code, sink, fix, fiy, fiz, E);
                 }
             }
-            R rr = sqrt_(r2);
-            if (rr < P.Srhi[p]) {
-                int q = atomicAdd(a.nbq, 1);
-                if (q < a.bq_cap) a.bq[q] = make_int4(i, e, mi, 0);
-                continue;
+            for (int b = 0; b < 2; b++) {
+                int want = b == 0 ? 1 : 3;
+                unsigned m = __ballot_sync(0xffffffffu, st == want);
+                if (st == want) {
+                    int s = cnt[b] + __popc(m & lt);
+                    B.dx[b][s] = dx; B.dy[b][s] = dy; B.dz[b][s] = dz; B.jp[b][s] = j | (p << 30);
+                }
+                cnt[b] += __popc(m);
+                __syncwarp();
+                if (cnt[b] >= 32) {
+                    lj_batch<R>(P, B, b, lane, sink, fix, fiy, fiz, E);
+                    __syncwarp();
+                    if (lane < cnt[b] - 32) {
+                        int s = 32 + lane;
+                        B.dx[b][lane] = B.dx[b][s]; B.dy[b][lane] = B.dy[b][s]; B.dz[b][lane] = B.dz[b][s];
+                        B.jp[b][lane] = B.jp[b][s];
+                    }
+                    cnt[b] -= 32;
+                    __syncwarp();
+                }
             }
-            R inv_r = R(1) / rr;
-            R dV;
-            R V = vlj<R>(P, p, rr, inv_r * inv_r, dV);
-            E += (double)(C * V);
-            double c = (double)(C * dV * inv_r);
-            double gx = c * dx, gy = c * dy, gz = c * dz;
-            sink.half(j, dx, dy, dz, gx, gy, gz, fix, fiy, fiz);
-            if (code >= 0) path_forces<R>(a.G, i, code, -V, sink, fix, fiy, fiz);
         }
+        for (int b = 0; b < 2; b++)
+            if (lane < cnt[b]) lj_batch<R>(P, B, b, lane, sink, fix, fiy, fiz, E);
+        __syncwarp();
         fix = warp_sum(fix); fiy = warp_sum(fiy); fiz = warp_sum(fiz);
         if (lane == 0) {
             atomicAdd(a.f + i, fix); atomicAdd(a.f + n + i, fiy); atomicAdd(a.f + 2 * n + i, fiz);
@@ -209,44 +268,72 @@ __global__ void __launch_bounds__(256) k_lj(StepArgs<R> a) {
     }
     unsigned ev = __reduce_add_sync(0xffffffffu, evaluated);
     if (lane == 0 && ev) atomicAdd(a.counters + CNT_LJ, (unsigned long long)ev);
-    block_accumulate<256>(E, sink.W, a.virial, a.acc + 1, a.acc + 3);
+    block_accumulate<LJ_THREADS>(E, sink.W, a.virial, a.acc + 1, a.acc + 3);
 }
 
 // ------------------------------------------------------------------ b* pairs
+// Phase 1: every queued pair.  Pairs whose S_b is in its transition go to a
+// second queue, so that the reverse bond order runs compactly in phase 2.
 template <class R>
 __global__ void __launch_bounds__(128) k_bstar(StepArgs<R> a) {
     const DevParams<R>& P = *a.P;
     Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}};
     double E = 0;
-    unsigned dsb = 0;
-    int nq = *a.nbq;
-    if (nq > a.bq_cap) nq = a.bq_cap;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nq; t += gridDim.x * blockDim.x) {
+    int n0 = min(a.nbq[0], a.bq_cap), n1 = min(a.nbq[1], a.bq_cap), n2 = min(a.nbq[2], a.bq_cap);
+    int nq = n0 + n1 + n2;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nq; u += gridDim.x * blockDim.x) {
+        // the queue is kept per species pair (CC, CH, HH), so that warps are uniform
+        int t = u < n0 ? u : (u < n0 + n1 ? a.bq_cap + (u - n0) : 2 * a.bq_cap + (u - n0 - n1));
         int4 q = a.bq[t];
         int i = q.x;
         int2 ent = a.lj[(size_t)i * a.lj_cap + q.y];
         int j = ent.x;
         double dx, dy, dz;
         load_disp(a.pos, a.n, a.L, i, j, ent.y, dx, dy, dz);
-        double r = sqrt(dx * dx + dy * dy + dz * dz);
+        R rx = (R)dx, ry = (R)dy, rz = (R)dz;
+        R r2 = rx * rx + ry * ry + rz * rz;
         R C = R(1);
         int code = -1;
         if (q.z >= 0) {
-            C = R(1) - a.M.wt[(size_t)i * a.M.cap + q.z];
+            C = a.M.wt[(size_t)i * a.M.cap + q.z];
             code = a.M.path[(size_t)i * a.M.cap + q.z];
         }
-        E += bstar_pair<R>(P, a.G, i, j, (R)dx, (R)dy, (R)dz, (R)r, C, code, sink, &dsb);
+        R eps;
+        E += bstar_pair<R>(P, a.G, i, j, rx, ry, rz, r2, C, code, sink, eps);
+        if (eps != R(0)) {
+            int s = atomicAdd(a.nbq2, 1);
+            if (s < 3 * a.bq_cap) { a.bq2[s] = t; a.bq2_eps[s] = (double)eps; }
+        }
     }
-    unsigned s = __reduce_add_sync(0xffffffffu, dsb);
-    if ((threadIdx.x & 31) == 0 && s) atomicAdd(a.counters + CNT_DSB, (unsigned long long)s);
     block_accumulate<128>(E, sink.W, a.virial, a.acc + 1, a.acc + 3);
+}
+
+// Phase 2: the force through b* for the pairs of the second queue.
+template <class R>
+__global__ void __launch_bounds__(128) k_bstar_rev(StepArgs<R> a) {
+    const DevParams<R>& P = *a.P;
+    Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}};
+    int nq = min(*a.nbq2, 3 * a.bq_cap);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nq; s += gridDim.x * blockDim.x) {
+        int4 q = a.bq[a.bq2[s]];
+        int i = q.x;
+        int2 ent = a.lj[(size_t)i * a.lj_cap + q.y];
+        int j = ent.x;
+        double dx, dy, dz;
+        load_disp(a.pos, a.n, a.L, i, j, ent.y, dx, dy, dz);
+        R rx = (R)dx, ry = (R)dy, rz = (R)dz;
+        R r2 = rx * rx + ry * ry + rz * rz;
+        bstar_reverse<R>(P, a.G, i, j, rx, ry, rz, r2, (R)a.bq2_eps[s], sink);
+    }
+    block_accumulate<128>(0.0, sink.W, a.virial, a.acc + 1, a.acc + 3);
 }
 
 template <class R>
 __global__ void k_finish_counters(StepArgs<R> a) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
-        a.counters[CNT_BONDS] = (unsigned long long)*a.nbonds;
-        a.counters[CNT_BSTAR] = (unsigned long long)*a.nbq;
+        a.counters[CNT_BONDS] = (unsigned long long)(*a.nbonds + *a.nccbonds);
+        a.counters[CNT_BSTAR] = (unsigned long long)(a.nbq[0] + a.nbq[1] + a.nbq[2]);
+        a.counters[CNT_DSB] = (unsigned long long)*a.nbq2;
     }
 }
 
@@ -265,9 +352,18 @@ void launch_compute_impl(const StepArgs<R>& a, cudaStream_t s, int num_sms, cuda
     mark(3);
     if (a.lj_on) k_path_map<R><<<(n + 127) / 128, 128, 0, s>>>(a);
     mark(4);
-    if (a.lj_on) k_lj<R><<<(n + 7) / 8, 256, 0, s>>>(a);
+    if (a.lj_on) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lj<R>, LJ_THREADS, 0);
+        int blocks = num_sms * (per_sm > 0 ? per_sm : 1);
+        int need = (n + LJ_WARPS - 1) / LJ_WARPS;
+        k_lj<R><<<blocks < need ? blocks : need, LJ_THREADS, 0, s>>>(a);
+    }
     mark(5);
-    if (a.lj_on) k_bstar<R><<<grid_bonds, 128, 0, s>>>(a);
+    if (a.lj_on) {
+        k_bstar<R><<<grid_bonds, 128, 0, s>>>(a);
+        k_bstar_rev<R><<<grid_bonds, 128, 0, s>>>(a);
+    }
     mark(6);
     k_finish_counters<R><<<1, 32, 0, s>>>(a);
 }

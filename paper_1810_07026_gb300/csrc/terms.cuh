@@ -64,6 +64,14 @@ HD float rsqrt_(float x) {
     return 1.0f / std::sqrt(x);
 #endif
 }
+HD double rcp_(double x) {
+#ifdef __CUDA_ARCH__
+    return __drcp_rn(x);
+#else
+    return 1.0 / x;
+#endif
+}
+HD float rcp_(float x) { return 1.0f / x; }
 HD double sqrt_(double x) { return sqrt(x); }
 HD float sqrt_(float x) { return sqrtf(x); }
 HD double exp_(double x) { return exp(x); }
@@ -101,7 +109,7 @@ template <class R> struct DevParams {
     R gN0, gNinv, Fx0, Fxinv;
     Quintic<R> gC1, gC2, gH;
     R guard0, guardinv;
-    R sigma[3], eps4[3], rc2[3], swlo[3], swinv[3], Srlo[3], Srhi[3], Srinv[3];
+    R sigma[3], sig2[3], eps4[3], rc2[3], swlo[3], swlo2[3], swinv[3], Srlo[3], Srhi[3], Srhi2[3], Srinv[3];
     R bmin[3], binv[3], rstar[3];
     R teps[3];
     R rpath2;                        // no C_ij path reaches beyond sqrt(rpath2)
@@ -112,6 +120,17 @@ template <class R> struct DevParams {
 };
 
 HD int pidx(int ti, int tj) { return ti + tj; }
+
+// a < b for non-negative, non-NaN a and b, by their IEEE bit patterns: an
+// integer compare, which keeps squared-distance tests off the FP64 pipe
+HD bool lt_nonneg(double a, double b) {
+#ifdef __CUDA_ARCH__
+    return __double_as_longlong(a) < __double_as_longlong(b);
+#else
+    return a < b;
+#endif
+}
+HD bool lt_nonneg(float a, float b) { return a < b; }
 
 // ------------------------------------------------------------------ switches
 // S(t) = 1 for t <= 0, 0 for t >= 1, (1 + cos pi t)/2 between; dS = dS/dt
@@ -130,9 +149,22 @@ template <class R> HD R wfun(const DevParams<R>& P, int p, R r, R& dw) {
     dw = dS * P.Dinv[p];
     return w;
 }
+// the same with 1 - w formed without cancellation (1 - cos = sin^2 / (1 + cos)),
+// so that C_ij = 1 - w keeps its relative precision when w is close to 1
+template <class R> HD R wfun_c(const DevParams<R>& P, int p, R r, R& dw, R& omw) {
+    R t = (r - P.Dmin[p]) * P.Dinv[p];
+    if (t <= R(0)) { dw = R(0); omw = R(0); return R(1); }
+    if (t >= R(1)) { dw = R(0); omw = R(1); return R(0); }
+    R s, c;
+    sincospi_(t, &s, &c);
+    dw = R(-0.5 * M_PI) * s * P.Dinv[p];
+    omw = c > R(0) ? R(0.5) * s * s / (R(1) + c) : R(0.5) * (R(1) - c);
+    return R(0.5) * (R(1) + c);
+}
 
 // ------------------------------------------------------------------ splines
-template <class R> HD R quintic(const Quintic<R>& q, R x, R& dfdx) {
+// D = true: value and derivative(s); D = false: value only
+template <class R, bool D = true> HD R quintic(const Quintic<R>& q, R x, R& dfdx) {
     bool cl = false;
     if (x < q.k[0]) { x = q.k[0]; cl = true; }
     if (x > q.k[q.n]) { x = q.k[q.n]; cl = true; }
@@ -141,13 +173,22 @@ template <class R> HD R quintic(const Quintic<R>& q, R x, R& dfdx) {
     while (m + 1 < q.n && x > q.k[m + 1]) m++;
     R t = (x - q.k[m]) * q.invh[m];
     const R* a = q.a[m];
-    R f = a[5], d = R(5) * a[5];
-    f = f * t + a[4]; d = d * t + R(4) * a[4];
-    f = f * t + a[3]; d = d * t + R(3) * a[3];
-    f = f * t + a[2]; d = d * t + R(2) * a[2];
-    f = f * t + a[1]; d = d * t + a[1];
+    R f = a[5];
+    f = f * t + a[4];
+    f = f * t + a[3];
+    f = f * t + a[2];
+    f = f * t + a[1];
     f = f * t + a[0];
-    dfdx = cl ? R(0) : d * q.invh[m];
+    if (D) {
+        R d = R(5) * a[5];
+        d = d * t + R(4) * a[4];
+        d = d * t + R(3) * a[3];
+        d = d * t + R(2) * a[2];
+        d = d * t + a[1];
+        dfdx = cl ? R(0) : d * q.invh[m];
+    } else {
+        dfdx = R(0);
+    }
     return f;
 }
 
@@ -160,7 +201,7 @@ template <class R> HD void clamp_arg(R& x, R lo, R hi, bool& cl) {
 HD int clamp_cell(int c, int hi) { return c < 0 ? 0 : (c > hi ? hi : c); }
 
 // bicubic on the integer grid [0,4]^2, 16 power-basis coefficients per cell
-template <class R> HD R bicubic(const R* tab, R x, R y, R& fx, R& fy) {
+template <class R, bool D = true> HD R bicubic(const R* tab, R x, R y, R& fx, R& fy) {
     bool cx, cy;
     clamp_arg<R>(x, R(0), R(4), cx);
     clamp_arg<R>(y, R(0), R(4), cy);
@@ -172,13 +213,15 @@ template <class R> HD R bicubic(const R* tab, R x, R y, R& fx, R& fy) {
     for (int p = 3; p >= 0; p--) {
         const R* c = a + p * 4;
         R cp = ((c[3] * ty + c[2]) * ty + c[1]) * ty + c[0];
-        R dcp = (R(3) * c[3] * ty + R(2) * c[2]) * ty + c[1];
-        dx = dx * tx + f;
+        if (D) {
+            R dcp = (R(3) * c[3] * ty + R(2) * c[2]) * ty + c[1];
+            dx = dx * tx + f;
+            dy = dy * tx + dcp;
+        }
         f = f * tx + cp;
-        dy = dy * tx + dcp;
     }
-    fx = cx ? R(0) : dx;
-    fy = cy ? R(0) : dy;
+    fx = (D && !cx) ? dx : R(0);
+    fy = (D && !cy) ? dy : R(0);
     return f;
 }
 
@@ -193,26 +236,31 @@ template <class R> HD int tri_cell_index(R& x, R& y, R& z, bool* cl, R& tx, R& t
     tx = x - R(ix); ty = y - R(iy); tz = z - R(1) - R(iz);
     return (ix * 4 + iy) * 8 + iz;
 }
-template <class R> HD R tricubic_cell(const R* a, R tx, R ty, R tz, const bool* cl, R& fx, R& fy, R& fz) {
+template <class R, bool D = true>
+HD R tricubic_cell(const R* a, R tx, R ty, R tz, const bool* cl, R& fx, R& fy, R& fz) {
     R f = 0, dx = 0, dy = 0, dz = 0;
     for (int p = 3; p >= 0; p--) {
         R cp = 0, cpy = 0, cpz = 0;
         for (int q = 3; q >= 0; q--) {
             const R* c = a + (p * 4 + q) * 4;
             R cq = ((c[3] * tz + c[2]) * tz + c[1]) * tz + c[0];
-            R dcq = (R(3) * c[3] * tz + R(2) * c[2]) * tz + c[1];
-            cpy = cpy * ty + cp;
+            if (D) {
+                R dcq = (R(3) * c[3] * tz + R(2) * c[2]) * tz + c[1];
+                cpy = cpy * ty + cp;
+                cpz = cpz * ty + dcq;
+            }
             cp = cp * ty + cq;
-            cpz = cpz * ty + dcq;
         }
-        dx = dx * tx + f;
+        if (D) {
+            dx = dx * tx + f;
+            dy = dy * tx + cpy;
+            dz = dz * tx + cpz;
+        }
         f = f * tx + cp;
-        dy = dy * tx + cpy;
-        dz = dz * tx + cpz;
     }
-    fx = cl[0] ? R(0) : dx;
-    fy = cl[1] ? R(0) : dy;
-    fz = cl[2] ? R(0) : dz;
+    fx = (D && !cl[0]) ? dx : R(0);
+    fy = (D && !cl[1]) ? dy : R(0);
+    fz = (D && !cl[2]) ? dz : R(0);
     return f;
 }
 
@@ -225,7 +273,8 @@ template <class R> struct Graph {
     const int* nj;           // neighbour atom
     const int* nimg;         // packed image of the neighbour relative to i
     const R* dx; const R* dy; const R* dz;   // x_j + S L - x_i
-    const R* r; const R* w; const R* dw;
+    const R* r; const R* ir; const R* w; const R* dw;   // |d|, 1/|d|, w, dw/dr
+    const R* omw;                            // 1 - w
     const R* nC; const R* nH;                // sum of w over C / H neighbours
 };
 
@@ -266,29 +315,37 @@ template <class R> struct Side {
     R p;                // p^{sigma pi}
 };
 
-// angular function g_c(cos) (with the g_C mixing in N for a carbon centre)
-template <class R> HD R gfun(const DevParams<R>& P, int tc, R cs, R N, R& dg_dcos, R& dg_dN) {
+// angular function g_c(cos) (with the g_C mixing in N for a carbon centre);
+// only the branch the mixing weight needs is evaluated
+template <class R, bool D = true>
+HD R gfun(const DevParams<R>& P, int tc, R cs, R N, R& dg_dcos, R& dg_dN) {
+    dg_dN = R(0);
     if (tc == 0) {
-        R d1, d2, dQ;
-        R G = quintic<R>(P.gC1, cs, d1);
-        R gam = quintic<R>(P.gC2, cs, d2);
+        R dQ;
         R Qn = Sw<R>((N - P.gN0) * P.gNinv, dQ);
-        dg_dcos = d1 + Qn * (d2 - d1);
-        dg_dN = dQ * P.gNinv * (gam - G);
+        if (Qn == R(1)) return quintic<R, D>(P.gC2, cs, dg_dcos);
+        if (Qn == R(0)) return quintic<R, D>(P.gC1, cs, dg_dcos);
+        R d1, d2;
+        R G = quintic<R, D>(P.gC1, cs, d1);
+        R gam = quintic<R, D>(P.gC2, cs, d2);
+        if (D) {
+            dg_dcos = d1 + Qn * (d2 - d1);
+            dg_dN = dQ * P.gNinv * (gam - G);
+        }
         return G + Qn * (gam - G);
     }
-    dg_dN = R(0);
-    return quintic<R>(P.gH, cs, dg_dcos);
+    return quintic<R, D>(P.gH, cs, dg_dcos);
 }
 
-// lambda_jik = lam [(rho_kH - r_ik) - (rho_jH - r_ij)] for an H centre, else 0
-template <class R> HD R lambda(const DevParams<R>& P, int tc, int tk, int to, R rck, R umag) {
-    if (tc == 0) return R(0);
-    return P.lam * ((P.rhoH[tk] - rck) - (P.rhoH[to] - umag));
+// e^lambda_jik, lambda = lam [(rho_kH - r_ik) - (rho_jH - r_ij)] for an H centre, else 1
+template <class R> HD R exp_lambda(const DevParams<R>& P, int tc, int tk, int to, R rck, R umag) {
+    if (tc == 0) return R(1);
+    return exp_(P.lam * ((P.rhoH[tk] - rck) - (P.rhoH[to] - umag)));
 }
 
-template <class R>
-HD void side_forward(const DevParams<R>& P, const Graph<R>& G, int c, int o, R ux, R uy, R uz, R umag, Side<R>& s) {
+template <class R, bool D>
+HD void side_forward(const DevParams<R>& P, const Graph<R>& G, int c, int o, R ux, R uy, R uz, R inv_u, R umag,
+                     Side<R>& s) {
     int tc = G.type[c], to = G.type[o];
     int nc = G.cnt[c];
     s.NC = 0; s.NH = 0; s.conj = 0;
@@ -308,26 +365,24 @@ HD void side_forward(const DevParams<R>& P, const Graph<R>& G, int c, int o, R u
     }
     s.N = s.NC + s.NH;
     s.sum = 0; s.dsum_dN = 0;
-    R inv_u = R(1) / umag;
     for (int a = 0; a < nc; a++) {
         int q = c * MAXN + a;
         int k = G.nj[q];
         if (k == o) continue;
-        R rck = G.r[q];
-        R cs = (ux * G.dx[q] + uy * G.dy[q] + uz * G.dz[q]) * inv_u / rck;
+        R cs = (ux * G.dx[q] + uy * G.dy[q] + uz * G.dz[q]) * inv_u * G.ir[q];
         cs = cs < R(-1) ? R(-1) : (cs > R(1) ? R(1) : cs);
         R dgc, dgN;
-        R g = gfun<R>(P, tc, cs, s.N, dgc, dgN);
-        R e = exp_(lambda<R>(P, tc, G.type[k], to, rck, umag));
+        R g = gfun<R, D>(P, tc, cs, s.N, dgc, dgN);
+        R e = exp_lambda<R>(P, tc, G.type[k], to, G.r[q], umag);
         s.sum += G.w[q] * g * e;
-        s.dsum_dN += G.w[q] * dgN * e;
+        if (D) s.dsum_dN += G.w[q] * dgN * e;
     }
     s.P = 0; s.dPdNC = 0; s.dPdNH = 0;
     if (!(tc == 1 && to == 1)) {
         int tab = (tc == 0 && to == 0) ? 0 : (tc == 0 ? 1 : 2);
-        s.P = bicubic<R>(P.Ptab + tab * 256, s.NC, s.NH, s.dPdNC, s.dPdNH);
+        s.P = bicubic<R, D>(P.Ptab + tab * 256, s.NC, s.NH, s.dPdNC, s.dPdNH);
     }
-    s.p = R(1) / sqrt_(R(1) + s.sum + s.P);
+    s.p = rsqrt_(R(1) + s.sum + s.P);
 }
 
 // Reverse of one side.  dEdp: adjoint of p; dEdN_direct: adjoint of N_co
@@ -335,7 +390,7 @@ HD void side_forward(const DevParams<R>& P, const Graph<R>& G, int c, int o, R u
 // the gradient with respect to the partner vector u (sign as given) and to
 // its length; applies the forces on the neighbours of c.
 template <class R>
-HD void side_reverse(const DevParams<R>& P, const Graph<R>& G, int c, int o, R ux, R uy, R uz, R umag,
+HD void side_reverse(const DevParams<R>& P, const Graph<R>& G, int c, int o, R ux, R uy, R uz, R inv_u, R umag,
                      const Side<R>& s, R dEdp, R dEdN_direct, R dEdconj, Sink& sink,
                      R& gux, R& guy, R& guz, R& gumag, double& fcx, double& fcy, double& fcz) {
     int tc = G.type[c], to = G.type[o];
@@ -344,27 +399,24 @@ HD void side_reverse(const DevParams<R>& P, const Graph<R>& G, int c, int o, R u
     R dEdN = dEdN_direct + ac * s.dsum_dN;
     R dEdNC = dEdN + ac * s.dPdNC;
     R dEdNH = dEdN + ac * s.dPdNH;
-    R inv_u = R(1) / umag;
     for (int a = 0; a < nc; a++) {
         int q = c * MAXN + a;
         int k = G.nj[q];
         if (k == o) continue;
         int tk = G.type[k];
         R dxk = G.dx[q], dyk = G.dy[q], dzk = G.dz[q];
-        R rck = G.r[q], w = G.w[q], dw = G.dw[q];
-        R inv_r = R(1) / rck;
+        R rck = G.r[q], inv_r = G.ir[q], w = G.w[q], dw = G.dw[q];
         R cs_raw = (ux * dxk + uy * dyk + uz * dzk) * inv_u * inv_r;
         bool cl = cs_raw < R(-1) || cs_raw > R(1);
         R cs = cs_raw < R(-1) ? R(-1) : (cs_raw > R(1) ? R(1) : cs_raw);
         R dgc, dgN;
-        R g = gfun<R>(P, tc, cs, s.N, dgc, dgN);
-        R lam = lambda<R>(P, tc, tk, to, rck, umag);
-        R e = exp_(lam);
+        R g = gfun<R, true>(P, tc, cs, s.N, dgc, dgN);
+        R e = exp_lambda<R>(P, tc, tk, to, rck, umag);
         // d E / d w_ck
         R dEdw = (tk == 0 ? dEdNC : dEdNH) + ac * g * e;
-        R x = R(0), Fx = R(0), dFx = R(0);
+        R Fx = R(0), dFx = R(0);
         if (tk == 0) {
-            x = G.nC[k] + G.nH[k] - w;
+            R x = G.nC[k] + G.nH[k] - w;
             Fx = Sw<R>((x - P.Fx0) * P.Fxinv, dFx);
             dFx *= P.Fxinv;
             dEdw += dEdconj * Fx;
@@ -377,12 +429,14 @@ HD void side_reverse(const DevParams<R>& P, const Graph<R>& G, int c, int o, R u
         }
         R dEdcs = cl ? R(0) : ac * w * e * dgc;
         // cos = u.d / (|u| |d|)
-        R gxk = dEdr * dxk * inv_r + dEdcs * (ux * inv_u * inv_r - cs * dxk * inv_r * inv_r);
-        R gyk = dEdr * dyk * inv_r + dEdcs * (uy * inv_u * inv_r - cs * dyk * inv_r * inv_r);
-        R gzk = dEdr * dzk * inv_r + dEdcs * (uz * inv_u * inv_r - cs * dzk * inv_r * inv_r);
-        gux += dEdcs * (dxk * inv_u * inv_r - cs * ux * inv_u * inv_u);
-        guy += dEdcs * (dyk * inv_u * inv_r - cs * uy * inv_u * inv_u);
-        guz += dEdcs * (dzk * inv_u * inv_r - cs * uz * inv_u * inv_u);
+        R a1 = dEdcs * inv_u * inv_r, a2 = dEdcs * cs * inv_r * inv_r, a3 = dEdcs * cs * inv_u * inv_u;
+        R er = dEdr * inv_r;
+        R gxk = er * dxk + a1 * ux - a2 * dxk;
+        R gyk = er * dyk + a1 * uy - a2 * dyk;
+        R gzk = er * dzk + a1 * uz - a2 * dzk;
+        gux += a1 * dxk - a3 * ux;
+        guy += a1 * dyk - a3 * uy;
+        guz += a1 * dzk - a3 * uz;
         sink.half(k, dxk, dyk, dzk, gxk, gyk, gzk, fcx, fcy, fcz);
         // conjugation: x_ck = sum_{m in N(k), m != c} w_km
         if (tk == 0 && dFx != R(0) && dEdconj != R(0)) {
@@ -394,7 +448,7 @@ HD void side_reverse(const DevParams<R>& P, const Graph<R>& G, int c, int o, R u
                 if (m == c) continue;
                 R dwm = G.dw[qq];
                 if (dwm == R(0)) continue;
-                R t = coef * dwm / G.r[qq];
+                R t = coef * dwm * G.ir[qq];
                 sink.pair(k, m, G.dx[qq], G.dy[qq], G.dz[qq], t * G.dx[qq], t * G.dy[qq], t * G.dz[qq]);
             }
         }
@@ -413,54 +467,52 @@ template <class R> HD R guardf(const DevParams<R>& P, R cs, R& dgd) {
 // sum over k in N(i)\j, l in N(j)\{i,k} of (1 - cos^2 w) w_ik w_jl s_i s_j, and
 // (reverse) its gradient times dEdD.  u = vector standing for r_ij.
 template <class R>
-HD R dihedral_sum(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, R uy, R uz, R umag,
+HD R dihedral_sum(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, R uy, R uz, R inv_u,
                   bool reverse, R dEdD, Sink& sink, R& gux, R& guy, R& guz,
                   double& fix, double& fiy, double& fiz, double& fjx, double& fjy, double& fjz) {
     R D = 0;
     int ni = G.cnt[i], nj = G.cnt[j];
-    R inv_u = R(1) / umag;
     for (int a = 0; a < ni; a++) {
         int qa = i * MAXN + a;
         int k = G.nj[qa];
         if (k == j) continue;
         R ax = G.dx[qa], ay = G.dy[qa], az = G.dz[qa];
-        R ra = G.r[qa], wik = G.w[qa], dwik = G.dw[qa];
-        R csi = (ux * ax + uy * ay + uz * az) * inv_u / ra;
+        R inv_ra = G.ir[qa], wik = G.w[qa], dwik = G.dw[qa];
+        R csi = (ux * ax + uy * ay + uz * az) * inv_u * inv_ra;
         R dsi;
         R si = guardf<R>(P, csi, dsi);
         if (si == R(0)) continue;
         // n1 = u x a
         R n1x = uy * az - uz * ay, n1y = uz * ax - ux * az, n1z = ux * ay - uy * ax;
-        R n1 = sqrt_(n1x * n1x + n1y * n1y + n1z * n1z);
+        R n1s = n1x * n1x + n1y * n1y + n1z * n1z;
+        R in1s = R(1) / n1s;
         for (int b = 0; b < nj; b++) {
             int qb = j * MAXN + b;
             int l = G.nj[qb];
             if (l == i || l == k) continue;
             R bx = G.dx[qb], by = G.dy[qb], bz = G.dz[qb];
-            R rb = G.r[qb], wjl = G.w[qb], dwjl = G.dw[qb];
-            R csj = -(ux * bx + uy * by + uz * bz) * inv_u / rb;
+            R inv_rb = G.ir[qb], wjl = G.w[qb], dwjl = G.dw[qb];
+            R csj = -(ux * bx + uy * by + uz * bz) * inv_u * inv_rb;
             R dsj;
             R sj = guardf<R>(P, csj, dsj);
             if (sj == R(0)) continue;
             R n2x = uy * bz - uz * by, n2y = uz * bx - ux * bz, n2z = ux * by - uy * bx;
-            R n2 = sqrt_(n2x * n2x + n2y * n2y + n2z * n2z);
-            R inv12 = R(1) / (n1 * n2);
+            R n2s = n2x * n2x + n2y * n2y + n2z * n2z;
+            R inv12 = rsqrt_(n1s * n2s);
             R cw = (n1x * n2x + n1y * n2y + n1z * n2z) * inv12;
             R one_m = R(1) - cw * cw;
             D += one_m * wik * wjl * si * sj;
             if (!reverse) continue;
+            R in2s = R(1) / n2s;
             R dcw = dEdD * R(-2) * cw * wik * wjl * si * sj;
             R dwi = dEdD * one_m * wjl * si * sj;
             R dwj = dEdD * one_m * wik * si * sj;
             R dci = dEdD * one_m * wik * wjl * sj * dsi;   // dE/dcos theta_jik
             R dcj = dEdD * one_m * wik * wjl * si * dsj;   // dE/dcos theta_ijl
             // gradient of cw with respect to n1, n2
-            R g1x = dcw * (n2x * inv12 - cw * n1x / (n1 * n1));
-            R g1y = dcw * (n2y * inv12 - cw * n1y / (n1 * n1));
-            R g1z = dcw * (n2z * inv12 - cw * n1z / (n1 * n1));
-            R g2x = dcw * (n1x * inv12 - cw * n2x / (n2 * n2));
-            R g2y = dcw * (n1y * inv12 - cw * n2y / (n2 * n2));
-            R g2z = dcw * (n1z * inv12 - cw * n2z / (n2 * n2));
+            R c1 = dcw * cw * in1s, c2 = dcw * cw * in2s, c12 = dcw * inv12;
+            R g1x = c12 * n2x - c1 * n1x, g1y = c12 * n2y - c1 * n1y, g1z = c12 * n2z - c1 * n1z;
+            R g2x = c12 * n1x - c2 * n2x, g2y = c12 * n1y - c2 * n2y, g2z = c12 * n1z - c2 * n2z;
             // n1 = u x a: d/du = a x g1, d/da = g1 x u ; n2 = u x b likewise
             gux += ay * g1z - az * g1y + by * g2z - bz * g2y;
             guy += az * g1x - ax * g1z + bz * g2x - bx * g2z;
@@ -468,22 +520,16 @@ HD R dihedral_sum(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, 
             R gax = g1y * uz - g1z * uy, gay = g1z * ux - g1x * uz, gaz = g1x * uy - g1y * ux;
             R gbx = g2y * uz - g2z * uy, gby = g2z * ux - g2x * uz, gbz = g2x * uy - g2y * ux;
             // weights
-            R inv_ra = R(1) / ra, inv_rb = R(1) / rb;
-            gax += dwi * dwik * ax * inv_ra; gay += dwi * dwik * ay * inv_ra; gaz += dwi * dwik * az * inv_ra;
-            gbx += dwj * dwjl * bx * inv_rb; gby += dwj * dwjl * by * inv_rb; gbz += dwj * dwjl * bz * inv_rb;
+            R ea = dwi * dwik * inv_ra, eb = dwj * dwjl * inv_rb;
+            gax += ea * ax; gay += ea * ay; gaz += ea * az;
+            gbx += eb * bx; gby += eb * by; gbz += eb * bz;
             // guards: csi = u.a/(|u||a|), csj = -u.b/(|u||b|)
-            gax += dci * (ux * inv_u * inv_ra - csi * ax * inv_ra * inv_ra);
-            gay += dci * (uy * inv_u * inv_ra - csi * ay * inv_ra * inv_ra);
-            gaz += dci * (uz * inv_u * inv_ra - csi * az * inv_ra * inv_ra);
-            gux += dci * (ax * inv_u * inv_ra - csi * ux * inv_u * inv_u);
-            guy += dci * (ay * inv_u * inv_ra - csi * uy * inv_u * inv_u);
-            guz += dci * (az * inv_u * inv_ra - csi * uz * inv_u * inv_u);
-            gbx += dcj * (-ux * inv_u * inv_rb - csj * bx * inv_rb * inv_rb);
-            gby += dcj * (-uy * inv_u * inv_rb - csj * by * inv_rb * inv_rb);
-            gbz += dcj * (-uz * inv_u * inv_rb - csj * bz * inv_rb * inv_rb);
-            gux += dcj * (-bx * inv_u * inv_rb - csj * ux * inv_u * inv_u);
-            guy += dcj * (-by * inv_u * inv_rb - csj * uy * inv_u * inv_u);
-            guz += dcj * (-bz * inv_u * inv_rb - csj * uz * inv_u * inv_u);
+            R i1 = dci * inv_u * inv_ra, i2 = dci * csi * inv_ra * inv_ra, i3 = dci * csi * inv_u * inv_u;
+            gax += i1 * ux - i2 * ax; gay += i1 * uy - i2 * ay; gaz += i1 * uz - i2 * az;
+            gux += i1 * ax - i3 * ux; guy += i1 * ay - i3 * uy; guz += i1 * az - i3 * uz;
+            R j1 = dcj * inv_u * inv_rb, j2 = dcj * csj * inv_rb * inv_rb, j3 = dcj * csj * inv_u * inv_u;
+            gbx += -j1 * ux - j2 * bx; gby += -j1 * uy - j2 * by; gbz += -j1 * uz - j2 * bz;
+            gux += -j1 * bx - j3 * ux; guy += -j1 * by - j3 * uy; guz += -j1 * bz - j3 * uz;
             sink.half(k, ax, ay, az, gax, gay, gaz, fix, fiy, fiz);
             sink.half(l, bx, by, bz, gbx, gby, gbz, fjx, fjy, fjz);
         }
@@ -491,17 +537,19 @@ HD R dihedral_sum(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, 
     return D;
 }
 
-// b_ij with u standing for r_ij.  In reverse mode (eps = dE/db != 0) it applies
-// the forces on all neighbours and returns the gradient with respect to u and
-// its length in gu*, gumag, and the forces on i and j themselves in fi*, fj*
-// (excluding the u gradient, which the caller applies).
-template <class R>
-HD R bond_order(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, R uy, R uz, R umag,
-                bool reverse, R eps, Sink& sink, R& gux, R& guy, R& guz, R& gumag,
+// b_ij with u standing for r_ij (inv_u = 1/|u|).  REV = false: the value only,
+// without any derivative work.  REV = true: also the reverse pass with
+// eps = dE/db, which applies the forces on all neighbours and returns the
+// gradient with respect to u and its length in gu*, gumag, and the forces on
+// i and j themselves in fi*, fj* (excluding the u gradient, which the caller
+// applies).
+template <class R, bool REV>
+HD R bond_order(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, R uy, R uz, R umag, R inv_u,
+                R eps, Sink& sink, R& gux, R& guy, R& guz, R& gumag,
                 double& fix, double& fiy, double& fiz, double& fjx, double& fjy, double& fjz) {
     Side<R> si, sj;
-    side_forward<R>(P, G, i, j, ux, uy, uz, umag, si);
-    side_forward<R>(P, G, j, i, -ux, -uy, -uz, umag, sj);
+    side_forward<R, REV>(P, G, i, j, ux, uy, uz, inv_u, umag, si);
+    side_forward<R, REV>(P, G, j, i, -ux, -uy, -uz, inv_u, umag, sj);
     int ti = G.type[i], tj = G.type[j];
     R Nconj = R(1) + si.conj * si.conj + sj.conj * sj.conj;
     // pi^rc: the carbon side's coordination first for a C-H bond
@@ -512,32 +560,32 @@ HD R bond_order(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, R 
     R tx, ty, tz;
     int cell = tri_cell_index<R>(xa, xb, xc, cl, tx, ty, tz);
     R Fa, Fb, Fc;
-    R pirc = tricubic_cell<R>(P.Ftab + (tab * NTRI_CELLS + cell) * 64, tx, ty, tz, cl, Fa, Fb, Fc);
+    R pirc = tricubic_cell<R, REV>(P.Ftab + (tab * NTRI_CELLS + cell) * 64, tx, ty, tz, cl, Fa, Fb, Fc);
     R dFdNi = swap ? Fb : Fa, dFdNj = swap ? Fa : Fb;
     // pi^dh (C-C only), skipped where the T_CC cell is identically zero
     R pidh = 0, D = 0, Tv = 0, Ta = 0, Tb = 0, Tc = 0;
     bool dih = (ti == 0 && tj == 0) && P.Tnz[cell];
     if (dih) {
-        Tv = tricubic_cell<R>(P.Ttab + cell * 64, tx, ty, tz, cl, Ta, Tb, Tc);
+        Tv = tricubic_cell<R, REV>(P.Ttab + cell * 64, tx, ty, tz, cl, Ta, Tb, Tc);
         R dummy = 0;
-        D = dihedral_sum<R>(P, G, i, j, ux, uy, uz, umag, false, R(0), sink, dummy, dummy, dummy,
+        D = dihedral_sum<R>(P, G, i, j, ux, uy, uz, inv_u, false, R(0), sink, dummy, dummy, dummy,
                             fix, fiy, fiz, fjx, fjy, fjz);
         pidh = Tv * D;
     }
     R b = R(0.5) * (si.p + sj.p) + pirc + pidh;
-    if (!reverse) return b;
+    if (!REV) return b;
     R dEdNi = eps * (dFdNi + D * Ta);
     R dEdNj = eps * (dFdNj + D * Tb);
     R dEdNconj = eps * (Fc + D * Tc);
     R half = R(0.5) * eps;
     R gvx = 0, gvy = 0, gvz = 0;     // side j works on -u
-    side_reverse<R>(P, G, i, j, ux, uy, uz, umag, si, half, dEdNi, dEdNconj * R(2) * si.conj, sink,
+    side_reverse<R>(P, G, i, j, ux, uy, uz, inv_u, umag, si, half, dEdNi, dEdNconj * R(2) * si.conj, sink,
                     gux, guy, guz, gumag, fix, fiy, fiz);
-    side_reverse<R>(P, G, j, i, -ux, -uy, -uz, umag, sj, half, dEdNj, dEdNconj * R(2) * sj.conj, sink,
+    side_reverse<R>(P, G, j, i, -ux, -uy, -uz, inv_u, umag, sj, half, dEdNj, dEdNconj * R(2) * sj.conj, sink,
                     gvx, gvy, gvz, gumag, fjx, fjy, fjz);
     gux -= gvx; guy -= gvy; guz -= gvz;
     if (dih) {
-        dihedral_sum<R>(P, G, i, j, ux, uy, uz, umag, true, eps * Tv, sink, gux, guy, guz,
+        dihedral_sum<R>(P, G, i, j, ux, uy, uz, inv_u, true, eps * Tv, sink, gux, guy, guz,
                         fix, fiy, fiz, fjx, fjy, fjz);
     }
     return b;
@@ -549,12 +597,13 @@ HD double rebo_bond(const DevParams<R>& P, const Graph<R>& G, int i, int slot, S
     int q = i * MAXN + slot;
     int j = G.nj[q];
     int p = pidx(G.type[i], G.type[j]);
-    R ux = G.dx[q], uy = G.dy[q], uz = G.dz[q], r = G.r[q];
+    R ux = G.dx[q], uy = G.dy[q], uz = G.dz[q], r = G.r[q], ir = G.ir[q];
     R w = G.w[q], dw = G.dw[q];
     R eR = exp_(-P.alpha[p] * r);
-    R qr = R(1) + P.Q[p] / r;
-    R fR = w * qr * P.A[p] * eR;
-    R dfR = dw * qr * P.A[p] * eR + w * (-P.Q[p] / (r * r)) * P.A[p] * eR - P.alpha[p] * fR;
+    R qr = R(1) + P.Q[p] * ir;
+    R AeR = P.A[p] * eR;
+    R fR = w * qr * AeR;
+    R dfR = dw * qr * AeR - w * P.Q[p] * ir * ir * AeR - P.alpha[p] * fR;
     R sB = 0, dsB = 0;
     for (int m = 0; m < P.nB[p]; m++) {
         R e = P.B[p][m] * exp_(-P.beta[p][m] * r);
@@ -565,11 +614,11 @@ HD double rebo_bond(const DevParams<R>& P, const Graph<R>& G, int i, int slot, S
     R dfA = -dw * sB - w * dsB;
     R gux = 0, guy = 0, guz = 0, gumag = 0;
     double fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
-    R b = bond_order<R>(P, G, i, j, ux, uy, uz, r, true, fA, sink, gux, guy, guz, gumag,
-                        fix, fiy, fiz, fjx, fjy, fjz);
+    R b = bond_order<R, true>(P, G, i, j, ux, uy, uz, r, ir, fA, sink, gux, guy, guz, gumag,
+                              fix, fiy, fiz, fjx, fjy, fjz);
     R dEdr = dfR + b * dfA + gumag;
-    R inv_r = R(1) / r;
-    gux += dEdr * ux * inv_r; guy += dEdr * uy * inv_r; guz += dEdr * uz * inv_r;
+    R e = dEdr * ir;
+    gux += e * ux; guy += e * uy; guz += e * uz;
     // vector u runs from i to j
     double gx = gux, gy = guy, gz = guz;
     atomic_add(sink.f + i, fix + gx); atomic_add(sink.f + sink.n + i, fiy + gy); atomic_add(sink.f + 2 * sink.n + i, fiz + gz);
@@ -587,10 +636,11 @@ template <class R>
 HD double torsion_bond(const DevParams<R>& P, const Graph<R>& G, int i, int slot, Sink& sink) {
     int q = i * MAXN + slot;
     int j = G.nj[q];
-    R ux = G.dx[q], uy = G.dy[q], uz = G.dz[q], r = G.r[q];
+    R ux = G.dx[q], uy = G.dy[q], uz = G.dz[q];
     R wij = G.w[q], dwij = G.dw[q];
-    R inv_u = R(1) / r;
+    R inv_u = G.ir[q];
     double E = 0;
+    bool any = false;
     R gux = 0, guy = 0, guz = 0;
     double fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
     int ni = G.cnt[i], nj = G.cnt[j];
@@ -599,21 +649,22 @@ HD double torsion_bond(const DevParams<R>& P, const Graph<R>& G, int i, int slot
         int k = G.nj[qa];
         if (k == j) continue;
         R ax = G.dx[qa], ay = G.dy[qa], az = G.dz[qa];
-        R ra = G.r[qa], wik = G.w[qa], dwik = G.dw[qa];
-        R inv_ra = R(1) / ra;
+        R wik = G.w[qa], dwik = G.dw[qa];
+        R inv_ra = G.ir[qa];
         R csi = (ux * ax + uy * ay + uz * az) * inv_u * inv_ra;
         R dsi;
         R si = guardf<R>(P, csi, dsi);
         if (si == R(0)) continue;
         R n1x = uy * az - uz * ay, n1y = uz * ax - ux * az, n1z = ux * ay - uy * ax;
         R n1s = n1x * n1x + n1y * n1y + n1z * n1z;
+        R in1s = R(1) / n1s;
         for (int b = 0; b < nj; b++) {
             int qb = j * MAXN + b;
             int l = G.nj[qb];
             if (l == i || l == k) continue;
             R bx = G.dx[qb], by = G.dy[qb], bz = G.dz[qb];
-            R rb = G.r[qb], wjl = G.w[qb], dwjl = G.dw[qb];
-            R inv_rb = R(1) / rb;
+            R wjl = G.w[qb], dwjl = G.dw[qb];
+            R inv_rb = G.ir[qb];
             R csj = -(ux * bx + uy * by + uz * bz) * inv_u * inv_rb;
             R dsj;
             R sj = guardf<R>(P, csj, dsj);
@@ -621,6 +672,7 @@ HD double torsion_bond(const DevParams<R>& P, const Graph<R>& G, int i, int slot
             R n2x = uy * bz - uz * by, n2y = uz * bx - ux * bz, n2z = ux * by - uy * bx;
             R n2s = n2x * n2x + n2y * n2y + n2z * n2z;
             R inv12 = rsqrt_(n1s * n2s);
+            R in2s = inv12 * inv12 * n1s;
             R cw = (n1x * n2x + n1y * n2y + n1z * n2z) * inv12;
             R h = R(0.5) * (R(1) + cw);
             R h2 = h * h, h4 = h2 * h2;
@@ -630,44 +682,37 @@ HD double torsion_bond(const DevParams<R>& P, const Graph<R>& G, int i, int slot
             R wprod = wik * wij * wjl;
             R ss = si * sj;
             E += (double)(wprod * ss * Vt);
+            any = true;
             R dcw = wprod * ss * dVdcw;
-            R dwi = dwik * wij * wjl * ss * Vt;
-            R dwj = wik * wij * dwjl * ss * Vt;
-            R dwm = wik * dwij * wjl * ss * Vt;
+            R sV = ss * Vt;
+            R dwi = dwik * wij * wjl * sV;
+            R dwj = wik * wij * dwjl * sV;
+            R dwm = wik * dwij * wjl * sV;
             R dci = wprod * sj * dsi * Vt;
             R dcj = wprod * si * dsj * Vt;
-            R g1x = dcw * (n2x * inv12 - cw * n1x / n1s);
-            R g1y = dcw * (n2y * inv12 - cw * n1y / n1s);
-            R g1z = dcw * (n2z * inv12 - cw * n1z / n1s);
-            R g2x = dcw * (n1x * inv12 - cw * n2x / n2s);
-            R g2y = dcw * (n1y * inv12 - cw * n2y / n2s);
-            R g2z = dcw * (n1z * inv12 - cw * n2z / n2s);
+            R c1 = dcw * cw * in1s, c2 = dcw * cw * in2s, c12 = dcw * inv12;
+            R g1x = c12 * n2x - c1 * n1x, g1y = c12 * n2y - c1 * n1y, g1z = c12 * n2z - c1 * n1z;
+            R g2x = c12 * n1x - c2 * n2x, g2y = c12 * n1y - c2 * n2y, g2z = c12 * n1z - c2 * n2z;
             gux += ay * g1z - az * g1y + by * g2z - bz * g2y;
             guy += az * g1x - ax * g1z + bz * g2x - bx * g2z;
             guz += ax * g1y - ay * g1x + bx * g2y - by * g2x;
             R gax = g1y * uz - g1z * uy, gay = g1z * ux - g1x * uz, gaz = g1x * uy - g1y * ux;
             R gbx = g2y * uz - g2z * uy, gby = g2z * ux - g2x * uz, gbz = g2x * uy - g2y * ux;
-            gax += dwi * ax * inv_ra; gay += dwi * ay * inv_ra; gaz += dwi * az * inv_ra;
-            gbx += dwj * bx * inv_rb; gby += dwj * by * inv_rb; gbz += dwj * bz * inv_rb;
-            gux += dwm * ux * inv_u; guy += dwm * uy * inv_u; guz += dwm * uz * inv_u;
-            gax += dci * (ux * inv_u * inv_ra - csi * ax * inv_ra * inv_ra);
-            gay += dci * (uy * inv_u * inv_ra - csi * ay * inv_ra * inv_ra);
-            gaz += dci * (uz * inv_u * inv_ra - csi * az * inv_ra * inv_ra);
-            gux += dci * (ax * inv_u * inv_ra - csi * ux * inv_u * inv_u);
-            guy += dci * (ay * inv_u * inv_ra - csi * uy * inv_u * inv_u);
-            guz += dci * (az * inv_u * inv_ra - csi * uz * inv_u * inv_u);
-            gbx += dcj * (-ux * inv_u * inv_rb - csj * bx * inv_rb * inv_rb);
-            gby += dcj * (-uy * inv_u * inv_rb - csj * by * inv_rb * inv_rb);
-            gbz += dcj * (-uz * inv_u * inv_rb - csj * bz * inv_rb * inv_rb);
-            gux += dcj * (-bx * inv_u * inv_rb - csj * ux * inv_u * inv_u);
-            guy += dcj * (-by * inv_u * inv_rb - csj * uy * inv_u * inv_u);
-            guz += dcj * (-bz * inv_u * inv_rb - csj * uz * inv_u * inv_u);
+            R ea = dwi * inv_ra, eb = dwj * inv_rb, em = dwm * inv_u;
+            gax += ea * ax; gay += ea * ay; gaz += ea * az;
+            gbx += eb * bx; gby += eb * by; gbz += eb * bz;
+            gux += em * ux; guy += em * uy; guz += em * uz;
+            R i1 = dci * inv_u * inv_ra, i2 = dci * csi * inv_ra * inv_ra, i3 = dci * csi * inv_u * inv_u;
+            gax += i1 * ux - i2 * ax; gay += i1 * uy - i2 * ay; gaz += i1 * uz - i2 * az;
+            gux += i1 * ax - i3 * ux; guy += i1 * ay - i3 * uy; guz += i1 * az - i3 * uz;
+            R j1 = dcj * inv_u * inv_rb, j2 = dcj * csj * inv_rb * inv_rb, j3 = dcj * csj * inv_u * inv_u;
+            gbx += -j1 * ux - j2 * bx; gby += -j1 * uy - j2 * by; gbz += -j1 * uz - j2 * bz;
+            gux += -j1 * bx - j3 * ux; guy += -j1 * by - j3 * uy; guz += -j1 * bz - j3 * uz;
             sink.half(k, ax, ay, az, gax, gay, gaz, fix, fiy, fiz);
             sink.half(l, bx, by, bz, gbx, gby, gbz, fjx, fjy, fjz);
         }
     }
-    if (E == 0.0 && gux == R(0) && guy == R(0) && guz == R(0) && fix == 0.0 && fjx == 0.0 && fiy == 0.0 && fjy == 0.0)
-        return 0.0;
+    if (!any) return 0.0;
     double gx = gux, gy = guy, gz = guz;
     atomic_add(sink.f + i, fix + gx); atomic_add(sink.f + sink.n + i, fiy + gy); atomic_add(sink.f + 2 * sink.n + i, fiz + gz);
     atomic_add(sink.f + j, fjx - gx); atomic_add(sink.f + sink.n + j, fjy - gy); atomic_add(sink.f + 2 * sink.n + j, fjz - gz);
@@ -693,13 +738,16 @@ template <class R> struct PathMap {
     int cap;
     int* cnt;            // entries per atom
     long long* key;      // [n * cap]
-    R* wt;
+    R* wt;               // C = 1 - largest path weight
     int* path;
 };
 
-// Ties: larger weight, then the shorter path, then the smaller k, then the smaller l.
-HD bool path_better(double w, int len, int k, int l, double w0, int len0, int k0, int l0) {
-    if (w != w0) return w > w0;
+// Ties: larger weight (smaller C), then the shorter path, then the smaller k,
+// then the smaller l.  The map stores C = 1 - weight, formed from the 1 - w of
+// each bond (1 - w1 w2 = (1 - w1) + w1 (1 - w2), and so on), which keeps the
+// relative precision of small C in FP32.
+HD bool path_better(double c, int len, int k, int l, double c0, int len0, int k0, int l0) {
+    if (c != c0) return c < c0;
     if (len != len0) return len < len0;
     if (k != k0) return k < k0;
     return l < l0;
@@ -709,7 +757,7 @@ template <class R>
 HD int build_path_map(const Graph<R>& G, PathMap<R>& M, int i) {
     int base = i * M.cap;
     int count = 0, overflow = 0;
-    auto insert = [&](int atom, int img, R w, int len, int k, int l, int code) {
+    auto insert = [&](int atom, int img, R c, int len, int k, int l, int code) {
         long long key = map_key(atom, img);
         for (int e = 0; e < count; e++) {
             if (M.key[base + e] == key) {
@@ -717,8 +765,8 @@ HD int build_path_map(const Graph<R>& G, PathMap<R>& M, int i) {
                 int k0 = path_len(p0) >= 2 ? G.nj[i * MAXN + path_a(p0)] : -1;
                 int l0 = -1;
                 if (path_len(p0) == 3) l0 = G.nj[G.nj[i * MAXN + path_a(p0)] * MAXN + path_b(p0)];
-                if (path_better((double)w, len, k, l, (double)M.wt[base + e], path_len(p0), k0, l0)) {
-                    M.wt[base + e] = w;
+                if (path_better((double)c, len, k, l, (double)M.wt[base + e], path_len(p0), k0, l0)) {
+                    M.wt[base + e] = c;
                     M.path[base + e] = code;
                 }
                 return;
@@ -726,7 +774,7 @@ HD int build_path_map(const Graph<R>& G, PathMap<R>& M, int i) {
         }
         if (count < M.cap) {
             M.key[base + count] = key;
-            M.wt[base + count] = w;
+            M.wt[base + count] = c;
             M.path[base + count] = code;
             count++;
         } else {
@@ -738,8 +786,8 @@ HD int build_path_map(const Graph<R>& G, PathMap<R>& M, int i) {
         int qa = i * MAXN + a;
         int k = G.nj[qa];
         int Sk = G.nimg[qa];
-        R w1 = G.w[qa];
-        insert(k, Sk, w1, 1, -1, -1, path_pack(1, a, 0, 0));
+        R w1 = G.w[qa], c1 = G.omw[qa];
+        insert(k, Sk, c1, 1, -1, -1, path_pack(1, a, 0, 0));
         int nk = G.cnt[k];
         for (int b = 0; b < nk; b++) {
             int qb = k * MAXN + b;
@@ -747,14 +795,15 @@ HD int build_path_map(const Graph<R>& G, PathMap<R>& M, int i) {
             if (l == i) continue;
             int Sl = img_add(Sk, G.nimg[qb]);
             R w2 = w1 * G.w[qb];
-            insert(l, Sl, w2, 2, k, -1, path_pack(2, a, b, 0));
+            R c2 = c1 + w1 * G.omw[qb];
+            insert(l, Sl, c2, 2, k, -1, path_pack(2, a, b, 0));
             int nl = G.cnt[l];
             for (int c = 0; c < nl; c++) {
                 int qc = l * MAXN + c;
                 int m = G.nj[qc];
                 if (m == i || m == k) continue;
                 int Sm = img_add(Sl, G.nimg[qc]);
-                insert(m, Sm, w2 * G.w[qc], 3, k, l, path_pack(3, a, b, c));
+                insert(m, Sm, c2 + w2 * G.omw[qc], 3, k, l, path_pack(3, a, b, c));
             }
         }
     }
@@ -777,7 +826,7 @@ HD void path_forces(const Graph<R>& G, int i, int code, R dEdw, Sink& sink, doub
         if (dw[s] == R(0)) continue;
         R other = R(1);
         for (int t = 0; t < len; t++) if (t != s) other *= w[t];
-        R c = dEdw * other * dw[s] / G.r[q[s]];
+        R c = dEdw * other * dw[s] * G.ir[q[s]];
         R gx = c * G.dx[q[s]], gy = c * G.dy[q[s]], gz = c * G.dz[q[s]];
         if (from[s] == i) sink.half(G.nj[q[s]], G.dx[q[s]], G.dy[q[s]], G.dz[q[s]], gx, gy, gz, fix, fiy, fiz);
         else sink.pair(from[s], G.nj[q[s]], G.dx[q[s]], G.dy[q[s]], G.dz[q[s]], gx, gy, gz);
@@ -785,32 +834,116 @@ HD void path_forces(const Graph<R>& G, int i, int code, R dEdw, Sink& sink, doub
 }
 
 // ------------------------------------------------------------------ LJ (Alg. 3)
-// V^LJ(r) 4 eps [(s/r)^12 - (s/r)^6] times the C^1 cubic cut-off; returns dV/dr
-template <class R> HD R vlj(const DevParams<R>& P, int p, R r, R inv_r2, R& dV) {
-    R s2 = P.sigma[p] * P.sigma[p] * inv_r2;
+// V^LJ = 4 eps [(s/r)^12 - (s/r)^6] times the C^1 cubic cut-off, from r^2;
+// dVr = (dV/dr)/r.  The cut-off switch is evaluated without a branch (t is
+// clamped at 0, where it is the identity), so lanes of a warp never diverge.
+template <class R> HD R vlj(const DevParams<R>& P, int p, R r2, R& dVr) {
+    R ir = rsqrt_(r2);
+    R ir2 = ir * ir;
+    R s2 = P.sig2[p] * ir2;
     R s6 = s2 * s2 * s2;
     R v = P.eps4[p] * (s6 * s6 - s6);
-    R dv = P.eps4[p] * (R(-12) * s6 * s6 + R(6) * s6) / r;
+    R dvr = P.eps4[p] * (R(-12) * s6 * s6 + R(6) * s6) * ir2;
+    R r = r2 * ir;
     R t = (r - P.swlo[p]) * P.swinv[p];
-    if (t > R(0)) {
-        R so = R(1) - t * t * (R(3) - R(2) * t);
-        R dso = R(-6) * t * (R(1) - t) * P.swinv[p];
-        dV = dv * so + v * dso;
-        return v * so;
+    t = t > R(0) ? t : R(0);
+    R so = R(1) - t * t * (R(3) - R(2) * t);
+    R dso = R(-6) * t * (R(1) - t) * P.swinv[p];
+    dVr = dvr * so + v * dso * ir;
+    return v * so;
+}
+
+// Energy and forces of one LJ pair with S_r = 0 (C and its path known).
+template <class R>
+HD void lj_eval(const DevParams<R>& P, const Graph<R>& G, int i, int p, int j, double dx, double dy, double dz,
+                R C, int code, Sink& sink, double& fix, double& fiy, double& fiz, double& E) {
+    R rx = (R)dx, ry = (R)dy, rz = (R)dz;
+    R r2 = rx * rx + ry * ry + rz * rz;
+    R dVr;
+    R V = vlj<R>(P, p, r2, dVr);
+    E += (double)(C * V);
+    double c = (double)(C * dVr);
+    sink.half(j, dx, dy, dz, c * dx, c * dy, c * dz, fix, fiy, fiz);
+    if (code >= 0) path_forces<R>(G, i, code, -V, sink, fix, fiy, fiz);
+}
+
+// The common LJ pair: C = 1, no path, r inside 2.7 sigma (no cut-off switch):
+// V and (dV/dr)/r from 1/r^2 alone.
+template <class R>
+HD void lj_eval_inner(const DevParams<R>& P, int p, int j, double dx, double dy, double dz, Sink& sink,
+                      double& fix, double& fiy, double& fiz, double& E) {
+    R rx = (R)dx, ry = (R)dy, rz = (R)dz;
+    R ir2 = rcp_(rx * rx + ry * ry + rz * rz);
+    R s2 = P.sig2[p] * ir2;
+    R s6 = s2 * s2 * s2;
+    R e4 = P.eps4[p];
+    E += (double)(e4 * (s6 * s6 - s6));
+    double c = (double)(e4 * (R(6) * s6 - R(12) * s6 * s6) * ir2);
+    sink.half(j, dx, dy, dz, c * dx, c * dy, c * dz, fix, fiy, fiz);
+}
+
+// C = 1, no path, r inside the cut-off switch.
+template <class R>
+HD void lj_eval_switch(const DevParams<R>& P, int p, int j, double dx, double dy, double dz, Sink& sink,
+                       double& fix, double& fiy, double& fiz, double& E) {
+    R rx = (R)dx, ry = (R)dy, rz = (R)dz;
+    R r2 = rx * rx + ry * ry + rz * rz;
+    R ir = rsqrt_(r2);
+    R ir2 = ir * ir;
+    R s2 = P.sig2[p] * ir2;
+    R s6 = s2 * s2 * s2;
+    R v = P.eps4[p] * (s6 * s6 - s6);
+    R dvr = P.eps4[p] * (R(-12) * s6 * s6 + R(6) * s6) * ir2;
+    R t = (r2 * ir - P.swlo[p]) * P.swinv[p];          // > 0 in this class
+    R so = R(1) - t * t * (R(3) - R(2) * t);
+    R dso = R(-6) * t * (R(1) - t) * P.swinv[p];
+    E += (double)(v * so);
+    double c = (double)(dvr * so + v * dso * ir);
+    sink.half(j, dx, dy, dz, c * dx, c * dy, c * dz, fix, fiy, fiz);
+}
+
+// The tests of one LJ pair i -> (j, image) with FP64 displacement d: the
+// cut-off, and the C_ij lookup in i's connectivity map.  Returns
+//   0: beyond the cut-off, or C = 0;
+//   1: C = 1, no path, inside 2.7 sigma (lj_eval_inner);
+//   2: to be queued for b* (S_r != 0);
+//   3: C = 1, no path, inside the cut-off switch (lj_eval_switch);
+//   4: 0 < C < 1 along a path (lj_eval).
+// C, the path code and the map entry are returned.
+template <class R>
+HD int lj_classify(const DevParams<R>& P, const PathMap<R>& M, int i, int p, int j, int img, R r2,
+                   R& C, int& code, int& mi) {
+    mi = -1; code = -1; C = R(1);
+    if (!lt_nonneg(r2, P.rc2[p])) return 0;
+    if (lt_nonneg(r2, P.rpath2)) {
+        long long key = map_key(j, img);
+        int c = M.cnt[i];
+        const long long* k = M.key + (size_t)i * M.cap;
+        for (int e = 0; e < c; e++)
+            if (k[e] == key) { mi = e; break; }
+        if (mi >= 0) {
+            C = M.wt[(size_t)i * M.cap + mi];
+            if (!(C > R(0))) return 0;
+            code = M.path[(size_t)i * M.cap + mi];
+        }
     }
-    dV = dv;
-    return v;
+    if (lt_nonneg(r2, P.Srhi2[p])) return 2;
+    if (mi >= 0) return 4;
+    return lt_nonneg(P.swlo2[p], r2) ? 3 : 1;
 }
 
 // b* pair: (S_r S_b + 1 - S_r) C V for the pair i -> (j, image) with
-// displacement d (FP64 in, R for the arithmetic); C and its path given.
+// displacement d; C and its path given.  Applies every force except the one
+// through db*, which is needed only where S_b is in its transition: then
+// eps_out = dE/db* != 0 and bstar_reverse applies it.
 template <class R>
-HD double bstar_pair(const DevParams<R>& P, const Graph<R>& G, int i, int j, R dx, R dy, R dz, R r,
-                     R C, int path_code, Sink& sink, unsigned* dsb_count) {
+HD double bstar_pair(const DevParams<R>& P, const Graph<R>& G, int i, int j, R dx, R dy, R dz, R r2,
+                     R C, int path_code, Sink& sink, R& eps_out) {
     int p = pidx(G.type[i], G.type[j]);
-    R inv_r = R(1) / r;
-    R dV;
-    R V = vlj<R>(P, p, r, inv_r * inv_r, dV);
+    R inv_r = rsqrt_(r2);
+    R r = r2 * inv_r;
+    R dVr;
+    R V = vlj<R>(P, p, r2, dVr);
     R dSr;
     R Sr = Sw<R>((r - P.Srlo[p]) * P.Srinv[p], dSr);
     dSr *= P.Srinv[p];
@@ -818,36 +951,50 @@ HD double bstar_pair(const DevParams<R>& P, const Graph<R>& G, int i, int j, R d
     R ux = dx * inv_r * rs, uy = dy * inv_r * rs, uz = dz * inv_r * rs;
     R gux = 0, guy = 0, guz = 0, gumag = 0;
     double fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
-    R bs = bond_order<R>(P, G, i, j, ux, uy, uz, rs, false, R(0), sink, gux, guy, guz, gumag,
-                         fix, fiy, fiz, fjx, fjy, fjz);
+    R bs = bond_order<R, false>(P, G, i, j, ux, uy, uz, rs, R(1) / rs, R(0), sink, gux, guy, guz, gumag,
+                                fix, fiy, fiz, fjx, fjy, fjz);
     R dSb;
     R Sb = Sw<R>((bs - P.bmin[p]) * P.binv[p], dSb);
     dSb *= P.binv[p];
     R factor = Sr * Sb + R(1) - Sr;
     R E = factor * C * V;
-    R dEdr = (dSr * (Sb - R(1))) * C * V + factor * C * dV;
-    R gx = dEdr * dx * inv_r, gy = dEdr * dy * inv_r, gz = dEdr * dz * inv_r;
-    if (dSb != R(0)) {
-        if (dsb_count) *dsb_count += 1;
-        R eps = Sr * C * V * dSb;
-        bond_order<R>(P, G, i, j, ux, uy, uz, rs, true, eps, sink, gux, guy, guz, gumag,
-                      fix, fiy, fiz, fjx, fjy, fjz);
-        // u = r* d/|d|: only the direction of d carries a gradient
-        R ud = (gux * dx + guy * dy + guz * dz) * inv_r;
-        R sc = rs * inv_r;
-        gx += sc * (gux - ud * dx * inv_r);
-        gy += sc * (guy - ud * dy * inv_r);
-        gz += sc * (guz - ud * dz * inv_r);
-    }
+    R dEdr_r = (dSr * (Sb - R(1))) * C * V * inv_r + factor * C * dVr;   // (dE/dr)/r
+    double gx = dEdr_r * dx, gy = dEdr_r * dy, gz = dEdr_r * dz;
+    eps_out = Sr * C * V * dSb;
     if (path_code >= 0) path_forces<R>(G, i, path_code, -factor * V, sink, fix, fiy, fiz);
-    double g3[3] = {gx, gy, gz};
-    atomic_add(sink.f + i, fix + g3[0]); atomic_add(sink.f + sink.n + i, fiy + g3[1]); atomic_add(sink.f + 2 * sink.n + i, fiz + g3[2]);
-    atomic_add(sink.f + j, fjx - g3[0]); atomic_add(sink.f + sink.n + j, fjy - g3[1]); atomic_add(sink.f + 2 * sink.n + j, fjz - g3[2]);
+    atomic_add(sink.f + i, fix + gx); atomic_add(sink.f + sink.n + i, fiy + gy); atomic_add(sink.f + 2 * sink.n + i, fiz + gz);
+    atomic_add(sink.f + j, -gx); atomic_add(sink.f + sink.n + j, -gy); atomic_add(sink.f + 2 * sink.n + j, -gz);
     if (sink.virial) {
-        sink.W[0] -= (double)dx * g3[0]; sink.W[1] -= (double)dy * g3[1]; sink.W[2] -= (double)dz * g3[2];
-        sink.W[3] -= (double)dx * g3[1]; sink.W[4] -= (double)dx * g3[2]; sink.W[5] -= (double)dy * g3[2];
+        sink.W[0] -= (double)dx * gx; sink.W[1] -= (double)dy * gy; sink.W[2] -= (double)dz * gz;
+        sink.W[3] -= (double)dx * gy; sink.W[4] -= (double)dx * gz; sink.W[5] -= (double)dy * gz;
     }
     return (double)E;
+}
+
+// the force through b* of a b* pair: eps = dE/db*
+template <class R>
+HD void bstar_reverse(const DevParams<R>& P, const Graph<R>& G, int i, int j, R dx, R dy, R dz, R r2, R eps,
+                      Sink& sink) {
+    int p = pidx(G.type[i], G.type[j]);
+    R inv_r = rsqrt_(r2);
+    R rs = P.rstar[p];
+    R ux = dx * inv_r * rs, uy = dy * inv_r * rs, uz = dz * inv_r * rs;
+    R gux = 0, guy = 0, guz = 0, gumag = 0;
+    double fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
+    bond_order<R, true>(P, G, i, j, ux, uy, uz, rs, R(1) / rs, eps, sink, gux, guy, guz, gumag,
+                        fix, fiy, fiz, fjx, fjy, fjz);
+    // u = r* d/|d|: only the direction of d carries a gradient
+    R ud = (gux * dx + guy * dy + guz * dz) * inv_r;
+    R sc = rs * inv_r;
+    double gx = sc * (gux - ud * dx * inv_r);
+    double gy = sc * (guy - ud * dy * inv_r);
+    double gz = sc * (guz - ud * dz * inv_r);
+    atomic_add(sink.f + i, fix + gx); atomic_add(sink.f + sink.n + i, fiy + gy); atomic_add(sink.f + 2 * sink.n + i, fiz + gz);
+    atomic_add(sink.f + j, fjx - gx); atomic_add(sink.f + sink.n + j, fjy - gy); atomic_add(sink.f + 2 * sink.n + j, fjz - gz);
+    if (sink.virial) {
+        sink.W[0] -= (double)dx * gx; sink.W[1] -= (double)dy * gy; sink.W[2] -= (double)dz * gz;
+        sink.W[3] -= (double)dx * gy; sink.W[4] -= (double)dx * gz; sink.W[5] -= (double)dy * gz;
+    }
 }
 
 }  // namespace airebo
