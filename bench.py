@@ -57,6 +57,28 @@ def peaks_nominal():
     return f64, f32
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest of the ranks' values (the slowest rank's time); the value
+    itself when there is no process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(n_atoms: int, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job atom-steps/s of `world` independent replicas (weak scaling)."""
+    return world * n_atoms * steps / (max_ms * 1e-3)
+
+
+def config_of(workload: str, n: int, world: int) -> dict:
+    return {"workload": f"polyethylene {workload}: {n} atoms, 300 K, dt 0.5 fs, skin 1 A",
+            "global_batch": n * world, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "l2": "working set > L2 (lists ~3 GB at 1M atoms), no flush"}
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -150,7 +172,7 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    pos, types, box = inputs.workload(WORKLOAD)
+    pos, types, box = inputs.workload(args.workload)
     rates = []
     nth = None
     sample = ""
@@ -163,8 +185,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * len(types) / v, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "polyethylene 34x40x64 cells, 1,044,480 atoms, 300 K, dt 0.5 fs",
-                       "global_batch": len(types), "parallelism": "cpu"},
+            "config": config_of(args.workload, len(types), 1),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": nth, "kind": "oracle",
                              "sample": sample + " per step; value is the median over the steps",
                              "cpu": cpu_model()},
@@ -231,10 +252,7 @@ def run_ours(args):
             builds = ev.counters()["list_builds"] - builds0
             e_end = ev.nve(pos, vel, f, DT, 1).cpu().numpy()
             e_beg = e_start.cpu().numpy()
-            if dist:
-                tt = torch.tensor([ms], device=dev)
-                dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-                ms = tt.item()
+            ms = max_over_ranks(ms, dist, dev)
             results[name] = dict(ms=ms, kt=kt, clocks=ck, builds=builds, counters=ev.counters(),
                                  drift=(e_end[2] - e_beg[2]) / (args.steps + args.warmup + 1) / n,
                                  etot=float(e_end[2]))
@@ -264,8 +282,8 @@ def run_ours(args):
                "d2h_bytes_per_step": 3 * 24 * n + 32}
 
     r64 = results["fp64"]
-    value = ws * n * args.steps / (r64["ms"] * 1e-3)
-    mixed_value = ws * n * args.steps / (results["mixed"]["ms"] * 1e-3)
+    value = replica_throughput(n, args.steps, ws, r64["ms"])
+    mixed_value = replica_throughput(n, args.steps, ws, results["mixed"]["ms"])
     # roofline of the dominant kernel (FP64 path)
     kt = r64["kt"]
     dom = max((k for k in kt if k not in ("neighbor",)), key=lambda k: kt[k][0])
@@ -298,9 +316,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r64["ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"polyethylene {args.workload}: {n} atoms, 300 K, dt 0.5 fs, skin 1 A",
-                       "global_batch": n * ws, "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                       "l2": "working set > L2 (lists ~3 GB), no flush"},
+            "config": config_of(args.workload, n, ws),
             "mixed": {"value": mixed_value, "unit": UNIT, "ms_per_step": results["mixed"]["ms"] / args.steps,
                       "max_abs_dF_vs_fp64": df, "max_rel_dF_vs_fp64": df / fscale,
                       "drift_eV_per_atom_step": results["mixed"]["drift"],

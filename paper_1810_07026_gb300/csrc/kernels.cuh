@@ -158,29 +158,32 @@ constexpr int LJ_WARPS = LJ_THREADS / 32;
 constexpr int LJ_CHUNK = 8;
 
 // two compaction buffers per warp: 0 = inner pairs, 1 = pairs in the cut-off switch
-struct LjBuf {
+template <class R> struct LjBuf {
     double dx[2][64], dy[2][64], dz[2][64];
+    R r2[2][64];
     int jp[2][64];          // j | species pair << 30
 };
 
 template <class R>
-__device__ __forceinline__ void lj_batch(const DevParams<R>& P, LjBuf& B, int b, int lane, Sink& sink,
+__device__ __forceinline__ void lj_batch(const DevParams<R>& P, LjBuf<R>& B, int b, int lane, Sink& sink,
                                          double& fix, double& fiy, double& fiz, double& E) {
     int jp = B.jp[b][lane];
     int j = jp & 0x3fffffff, p = (unsigned)jp >> 30;
-    if (b == 0) lj_eval_inner<R>(P, p, j, B.dx[b][lane], B.dy[b][lane], B.dz[b][lane], sink, fix, fiy, fiz, E);
-    else lj_eval_switch<R>(P, p, j, B.dx[b][lane], B.dy[b][lane], B.dz[b][lane], sink, fix, fiy, fiz, E);
+    if (b == 0)
+        lj_eval_inner<R>(P, p, j, B.dx[b][lane], B.dy[b][lane], B.dz[b][lane], B.r2[b][lane], sink, fix, fiy, fiz, E);
+    else
+        lj_eval_switch<R>(P, p, j, B.dx[b][lane], B.dy[b][lane], B.dz[b][lane], B.r2[b][lane], sink, fix, fiy, fiz, E);
 }
 
 template <class R>
 __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
     const DevParams<R>& P = *a.P;
     __shared__ double shift[3][9];                // image shifts S L for S in [-4, 4]
-    __shared__ LjBuf bufs[LJ_WARPS];
+    __shared__ LjBuf<R> bufs[LJ_WARPS];
     if (threadIdx.x < 27) shift[threadIdx.x / 9][threadIdx.x % 9] = (double)((int)(threadIdx.x % 9) - 4) * a.L[threadIdx.x / 9];
     __syncthreads();
     int lane = threadIdx.x & 31;
-    LjBuf& B = bufs[threadIdx.x >> 5];
+    LjBuf<R>& B = bufs[threadIdx.x >> 5];
     unsigned lt = (1u << lane) - 1u;
     Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}};
     double E = 0;
@@ -208,6 +211,7 @@ __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
             int e = base + lane;
             int st = 0, j = 0, p = 0;
             double dx = 0, dy = 0, dz = 0;
+            R r2 = R(0);
             if (e < ne) {
                 int2 ent = row[e];
                 j = ent.x;
@@ -223,7 +227,7 @@ __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
                     }
                 }
                 R rx = (R)dx, ry = (R)dy, rz = (R)dz;
-                R r2 = rx * rx + ry * ry + rz * rz;
+                r2 = rx * rx + ry * ry + rz * rz;
                 p = pidx(ti, a.G.type[j]);
                 evaluated += lt_nonneg(r2, P.rc2[p]);
                 R C;
@@ -241,7 +245,7 @@ __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
                 unsigned m = __ballot_sync(0xffffffffu, st == want);
                 if (st == want) {
                     int s = cnt[b] + __popc(m & lt);
-                    B.dx[b][s] = dx; B.dy[b][s] = dy; B.dz[b][s] = dz; B.jp[b][s] = j | (p << 30);
+                    B.dx[b][s] = dx; B.dy[b][s] = dy; B.dz[b][s] = dz; B.r2[b][s] = r2; B.jp[b][s] = j | (p << 30);
                 }
                 cnt[b] += __popc(m);
                 __syncwarp();
@@ -251,7 +255,7 @@ __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
                     if (lane < cnt[b] - 32) {
                         int s = 32 + lane;
                         B.dx[b][lane] = B.dx[b][s]; B.dy[b][lane] = B.dy[b][s]; B.dz[b][lane] = B.dz[b][s];
-                        B.jp[b][lane] = B.jp[b][s];
+                        B.r2[b][lane] = B.r2[b][s]; B.jp[b][lane] = B.jp[b][s];
                     }
                     cnt[b] -= 32;
                     __syncwarp();

@@ -50,6 +50,14 @@ HD void atomic_add(double* p, double v) {
 }
 
 // ------------------------------------------------------------------ math wrappers
+// -x by flipping the sign bit: an integer op, not an FP64 instruction
+HD double neg_(double x) {
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
+#else
+    return -x;
+#endif
+}
 HD double rsqrt_(double x) {
 #ifdef __CUDA_ARCH__
     return rsqrt(x);
@@ -285,7 +293,7 @@ struct Sink {
     bool virial;
     double W[6];
     HD void pair(int a, int b, double vx, double vy, double vz, double gx, double gy, double gz) {
-        atomic_add(f + b, -gx); atomic_add(f + n + b, -gy); atomic_add(f + 2 * n + b, -gz);
+        atomic_add(f + b, neg_(gx)); atomic_add(f + n + b, neg_(gy)); atomic_add(f + 2 * n + b, neg_(gz));
         atomic_add(f + a, gx); atomic_add(f + n + a, gy); atomic_add(f + 2 * n + a, gz);
         if (virial) {
             W[0] -= vx * gx; W[1] -= vy * gy; W[2] -= vz * gz;
@@ -295,7 +303,7 @@ struct Sink {
     // gradient on the vector from a to b, where the force on a is kept by the caller
     HD void half(int b, double vx, double vy, double vz, double gx, double gy, double gz,
                  double& fax, double& fay, double& faz) {
-        atomic_add(f + b, -gx); atomic_add(f + n + b, -gy); atomic_add(f + 2 * n + b, -gz);
+        atomic_add(f + b, neg_(gx)); atomic_add(f + n + b, neg_(gy)); atomic_add(f + 2 * n + b, neg_(gz));
         fax += gx; fay += gy; faz += gz;
         if (virial) {
             W[0] -= vx * gx; W[1] -= vy * gy; W[2] -= vz * gz;
@@ -870,10 +878,9 @@ HD void lj_eval(const DevParams<R>& P, const Graph<R>& G, int i, int p, int j, d
 // The common LJ pair: C = 1, no path, r inside 2.7 sigma (no cut-off switch):
 // V and (dV/dr)/r from 1/r^2 alone.
 template <class R>
-HD void lj_eval_inner(const DevParams<R>& P, int p, int j, double dx, double dy, double dz, Sink& sink,
+HD void lj_eval_inner(const DevParams<R>& P, int p, int j, double dx, double dy, double dz, R r2, Sink& sink,
                       double& fix, double& fiy, double& fiz, double& E) {
-    R rx = (R)dx, ry = (R)dy, rz = (R)dz;
-    R ir2 = rcp_(rx * rx + ry * ry + rz * rz);
+    R ir2 = rcp_(r2);
     R s2 = P.sig2[p] * ir2;
     R s6 = s2 * s2 * s2;
     R e4 = P.eps4[p];
@@ -884,10 +891,8 @@ HD void lj_eval_inner(const DevParams<R>& P, int p, int j, double dx, double dy,
 
 // C = 1, no path, r inside the cut-off switch.
 template <class R>
-HD void lj_eval_switch(const DevParams<R>& P, int p, int j, double dx, double dy, double dz, Sink& sink,
+HD void lj_eval_switch(const DevParams<R>& P, int p, int j, double dx, double dy, double dz, R r2, Sink& sink,
                        double& fix, double& fiy, double& fiz, double& E) {
-    R rx = (R)dx, ry = (R)dy, rz = (R)dz;
-    R r2 = rx * rx + ry * ry + rz * rz;
     R ir = rsqrt_(r2);
     R ir2 = ir * ir;
     R s2 = P.sig2[p] * ir2;

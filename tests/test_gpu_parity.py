@@ -266,3 +266,27 @@ def test_nve_energy_conservation(A, param_text):
         tot.append(ev.nve(p, v, f, 0.5, 5)[2].item())
     tot = np.array(tot)
     assert (tot.max() - tot.min()) < 3e-4 * abs(tot[0])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_nve_pe32k_1000_steps_energy(A, param_text, precision):
+    """1,000 velocity-Verlet steps of 0.5 fs on the 32,640-atom PE at 300 K:
+    the total energy fluctuates (Verlet) but does not drift."""
+    pos, types, box = inputs.workload("pe32k")
+    vel = inputs.velocities(types, 300.0, seed=2)
+    n = len(types)
+    ev = A.Airebo(param_text, precision=precision)
+    p = torch.tensor(pos, device="cuda")
+    v = torch.tensor(vel, device="cuda")
+    ev.neighbor(p, torch.tensor(types, device="cuda"), box)
+    f, _, _ = ev.compute(p)
+    tot = []
+    for _ in range(20):
+        e4 = ev.nve(p, v, f, 0.5, 50).cpu().numpy()
+        tot.append(e4[2] / n)
+    tot = np.array(tot)
+    slope = np.polyfit(np.arange(len(tot)) * 50.0, tot, 1)[0]        # eV/atom/step
+    print(f"precision {precision}: E/atom spread {tot.max() - tot.min():.3e}, drift {slope:.3e} eV/atom/step, "
+          f"list builds {e4[3]:.0f}")
+    assert tot.max() - tot.min() < 2e-3
+    assert abs(slope) < 5e-7
