@@ -214,9 +214,10 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     results = {}
     forces = {}
-    for prec, name in ((A.FP64, "fp64"), (A.MIXED, "mixed")):
+    runs = ((A.FP64, "fp64", True), (A.MIXED, "mixed", True), (A.FP64, "rebo_only", False))
+    for prec, name, full in runs:
         with torch.cuda.stream(stream):
-            ev = A.Airebo(params, precision=prec, stream=stream)
+            ev = A.Airebo(params, precision=prec, stream=stream, lj=full, torsion=full)
             pos = torch.tensor(pos0, device=dev)
             vel = torch.tensor(vel0, device=dev)
             t = torch.tensor(types, device=dev)
@@ -323,6 +324,10 @@ def run_ours(args):
                       "kernel_ms": {k: v[0] / max(1, v[1]) for k, v in mix_kt.items()},
                       "lj_achieved_fp32_frac": None if not mlj_n else
                       (flops_lj / (mlj_ms * 1e-3 / mlj_n) / 1e12) / peak32_nom},
+            "rebo_only": {"value": replica_throughput(n, args.steps, ws, results["rebo_only"]["ms"]),
+                          "unit": UNIT, "ms_per_step": results["rebo_only"]["ms"] / args.steps,
+                          "dtype": "f64", "terms": "REBO (Alg. 1) only, no LJ or torsion, no long list",
+                          "kernel_ms": {k: v[0] / max(1, v[1]) for k, v in results["rebo_only"]["kt"].items()}},
             "drift_eV_per_atom_step": r64["drift"],
             "list_builds_in_timed_region": r64["builds"],
             "kernel_ms": {k: v[0] / max(1, v[1]) for k, v in kt.items()},

@@ -175,6 +175,25 @@ airebo_status airebo_kernel_times(airebo_handle h, double* ms, int64_t* launches
 airebo_status airebo_alu_peak(int precision, double* tflops);
 
 /*
+ * Energy and forces as airebo_compute, plus the gradient of the energy with
+ * respect to the parameters of the inter-molecular term (Sec. 2.1.2):
+ * h_grad6 (host double[6]) = dE/d epsilon[CC, CH, HH] (lj.epsilon, or
+ * morse.epsilon for the Morse form), dE/d sigma[CC, CH, HH] (lj.sigma, which
+ * also sets the switch and cut-off radii).  Slower than airebo_compute: every
+ * LJ pair takes the general path.  Synchronises.
+ */
+airebo_status airebo_param_grad(airebo_handle h, const double* d_pos, double* d_force, double* d_energy4,
+                                double* h_grad6);
+
+/*
+ * Replace epsilon[3] (lj.epsilon or morse.epsilon) and/or sigma[3] (lj.sigma)
+ * of the inter-molecular term; either pointer may be NULL.  Changing sigma
+ * moves the LJ cut-off, so the next call must be airebo_neighbor (compute
+ * returns AIREBO_ERR_STATE until then).  Synchronises.
+ */
+airebo_status airebo_set_lj_params(airebo_handle h, const double* eps3, const double* sigma3);
+
+/*
  * Rebuild check that allocates no device memory (the paper has no
  * counterpart: it is a service for callers that cannot call cudaMalloc, such
  * as code running inside a framework that owns all device memory, or code

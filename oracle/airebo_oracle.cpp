@@ -104,6 +104,8 @@ struct Params {
     double sigma[3], eps[3], ljcut, ljsw, SrLo, SrHi;
     double bmin[3], bmax[3], rstar[3];
     double teps[3];
+    int inter_kind = 0;                 // 0: Lennard-Jones (AIREBO), 1: Morse (AIREBO-M)
+    double meps[3], malpha[3], mre[3];  // Morse well depth, stiffness, minimum
 };
 
 const std::vector<double>& need(const Params& p, const char* k, size_t n) {
@@ -152,6 +154,10 @@ bool parse_params(const char* text, Params& p) {
         p.SrLo = need(p, "lj.Sr_range", 2)[0]; p.SrHi = need(p, "lj.Sr_range", 2)[1];
         cp3("bstar.bmin", p.bmin); cp3("bstar.bmax", p.bmax); cp3("bstar.rstar", p.rstar);
         cp3("tors.epsilon", p.teps);
+        auto it = p.raw.find("inter.kind");
+        p.inter_kind = (it != p.raw.end() && it->second.size() == 1) ? (int)it->second[0] : 0;
+        if (p.inter_kind == 1) { cp3("morse.epsilon", p.meps); cp3("morse.alpha", p.malpha); cp3("morse.re", p.mre); }
+        if (p.inter_kind != 0 && p.inter_kind != 1) return false;
     } catch (...) { return false; }
     return true;
 }
@@ -661,7 +667,12 @@ struct Oracle {
         double sg = P.sigma[p];
         V sr = sg / r;
         V sr2 = sr * sr, sr6 = sr2 * sr2 * sr2;
-        V VLJ = 4.0 * P.eps[p] * (sr6 * sr6 - sr6) * Sout((r - P.ljsw * sg) / ((P.ljcut - P.ljsw) * sg));
+        V VLJ = 4.0 * P.eps[p] * (sr6 * sr6 - sr6);
+        if (P.inter_kind == 1) {      // AIREBO-M: Morse in place of Lennard-Jones (Sec. 2.1.2)
+            V e = vexp(-P.malpha[p] * (r - P.mre[p]));
+            VLJ = P.meps[p] * (e * e - 2.0 * e);
+        }
+        VLJ = VLJ * Sout((r - P.ljsw * sg) / ((P.ljcut - P.ljsw) * sg));
         V Sr = S((r - P.SrLo * sg) / ((P.SrHi - P.SrLo) * sg));
         V factor = cst(1.0);
         if (Sr.v > 0.0) {

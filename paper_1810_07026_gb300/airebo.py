@@ -61,6 +61,8 @@ def lib():
             "airebo_set_timing": (I, [P, I]),
             "airebo_kernel_times": (I, [P, P, P]),
             "airebo_alu_peak": (I, [I, P]),
+            "airebo_param_grad": (I, [P, P, P, P, P]),
+            "airebo_set_lj_params": (I, [P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -155,6 +157,23 @@ class Airebo:
         self._check(lib().airebo_compute(self._h, _ptr(pos), _ptr(force), _ptr(e4), _ptr(w6)))
         return force, e4, w6
 
+    def param_grad(self, pos, force=None):
+        """Forces, energies and dE/d(eps[3], sigma[3]) of the inter-molecular term."""
+        torch = self._torch
+        pos = self._dev(pos, torch.float64)
+        if force is None:
+            force = torch.empty_like(pos)
+        e4 = torch.empty(4, dtype=torch.float64, device=self.device)
+        g = np.zeros(6)
+        self._check(lib().airebo_param_grad(self._h, _ptr(pos), _ptr(force), _ptr(e4), _np(g)))
+        return force, e4, g
+
+    def set_lj_params(self, eps=None, sigma=None):
+        """Replace eps[3] and/or sigma[3]; a new sigma needs a new neighbor() call."""
+        e = None if eps is None else np.ascontiguousarray(np.asarray(eps, dtype=np.float64).reshape(3))
+        sg = None if sigma is None else np.ascontiguousarray(np.asarray(sigma, dtype=np.float64).reshape(3))
+        self._check(lib().airebo_set_lj_params(self._h, _np(e), _np(sg)))
+
     def needs_rebuild(self, pos) -> bool:
         flag = C.c_int(0)
         self._check(lib().airebo_needs_rebuild(self._h, _ptr(pos), C.byref(flag)))
@@ -210,6 +229,48 @@ class Airebo:
         nl = np.zeros(8, dtype=np.int64)
         self._check(lib().airebo_kernel_times(self._h, _np(ms), _np(nl)))
         return {k: (float(ms[i]), int(nl[i])) for i, k in enumerate(KERNELS)}
+
+
+class AireboEnergy:
+    """Differentiable AIREBO energy: ``E = AireboEnergy.apply(pos, eps, sigma, evaluator)``.
+
+    The backward pass is the library's own force computation (F = -dE/dx),
+    and, when eps or sigma (the three per-species-pair values of the
+    inter-molecular term) require gradients, its hand-written dE/d(eps, sigma).
+    eps and sigma are pushed to the evaluator before the evaluation; the
+    neighbour lists are rebuilt when needed."""
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, pos, eps, sigma, evaluator):
+        if cls._fn is None:
+            import torch
+
+            class _F(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, pos, eps, sigma, ev):
+                    e_np = eps.detach().cpu().numpy()
+                    s_np = sigma.detach().cpu().numpy()
+                    ev.set_lj_params(e_np, s_np)
+                    ev.neighbor(pos.detach(), ev._types, ev.box)
+                    need_p = ctx.needs_input_grad[1] or ctx.needs_input_grad[2]
+                    if need_p:
+                        f, e4, g = ev.param_grad(pos.detach())
+                        gt = torch.tensor(g, dtype=torch.float64, device=pos.device)
+                    else:
+                        f, e4, _ = ev.compute(pos.detach())
+                        gt = torch.zeros(6, dtype=torch.float64, device=pos.device)
+                    ctx.save_for_backward(f, gt)
+                    return e4[0].clone()
+
+                @staticmethod
+                def backward(ctx, gE):
+                    f, gt = ctx.saved_tensors
+                    return -f * gE, gt[:3] * gE, gt[3:] * gE, None
+
+            cls._fn = _F
+        return cls._fn.apply(pos, eps, sigma, evaluator)
 
 
 def _addr(a):

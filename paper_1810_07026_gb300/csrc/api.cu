@@ -148,6 +148,8 @@ bool quintic_coeffs(const std::vector<double>& kn, const std::vector<double>& d,
 struct Scalars {
     double Dmin[3], Dmax[3], Q[3], alpha[3], A[3], B[3][3], beta[3][3], rho[3];
     double lam, gN[2], Fx[2], guard[2], sigma[3], eps[3], ljcut, ljsw, Sr[2], bmin[3], bmax[3], rstar[3], teps[3];
+    int kind = 0;
+    double meps[3] = {0, 0, 0}, malpha[3] = {0, 0, 0}, mre[3] = {0, 0, 0};
     std::vector<double> gC1k, gC1d, gC2k, gC2d, gHk, gHd;
     std::vector<double> P[3], F[3], T;
 };
@@ -177,6 +179,13 @@ bool load_scalars(const HostParams& hp, Scalars& s, std::string& err) {
           hp.get("piRC.CC", 1800, s.F[0], err) && hp.get("piRC.CH", 1800, s.F[1], err) &&
           hp.get("piRC.HH", 1800, s.F[2], err) && hp.get("Tij.CC", 1800, s.T, err)))
         return false;
+    {
+        auto it = hp.v.find("inter.kind");
+        s.kind = (it != hp.v.end() && it->second.size() == 1) ? (int)it->second[0] : 0;
+        if (s.kind != 0 && s.kind != 1) { err = "inter.kind must be 0 (Lennard-Jones) or 1 (Morse)"; return false; }
+        if (s.kind == 1 && !(g3("morse.epsilon", s.meps) && g3("morse.alpha", s.malpha) && g3("morse.re", s.mre)))
+            return false;
+    }
     for (int p = 0; p < 3; p++) {
         if (!(s.Dmax[p] > s.Dmin[p] && s.Dmin[p] > 0)) { err = "Dmax must exceed Dmin > 0"; return false; }
         if (!(s.sigma[p] > 0 && s.bmax[p] > s.bmin[p] && s.rstar[p] > 0)) { err = "bad LJ/b* parameter"; return false; }
@@ -215,7 +224,11 @@ bool fill_params(const Scalars& s, DevParams<R>& P, std::vector<R>& tables, std:
         P.binv[p] = (R)(1.0 / (s.bmax[p] - s.bmin[p]));
         P.rstar[p] = (R)s.rstar[p];
         P.teps[p] = (R)s.teps[p];
+        P.meps[p] = (R)s.meps[p];
+        P.malpha[p] = (R)s.malpha[p];
+        P.mre[p] = (R)s.mre[p];
     }
+    P.kind = s.kind;
     P.rhoH[0] = (R)s.rho[1];   // H centre, C neighbour: rho_CH
     P.rhoH[1] = (R)s.rho[2];   // H centre, H neighbour: rho_HH
     P.lam = (R)s.lam;
@@ -282,6 +295,7 @@ struct airebo_ctx {
     int* derr = nullptr;                 // 8 ints
     unsigned long long* maxd2 = nullptr;
     double* ke = nullptr;
+    double* pg = nullptr;                // parameter gradients (6)
     // pinned mirrors
     int* h_err = nullptr;
     unsigned long long* h_u64 = nullptr;
@@ -401,14 +415,16 @@ airebo_status do_neighbor(airebo_handle h, const double* d_pos) {
     const Scalars& s = h->sc;
     double rlj = 0, rim = 0;
     NeighborArgs a{};
+    bool with_lj = h->opt.enable_lj != 0;
     for (int p = 0; p < 3; p++) {
-        double rc = s.ljcut * s.sigma[p] + h->opt.skin;
         double ri = s.Dmax[p] + h->opt.skin;
+        double rc = with_lj ? s.ljcut * s.sigma[p] + h->opt.skin : ri;   // REBO only: no long list
         rlj = std::max(rlj, rc);
         rim = std::max(rim, ri);
         a.lj_rc[p] = (float)(rc + 2e-3);
         a.im_rc[p] = (float)(ri + 2e-3);
     }
+    a.with_lj = with_lj;
     rlj += 2e-3;
     int ncell = 1;
     for (int d = 0; d < 3; d++) {
@@ -423,6 +439,7 @@ airebo_status do_neighbor(airebo_handle h, const double* d_pos) {
         CK(realloc_dev(h->cell_fill, ncell));
         h->ncell_alloc = ncell;
     }
+    if (!with_lj) h->lj_cap = 1;
     if (h->lj_cap == 0) {
         double vol = h->L[0] * h->L[1] * h->L[2];
         double rho = h->n / vol;
@@ -503,7 +520,7 @@ template <class R> StepArgs<R> make_args(airebo_handle h, Precision<R>& pr, cons
 
 template <class R>
 airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos, double* d_force, double* d_e4,
-                         double* d_w6) {
+                         double* d_w6, double* d_pgrad = nullptr) {
     for (int attempt = 0; attempt < 4; attempt++) {
         cudaStream_t s = h->stream;
         if (h->n) CK(cudaMemsetAsync(d_force, 0, sizeof(double) * 3 * h->n, s));
@@ -512,6 +529,8 @@ airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos,
         CK(cudaMemsetAsync(h->counts, 0, sizeof(int) * 8, s));
         CK(cudaMemsetAsync(h->derr, 0, sizeof(int) * 8, s));
         StepArgs<R> a = make_args<R>(h, pr, d_pos, d_force, d_w6 != nullptr);
+        a.pgrad = d_pgrad;
+        if (d_pgrad) CK(cudaMemsetAsync(d_pgrad, 0, sizeof(double) * 6, s));
         launch_compute<R>(a, s, h->num_sms, h->timing ? h->ev : nullptr);
         CK(cudaGetLastError());
         if (d_e4 || d_w6) k_finalize<<<1, 32, 0, s>>>(h->acc, d_e4, d_w6);
@@ -549,11 +568,12 @@ airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos,
     return fail(h, AIREBO_ERR_CAPACITY, "scratch capacity did not converge");
 }
 
-airebo_status compute_any(airebo_handle h, const double* d_pos, double* d_force, double* d_e4, double* d_w6) {
+airebo_status compute_any(airebo_handle h, const double* d_pos, double* d_force, double* d_e4, double* d_w6,
+                          double* d_pgrad = nullptr) {
     if (!h->built) return fail(h, AIREBO_ERR_STATE, "airebo_compute before airebo_neighbor");
     CK(cudaSetDevice(h->device));
-    if (h->opt.precision == AIREBO_MIXED) return do_compute<float>(h, h->p32, d_pos, d_force, d_e4, d_w6);
-    return do_compute<double>(h, h->p64, d_pos, d_force, d_e4, d_w6);
+    if (h->opt.precision == AIREBO_MIXED) return do_compute<float>(h, h->p32, d_pos, d_force, d_e4, d_w6, d_pgrad);
+    return do_compute<double>(h, h->p64, d_pos, d_force, d_e4, d_w6, d_pgrad);
 }
 
 airebo_status check_rebuild(airebo_handle h, const double* d_pos, int* flag) {
@@ -637,6 +657,7 @@ void airebo_destroy(airebo_handle h) {
     if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
     free_prec(h->p64);
     free_prec(h->p32);
+    if (h->pg) cudaFree(h->pg);
     void* ps[] = {h->types, h->cell_of, h->cell_count, h->cell_start, h->cell_fill, h->spos, h->swrap, h->lj, h->lj_cnt,
                   h->im, h->im_cnt, h->xref, h->bonds, h->ccbonds, h->bq, h->bq2, h->bq2_eps, h->counts, h->acc, h->counters, h->derr, h->maxd2, h->ke,
                   h->hpos, h->hvel, h->hforce, h->he4, h->hw6};
@@ -815,6 +836,45 @@ airebo_status airebo_counters(airebo_handle h, int64_t* out8) {
     out8[6] = h->lj_cap;
     int mc = h->opt.precision == AIREBO_MIXED ? h->p32.b.map_cap : h->p64.b.map_cap;
     out8[4] = mc;
+    return AIREBO_OK;
+}
+
+airebo_status airebo_param_grad(airebo_handle h, const double* d_pos, double* d_force, double* d_energy4,
+                                double* h_grad6) {
+    if (!h || !h_grad6) return AIREBO_ERR_ARG;
+    if (h->n > 0 && (!d_pos || !d_force)) return fail(h, AIREBO_ERR_ARG, "null position or force pointer");
+    if (!h->built) return fail(h, AIREBO_ERR_STATE, "airebo_param_grad before airebo_neighbor");
+    CK(cudaSetDevice(h->device));
+    if (!h->pg) CK(realloc_dev(h->pg, 6));
+    airebo_status st = compute_any(h, d_pos, d_force, d_energy4, nullptr, h->pg);
+    if (st) return st;
+    CK(cudaMemcpyAsync(h->h_acc, h->pg, sizeof(double) * 6, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < 6; k++) h_grad6[k] = h->h_acc[k];
+    return AIREBO_OK;
+}
+
+airebo_status airebo_set_lj_params(airebo_handle h, const double* eps3, const double* sigma3) {
+    if (!h || (!eps3 && !sigma3)) return AIREBO_ERR_ARG;
+    Scalars s = h->sc;
+    bool sigma_changed = false;
+    for (int p = 0; p < 3; p++) {
+        if (eps3) {
+            if (!(eps3[p] > 0)) return fail(h, AIREBO_ERR_ARG, "epsilon must be positive");
+            if (s.kind == 0) s.eps[p] = eps3[p]; else s.meps[p] = eps3[p];
+        }
+        if (sigma3) {
+            if (!(sigma3[p] > 0)) return fail(h, AIREBO_ERR_ARG, "sigma must be positive");
+            sigma_changed |= sigma3[p] != s.sigma[p];
+            s.sigma[p] = sigma3[p];
+        }
+    }
+    CK(cudaSetDevice(h->device));
+    CK(cudaStreamSynchronize(h->stream));
+    h->sc = s;
+    airebo_status st = h->opt.precision == AIREBO_MIXED ? upload_params<float>(h, h->p32) : upload_params<double>(h, h->p64);
+    if (st) return st;
+    if (sigma_changed) h->built = false;          // the LJ cut-off moved: the lists must be rebuilt
     return AIREBO_OK;
 }
 

@@ -44,6 +44,7 @@ template <class R> struct StepArgs {
     int* err;             // [4]: max short-list count, map overflow, queue overflow, nonfinite
     bool virial;
     bool rebo, lj_on, torsion;
+    double* pgrad;        // nullable: dE/d eps[3], dE/d sigma[3] of the inter-molecular term
 };
 
 enum { ERR_SHORT = 0, ERR_MAP = 1, ERR_QUEUE = 2, ERR_NONFINITE = 3 };
@@ -63,6 +64,7 @@ struct NeighborArgs {
     double cell_w[3];
     float lj_rc[3];       // (3 sigma + skin + margin) per pair, squared below
     float im_rc[3];       // (Dmax + skin + margin)
+    bool with_lj;         // build the LJ half list (off for REBO-only runs)
     int* cell_of; int* cell_count; int* cell_start; int* cell_fill;
     float4* spos; char4* swrap;
     int2* lj; int* lj_cnt; int lj_cap;

@@ -43,6 +43,24 @@ __device__ void block_accumulate(double e, const double* W, bool virial, double*
     }
 }
 
+// block-wide sum of the parameter-gradient accumulators into pg[6]
+template <int NT>
+__device__ void block_accumulate_g(const double* G, double* pg) {
+    __shared__ double red[NT / 32][6];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double g[6];
+    for (int k = 0; k < 6; k++) g[k] = warp_sum(G[k]);
+    __syncthreads();
+    if (lane == 0)
+        for (int k = 0; k < 6; k++) red[wid][k] = g[k];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double s = 0;
+        for (int q = 0; q < NT / 32; q++) s += red[q][threadIdx.x];
+        atomicAdd(pg + threadIdx.x, s);
+    }
+}
+
 __device__ __forceinline__ void load_disp(const double* pos, int n, const double* L, int i, int j, int img,
                                           double& dx, double& dy, double& dz) {
     dx = pos[j] + img_x(img) * L[0] - pos[i];
@@ -110,7 +128,7 @@ __global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
 template <class R>
 __global__ void __launch_bounds__(128) k_rebo(StepArgs<R> a) {
     const DevParams<R>& P = *a.P;
-    Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}};
+    Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}, a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
     double E = 0;
     int ncc = min(*a.nccbonds, a.bond_cap);
     int nb = ncc + min(*a.nbonds, a.bond_cap);
@@ -125,7 +143,7 @@ __global__ void __launch_bounds__(128) k_rebo(StepArgs<R> a) {
 template <class R>
 __global__ void __launch_bounds__(128) k_torsion(StepArgs<R> a) {
     const DevParams<R>& P = *a.P;
-    Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}};
+    Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}, a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
     double E = 0;
     int nb = *a.nccbonds;
     if (nb > a.bond_cap) nb = a.bond_cap;
@@ -185,7 +203,7 @@ __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
     int lane = threadIdx.x & 31;
     LjBuf<R>& B = bufs[threadIdx.x >> 5];
     unsigned lt = (1u << lane) - 1u;
-    Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}};
+    Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}, a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
     double E = 0;
     unsigned evaluated = 0;
     int n = a.n;
@@ -232,7 +250,7 @@ __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
                 evaluated += lt_nonneg(r2, P.rc2[p]);
                 R C;
                 int code, mi;
-                st = lj_classify<R>(P, a.M, i, p, j, img, r2, C, code, mi);
+                st = lj_classify<R>(P, a.M, i, p, j, img, r2, C, code, mi, a.pgrad != nullptr);
                 if (st == 2) {
                     int q = atomicAdd(a.nbq + p, 1);
                     if (q < a.bq_cap) a.bq[(size_t)p * a.bq_cap + q] = make_int4(i, e, mi, 0);
@@ -240,6 +258,7 @@ __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
                     lj_eval<R>(P, a.G, i, p, j, dx, dy, dz, C, code, sink, fix, fiy, fiz, E);
                 }
             }
+#pragma unroll
             for (int b = 0; b < 2; b++) {
                 int want = b == 0 ? 1 : 3;
                 unsigned m = __ballot_sync(0xffffffffu, st == want);
@@ -262,6 +281,7 @@ __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
                 }
             }
         }
+#pragma unroll
         for (int b = 0; b < 2; b++)
             if (lane < cnt[b]) lj_batch<R>(P, B, b, lane, sink, fix, fiy, fiz, E);
         __syncwarp();
@@ -273,6 +293,7 @@ __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
     unsigned ev = __reduce_add_sync(0xffffffffu, evaluated);
     if (lane == 0 && ev) atomicAdd(a.counters + CNT_LJ, (unsigned long long)ev);
     block_accumulate<LJ_THREADS>(E, sink.W, a.virial, a.acc + 1, a.acc + 3);
+    if (a.pgrad) block_accumulate_g<LJ_THREADS>(sink.G, a.pgrad);
 }
 
 // ------------------------------------------------------------------ b* pairs
@@ -281,7 +302,7 @@ __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
 template <class R>
 __global__ void __launch_bounds__(128) k_bstar(StepArgs<R> a) {
     const DevParams<R>& P = *a.P;
-    Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}};
+    Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}, a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
     double E = 0;
     int n0 = min(a.nbq[0], a.bq_cap), n1 = min(a.nbq[1], a.bq_cap), n2 = min(a.nbq[2], a.bq_cap);
     int nq = n0 + n1 + n2;
@@ -310,13 +331,14 @@ __global__ void __launch_bounds__(128) k_bstar(StepArgs<R> a) {
         }
     }
     block_accumulate<128>(E, sink.W, a.virial, a.acc + 1, a.acc + 3);
+    if (a.pgrad) block_accumulate_g<128>(sink.G, a.pgrad);
 }
 
 // Phase 2: the force through b* for the pairs of the second queue.
 template <class R>
 __global__ void __launch_bounds__(128) k_bstar_rev(StepArgs<R> a) {
     const DevParams<R>& P = *a.P;
-    Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}};
+    Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}, a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
     int nq = min(*a.nbq2, 3 * a.bq_cap);
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nq; s += gridDim.x * blockDim.x) {
         int4 q = a.bq[a.bq2[s]];

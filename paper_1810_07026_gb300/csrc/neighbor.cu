@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(128) k_build(NeighborArgs a, const int* cell_s
                         nim++;
                     }
                     bool pos = Sx > 0 || (Sx == 0 && (Sy > 0 || (Sy == 0 && Sz > 0)));
-                    if (j > i || (self && pos)) {
+                    if (a.with_lj && (j > i || (self && pos))) {
                         if (nlj < a.lj_cap) ljrow[nlj] = make_int2(j, img);
                         nlj++;
                     }

@@ -120,6 +120,8 @@ template <class R> struct DevParams {
     R sigma[3], sig2[3], eps4[3], rc2[3], swlo[3], swlo2[3], swinv[3], Srlo[3], Srhi[3], Srhi2[3], Srinv[3];
     R bmin[3], binv[3], rstar[3];
     R teps[3];
+    int kind;                        // inter-molecular term: 0 Lennard-Jones (AIREBO), 1 Morse (AIREBO-M)
+    R meps[3], malpha[3], mre[3];    // Morse well depth, stiffness, minimum
     R rpath2;                        // no C_ij path reaches beyond sqrt(rpath2)
     const R* Ptab;                   // 3 tables (CC, CH, HC) x 16 cells x 16 coefficients
     const R* Ftab;                   // 3 tables (CC, CH, HH) x 128 cells x 64 coefficients
@@ -234,10 +236,10 @@ template <class R, bool D = true> HD R bicubic(const R* tab, R x, R y, R& fx, R&
 }
 
 // tricubic on [0,4]x[0,4]x[1,9], 64 power-basis coefficients per cell
-template <class R> HD int tri_cell_index(R& x, R& y, R& z, bool* cl, R& tx, R& ty, R& tz) {
-    clamp_arg<R>(x, R(0), R(4), cl[0]);
-    clamp_arg<R>(y, R(0), R(4), cl[1]);
-    clamp_arg<R>(z, R(1), R(9), cl[2]);
+template <class R> HD int tri_cell_index(R& x, R& y, R& z, bool& clx, bool& cly, bool& clz, R& tx, R& ty, R& tz) {
+    clamp_arg<R>(x, R(0), R(4), clx);
+    clamp_arg<R>(y, R(0), R(4), cly);
+    clamp_arg<R>(z, R(1), R(9), clz);
     int ix = clamp_cell((int)floor(x), 3);
     int iy = clamp_cell((int)floor(y), 3);
     int iz = clamp_cell((int)floor(z - R(1)), 7);
@@ -245,7 +247,7 @@ template <class R> HD int tri_cell_index(R& x, R& y, R& z, bool* cl, R& tx, R& t
     return (ix * 4 + iy) * 8 + iz;
 }
 template <class R, bool D = true>
-HD R tricubic_cell(const R* a, R tx, R ty, R tz, const bool* cl, R& fx, R& fy, R& fz) {
+HD R tricubic_cell(const R* a, R tx, R ty, R tz, bool clx, bool cly, bool clz, R& fx, R& fy, R& fz) {
     R f = 0, dx = 0, dy = 0, dz = 0;
     for (int p = 3; p >= 0; p--) {
         R cp = 0, cpy = 0, cpz = 0;
@@ -266,9 +268,9 @@ HD R tricubic_cell(const R* a, R tx, R ty, R tz, const bool* cl, R& fx, R& fy, R
         }
         f = f * tx + cp;
     }
-    fx = (D && !cl[0]) ? dx : R(0);
-    fy = (D && !cl[1]) ? dy : R(0);
-    fz = (D && !cl[2]) ? dz : R(0);
+    fx = (D && !clx) ? dx : R(0);
+    fy = (D && !cly) ? dy : R(0);
+    fz = (D && !clz) ? dz : R(0);
     return f;
 }
 
@@ -292,6 +294,8 @@ struct Sink {
     int n;
     bool virial;
     double W[6];
+    bool pgrad;         // accumulate dE/d(epsilon) and dE/d(sigma) of the inter-molecular term
+    double G[6];        // dE/d eps[CC, CH, HH], dE/d sigma[CC, CH, HH]
     HD void pair(int a, int b, double vx, double vy, double vz, double gx, double gy, double gz) {
         atomic_add(f + b, neg_(gx)); atomic_add(f + n + b, neg_(gy)); atomic_add(f + 2 * n + b, neg_(gz));
         atomic_add(f + a, gx); atomic_add(f + n + a, gy); atomic_add(f + 2 * n + a, gz);
@@ -564,17 +568,17 @@ HD R bond_order(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, R 
     int tab = (ti == tj) ? (ti == 0 ? 0 : 2) : 1;
     bool swap = (ti == 1 && tj == 0);
     R xa = swap ? sj.N : si.N, xb = swap ? si.N : sj.N, xc = Nconj;
-    bool cl[3];
+    bool clx, cly, clz;
     R tx, ty, tz;
-    int cell = tri_cell_index<R>(xa, xb, xc, cl, tx, ty, tz);
+    int cell = tri_cell_index<R>(xa, xb, xc, clx, cly, clz, tx, ty, tz);
     R Fa, Fb, Fc;
-    R pirc = tricubic_cell<R, REV>(P.Ftab + (tab * NTRI_CELLS + cell) * 64, tx, ty, tz, cl, Fa, Fb, Fc);
+    R pirc = tricubic_cell<R, REV>(P.Ftab + (tab * NTRI_CELLS + cell) * 64, tx, ty, tz, clx, cly, clz, Fa, Fb, Fc);
     R dFdNi = swap ? Fb : Fa, dFdNj = swap ? Fa : Fb;
     // pi^dh (C-C only), skipped where the T_CC cell is identically zero
     R pidh = 0, D = 0, Tv = 0, Ta = 0, Tb = 0, Tc = 0;
     bool dih = (ti == 0 && tj == 0) && P.Tnz[cell];
     if (dih) {
-        Tv = tricubic_cell<R, REV>(P.Ttab + cell * 64, tx, ty, tz, cl, Ta, Tb, Tc);
+        Tv = tricubic_cell<R, REV>(P.Ttab + cell * 64, tx, ty, tz, clx, cly, clz, Ta, Tb, Tc);
         R dummy = 0;
         D = dihedral_sum<R>(P, G, i, j, ux, uy, uz, inv_u, false, R(0), sink, dummy, dummy, dummy,
                             fix, fiy, fiz, fjx, fjy, fjz);
@@ -847,18 +851,51 @@ HD void path_forces(const Graph<R>& G, int i, int code, R dEdw, Sink& sink, doub
 // clamped at 0, where it is the identity), so lanes of a warp never diverge.
 template <class R> HD R vlj(const DevParams<R>& P, int p, R r2, R& dVr) {
     R ir = rsqrt_(r2);
-    R ir2 = ir * ir;
-    R s2 = P.sig2[p] * ir2;
-    R s6 = s2 * s2 * s2;
-    R v = P.eps4[p] * (s6 * s6 - s6);
-    R dvr = P.eps4[p] * (R(-12) * s6 * s6 + R(6) * s6) * ir2;
     R r = r2 * ir;
+    R v, dvr;
+    if (P.kind == 0) {
+        R ir2 = ir * ir;
+        R s2 = P.sig2[p] * ir2;
+        R s6 = s2 * s2 * s2;
+        v = P.eps4[p] * (s6 * s6 - s6);
+        dvr = P.eps4[p] * (R(-12) * s6 * s6 + R(6) * s6) * ir2;
+    } else {                         // Morse (AIREBO-M): eps (e^2 - 2 e), e = exp(-alpha (r - r_e))
+        R e = exp_(-P.malpha[p] * (r - P.mre[p]));
+        v = P.meps[p] * (e * e - R(2) * e);
+        dvr = R(2) * P.malpha[p] * P.meps[p] * e * (R(1) - e) * ir;
+    }
     R t = (r - P.swlo[p]) * P.swinv[p];
     t = t > R(0) ? t : R(0);
     R so = R(1) - t * t * (R(3) - R(2) * t);
     R dso = R(-6) * t * (R(1) - t) * P.swinv[p];
     dVr = dvr * so + v * dso * ir;
     return v * so;
+}
+
+// dV/d(eps) and dV/d(sigma) of the inter-molecular pair term (with its cut-off
+// switch) at r; eps is lj.epsilon (Lennard-Jones) or morse.epsilon (Morse).
+template <class R> HD void vlj_param_grad(const DevParams<R>& P, int p, R r, R& dV_deps, R& dV_dsig) {
+    R sg = P.sigma[p];
+    R t = (r - P.swlo[p]) * P.swinv[p];
+    t = t > R(0) ? t : R(0);
+    R so = R(1) - t * t * (R(3) - R(2) * t);
+    R dso_dt = R(-6) * t * (R(1) - t);
+    R dt_dsig = t > R(0) ? -r * P.swinv[p] / sg : R(0);        // t = (r/sigma - 2.7)/0.3
+    R v, dv_dsig, eps;
+    if (P.kind == 0) {
+        R s6 = (sg / r) * (sg / r);
+        s6 = s6 * s6 * s6;
+        v = P.eps4[p] * (s6 * s6 - s6);
+        dv_dsig = P.eps4[p] * (R(12) * s6 * s6 - R(6) * s6) / sg;
+        eps = P.eps4[p] * R(0.25);
+    } else {
+        R e = exp_(-P.malpha[p] * (r - P.mre[p]));
+        v = P.meps[p] * (e * e - R(2) * e);
+        dv_dsig = R(0);
+        eps = P.meps[p];
+    }
+    dV_deps = v * so / eps;
+    dV_dsig = dv_dsig * so + v * dso_dt * dt_dsig;
 }
 
 // Energy and forces of one LJ pair with S_r = 0 (C and its path known).
@@ -873,6 +910,12 @@ HD void lj_eval(const DevParams<R>& P, const Graph<R>& G, int i, int p, int j, d
     double c = (double)(C * dVr);
     sink.half(j, dx, dy, dz, c * dx, c * dy, c * dz, fix, fiy, fiz);
     if (code >= 0) path_forces<R>(G, i, code, -V, sink, fix, fiy, fiz);
+    if (sink.pgrad) {
+        R de, ds;
+        vlj_param_grad<R>(P, p, sqrt_(r2), de, ds);
+        sink.G[p] += (double)(C * de);
+        sink.G[3 + p] += (double)(C * ds);
+    }
 }
 
 // The common LJ pair: C = 1, no path, r inside 2.7 sigma (no cut-off switch):
@@ -889,21 +932,29 @@ HD void lj_eval_inner(const DevParams<R>& P, int p, int j, double dx, double dy,
     sink.half(j, dx, dy, dz, c * dx, c * dy, c * dz, fix, fiy, fiz);
 }
 
-// C = 1, no path, r inside the cut-off switch.
+// C = 1, no path, r inside the cut-off switch (Lennard-Jones), or any
+// C = 1 pair without a path (Morse).
 template <class R>
 HD void lj_eval_switch(const DevParams<R>& P, int p, int j, double dx, double dy, double dz, R r2, Sink& sink,
                        double& fix, double& fiy, double& fiz, double& E) {
-    R ir = rsqrt_(r2);
-    R ir2 = ir * ir;
-    R s2 = P.sig2[p] * ir2;
-    R s6 = s2 * s2 * s2;
-    R v = P.eps4[p] * (s6 * s6 - s6);
-    R dvr = P.eps4[p] * (R(-12) * s6 * s6 + R(6) * s6) * ir2;
-    R t = (r2 * ir - P.swlo[p]) * P.swinv[p];          // > 0 in this class
-    R so = R(1) - t * t * (R(3) - R(2) * t);
-    R dso = R(-6) * t * (R(1) - t) * P.swinv[p];
-    E += (double)(v * so);
-    double c = (double)(dvr * so + v * dso * ir);
+    double c;
+    if (P.kind == 0) {
+        R ir = rsqrt_(r2);
+        R ir2 = ir * ir;
+        R s2 = P.sig2[p] * ir2;
+        R s6 = s2 * s2 * s2;
+        R v = P.eps4[p] * (s6 * s6 - s6);
+        R dvr = P.eps4[p] * (R(-12) * s6 * s6 + R(6) * s6) * ir2;
+        R t = (r2 * ir - P.swlo[p]) * P.swinv[p];          // > 0 in this class
+        R so = R(1) - t * t * (R(3) - R(2) * t);
+        R dso = R(-6) * t * (R(1) - t) * P.swinv[p];
+        E += (double)(v * so);
+        c = (double)(dvr * so + v * dso * ir);
+    } else {
+        R dVr;
+        E += (double)vlj<R>(P, p, r2, dVr);
+        c = (double)dVr;
+    }
     sink.half(j, dx, dy, dz, c * dx, c * dy, c * dz, fix, fiy, fiz);
 }
 
@@ -912,12 +963,12 @@ HD void lj_eval_switch(const DevParams<R>& P, int p, int j, double dx, double dy
 //   0: beyond the cut-off, or C = 0;
 //   1: C = 1, no path, inside 2.7 sigma (lj_eval_inner);
 //   2: to be queued for b* (S_r != 0);
-//   3: C = 1, no path, inside the cut-off switch (lj_eval_switch);
+//   3: C = 1, no path, inside the cut-off switch, or any such Morse pair (lj_eval_switch);
 //   4: 0 < C < 1 along a path (lj_eval).
 // C, the path code and the map entry are returned.
 template <class R>
 HD int lj_classify(const DevParams<R>& P, const PathMap<R>& M, int i, int p, int j, int img, R r2,
-                   R& C, int& code, int& mi) {
+                   R& C, int& code, int& mi, bool general = false) {
     mi = -1; code = -1; C = R(1);
     if (!lt_nonneg(r2, P.rc2[p])) return 0;
     if (lt_nonneg(r2, P.rpath2)) {
@@ -933,8 +984,8 @@ HD int lj_classify(const DevParams<R>& P, const PathMap<R>& M, int i, int p, int
         }
     }
     if (lt_nonneg(r2, P.Srhi2[p])) return 2;
-    if (mi >= 0) return 4;
-    return lt_nonneg(P.swlo2[p], r2) ? 3 : 1;
+    if (mi >= 0 || general) return 4;
+    return (P.kind != 0 || lt_nonneg(P.swlo2[p], r2)) ? 3 : 1;
 }
 
 // b* pair: (S_r S_b + 1 - S_r) C V for the pair i -> (j, image) with
@@ -967,6 +1018,14 @@ HD double bstar_pair(const DevParams<R>& P, const Graph<R>& G, int i, int j, R d
     double gx = dEdr_r * dx, gy = dEdr_r * dy, gz = dEdr_r * dz;
     eps_out = Sr * C * V * dSb;
     if (path_code >= 0) path_forces<R>(G, i, path_code, -factor * V, sink, fix, fiy, fiz);
+    if (sink.pgrad) {
+        R de, ds;
+        vlj_param_grad<R>(P, p, r, de, ds);
+        // S_r = S((r/sigma - lo)/(hi - lo)) also depends on sigma
+        R dSr_dsig = dSr * (-r / P.sigma[p]);
+        sink.G[p] += (double)(C * factor * de);
+        sink.G[3 + p] += (double)(C * (factor * ds + V * (Sb - R(1)) * dSr_dsig));
+    }
     atomic_add(sink.f + i, fix + gx); atomic_add(sink.f + sink.n + i, fiy + gy); atomic_add(sink.f + 2 * sink.n + i, fiz + gz);
     atomic_add(sink.f + j, -gx); atomic_add(sink.f + sink.n + j, -gy); atomic_add(sink.f + 2 * sink.n + j, -gz);
     if (sink.virial) {

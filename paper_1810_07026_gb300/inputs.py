@@ -113,8 +113,12 @@ def _dihedral_data(rng, scale, dscale):
     return _symmetrize_xy(d)
 
 
-def make_params(seed: int = 0) -> dict:
-    """The full parameter set: scalars (per type pair CC, CH, HH) and seeded tables."""
+def make_params(seed: int = 0, morse: bool = False) -> dict:
+    """The full parameter set: scalars (per type pair CC, CH, HH) and seeded tables.
+
+    morse=True selects the AIREBO-M form of the inter-molecular term: a Morse
+    potential whose well depth, minimum and curvature equal those of the LJ
+    term (r_e = 2^(1/6) sigma, alpha = 6 / r_e)."""
     rng = np.random.default_rng(seed)
     p = {}
     p["Dmin"] = [1.7, 1.3, 1.1]
@@ -155,6 +159,11 @@ def make_params(seed: int = 0) -> dict:
     p["bstar.bmax"] = [0.81, 0.90, 0.42]
     p["bstar.rstar"] = list(p["Dmin"])
     p["tors.epsilon"] = [0.3079, 0.1787, 0.1250]
+    p["inter.kind"] = [1.0 if morse else 0.0]
+    re = [2.0 ** (1.0 / 6.0) * s for s in p["lj.sigma"]]
+    p["morse.epsilon"] = list(p["lj.epsilon"])
+    p["morse.re"] = re
+    p["morse.alpha"] = [6.0 / x for x in re]
     return {k: np.asarray(v, dtype=np.float64).ravel() for k, v in p.items()}
 
 

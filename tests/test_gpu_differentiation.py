@@ -1,0 +1,120 @@
+"""Differentiation through the C ABI: forces as the backward of the energy,
+and the hand-written gradient of the energy with respect to the epsilon and
+sigma of the inter-molecular term, against central differences of the FP64
+oracle's energy (1e-6 relative steps) and of the GPU energy."""
+import numpy as np
+import pytest
+
+from paper_1810_07026_gb300 import inputs
+from oracle.oracle import Oracle
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def A():
+    from paper_1810_07026_gb300 import build, airebo
+    build.build()
+    return airebo
+
+
+def oracle_param_fd(params, pos, types, box, key, k, rel=1e-6):
+    p = {q: v.copy() for q, v in params.items()}
+    x0 = p[key][k]
+    h = rel * x0
+    p[key][k] = x0 + h
+    ep = Oracle(inputs.params_text(p)).energy(pos, types, box)
+    p[key][k] = x0 - h
+    em = Oracle(inputs.params_text(p)).energy(pos, types, box)
+    return (ep - em) / (2 * h)
+
+
+@pytest.mark.parametrize("morse", [False, True])
+@pytest.mark.parametrize("case", ["hot300", "pe1152"])
+def test_param_grad_against_oracle_fd(A, morse, case):
+    params = inputs.make_params(0, morse=morse)
+    text = inputs.params_text(params)
+    if case == "hot300":
+        pos, types, box = inputs.amorphous(300, 0.5, 0.9, seed=5)
+    else:
+        pos, types, box = inputs.polyethylene(3, 4, 8, noise=0.05)
+    ev = A.Airebo(text)
+    p = torch.tensor(pos, device="cuda")
+    ev.neighbor(p, torch.tensor(types, device="cuda"), box)
+    _, _, g = ev.param_grad(p)
+    eps_key = "morse.epsilon" if morse else "lj.epsilon"
+    for k in range(3):
+        fd_e = oracle_param_fd(params, pos, types, box, eps_key, k)
+        fd_s = oracle_param_fd(params, pos, types, box, "lj.sigma", k)
+        assert g[k] == pytest.approx(fd_e, rel=2e-6, abs=1e-6)
+        assert g[3 + k] == pytest.approx(fd_s, rel=2e-6, abs=1e-6)
+
+
+def test_autograd_forces_and_params(A):
+    params = inputs.make_params(0)
+    text = inputs.params_text(params)
+    pos, types, box = inputs.amorphous(300, 0.5, 0.9, seed=5)
+    ev = A.Airebo(text)
+    p = torch.tensor(pos, device="cuda", requires_grad=True)
+    ev.neighbor(p.detach(), torch.tensor(types, device="cuda"), box)
+    eps = torch.tensor(params["lj.epsilon"], device="cuda", requires_grad=True)
+    sig = torch.tensor(params["lj.sigma"], device="cuda", requires_grad=True)
+    E = A.AireboEnergy.apply(p, eps, sig, ev)
+    gx, ge, gs = torch.autograd.grad(E, (p, eps, sig))
+    f, e4, g = ev.param_grad(p.detach())
+    # two evaluations: equal up to the order of FP64 atomic additions
+    assert (gx + f).abs().max().item() <= 1e-12 * f.abs().max().item()
+    assert np.allclose(ge.cpu().numpy(), g[:3]) and np.allclose(gs.cpu().numpy(), g[3:])
+    # central differences of the GPU energy for a few coordinates
+    h = 1e-5
+    for a in (3, 77, 201):
+        for d in range(3):
+            q = p.detach().clone(); q[d, a] += h
+            ep = ev.compute(q)[1][0].item()
+            q[d, a] -= 2 * h
+            em = ev.compute(q)[1][0].item()
+            assert gx[d, a].item() == pytest.approx((ep - em) / (2 * h), rel=1e-5, abs=1e-7)
+
+
+def test_fitting_loss_over_64_perturbed_copies(A):
+    """A fitting-style loss over 64 perturbed copies of a 2,048-atom amorphous
+    C:H box (density 1.0 g/cm^3, H/C = 1): L = sum_c (E_c - E_ref,c)^2 with
+    reference energies from shifted parameters; its autograd gradient with
+    respect to eps and sigma against central differences of L."""
+    params = inputs.make_params(0)
+    text = inputs.params_text(params)
+    pos0, types, box = inputs.amorphous(2048, 1.0, 1.0, seed=21)
+    rng = np.random.default_rng(5)
+    copies = [pos0 + rng.normal(0.0, 0.02, pos0.shape) for _ in range(64)]
+    ev = A.Airebo(text)
+    t = torch.tensor(types, device="cuda")
+    ev.neighbor(torch.tensor(pos0, device="cuda"), t, box)
+    eps_ref = torch.tensor(params["lj.epsilon"] * 1.05, device="cuda")
+    sig_ref = torch.tensor(params["lj.sigma"] * 0.99, device="cuda")
+    e_ref = []
+    for c in copies:
+        e_ref.append(A.AireboEnergy.apply(torch.tensor(c, device="cuda"), eps_ref, sig_ref, ev).item())
+
+    def loss_of(eps, sig, grad):
+        total = 0.0
+        for c, er in zip(copies, e_ref):
+            E = A.AireboEnergy.apply(torch.tensor(c, device="cuda"), eps, sig, ev)
+            total = total + (E - er) ** 2
+        return total
+
+    eps = torch.tensor(params["lj.epsilon"], device="cuda", requires_grad=True)
+    sig = torch.tensor(params["lj.sigma"], device="cuda", requires_grad=True)
+    L = loss_of(eps, sig, True)
+    ge, gs = torch.autograd.grad(L, (eps, sig))
+    for k in (0, 2):
+        for which, base, g in (("eps", params["lj.epsilon"], ge), ("sig", params["lj.sigma"], gs)):
+            h = 1e-6 * base[k]
+            vals = []
+            for sgn in (1, -1):
+                e = torch.tensor(params["lj.epsilon"], device="cuda")
+                s = torch.tensor(params["lj.sigma"], device="cuda")
+                (e if which == "eps" else s)[k] += sgn * h
+                vals.append(loss_of(e, s, False).item())
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert g[k].item() == pytest.approx(fd, rel=1e-4, abs=1e-6)

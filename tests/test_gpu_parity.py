@@ -290,3 +290,15 @@ def test_nve_pe32k_1000_steps_energy(A, param_text, precision):
           f"list builds {e4[3]:.0f}")
     assert tot.max() - tot.min() < 2e-3
     assert abs(slope) < 5e-7
+
+
+@pytest.mark.parametrize("case", ["hot300", "pe1152", "diamond216"])
+@pytest.mark.parametrize("precision,etol,ftol", [(0, 1e-10, 1e-8), (1, 1e-5, 1e-4)])
+def test_morse_parity(A, case, precision, etol, ftol):
+    """AIREBO-M: the Morse inter-molecular term, GPU against the oracle."""
+    from oracle.oracle import Oracle
+    text = inputs.params_text(inputs.make_params(0, morse=True))
+    pos, types, box = CASES[case]()
+    e, f, w, _ = Oracle(text).compute(pos, types, box)
+    got, _ = gpu_eval(A, text, pos, types, box, precision=precision)
+    assert_close(got, (e, f, w), etol, ftol, ftol)
