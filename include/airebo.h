@@ -46,7 +46,7 @@ typedef enum {
     AIREBO_OK = 0,
     AIREBO_ERR_ARG = 1,        /* bad argument: null pointer, size, box too small, bad parameter text */
     AIREBO_ERR_CUDA = 2,       /* a CUDA runtime call failed (text in airebo_last_error) */
-    AIREBO_ERR_CAPACITY = 3,   /* more than 8 REBO neighbours on an atom (the bound of Sec. 4.3) */
+    AIREBO_ERR_CAPACITY = 3,   /* more than 16 REBO neighbours on an atom (twice the bound of Sec. 4.3) */
     AIREBO_ERR_TIMEOUT = 4,    /* reserved: a bounded device-side wait gave up */
     AIREBO_ERR_NONFINITE = 5,  /* a position is NaN or infinite */
     AIREBO_ERR_STATE = 6       /* call out of order, e.g. compute before neighbor */
@@ -192,6 +192,44 @@ airebo_status airebo_param_grad(airebo_handle h, const double* d_pos, double* d_
  * returns AIREBO_ERR_STATE until then).  Synchronises.
  */
 airebo_status airebo_set_lj_params(airebo_handle h, const double* eps3, const double* sigma3);
+
+/*
+ * Batched independent systems: nsys periodic boxes evaluated as one set of
+ * launches.  d_pos/d_types hold all atoms, system s owning atoms
+ * [h_offsets[s], h_offsets[s+1]) (host int64[nsys+1], from 0 to n);
+ * h_boxes: host double[3 * nsys], each edge > 4 x the largest REBO cut-off.
+ * Builds one cell grid per system; no pair crosses systems.  After it,
+ * airebo_compute, airebo_nve and the other calls act on all systems at once.
+ */
+airebo_status airebo_neighbor_batch(airebo_handle h, const double* d_pos, const int8_t* d_types, int64_t n,
+                                    int nsys, const int64_t* h_offsets, const double* h_boxes);
+
+/* Forces (d_force, device double[3][n]) and the potential energy of each
+ * system (d_energy_sys, device double[nsys]; one system after
+ * airebo_neighbor).  Synchronises like airebo_compute. */
+airebo_status airebo_compute_batch(airebo_handle h, const double* d_pos, double* d_force, double* d_energy_sys);
+
+/*
+ * Enqueue one evaluation without any host synchronisation or capacity growth
+ * (d_energy4, d_energy_sys nullable; per-system energies need one earlier
+ * synchronous evaluation that wanted them).  Capacity flags are read by
+ * airebo_check, which synchronises and returns AIREBO_ERR_CAPACITY if a
+ * scratch capacity was exceeded (run airebo_compute once, then retry).
+ */
+airebo_status airebo_compute_async(airebo_handle h, const double* d_pos, double* d_force, double* d_energy4,
+                                   double* d_energy_sys);
+airebo_status airebo_check(airebo_handle h);
+
+/*
+ * Capture one evaluation (as airebo_compute_async, with these pointers) into
+ * a CUDA graph on the handle's stream, after a synchronous evaluation that
+ * grows every capacity; airebo_graph_launch replays it.  The handle must have
+ * been created on a non-default stream.  A neighbour rebuild or a new atom
+ * count needs a new capture.
+ */
+airebo_status airebo_graph_capture(airebo_handle h, const double* d_pos, double* d_force, double* d_energy4,
+                                   double* d_energy_sys);
+airebo_status airebo_graph_launch(airebo_handle h);
 
 /*
  * Rebuild check that allocates no device memory (the paper has no

@@ -63,6 +63,12 @@ def lib():
             "airebo_alu_peak": (I, [I, P]),
             "airebo_param_grad": (I, [P, P, P, P, P]),
             "airebo_set_lj_params": (I, [P, P, P]),
+            "airebo_neighbor_batch": (I, [P, P, P, I64, I, P, P]),
+            "airebo_compute_batch": (I, [P, P, P, P]),
+            "airebo_compute_async": (I, [P, P, P, P, P]),
+            "airebo_check": (I, [P]),
+            "airebo_graph_capture": (I, [P, P, P, P, P]),
+            "airebo_graph_launch": (I, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -145,6 +151,43 @@ class Airebo:
         self.n = pos.shape[1]
         self._types = types
         self.box = b
+
+    def neighbor_batch(self, pos, types, offsets, boxes):
+        """Lists for independent systems: system s owns atoms offsets[s]:offsets[s+1]."""
+        torch = self._torch
+        pos = self._dev(pos, torch.float64)
+        types = self._dev(types, torch.int8)
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        bx = np.ascontiguousarray(np.asarray(boxes, dtype=np.float64).reshape(-1, 3))
+        self._check(lib().airebo_neighbor_batch(self._h, _ptr(pos), _ptr(types), pos.shape[1], len(off) - 1,
+                                                _np(off), _np(bx)))
+        self.n = pos.shape[1]
+        self._types = types
+        self.nsys = len(off) - 1
+
+    def compute_batch(self, pos, force=None, energy=None):
+        """Forces and the energy of each system."""
+        torch = self._torch
+        pos = self._dev(pos, torch.float64)
+        if force is None:
+            force = torch.empty_like(pos)
+        if energy is None:
+            energy = torch.empty(getattr(self, "nsys", 1), dtype=torch.float64, device=self.device)
+        self._check(lib().airebo_compute_batch(self._h, _ptr(pos), _ptr(force), _ptr(energy)))
+        return force, energy
+
+    def compute_async(self, pos, force, energy4=None, energy_sys=None):
+        self._check(lib().airebo_compute_async(self._h, _ptr(pos), _ptr(force), _ptr(energy4), _ptr(energy_sys)))
+
+    def check(self):
+        self._check(lib().airebo_check(self._h))
+
+    def graph_capture(self, pos, force, energy4=None, energy_sys=None):
+        """Capture one evaluation with these buffers into a CUDA graph."""
+        self._check(lib().airebo_graph_capture(self._h, _ptr(pos), _ptr(force), _ptr(energy4), _ptr(energy_sys)))
+
+    def graph_launch(self):
+        self._check(lib().airebo_graph_launch(self._h))
 
     def compute(self, pos, force=None, virial=False):
         """Forces (3, N), energies (total, REBO, LJ, torsion) and the virial (or None)."""

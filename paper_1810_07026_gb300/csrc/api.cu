@@ -293,6 +293,19 @@ struct airebo_ctx {
     double* acc = nullptr;               // 9 doubles
     unsigned long long* counters = nullptr;   // 8
     int* derr = nullptr;                 // 8 ints
+    int stride = 8;                      // REBO slots per atom (grows to MAXN)
+    // batched systems (nsys = 0: one system with box L)
+    int nsys = 0;
+    std::vector<double> Lsys_h;
+    std::vector<long long> off_h;
+    int *d_sys = nullptr, *d_snc = nullptr, *d_sreach = nullptr, *d_scell0 = nullptr;
+    double *d_Lsys = nullptr, *d_scw = nullptr;
+    long long* d_off = nullptr;
+    double* eatom = nullptr;
+    int eatom_n = 0;
+    // captured compute
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
     unsigned long long* maxd2 = nullptr;
     double* ke = nullptr;
     double* pg = nullptr;                // parameter gradients (6)
@@ -350,7 +363,7 @@ template <class R> airebo_status upload_params(airebo_handle h, Precision<R>& pr
 
 template <class R> airebo_status alloc_step(airebo_handle h, Precision<R>& pr, int n) {
     StepBuffers<R>& b = pr.b;
-    size_t m = (size_t)n * MAXN;
+    size_t m = (size_t)n * h->stride;
     CK(realloc_dev(b.cnt, n)); CK(realloc_dev(b.nj, m)); CK(realloc_dev(b.nimg, m));
     CK(realloc_dev(b.dx, m)); CK(realloc_dev(b.dy, m)); CK(realloc_dev(b.dz, m));
     CK(realloc_dev(b.r, m)); CK(realloc_dev(b.ir, m)); CK(realloc_dev(b.w, m)); CK(realloc_dev(b.dw, m)); CK(realloc_dev(b.omw, m));
@@ -427,11 +440,40 @@ airebo_status do_neighbor(airebo_handle h, const double* d_pos) {
     a.with_lj = with_lj;
     rlj += 2e-3;
     int ncell = 1;
-    for (int d = 0; d < 3; d++) {
-        h->nc[d] = std::max(1, (int)std::floor(h->L[d] / rlj));
-        h->cell_w[d] = h->L[d] / h->nc[d];
-        h->reach[d] = (int)std::ceil(rlj / h->cell_w[d]);
-        ncell *= h->nc[d];
+    double rho_max = 0;
+    if (h->nsys == 0) {
+        for (int d = 0; d < 3; d++) {
+            h->nc[d] = std::max(1, (int)std::floor(h->L[d] / rlj));
+            h->cell_w[d] = h->L[d] / h->nc[d];
+            h->reach[d] = (int)std::ceil(rlj / h->cell_w[d]);
+            ncell *= h->nc[d];
+        }
+        rho_max = h->n / (h->L[0] * h->L[1] * h->L[2]);
+    } else {
+        // one cell grid per system, numbered consecutively
+        std::vector<int> nc(3 * h->nsys), reach(3 * h->nsys), cell0(h->nsys + 1);
+        std::vector<double> cw(3 * h->nsys);
+        ncell = 0;
+        for (int s = 0; s < h->nsys; s++) {
+            int cs = 1;
+            for (int d = 0; d < 3; d++) {
+                double L = h->Lsys_h[3 * s + d];
+                nc[3 * s + d] = std::max(1, (int)std::floor(L / rlj));
+                cw[3 * s + d] = L / nc[3 * s + d];
+                reach[3 * s + d] = (int)std::ceil(rlj / cw[3 * s + d]);
+                cs *= nc[3 * s + d];
+            }
+            cell0[s] = ncell;
+            ncell += cs;
+            double vol = h->Lsys_h[3 * s] * h->Lsys_h[3 * s + 1] * h->Lsys_h[3 * s + 2];
+            rho_max = std::max(rho_max, (h->off_h[s + 1] - h->off_h[s]) / vol);
+        }
+        cell0[h->nsys] = ncell;
+        CK(cudaMemcpyAsync(h->d_snc, nc.data(), sizeof(int) * nc.size(), cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(h->d_sreach, reach.data(), sizeof(int) * reach.size(), cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(h->d_scw, cw.data(), sizeof(double) * cw.size(), cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(h->d_scell0, cell0.data(), sizeof(int) * cell0.size(), cudaMemcpyHostToDevice, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
     }
     if (ncell > h->ncell_alloc) {
         CK(realloc_dev(h->cell_count, ncell));
@@ -441,9 +483,7 @@ airebo_status do_neighbor(airebo_handle h, const double* d_pos) {
     }
     if (!with_lj) h->lj_cap = 1;
     if (h->lj_cap == 0) {
-        double vol = h->L[0] * h->L[1] * h->L[2];
-        double rho = h->n / vol;
-        double est = 0.5 * 4.0 / 3.0 * M_PI * rlj * rlj * rlj * rho;
+        double est = 0.5 * 4.0 / 3.0 * M_PI * rlj * rlj * rlj * rho_max;
         h->lj_cap = h->opt.max_lj_nbrs > 0 ? h->opt.max_lj_nbrs : ((int)(1.2 * est + 32) + 31) / 32 * 32;
     }
     for (int attempt = 0; attempt < 4; attempt++) {
@@ -456,9 +496,12 @@ airebo_status do_neighbor(airebo_handle h, const double* d_pos) {
         a.lj = h->lj; a.lj_cnt = h->lj_cnt; a.lj_cap = h->lj_cap;
         a.im = h->im; a.im_cnt = h->im_cnt; a.im_cap = h->im_cap;
         a.err = h->derr; a.xref = h->xref;
+        a.sys = h->nsys ? h->d_sys : nullptr;
+        a.Lsys = h->nsys ? h->d_Lsys : nullptr;
+        a.snc = h->d_snc; a.sreach = h->d_sreach; a.scw = h->d_scw; a.scell0 = h->d_scell0;
         CK(cudaMemsetAsync(h->derr, 0, sizeof(int) * 8, h->stream));
         if (h->timing) CK(cudaEventRecord(h->ev[7], h->stream));
-        launch_neighbor(a, h->stream);
+        launch_neighbor(a, h->stream, ncell);
         CK(cudaGetLastError());
         if (h->timing) CK(cudaEventRecord(h->ev[8], h->stream));
         CK(cudaMemcpyAsync(h->h_err, h->derr, sizeof(int) * 8, cudaMemcpyDeviceToHost, h->stream));
@@ -496,7 +539,7 @@ template <class R> StepArgs<R> make_args(airebo_handle h, Precision<R>& pr, cons
     StepBuffers<R>& b = pr.b;
     a.n = h->n;
     a.P = b.P;
-    a.G.n = h->n; a.G.type = h->types; a.G.cnt = b.cnt; a.G.nj = b.nj; a.G.nimg = b.nimg;
+    a.G.n = h->n; a.G.stride = h->stride; a.G.type = h->types; a.G.cnt = b.cnt; a.G.nj = b.nj; a.G.nimg = b.nimg;
     a.G.dx = b.dx; a.G.dy = b.dy; a.G.dz = b.dz; a.G.r = b.r; a.G.ir = b.ir; a.G.w = b.w; a.G.dw = b.dw; a.G.omw = b.omw; a.G.nC = b.nC; a.G.nH = b.nH;
     a.g_cnt = b.cnt; a.g_nj = b.nj; a.g_nimg = b.nimg; a.g_dx = b.dx; a.g_dy = b.dy; a.g_dz = b.dz;
     a.g_r = b.r; a.g_ir = b.ir; a.g_w = b.w; a.g_dw = b.dw; a.g_omw = b.omw; a.g_nC = b.nC; a.g_nH = b.nH;
@@ -512,15 +555,21 @@ template <class R> StepArgs<R> make_args(airebo_handle h, Precision<R>& pr, cons
     a.lj_next = h->counts + 7;
     a.f = d_force; a.acc = h->acc; a.counters = h->counters; a.err = h->derr;
     a.virial = virial;
+    a.sys = h->nsys ? h->d_sys : nullptr;
+    a.Lsys = h->nsys ? h->d_Lsys : nullptr;
+    a.eatom = nullptr;
     a.rebo = h->opt.enable_rebo != 0;
     a.lj_on = h->opt.enable_lj != 0;
     a.torsion = h->opt.enable_torsion != 0;
     return a;
 }
 
+// One evaluation.  eatom: per-atom energies wanted (summed per system into
+// d_esys).  async: enqueue only (no host synchronisation, no regrowth; the
+// capacity flags are read by airebo_check), as needed for graph capture.
 template <class R>
 airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos, double* d_force, double* d_e4,
-                         double* d_w6, double* d_pgrad = nullptr) {
+                         double* d_w6, double* d_pgrad = nullptr, double* d_esys = nullptr, bool async = false) {
     for (int attempt = 0; attempt < 4; attempt++) {
         cudaStream_t s = h->stream;
         if (h->n) CK(cudaMemsetAsync(d_force, 0, sizeof(double) * 3 * h->n, s));
@@ -531,9 +580,15 @@ airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos,
         StepArgs<R> a = make_args<R>(h, pr, d_pos, d_force, d_w6 != nullptr);
         a.pgrad = d_pgrad;
         if (d_pgrad) CK(cudaMemsetAsync(d_pgrad, 0, sizeof(double) * 6, s));
-        launch_compute<R>(a, s, h->num_sms, h->timing ? h->ev : nullptr);
+        if (d_esys) {
+            a.eatom = h->eatom;
+            if (h->n) CK(cudaMemsetAsync(h->eatom, 0, sizeof(double) * h->n, s));
+        }
+        launch_compute<R>(a, s, h->num_sms, (h->timing && !async) ? h->ev : nullptr);
         CK(cudaGetLastError());
         if (d_e4 || d_w6) k_finalize<<<1, 32, 0, s>>>(h->acc, d_e4, d_w6);
+        if (d_esys) launch_system_energy(h->eatom, h->d_off, std::max(h->nsys, 1), d_esys, s);
+        if (async) return AIREBO_OK;
         CK(cudaMemcpyAsync(h->h_err, h->derr, sizeof(int) * 8, cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(h->h_u64, h->counts, sizeof(int) * 8, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -546,9 +601,16 @@ airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos,
             }
         }
         if (h->h_err[ERR_NONFINITE]) return fail(h, AIREBO_ERR_NONFINITE, "non-finite position");
-        if (h->h_err[ERR_SHORT] > MAXN)
-            return fail(h, AIREBO_ERR_CAPACITY, "an atom has more than 8 REBO neighbours (" + std::to_string(h->h_err[ERR_SHORT]) + ")");
         bool again = false;
+        if (h->h_err[ERR_SHORT] > h->stride) {
+            if (h->h_err[ERR_SHORT] > MAXN)
+                return fail(h, AIREBO_ERR_CAPACITY, "an atom has more than " + std::to_string(MAXN) +
+                                                    " REBO neighbours (" + std::to_string(h->h_err[ERR_SHORT]) + ")");
+            h->stride = MAXN;
+            airebo_status st = alloc_step<R>(h, pr, h->n_alloc);
+            if (st) return st;
+            again = true;
+        }
         if (h->h_err[ERR_MAP]) {
             airebo_status st = grow_map<R>(h, pr, h->h_err[ERR_MAP]);
             if (st) return st;
@@ -569,11 +631,17 @@ airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos,
 }
 
 airebo_status compute_any(airebo_handle h, const double* d_pos, double* d_force, double* d_e4, double* d_w6,
-                          double* d_pgrad = nullptr) {
+                          double* d_pgrad = nullptr, double* d_esys = nullptr, bool async = false) {
     if (!h->built) return fail(h, AIREBO_ERR_STATE, "airebo_compute before airebo_neighbor");
     CK(cudaSetDevice(h->device));
-    if (h->opt.precision == AIREBO_MIXED) return do_compute<float>(h, h->p32, d_pos, d_force, d_e4, d_w6, d_pgrad);
-    return do_compute<double>(h, h->p64, d_pos, d_force, d_e4, d_w6, d_pgrad);
+    if (d_esys && (h->eatom_n < h->n || !h->eatom)) {
+        if (async) return fail(h, AIREBO_ERR_STATE, "per-system energies need one synchronous evaluation first");
+        CK(realloc_dev(h->eatom, std::max(h->n, 1)));
+        h->eatom_n = h->n;
+    }
+    if (h->opt.precision == AIREBO_MIXED)
+        return do_compute<float>(h, h->p32, d_pos, d_force, d_e4, d_w6, d_pgrad, d_esys, async);
+    return do_compute<double>(h, h->p64, d_pos, d_force, d_e4, d_w6, d_pgrad, d_esys, async);
 }
 
 airebo_status check_rebuild(airebo_handle h, const double* d_pos, int* flag) {
@@ -598,6 +666,10 @@ airebo_status set_system(airebo_handle h, const int8_t* d_types, int64_t n, cons
     airebo_status st = alloc_atoms(h, (int)n);
     if (st) return st;
     h->n = (int)n;
+    h->nsys = 0;
+    h->off_h.assign({0, (long long)n});
+    CK(realloc_dev(h->d_off, 2));
+    CK(cudaMemcpy(h->d_off, h->off_h.data(), sizeof(long long) * 2, cudaMemcpyHostToDevice));
     for (int d = 0; d < 3; d++) h->L[d] = box[d];
     if (n) CK(cudaMemcpyAsync(h->types, d_types, n, types_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->stream));
     return AIREBO_OK;
@@ -658,6 +730,12 @@ void airebo_destroy(airebo_handle h) {
     free_prec(h->p64);
     free_prec(h->p32);
     if (h->pg) cudaFree(h->pg);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    {
+        void* bs[] = {h->d_sys, h->d_snc, h->d_sreach, h->d_scell0, h->d_Lsys, h->d_scw, h->d_off, h->eatom};
+        for (void* p : bs) if (p) cudaFree(p);
+    }
     void* ps[] = {h->types, h->cell_of, h->cell_count, h->cell_start, h->cell_fill, h->spos, h->swrap, h->lj, h->lj_cnt,
                   h->im, h->im_cnt, h->xref, h->bonds, h->ccbonds, h->bq, h->bq2, h->bq2_eps, h->counts, h->acc, h->counters, h->derr, h->maxd2, h->ke,
                   h->hpos, h->hvel, h->hforce, h->he4, h->hw6};
@@ -839,6 +917,97 @@ airebo_status airebo_counters(airebo_handle h, int64_t* out8) {
     return AIREBO_OK;
 }
 
+airebo_status airebo_neighbor_batch(airebo_handle h, const double* d_pos, const int8_t* d_types, int64_t n,
+                                    int nsys, const int64_t* h_offsets, const double* h_boxes) {
+    if (!h || nsys < 1 || !h_offsets || !h_boxes) return AIREBO_ERR_ARG;
+    if (n > 0 && (!d_pos || !d_types)) return fail(h, AIREBO_ERR_ARG, "null position or type pointer");
+    if (h_offsets[0] != 0 || h_offsets[nsys] != n) return fail(h, AIREBO_ERR_ARG, "offsets must run from 0 to n");
+    double dm = max3(h->sc.Dmax);
+    for (int s = 0; s < nsys; s++) {
+        if (h_offsets[s + 1] < h_offsets[s]) return fail(h, AIREBO_ERR_ARG, "offsets must not decrease");
+        for (int d = 0; d < 3; d++)
+            if (!(h_boxes[3 * s + d] > 4.0 * dm))
+                return fail(h, AIREBO_ERR_ARG, "box edge must exceed 4 x the largest REBO cut-off");
+    }
+    CK(cudaSetDevice(h->device));
+    airebo_status st = set_system(h, d_types, n, h_boxes, false);
+    if (st) return st;
+    h->nsys = nsys;
+    h->Lsys_h.assign(h_boxes, h_boxes + 3 * nsys);
+    h->off_h.assign(h_offsets, h_offsets + nsys + 1);
+    std::vector<int> sys((size_t)std::max<int64_t>(n, 1));
+    for (int s = 0; s < nsys; s++)
+        for (int64_t i = h_offsets[s]; i < h_offsets[s + 1]; i++) sys[i] = s;
+    CK(realloc_dev(h->d_sys, sys.size()));
+    CK(realloc_dev(h->d_Lsys, 3 * (size_t)nsys));
+    CK(realloc_dev(h->d_snc, 3 * (size_t)nsys));
+    CK(realloc_dev(h->d_sreach, 3 * (size_t)nsys));
+    CK(realloc_dev(h->d_scw, 3 * (size_t)nsys));
+    CK(realloc_dev(h->d_scell0, (size_t)nsys + 1));
+    CK(realloc_dev(h->d_off, (size_t)nsys + 1));
+    CK(cudaMemcpy(h->d_sys, sys.data(), sizeof(int) * sys.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_Lsys, h_boxes, sizeof(double) * 3 * nsys, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_off, h->off_h.data(), sizeof(long long) * (nsys + 1), cudaMemcpyHostToDevice));
+    return do_neighbor(h, d_pos);
+}
+
+airebo_status airebo_compute_batch(airebo_handle h, const double* d_pos, double* d_force, double* d_energy_sys) {
+    if (!h || !d_energy_sys) return AIREBO_ERR_ARG;
+    if (h->n > 0 && (!d_pos || !d_force)) return fail(h, AIREBO_ERR_ARG, "null position or force pointer");
+    return compute_any(h, d_pos, d_force, nullptr, nullptr, nullptr, d_energy_sys, false);
+}
+
+airebo_status airebo_compute_async(airebo_handle h, const double* d_pos, double* d_force, double* d_energy4,
+                                   double* d_energy_sys) {
+    if (!h) return AIREBO_ERR_ARG;
+    if (h->n > 0 && (!d_pos || !d_force)) return fail(h, AIREBO_ERR_ARG, "null position or force pointer");
+    return compute_any(h, d_pos, d_force, d_energy4, nullptr, nullptr, d_energy_sys, true);
+}
+
+airebo_status airebo_check(airebo_handle h) {
+    if (!h) return AIREBO_ERR_ARG;
+    CK(cudaSetDevice(h->device));
+    CK(cudaMemcpyAsync(h->h_err, h->derr, sizeof(int) * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(h->h_u64, h->counts, sizeof(int) * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    const int* cn = (const int*)h->h_u64;
+    if (h->h_err[ERR_NONFINITE]) return fail(h, AIREBO_ERR_NONFINITE, "non-finite position");
+    if (h->h_err[ERR_SHORT] > h->stride || h->h_err[ERR_MAP] ||
+        std::max(cn[4], std::max(cn[5], cn[6])) > h->bq_cap)
+        return fail(h, AIREBO_ERR_CAPACITY, "a scratch capacity was exceeded; run airebo_compute once to grow it");
+    return AIREBO_OK;
+}
+
+airebo_status airebo_graph_capture(airebo_handle h, const double* d_pos, double* d_force, double* d_energy4,
+                                   double* d_energy_sys) {
+    if (!h) return AIREBO_ERR_ARG;
+    if (!h->stream) return fail(h, AIREBO_ERR_ARG, "graph capture needs a handle created on a non-default stream");
+    if (!h->built) return fail(h, AIREBO_ERR_STATE, "airebo_graph_capture before airebo_neighbor");
+    CK(cudaSetDevice(h->device));
+    // one synchronous evaluation grows every capacity the graph will need
+    airebo_status st = compute_any(h, d_pos, d_force, d_energy4, nullptr, nullptr, d_energy_sys, false);
+    if (st) return st;
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    st = compute_any(h, d_pos, d_force, d_energy4, nullptr, nullptr, d_energy_sys, true);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (st) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) return fail(h, AIREBO_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+    h->graph = g;
+    CK(cudaGraphInstantiate(&h->gexec, g, 0));
+    return AIREBO_OK;
+}
+
+airebo_status airebo_graph_launch(airebo_handle h) {
+    if (!h) return AIREBO_ERR_ARG;
+    if (!h->gexec) return fail(h, AIREBO_ERR_STATE, "no captured graph");
+    CK(cudaSetDevice(h->device));
+    CK(cudaGraphLaunch(h->gexec, h->stream));
+    return AIREBO_OK;
+}
+
 airebo_status airebo_param_grad(airebo_handle h, const double* d_pos, double* d_force, double* d_energy4,
                                 double* h_grad6) {
     if (!h || !h_grad6) return AIREBO_ERR_ARG;
@@ -891,8 +1060,8 @@ airebo_status airebo_export_lists(airebo_handle h, int which, int32_t* h_cnt, in
         const int* dcnt = h->opt.precision == AIREBO_MIXED ? h->p32.b.cnt : h->p64.b.cnt;
         const int* dnj = h->opt.precision == AIREBO_MIXED ? h->p32.b.nj : h->p64.b.nj;
         const int* dimg = h->opt.precision == AIREBO_MIXED ? h->p32.b.nimg : h->p64.b.nimg;
-        rowcap = MAXN;
-        std::vector<int> nj((size_t)n * MAXN), im((size_t)n * MAXN);
+        rowcap = h->stride;
+        std::vector<int> nj((size_t)n * h->stride), im((size_t)n * h->stride);
         if (n) {
             CK(cudaMemcpy(cnt.data(), dcnt, sizeof(int) * n, cudaMemcpyDeviceToHost));
             CK(cudaMemcpy(nj.data(), dnj, sizeof(int) * nj.size(), cudaMemcpyDeviceToHost));

@@ -38,6 +38,9 @@ template <class R> struct StepArgs {
     int4* bq; int* nbq; int bq_cap;
     int* bq2; double* bq2_eps; int* nbq2;  // b* pairs whose S_b is in its transition, and dE/db*
     int* lj_next;                          // work counter of the LJ kernel's warps
+    const int* sys;                        // batched systems: system of each atom (null: one system, box L)
+    const double* Lsys;                    // batched systems: box of each system (3 per system)
+    double* eatom;                         // nullable: energy of each atom's anchored terms
     double* f;
     double* acc;          // E_rebo, E_lj, E_tors, W[6]
     unsigned long long* counters;   // [8]
@@ -71,8 +74,18 @@ struct NeighborArgs {
     int2* im; int* im_cnt; int im_cap;
     int* err;             // [0] max lj count, [1] max im count, [2] nonfinite / out of range, [3] bad type
     double* xref;         // copy of positions at the build (rebuild trigger)
+    // batched systems (all null for one system): per atom its system; per
+    // system its box, cell grid (cells, stencil reach, cell width) and first cell
+    const int* sys;
+    const double* Lsys;
+    const int* snc;
+    const int* sreach;
+    const double* scw;
+    const int* scell0;
 };
-void launch_neighbor(NeighborArgs& a, cudaStream_t s);
+void launch_neighbor(NeighborArgs& a, cudaStream_t s, int ncell);
+// per-system sums of per-atom energies (one block per system)
+void launch_system_energy(const double* eatom, const long long* offsets, int nsys, double* out, cudaStream_t s);
 
 // NVE helpers (neighbor.cu)
 void launch_nve_half(double* pos, double* vel, const double* f, const int8_t* type, int n, double dt,

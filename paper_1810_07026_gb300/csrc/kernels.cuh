@@ -61,6 +61,12 @@ __device__ void block_accumulate_g(const double* G, double* pg) {
     }
 }
 
+// the periodic box of atom i: the single system's, or its system's
+template <class R>
+__device__ __forceinline__ const double* box_of(const StepArgs<R>& a, int i) {
+    return a.sys ? a.Lsys + 3 * a.sys[i] : a.L;
+}
+
 __device__ __forceinline__ void load_disp(const double* pos, int n, const double* L, int i, int j, int img,
                                           double& dx, double& dy, double& dz) {
     dx = pos[j] + img_x(img) * L[0] - pos[i];
@@ -82,12 +88,13 @@ __global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
     R nC = 0, nH = 0;
     int ne = a.im_cnt[i];
     const int2* row = a.im + (size_t)i * a.im_cap;
+    const double* L = box_of(a, i);
     for (int e = 0; e < ne; e++) {
         int2 ent = row[e];
         int j = ent.x, img = ent.y;
-        double dx = a.pos[j] + img_x(img) * a.L[0] - xi;
-        double dy = a.pos[n + j] + img_y(img) * a.L[1] - yi;
-        double dz = a.pos[2 * n + j] + img_z(img) * a.L[2] - zi;
+        double dx = a.pos[j] + img_x(img) * L[0] - xi;
+        double dy = a.pos[n + j] + img_y(img) * L[1] - yi;
+        double dz = a.pos[2 * n + j] + img_z(img) * L[2] - zi;
         double r2 = dx * dx + dy * dy + dz * dz;
         int tj = a.G.type[j];
         int p = pidx(ti, tj);
@@ -97,8 +104,8 @@ __global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
         double r = r2 * ir;
         R dw, omw;
         R w = wfun_c<R>(P, p, (R)r, dw, omw);
-        if (cnt < MAXN) {
-            int q = i * MAXN + cnt;
+        if (cnt < a.G.stride) {
+            int q = i * a.G.stride + cnt;
             a.g_nj[q] = j; a.g_nimg[q] = img;
             a.g_dx[q] = (R)dx; a.g_dy[q] = (R)dy; a.g_dz[q] = (R)dz;
             a.g_r[q] = (R)r; a.g_ir[q] = (R)ir; a.g_w[q] = w; a.g_dw[q] = dw; a.g_omw[q] = omw;
@@ -118,8 +125,8 @@ __global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
         cnt++;
         if (tj == 0) nC += w; else nH += w;
     }
-    if (cnt > MAXN) atomicMax(a.err + ERR_SHORT, cnt);
-    a.g_cnt[i] = cnt < MAXN ? cnt : MAXN;
+    if (cnt > a.G.stride) atomicMax(a.err + ERR_SHORT, cnt);
+    a.g_cnt[i] = cnt < a.G.stride ? cnt : a.G.stride;
     a.g_nC[i] = nC;
     a.g_nH[i] = nH;
 }
@@ -134,7 +141,9 @@ __global__ void __launch_bounds__(128) k_rebo(StepArgs<R> a) {
     int nb = ncc + min(*a.nbonds, a.bond_cap);
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
         int2 bd = b < ncc ? a.ccbonds[b] : a.bonds[b - ncc];
-        E += rebo_bond<R>(P, a.G, bd.x, bd.y, sink);
+        double e = rebo_bond<R>(P, a.G, bd.x, bd.y, sink);
+        E += e;
+        if (a.eatom) atomicAdd(a.eatom + bd.x, e);
     }
     block_accumulate<128>(E, sink.W, a.virial, a.acc + 0, a.acc + 3);
 }
@@ -149,7 +158,9 @@ __global__ void __launch_bounds__(128) k_torsion(StepArgs<R> a) {
     if (nb > a.bond_cap) nb = a.bond_cap;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
         int2 bd = a.ccbonds[b];
-        E += torsion_bond<R>(P, a.G, bd.x, bd.y, sink);
+        double e = torsion_bond<R>(P, a.G, bd.x, bd.y, sink);
+        E += e;
+        if (a.eatom && e != 0.0) atomicAdd(a.eatom + bd.x, e);
     }
     block_accumulate<128>(E, sink.W, a.virial, a.acc + 2, a.acc + 3);
 }
@@ -224,6 +235,8 @@ __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
         double fix = 0, fiy = 0, fiz = 0;
         int ne = a.lj_cnt[i];
         const int2* row = a.lj + (size_t)i * a.lj_cap;
+        const double* L = box_of(a, i);
+        double E_before = E;
         int cnt[2] = {0, 0};
         for (int base = 0; base < ne; base += 32) {
             int e = base + lane;
@@ -238,8 +251,8 @@ __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
                 dx = a.pos[j] - xi; dy = a.pos[n + j] - yi; dz = a.pos[2 * n + j] - zi;
                 if (img != 0) {
                     int sx = img_x(img), sy = img_y(img), sz = img_z(img);
-                    if (sx < -4 || sx > 4 || sy < -4 || sy > 4 || sz < -4 || sz > 4) {
-                        dx += sx * a.L[0]; dy += sy * a.L[1]; dz += sz * a.L[2];
+                    if (a.sys || sx < -4 || sx > 4 || sy < -4 || sy > 4 || sz < -4 || sz > 4) {
+                        dx += sx * L[0]; dy += sy * L[1]; dz += sz * L[2];
                     } else {
                         dx += shift[0][sx + 4]; dy += shift[1][sy + 4]; dz += shift[2][sz + 4];
                     }
@@ -289,6 +302,10 @@ __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
         if (lane == 0) {
             atomicAdd(a.f + i, fix); atomicAdd(a.f + n + i, fiy); atomicAdd(a.f + 2 * n + i, fiz);
         }
+        if (a.eatom) {
+            double ei = warp_sum(E - E_before);
+            if (lane == 0) atomicAdd(a.eatom + i, ei);
+        }
     }
     unsigned ev = __reduce_add_sync(0xffffffffu, evaluated);
     if (lane == 0 && ev) atomicAdd(a.counters + CNT_LJ, (unsigned long long)ev);
@@ -314,7 +331,7 @@ __global__ void __launch_bounds__(128) k_bstar(StepArgs<R> a) {
         int2 ent = a.lj[(size_t)i * a.lj_cap + q.y];
         int j = ent.x;
         double dx, dy, dz;
-        load_disp(a.pos, a.n, a.L, i, j, ent.y, dx, dy, dz);
+        load_disp(a.pos, a.n, box_of(a, i), i, j, ent.y, dx, dy, dz);
         R rx = (R)dx, ry = (R)dy, rz = (R)dz;
         R r2 = rx * rx + ry * ry + rz * rz;
         R C = R(1);
@@ -324,7 +341,9 @@ __global__ void __launch_bounds__(128) k_bstar(StepArgs<R> a) {
             code = a.M.path[(size_t)i * a.M.cap + q.z];
         }
         R eps;
-        E += bstar_pair<R>(P, a.G, i, j, rx, ry, rz, r2, C, code, sink, eps);
+        double e = bstar_pair<R>(P, a.G, i, j, rx, ry, rz, r2, C, code, sink, eps);
+        E += e;
+        if (a.eatom) atomicAdd(a.eatom + i, e);
         if (eps != R(0)) {
             int s = atomicAdd(a.nbq2, 1);
             if (s < 3 * a.bq_cap) { a.bq2[s] = t; a.bq2_eps[s] = (double)eps; }
@@ -346,7 +365,7 @@ __global__ void __launch_bounds__(128) k_bstar_rev(StepArgs<R> a) {
         int2 ent = a.lj[(size_t)i * a.lj_cap + q.y];
         int j = ent.x;
         double dx, dy, dz;
-        load_disp(a.pos, a.n, a.L, i, j, ent.y, dx, dy, dz);
+        load_disp(a.pos, a.n, box_of(a, i), i, j, ent.y, dx, dy, dz);
         R rx = (R)dx, ry = (R)dy, rz = (R)dz;
         R r2 = rx * rx + ry * ry + rz * rz;
         bstar_reverse<R>(P, a.G, i, j, rx, ry, rz, r2, (R)a.bq2_eps[s], sink);
@@ -379,8 +398,8 @@ void launch_compute_impl(const StepArgs<R>& a, cudaStream_t s, int num_sms, cuda
     if (a.lj_on) k_path_map<R><<<(n + 127) / 128, 128, 0, s>>>(a);
     mark(4);
     if (a.lj_on) {
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lj<R>, LJ_THREADS, 0);
+        static int per_sm = -1;            // asked once: nothing but stream work during graph capture
+        if (per_sm < 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lj<R>, LJ_THREADS, 0);
         int blocks = num_sms * (per_sm > 0 ? per_sm : 1);
         int need = (n + LJ_WARPS - 1) / LJ_WARPS;
         k_lj<R><<<blocks < need ? blocks : need, LJ_THREADS, 0, s>>>(a);

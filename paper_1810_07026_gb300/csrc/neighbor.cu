@@ -15,20 +15,42 @@
 
 namespace airebo {
 
+// the cell grid an atom is binned on: the single system's, or its system's
+struct Grid {
+    int nc[3], reach[3], cell0;
+    double cw[3], L[3];
+};
+__device__ __forceinline__ Grid grid_of(const NeighborArgs& a, int i) {
+    Grid g;
+    if (!a.sys) {
+        for (int d = 0; d < 3; d++) { g.nc[d] = a.nc[d]; g.reach[d] = a.reach[d]; g.cw[d] = a.cell_w[d]; g.L[d] = a.L[d]; }
+        g.cell0 = 0;
+    } else {
+        int s = a.sys[i];
+        for (int d = 0; d < 3; d++) {
+            g.nc[d] = a.snc[3 * s + d]; g.reach[d] = a.sreach[3 * s + d];
+            g.cw[d] = a.scw[3 * s + d]; g.L[d] = a.Lsys[3 * s + d];
+        }
+        g.cell0 = a.scell0[s];
+    }
+    return g;
+}
+
 __global__ void k_bin(NeighborArgs a) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
+    Grid g = grid_of(a, i);
     int c[3];
     for (int d = 0; d < 3; d++) {
         double x = a.pos[d * a.n + i];
         if (!isfinite(x)) { atomicMax(a.err + 2, 1); x = 0.0; }
-        double w = floor(x / a.L[d]);
+        double w = floor(x / g.L[d]);
         if (w < -120.0 || w > 120.0) { atomicMax(a.err + 2, 2); w = 0.0; }
-        double xw = x - w * a.L[d];
-        int cd = (int)(xw / a.cell_w[d]);
-        c[d] = cd < 0 ? 0 : (cd >= a.nc[d] ? a.nc[d] - 1 : cd);
+        double xw = x - w * g.L[d];
+        int cd = (int)(xw / g.cw[d]);
+        c[d] = cd < 0 ? 0 : (cd >= g.nc[d] ? g.nc[d] - 1 : cd);
     }
-    int cell = (c[0] * a.nc[1] + c[1]) * a.nc[2] + c[2];
+    int cell = g.cell0 + (c[0] * g.nc[1] + c[1]) * g.nc[2] + c[2];
     if (a.type[i] != 0 && a.type[i] != 1) atomicMax(a.err + 3, 1);
     a.cell_of[i] = cell;
     atomicAdd(a.cell_count + cell, 1);
@@ -63,14 +85,15 @@ __global__ void k_scatter(NeighborArgs a) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     int slot = atomicAdd(a.cell_fill + a.cell_of[i], 1);
+    Grid g = grid_of(a, i);
     float xw[3];
     int wr[3];
     for (int d = 0; d < 3; d++) {
         double x = a.pos[d * a.n + i];
         if (!isfinite(x)) x = 0.0;
-        double w = floor(x / a.L[d]);
+        double w = floor(x / g.L[d]);
         if (w < -120.0 || w > 120.0) w = 0.0;
-        xw[d] = (float)(x - w * a.L[d]);
+        xw[d] = (float)(x - w * g.L[d]);
         wr[d] = (int)w;
     }
     a.spos[slot] = make_float4(xw[0], xw[1], xw[2], __int_as_float(i));
@@ -84,30 +107,31 @@ __global__ void __launch_bounds__(128) k_build(NeighborArgs a, const int* cell_s
     char4 wi = a.swrap[s];
     int i = __float_as_int(pi.w);
     int ti = wi.w;
-    int cell = a.cell_of[i];
-    int ci[3] = {cell / (a.nc[1] * a.nc[2]), (cell / a.nc[2]) % a.nc[1], cell % a.nc[2]};
+    Grid g = grid_of(a, i);
+    int cell = a.cell_of[i] - g.cell0;
+    int ci[3] = {cell / (g.nc[1] * g.nc[2]), (cell / g.nc[2]) % g.nc[1], cell % g.nc[2]};
     float lj2[2], im2[2];
     for (int t = 0; t < 2; t++) {
         lj2[t] = a.lj_rc[ti + t] * a.lj_rc[ti + t];
         im2[t] = a.im_rc[ti + t] * a.im_rc[ti + t];
     }
-    float Lf[3] = {(float)a.L[0], (float)a.L[1], (float)a.L[2]};
+    float Lf[3] = {(float)g.L[0], (float)g.L[1], (float)g.L[2]};
     int nlj = 0, nim = 0;
     int2* ljrow = a.lj + (size_t)i * a.lj_cap;
     int2* imrow = a.im + (size_t)i * a.im_cap;
-    for (int ox = -a.reach[0]; ox <= a.reach[0]; ox++) {
+    for (int ox = -g.reach[0]; ox <= g.reach[0]; ox++) {
         int qx = ci[0] + ox;
-        int sx = qx >= 0 ? qx / a.nc[0] : -((-qx + a.nc[0] - 1) / a.nc[0]);
-        int cx = qx - sx * a.nc[0];
-        for (int oy = -a.reach[1]; oy <= a.reach[1]; oy++) {
+        int sx = qx >= 0 ? qx / g.nc[0] : -((-qx + g.nc[0] - 1) / g.nc[0]);
+        int cx = qx - sx * g.nc[0];
+        for (int oy = -g.reach[1]; oy <= g.reach[1]; oy++) {
             int qy = ci[1] + oy;
-            int sy = qy >= 0 ? qy / a.nc[1] : -((-qy + a.nc[1] - 1) / a.nc[1]);
-            int cy = qy - sy * a.nc[1];
-            for (int oz = -a.reach[2]; oz <= a.reach[2]; oz++) {
+            int sy = qy >= 0 ? qy / g.nc[1] : -((-qy + g.nc[1] - 1) / g.nc[1]);
+            int cy = qy - sy * g.nc[1];
+            for (int oz = -g.reach[2]; oz <= g.reach[2]; oz++) {
                 int qz = ci[2] + oz;
-                int sz = qz >= 0 ? qz / a.nc[2] : -((-qz + a.nc[2] - 1) / a.nc[2]);
-                int cz = qz - sz * a.nc[2];
-                int c = (cx * a.nc[1] + cy) * a.nc[2] + cz;
+                int sz = qz >= 0 ? qz / g.nc[2] : -((-qz + g.nc[2] - 1) / g.nc[2]);
+                int cz = qz - sz * g.nc[2];
+                int c = g.cell0 + (cx * g.nc[1] + cy) * g.nc[2] + cz;
                 float shx = sx * Lf[0] - pi.x, shy = sy * Lf[1] - pi.y, shz = sz * Lf[2] - pi.z;
                 int e1 = cell_start[c + 1];
                 for (int t = cell_start[c]; t < e1; t++) {
@@ -141,15 +165,34 @@ __global__ void __launch_bounds__(128) k_build(NeighborArgs a, const int* cell_s
     if (nim > a.im_cap) atomicMax(a.err + 1, nim);
 }
 
-void launch_neighbor(NeighborArgs& a, cudaStream_t s) {
+void launch_neighbor(NeighborArgs& a, cudaStream_t s, int ncell) {
     if (a.n == 0) return;
-    int ncell = a.nc[0] * a.nc[1] * a.nc[2];
     cudaMemsetAsync(a.cell_count, 0, sizeof(int) * ncell, s);
     int nb = (a.n + 127) / 128;
     k_bin<<<nb, 128, 0, s>>>(a);
     k_scan<<<1, 1024, 0, s>>>(a.cell_count, a.cell_start, a.cell_fill, ncell);
     k_scatter<<<nb, 128, 0, s>>>(a);
     k_build<<<nb, 128, 0, s>>>(a, a.cell_start);
+}
+
+// per-system energy: sum of the per-atom energies of each system's atoms
+__global__ void k_system_energy(const double* eatom, const long long* off, double* out) {
+    __shared__ double red[8];
+    int s = blockIdx.x;
+    double e = 0;
+    for (long long i = off[s] + threadIdx.x; i < off[s + 1]; i += blockDim.x) e += eatom[i];
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+        out[s] = t;
+    }
+}
+
+void launch_system_energy(const double* eatom, const long long* offsets, int nsys, double* out, cudaStream_t s) {
+    if (nsys > 0) k_system_energy<<<nsys, 256, 0, s>>>(eatom, offsets, out);
 }
 
 // ------------------------------------------------------------------ NVE

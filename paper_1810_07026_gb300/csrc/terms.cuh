@@ -30,7 +30,8 @@
 
 namespace airebo {
 
-constexpr int MAXN = 8;            // REBO neighbours per atom (the bound of Sec. 4.3)
+constexpr int MAXN = 16;           // largest number of REBO neighbours per atom (slots fit 4 bits);
+                                   // the slot stride starts at 8, the bound assumed in Sec. 4.3, and grows
 constexpr int NTRI_CELLS = 4 * 4 * 8;
 
 // ------------------------------------------------------------------ images
@@ -275,9 +276,10 @@ HD R tricubic_cell(const R* a, R tx, R ty, R tz, bool clx, bool cly, bool clz, R
 }
 
 // ------------------------------------------------------------------ neighbour data
-// Short REBO list of one step: slot s of atom i at index i * MAXN + s.
+// Short REBO list of one step: slot s of atom i at index i * G.stride + s.
 template <class R> struct Graph {
     int n;
+    int stride;              // slots per atom (<= MAXN)
     const int8_t* type;
     const int* cnt;          // neighbours per atom
     const int* nj;           // neighbour atom
@@ -362,7 +364,7 @@ HD void side_forward(const DevParams<R>& P, const Graph<R>& G, int c, int o, R u
     int nc = G.cnt[c];
     s.NC = 0; s.NH = 0; s.conj = 0;
     for (int a = 0; a < nc; a++) {
-        int q = c * MAXN + a;
+        int q = c * G.stride + a;
         int k = G.nj[q];
         if (k == o) continue;
         R w = G.w[q];
@@ -378,7 +380,7 @@ HD void side_forward(const DevParams<R>& P, const Graph<R>& G, int c, int o, R u
     s.N = s.NC + s.NH;
     s.sum = 0; s.dsum_dN = 0;
     for (int a = 0; a < nc; a++) {
-        int q = c * MAXN + a;
+        int q = c * G.stride + a;
         int k = G.nj[q];
         if (k == o) continue;
         R cs = (ux * G.dx[q] + uy * G.dy[q] + uz * G.dz[q]) * inv_u * G.ir[q];
@@ -412,7 +414,7 @@ HD void side_reverse(const DevParams<R>& P, const Graph<R>& G, int c, int o, R u
     R dEdNC = dEdN + ac * s.dPdNC;
     R dEdNH = dEdN + ac * s.dPdNH;
     for (int a = 0; a < nc; a++) {
-        int q = c * MAXN + a;
+        int q = c * G.stride + a;
         int k = G.nj[q];
         if (k == o) continue;
         int tk = G.type[k];
@@ -455,7 +457,7 @@ HD void side_reverse(const DevParams<R>& P, const Graph<R>& G, int c, int o, R u
             R coef = dEdconj * w * dFx;
             int nk = G.cnt[k];
             for (int b = 0; b < nk; b++) {
-                int qq = k * MAXN + b;
+                int qq = k * G.stride + b;
                 int m = G.nj[qq];
                 if (m == c) continue;
                 R dwm = G.dw[qq];
@@ -485,7 +487,7 @@ HD R dihedral_sum(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, 
     R D = 0;
     int ni = G.cnt[i], nj = G.cnt[j];
     for (int a = 0; a < ni; a++) {
-        int qa = i * MAXN + a;
+        int qa = i * G.stride + a;
         int k = G.nj[qa];
         if (k == j) continue;
         R ax = G.dx[qa], ay = G.dy[qa], az = G.dz[qa];
@@ -499,7 +501,7 @@ HD R dihedral_sum(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, 
         R n1s = n1x * n1x + n1y * n1y + n1z * n1z;
         R in1s = R(1) / n1s;
         for (int b = 0; b < nj; b++) {
-            int qb = j * MAXN + b;
+            int qb = j * G.stride + b;
             int l = G.nj[qb];
             if (l == i || l == k) continue;
             R bx = G.dx[qb], by = G.dy[qb], bz = G.dz[qb];
@@ -606,7 +608,7 @@ HD R bond_order(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, R 
 // ------------------------------------------------------------------ REBO bond (Alg. 1)
 template <class R>
 HD double rebo_bond(const DevParams<R>& P, const Graph<R>& G, int i, int slot, Sink& sink) {
-    int q = i * MAXN + slot;
+    int q = i * G.stride + slot;
     int j = G.nj[q];
     int p = pidx(G.type[i], G.type[j]);
     R ux = G.dx[q], uy = G.dy[q], uz = G.dz[q], r = G.r[q], ir = G.ir[q];
@@ -646,7 +648,7 @@ HD double rebo_bond(const DevParams<R>& P, const Graph<R>& G, int i, int slot, S
 // omega is the dihedral angle with trans = pi; cos^2(omega/2) = (1 + cos omega)/2
 template <class R>
 HD double torsion_bond(const DevParams<R>& P, const Graph<R>& G, int i, int slot, Sink& sink) {
-    int q = i * MAXN + slot;
+    int q = i * G.stride + slot;
     int j = G.nj[q];
     R ux = G.dx[q], uy = G.dy[q], uz = G.dz[q];
     R wij = G.w[q], dwij = G.dw[q];
@@ -657,7 +659,7 @@ HD double torsion_bond(const DevParams<R>& P, const Graph<R>& G, int i, int slot
     double fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
     int ni = G.cnt[i], nj = G.cnt[j];
     for (int a = 0; a < ni; a++) {
-        int qa = i * MAXN + a;
+        int qa = i * G.stride + a;
         int k = G.nj[qa];
         if (k == j) continue;
         R ax = G.dx[qa], ay = G.dy[qa], az = G.dz[qa];
@@ -671,7 +673,7 @@ HD double torsion_bond(const DevParams<R>& P, const Graph<R>& G, int i, int slot
         R n1s = n1x * n1x + n1y * n1y + n1z * n1z;
         R in1s = R(1) / n1s;
         for (int b = 0; b < nj; b++) {
-            int qb = j * MAXN + b;
+            int qb = j * G.stride + b;
             int l = G.nj[qb];
             if (l == i || l == k) continue;
             R bx = G.dx[qb], by = G.dy[qb], bz = G.dz[qb];
@@ -774,9 +776,9 @@ HD int build_path_map(const Graph<R>& G, PathMap<R>& M, int i) {
         for (int e = 0; e < count; e++) {
             if (M.key[base + e] == key) {
                 int p0 = M.path[base + e];
-                int k0 = path_len(p0) >= 2 ? G.nj[i * MAXN + path_a(p0)] : -1;
+                int k0 = path_len(p0) >= 2 ? G.nj[i * G.stride + path_a(p0)] : -1;
                 int l0 = -1;
-                if (path_len(p0) == 3) l0 = G.nj[G.nj[i * MAXN + path_a(p0)] * MAXN + path_b(p0)];
+                if (path_len(p0) == 3) l0 = G.nj[G.nj[i * G.stride + path_a(p0)] * G.stride + path_b(p0)];
                 if (path_better((double)c, len, k, l, (double)M.wt[base + e], path_len(p0), k0, l0)) {
                     M.wt[base + e] = c;
                     M.path[base + e] = code;
@@ -795,14 +797,14 @@ HD int build_path_map(const Graph<R>& G, PathMap<R>& M, int i) {
     };
     int ni = G.cnt[i];
     for (int a = 0; a < ni; a++) {
-        int qa = i * MAXN + a;
+        int qa = i * G.stride + a;
         int k = G.nj[qa];
         int Sk = G.nimg[qa];
         R w1 = G.w[qa], c1 = G.omw[qa];
         insert(k, Sk, c1, 1, -1, -1, path_pack(1, a, 0, 0));
         int nk = G.cnt[k];
         for (int b = 0; b < nk; b++) {
-            int qb = k * MAXN + b;
+            int qb = k * G.stride + b;
             int l = G.nj[qb];
             if (l == i) continue;
             int Sl = img_add(Sk, G.nimg[qb]);
@@ -811,7 +813,7 @@ HD int build_path_map(const Graph<R>& G, PathMap<R>& M, int i) {
             insert(l, Sl, c2, 2, k, -1, path_pack(2, a, b, 0));
             int nl = G.cnt[l];
             for (int c = 0; c < nl; c++) {
-                int qc = l * MAXN + c;
+                int qc = l * G.stride + c;
                 int m = G.nj[qc];
                 if (m == i || m == k) continue;
                 int Sm = img_add(Sl, G.nimg[qc]);
@@ -828,10 +830,10 @@ template <class R>
 HD void path_forces(const Graph<R>& G, int i, int code, R dEdw, Sink& sink, double& fix, double& fiy, double& fiz) {
     int len = path_len(code);
     int q[3], from[3];
-    q[0] = i * MAXN + path_a(code); from[0] = i;
+    q[0] = i * G.stride + path_a(code); from[0] = i;
     int k = G.nj[q[0]];
-    if (len >= 2) { q[1] = k * MAXN + path_b(code); from[1] = k; }
-    if (len == 3) { int l = G.nj[q[1]]; q[2] = l * MAXN + path_c(code); from[2] = l; }
+    if (len >= 2) { q[1] = k * G.stride + path_b(code); from[1] = k; }
+    if (len == 3) { int l = G.nj[q[1]]; q[2] = l * G.stride + path_c(code); from[2] = l; }
     R w[3], dw[3];
     for (int s = 0; s < len; s++) { w[s] = G.w[q[s]]; dw[s] = G.dw[q[s]]; }
     for (int s = 0; s < len; s++) {

@@ -270,6 +270,53 @@ def amorphous(n: int, h_per_c: float, density_gcc: float, seed: int = 1,
     return np.ascontiguousarray(pos.T), types, box
 
 
+def amorphous_kd(n: int, h_per_c: float, density_gcc: float, seed: int = 1, min_sep: float = 1.0):
+    """Amorphous C:H box by seeded random insertion with a minimum separation,
+    accepting candidates in batches (a periodic KD-tree rejects those too close
+    to accepted atoms or to earlier candidates of the same batch)."""
+    from scipy.spatial import cKDTree
+    rng = np.random.default_rng(seed)
+    nc = int(round(n / (1.0 + h_per_c)))
+    types = np.zeros(n, dtype=np.int8)
+    types[nc:] = 1
+    rng.shuffle(types)
+    mass = np.where(types == 0, MASS[0], MASS[1]).sum()
+    L = (mass / 0.602214076 / density_gcc) ** (1.0 / 3.0)
+    acc = np.zeros((0, 3))
+    for _ in range(200):
+        need = n - len(acc)
+        if need == 0:
+            break
+        cand = rng.uniform(0.0, L, (max(2 * need, 64), 3))
+        if len(acc):
+            dist, _ = cKDTree(acc, boxsize=L).query(cand, k=1, distance_upper_bound=min_sep)
+            cand = cand[~np.isfinite(dist)]
+        keep = np.ones(len(cand), dtype=bool)
+        if len(cand) > 1:
+            for i, j in sorted(cKDTree(cand, boxsize=L).query_pairs(min_sep)):
+                if keep[i] and keep[j]:
+                    keep[j] = False
+        acc = np.vstack([acc, cand[keep][:need]])
+    if len(acc) < n:
+        raise RuntimeError("random insertion failed; density too high for min_sep")
+    return np.ascontiguousarray(acc.T), types, np.array([L, L, L])
+
+
+def ensemble(nsys: int = 256, nmin: int = 200, nmax: int = 8000, density_gcc: float = 0.9,
+             hc: tuple = (0.5, 2.0), seed: int = 7):
+    """Independent amorphous C:H boxes of uneven size, concatenated: positions
+    (3, N), types (N,), offsets (nsys + 1,), boxes (nsys, 3)."""
+    rng = np.random.default_rng(seed)
+    sizes = rng.integers(nmin, nmax + 1, nsys)
+    ratios = rng.uniform(hc[0], hc[1], nsys)
+    pos, typ, boxes = [], [], []
+    for s in range(nsys):
+        p, t, b = amorphous_kd(int(sizes[s]), float(ratios[s]), density_gcc, seed=seed * 100003 + s)
+        pos.append(p); typ.append(t); boxes.append(b)
+    offsets = np.concatenate([[0], np.cumsum([len(t) for t in typ])]).astype(np.int64)
+    return np.ascontiguousarray(np.hstack(pos)), np.concatenate(typ), offsets, np.array(boxes)
+
+
 def velocities(types, temperature: float, seed: int = 2):
     """Maxwell-Boltzmann velocities in A/fs with zero total momentum."""
     rng = np.random.default_rng(seed)

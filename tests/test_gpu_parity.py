@@ -184,12 +184,12 @@ def test_errors(A, param_text):
     with pytest.raises(A.AireboError) as ex:
         ev.compute(bad)
     assert ex.value.status == A.ERR_NONFINITE
-    # more than 8 REBO neighbours: a tight cluster of 12 carbons
+    # more than 16 REBO neighbours: a cluster of 20 carbons within 2 A of each other
     rng = np.random.default_rng(0)
-    cl = rng.uniform(-0.7, 0.7, (3, 12)) + 10.0
+    cl = rng.uniform(-0.5, 0.5, (3, 20)) + 10.0
     ev2 = A.Airebo(param_text)
     pc = torch.tensor(cl, device="cuda")
-    ev2.neighbor(pc, torch.zeros(12, dtype=torch.int8, device="cuda"), [20.0, 20.0, 20.0])
+    ev2.neighbor(pc, torch.zeros(20, dtype=torch.int8, device="cuda"), [20.0, 20.0, 20.0])
     with pytest.raises(A.AireboError) as ex:
         ev2.compute(pc)
     assert ex.value.status == A.ERR_CAPACITY
