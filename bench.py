@@ -278,6 +278,7 @@ def run_ours(args):
             vel = torch.tensor(vel0, device=dev)
             t = torch.tensor(types, device=dev)
             ev.neighbor(pos, t, box)
+            shape = ev.autotune(pos)
             f, e4, _ = ev.compute(pos)
             forces[name] = f.clone()
             e_start = ev.nve(pos, vel, f, DT, 1)
@@ -310,7 +311,7 @@ def run_ours(args):
             e_end = ev.nve(pos, vel, f, DT, 1).cpu().numpy()
             e_beg = e_start.cpu().numpy()
             ms = max_over_ranks(ms, dist, dev)
-            results[name] = dict(ms=ms, kt=kt, clocks=ck, builds=builds, counters=ev.counters(),
+            results[name] = dict(ms=ms, kt=kt, clocks=ck, shape=shape, builds=builds, counters=ev.counters(),
                                  drift=(e_end[2] - e_beg[2]) / (args.steps + args.warmup + 1) / n,
                                  etot=float(e_end[2]))
             ev.close()
@@ -322,6 +323,7 @@ def run_ours(args):
     e2e = None
     with torch.cuda.stream(stream):
         ev = A.Airebo(params, precision=A.FP64, stream=stream)
+        ev.set_launch_shape(*results["fp64"]["shape"])
         hp = torch.tensor(pos0).pin_memory()
         hv = torch.tensor(vel0).pin_memory()
         hf = torch.zeros_like(hp).pin_memory()
@@ -389,6 +391,8 @@ def run_ours(args):
                           "kernel_ms": {k: v[0] / max(1, v[1]) for k, v in results["rebo_only"]["kt"].items()}},
             "drift_eV_per_atom_step": r64["drift"],
             "list_builds_in_timed_region": r64["builds"],
+            "launch_shape": {k: {"lj_atoms_per_claim": results[k]["shape"][0],
+                                 "bond_blocks_per_sm": results[k]["shape"][1]} for k in results},
             "kernel_ms": {k: v[0] / max(1, v[1]) for k, v in kt.items()},
             "kernel_share": {k: v[0] / max(1e-9, sum(x[0] for x in kt.values())) for k, v in kt.items()},
             "roofline": roof,

@@ -232,6 +232,25 @@ airebo_status airebo_graph_capture(airebo_handle h, const double* d_pos, double*
 airebo_status airebo_graph_launch(airebo_handle h);
 
 /*
+ * Pick the launch shapes for this handle's system by timing them with CUDA
+ * events on the handle's stream: the number of atoms an LJ warp takes at a
+ * time (2..32) and the blocks per SM of the grid-stride REBO, torsion and b*
+ * kernels (4..16).  Runs about 25 evaluations at d_pos (d_force is
+ * overwritten).  out2 (nullable, host int[2]) receives the choice.  A graph
+ * captured earlier keeps the shapes it was captured with.  Errors: those of
+ * airebo_compute; AIREBO_ERR_STATE before airebo_neighbor.
+ */
+airebo_status airebo_autotune(airebo_handle h, const double* d_pos, double* d_force, int* out2);
+
+/*
+ * Set the launch shapes directly (for example to copy a tuned choice to
+ * another handle of the same system): lj_chunk in 1..64 atoms per warp claim,
+ * grid_per_sm in 1..32.  AIREBO_ERR_ARG outside those ranges.  Results do not
+ * depend on the shapes beyond the order of floating-point atomic additions.
+ */
+airebo_status airebo_set_launch_shape(airebo_handle h, int lj_chunk, int grid_per_sm);
+
+/*
  * Rebuild check that allocates no device memory (the paper has no
  * counterpart: it is a service for callers that cannot call cudaMalloc, such
  * as code running inside a framework that owns all device memory, or code

@@ -69,6 +69,8 @@ def lib():
             "airebo_check": (I, [P]),
             "airebo_graph_capture": (I, [P, P, P, P, P]),
             "airebo_graph_launch": (I, [P]),
+            "airebo_autotune": (I, [P, P, P, P]),
+            "airebo_set_launch_shape": (I, [P, I, I]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -185,6 +187,19 @@ class Airebo:
     def graph_capture(self, pos, force, energy4=None, energy_sys=None):
         """Capture one evaluation with these buffers into a CUDA graph."""
         self._check(lib().airebo_graph_capture(self._h, _ptr(pos), _ptr(force), _ptr(energy4), _ptr(energy_sys)))
+
+    def autotune(self, pos, force=None):
+        """Time the launch shapes on this system; returns (LJ atoms per warp claim, bond grid blocks per SM)."""
+        torch = self._torch
+        pos = self._dev(pos, torch.float64)
+        if force is None:
+            force = torch.empty_like(pos)
+        out = np.zeros(2, dtype=np.int32)
+        self._check(lib().airebo_autotune(self._h, _ptr(pos), _ptr(force), _np(out)))
+        return int(out[0]), int(out[1])
+
+    def set_launch_shape(self, lj_chunk, grid_per_sm):
+        self._check(lib().airebo_set_launch_shape(self._h, int(lj_chunk), int(grid_per_sm)))
 
     def graph_launch(self):
         self._check(lib().airebo_graph_launch(self._h))

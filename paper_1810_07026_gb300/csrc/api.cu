@@ -294,6 +294,7 @@ struct airebo_ctx {
     unsigned long long* counters = nullptr;   // 8
     int* derr = nullptr;                 // 8 ints
     int stride = 8;                      // REBO slots per atom (grows to MAXN)
+    int lj_chunk = 8, grid_per_sm = 8;   // launch shapes (airebo_autotune)
     // batched systems (nsys = 0: one system with box L)
     int nsys = 0;
     std::vector<double> Lsys_h;
@@ -553,6 +554,8 @@ template <class R> StepArgs<R> make_args(airebo_handle h, Precision<R>& pr, cons
     a.bq = h->bq; a.nbq = h->counts + 4; a.bq_cap = h->bq_cap;
     a.bq2 = h->bq2; a.bq2_eps = h->bq2_eps; a.nbq2 = h->counts + 3;
     a.lj_next = h->counts + 7;
+    a.lj_chunk = h->lj_chunk;
+    a.grid_per_sm = h->grid_per_sm;
     a.f = d_force; a.acc = h->acc; a.counters = h->counters; a.err = h->derr;
     a.virial = virial;
     a.sys = h->nsys ? h->d_sys : nullptr;
@@ -1005,6 +1008,60 @@ airebo_status airebo_graph_launch(airebo_handle h) {
     if (!h->gexec) return fail(h, AIREBO_ERR_STATE, "no captured graph");
     CK(cudaSetDevice(h->device));
     CK(cudaGraphLaunch(h->gexec, h->stream));
+    return AIREBO_OK;
+}
+
+airebo_status airebo_autotune(airebo_handle h, const double* d_pos, double* d_force, int* out2) {
+    if (!h) return AIREBO_ERR_ARG;
+    if (h->n > 0 && (!d_pos || !d_force)) return fail(h, AIREBO_ERR_ARG, "null position or force pointer");
+    if (!h->built) return fail(h, AIREBO_ERR_STATE, "airebo_autotune before airebo_neighbor");
+    CK(cudaSetDevice(h->device));
+    bool was_timing = h->timing;
+    airebo_status st = airebo_set_timing(h, 1);
+    if (st) return st;
+    st = compute_any(h, d_pos, d_force, nullptr, nullptr);        // settle every capacity first
+    if (st) return st;
+    const int chunks[] = {2, 4, 8, 16, 32};
+    const int grids[] = {4, 8, 16};
+    double best_lj = 1e300, best_b = 1e300;
+    int bc = h->lj_chunk, bg = h->grid_per_sm;
+    // the LJ chunk and the bond-kernel grid act on different kernels: tune each
+    for (int c : chunks) {
+        if (!h->opt.enable_lj) break;
+        h->lj_chunk = c;
+        double t = 0;
+        for (int rep = 0; rep < 3; rep++) {
+            for (int k = 0; k < 8; k++) { h->kt_ms[k] = 0; h->kt_n[k] = 0; }
+            st = compute_any(h, d_pos, d_force, nullptr, nullptr);
+            if (st) return st;
+            if (rep > 0) t += h->kt_ms[4];
+        }
+        if (t < best_lj) { best_lj = t; bc = c; }
+    }
+    h->lj_chunk = bc;
+    for (int g : grids) {
+        h->grid_per_sm = g;
+        double t = 0;
+        for (int rep = 0; rep < 3; rep++) {
+            for (int k = 0; k < 8; k++) { h->kt_ms[k] = 0; h->kt_n[k] = 0; }
+            st = compute_any(h, d_pos, d_force, nullptr, nullptr);
+            if (st) return st;
+            if (rep > 0) t += h->kt_ms[1] + h->kt_ms[2] + h->kt_ms[5];
+        }
+        if (t < best_b) { best_b = t; bg = g; }
+    }
+    h->grid_per_sm = bg;
+    airebo_set_timing(h, was_timing ? 1 : 0);
+    if (out2) { out2[0] = h->lj_chunk; out2[1] = h->grid_per_sm; }
+    return AIREBO_OK;
+}
+
+airebo_status airebo_set_launch_shape(airebo_handle h, int lj_chunk, int grid_per_sm) {
+    if (!h) return AIREBO_ERR_ARG;
+    if (lj_chunk < 1 || lj_chunk > 64 || grid_per_sm < 1 || grid_per_sm > 32)
+        return fail(h, AIREBO_ERR_ARG, "launch shape out of range (lj_chunk 1..64, grid_per_sm 1..32)");
+    h->lj_chunk = lj_chunk;
+    h->grid_per_sm = grid_per_sm;
     return AIREBO_OK;
 }
 

@@ -38,6 +38,8 @@ template <class R> struct StepArgs {
     int4* bq; int* nbq; int bq_cap;
     int* bq2; double* bq2_eps; int* nbq2;  // b* pairs whose S_b is in its transition, and dE/db*
     int* lj_next;                          // work counter of the LJ kernel's warps
+    int lj_chunk;                          // atoms a warp takes at a time (tuned)
+    int grid_per_sm;                       // blocks per SM of the grid-stride bond and b* kernels (tuned)
     const int* sys;                        // batched systems: system of each atom (null: one system, box L)
     const double* Lsys;                    // batched systems: box of each system (3 per system)
     double* eatom;                         // nullable: energy of each atom's anchored terms

@@ -184,7 +184,6 @@ __global__ void __launch_bounds__(128) k_path_map(StepArgs<R> a) {
 // so no lane idles through it.  Pairs with S_r != 0 go to the b* queue.
 constexpr int LJ_THREADS = 256;
 constexpr int LJ_WARPS = LJ_THREADS / 32;
-constexpr int LJ_CHUNK = 8;
 
 // two compaction buffers per warp: 0 = inner pairs, 1 = pairs in the cut-off switch
 template <class R> struct LjBuf {
@@ -218,16 +217,16 @@ __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
     double E = 0;
     unsigned evaluated = 0;
     int n = a.n;
-    // warps take chunks of LJ_CHUNK consecutive atoms from a global counter,
+    // warps take chunks of lj_chunk consecutive atoms from a global counter,
     // which balances C and H atoms (different list lengths) across warps
     int chunk_end = 0;
     for (int i = 0;; i++) {
         if (i >= chunk_end) {
             int c = 0;
-            if (lane == 0) c = atomicAdd(a.lj_next, LJ_CHUNK);
+            if (lane == 0) c = atomicAdd(a.lj_next, a.lj_chunk);
             c = __shfl_sync(0xffffffffu, c, 0);
             if (c >= n) break;
-            chunk_end = min(c + LJ_CHUNK, n);
+            chunk_end = min(c + a.lj_chunk, n);
             i = c;
         }
         double xi = a.pos[i], yi = a.pos[n + i], zi = a.pos[2 * n + i];
@@ -387,7 +386,7 @@ void launch_compute_impl(const StepArgs<R>& a, cudaStream_t s, int num_sms, cuda
     if (a.n == 0) return;
     int n = a.n;
     auto mark = [&](int k) { if (ev) cudaEventRecord(ev[k], s); };
-    int grid_bonds = num_sms * 8;
+    int grid_bonds = num_sms * a.grid_per_sm;
     mark(0);
     k_short_list<R><<<(n + 127) / 128, 128, 0, s>>>(a);
     mark(1);
