@@ -233,22 +233,46 @@ airebo_status airebo_graph_launch(airebo_handle h);
 
 /*
  * Pick the launch shapes for this handle's system by timing them with CUDA
- * events on the handle's stream: the number of atoms an LJ warp takes at a
- * time (2..32) and the blocks per SM of the grid-stride REBO, torsion and b*
- * kernels (4..16).  Runs about 25 evaluations at d_pos (d_force is
- * overwritten).  out2 (nullable, host int[2]) receives the choice.  A graph
- * captured earlier keeps the shapes it was captured with.  Errors: those of
- * airebo_compute; AIREBO_ERR_STATE before airebo_neighbor.
+ * events on the handle's stream: the number of atoms an LJ warp claims at a
+ * time (2..32), and the blocks per SM of the grid-stride REBO/torsion kernels
+ * and of the b* kernels (4, 8 or 16 each); each candidate is the median of 5
+ * evaluations.  Runs about 45 evaluations at d_pos (d_force is overwritten).
+ * out3 (nullable, host int[3]) receives (lj_chunk, bond_grid, bstar_grid).  A
+ * graph captured earlier keeps the shapes it was captured with.  Errors:
+ * those of airebo_compute; AIREBO_ERR_STATE before airebo_neighbor.
  */
-airebo_status airebo_autotune(airebo_handle h, const double* d_pos, double* d_force, int* out2);
+airebo_status airebo_autotune(airebo_handle h, const double* d_pos, double* d_force, int* out3);
 
 /*
  * Set the launch shapes directly (for example to copy a tuned choice to
  * another handle of the same system): lj_chunk in 1..64 atoms per warp claim,
- * grid_per_sm in 1..32.  AIREBO_ERR_ARG outside those ranges.  Results do not
- * depend on the shapes beyond the order of floating-point atomic additions.
+ * bond_grid and bstar_grid in 1..32 blocks per SM.  AIREBO_ERR_ARG outside
+ * those ranges.  Results do not depend on the shapes beyond the order of
+ * floating-point atomic additions.
  */
-airebo_status airebo_set_launch_shape(airebo_handle h, int lj_chunk, int grid_per_sm);
+airebo_status airebo_set_launch_shape(airebo_handle h, int lj_chunk, int bond_grid, int bstar_grid);
+
+/*
+ * Gradient of the total energy with respect to every spline knot datum of the
+ * parameter set (the tabulated data of the angular functions g_C, gamma_C and
+ * g_H, of the P_ij bicubic correction and of the pi^rc and T_ij tricubic
+ * splines, Sec. 2 (REBO bond order)), for fitting.  Each spline is built from
+ * its knot data linearly, so the energy depends on a datum only through the
+ * bond orders (b_ij and the b* of the LJ switch) that read it.
+ *
+ * Also evaluates forces and energy like airebo_compute (d_energy4 nullable).
+ * h_grad: host double[AIREBO_KNOT_COUNT] in the parameter file's order and
+ * layout: gC1.data (18), gC2.data (18), gH.data (12), P.CC, P.CH, P.HC (100
+ * each: 5 x 5 knots x (f, f_NC, f_NH, f_NC_NH)), piRC.CC, piRC.CH, piRC.HH
+ * and Tij.CC (1800 each: 5 x 5 x 9 knots x (f, fx, fy, fz, fxy, fxz, fyz,
+ * fxyz)).  count must equal AIREBO_KNOT_COUNT.  The gradient is in the
+ * handle's precision; the first call allocates a device buffer of about
+ * 270 KB that the handle keeps.  Errors: those of airebo_compute;
+ * AIREBO_ERR_ARG for a wrong count.
+ */
+#define AIREBO_KNOT_COUNT 7548
+airebo_status airebo_knot_grad(airebo_handle h, const double* d_pos, double* d_force, double* d_energy4,
+                               double* h_grad, int64_t count);
 
 /*
  * Rebuild check that allocates no device memory (the paper has no

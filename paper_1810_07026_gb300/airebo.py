@@ -20,6 +20,10 @@ LIB_PATH = os.path.join(_PKG, "libairebo.so")
 OK, ERR_ARG, ERR_CUDA, ERR_CAPACITY, ERR_TIMEOUT, ERR_NONFINITE, ERR_STATE = range(7)
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_CAPACITY", 4: "ERR_TIMEOUT", 5: "ERR_NONFINITE", 6: "ERR_STATE"}
 FP64, MIXED = 0, 1
+# the spline knot data, in the order of the parameter file and of knot_grad()
+KNOT_BLOCKS = (("gC1.data", 18), ("gC2.data", 18), ("gH.data", 12), ("P.CC", 100), ("P.CH", 100), ("P.HC", 100),
+               ("piRC.CC", 1800), ("piRC.CH", 1800), ("piRC.HH", 1800), ("Tij.CC", 1800))
+KNOT_COUNT = sum(c for _, c in KNOT_BLOCKS)
 KERNELS = ("short_list", "rebo", "torsion", "path_map", "lj", "bstar", "neighbor", "nve")
 
 
@@ -62,6 +66,7 @@ def lib():
             "airebo_kernel_times": (I, [P, P, P]),
             "airebo_alu_peak": (I, [I, P]),
             "airebo_param_grad": (I, [P, P, P, P, P]),
+            "airebo_knot_grad": (I, [P, P, P, P, P, I64]),
             "airebo_set_lj_params": (I, [P, P, P]),
             "airebo_neighbor_batch": (I, [P, P, P, I64, I, P, P]),
             "airebo_compute_batch": (I, [P, P, P, P]),
@@ -70,7 +75,7 @@ def lib():
             "airebo_graph_capture": (I, [P, P, P, P, P]),
             "airebo_graph_launch": (I, [P]),
             "airebo_autotune": (I, [P, P, P, P]),
-            "airebo_set_launch_shape": (I, [P, I, I]),
+            "airebo_set_launch_shape": (I, [P, I, I, I]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -189,17 +194,18 @@ class Airebo:
         self._check(lib().airebo_graph_capture(self._h, _ptr(pos), _ptr(force), _ptr(energy4), _ptr(energy_sys)))
 
     def autotune(self, pos, force=None):
-        """Time the launch shapes on this system; returns (LJ atoms per warp claim, bond grid blocks per SM)."""
+        """Time the launch shapes on this system; returns (LJ atoms per warp claim, REBO/torsion and b*
+        blocks per SM)."""
         torch = self._torch
         pos = self._dev(pos, torch.float64)
         if force is None:
             force = torch.empty_like(pos)
-        out = np.zeros(2, dtype=np.int32)
+        out = np.zeros(3, dtype=np.int32)
         self._check(lib().airebo_autotune(self._h, _ptr(pos), _ptr(force), _np(out)))
-        return int(out[0]), int(out[1])
+        return int(out[0]), int(out[1]), int(out[2])
 
-    def set_launch_shape(self, lj_chunk, grid_per_sm):
-        self._check(lib().airebo_set_launch_shape(self._h, int(lj_chunk), int(grid_per_sm)))
+    def set_launch_shape(self, lj_chunk, bond_grid, bstar_grid):
+        self._check(lib().airebo_set_launch_shape(self._h, int(lj_chunk), int(bond_grid), int(bstar_grid)))
 
     def graph_launch(self):
         self._check(lib().airebo_graph_launch(self._h))
@@ -224,6 +230,17 @@ class Airebo:
         e4 = torch.empty(4, dtype=torch.float64, device=self.device)
         g = np.zeros(6)
         self._check(lib().airebo_param_grad(self._h, _ptr(pos), _ptr(force), _ptr(e4), _np(g)))
+        return force, e4, g
+
+    def knot_grad(self, pos, force=None):
+        """Forces, energies and dE/d(spline knot data), KNOT_COUNT values in the parameter file's order."""
+        torch = self._torch
+        pos = self._dev(pos, torch.float64)
+        if force is None:
+            force = torch.empty_like(pos)
+        e4 = torch.empty(4, dtype=torch.float64, device=self.device)
+        g = np.zeros(KNOT_COUNT)
+        self._check(lib().airebo_knot_grad(self._h, _ptr(pos), _ptr(force), _ptr(e4), _np(g), KNOT_COUNT))
         return force, e4, g
 
     def set_lj_params(self, eps=None, sigma=None):

@@ -145,6 +145,71 @@ bool quintic_coeffs(const std::vector<double>& kn, const std::vector<double>& d,
     return true;
 }
 
+// Transposes of the three coefficient builders above: given dE/d(coefficient),
+// accumulate dE/d(knot datum).  The builders are linear in the knot data, so
+// these are exact.
+void bicubic_coeffs_adjoint(const double* g, double* out) {
+    const int comp[2][2] = {{0, 2}, {1, 3}};
+    for (int ix = 0; ix < 4; ix++)
+        for (int iy = 0; iy < 4; iy++) {
+            const double* a = g + (ix * 4 + iy) * 16;
+            for (int ex = 0; ex < 2; ex++)
+                for (int ey = 0; ey < 2; ey++)
+                    for (int dx = 0; dx < 2; dx++)
+                        for (int dy = 0; dy < 2; dy++) {
+                            double s = 0;
+                            for (int p = 0; p < 4; p++)
+                                for (int q = 0; q < 4; q++) s += a[p * 4 + q] * HB[dx][ex][p] * HB[dy][ey][q];
+                            out[((ix + ex) * 5 + (iy + ey)) * 4 + comp[dx][dy]] += s;
+                        }
+        }
+}
+
+void tricubic_coeffs_adjoint(const double* g, double* out) {
+    int comp[2][2][2];
+    comp[0][0][0] = 0; comp[1][0][0] = 1; comp[0][1][0] = 2; comp[0][0][1] = 3;
+    comp[1][1][0] = 4; comp[1][0][1] = 5; comp[0][1][1] = 6; comp[1][1][1] = 7;
+    for (int ix = 0; ix < 4; ix++)
+        for (int iy = 0; iy < 4; iy++)
+            for (int iz = 0; iz < 8; iz++) {
+                const double* a = g + ((ix * 4 + iy) * 8 + iz) * 64;
+                for (int ex = 0; ex < 2; ex++)
+                    for (int ey = 0; ey < 2; ey++)
+                        for (int ez = 0; ez < 2; ez++)
+                            for (int dx = 0; dx < 2; dx++)
+                                for (int dy = 0; dy < 2; dy++)
+                                    for (int dz = 0; dz < 2; dz++) {
+                                        double s = 0;
+                                        for (int p = 0; p < 4; p++)
+                                            for (int q = 0; q < 4; q++) {
+                                                double hpq = HB[dx][ex][p] * HB[dy][ey][q];
+                                                for (int r = 0; r < 4; r++)
+                                                    s += a[(p * 4 + q) * 4 + r] * hpq * HB[dz][ez][r];
+                                            }
+                                        out[(((ix + ex) * 5 + (iy + ey)) * 9 + (iz + ez)) * 8 + comp[dx][dy][dz]] += s;
+                                    }
+            }
+}
+
+// g: [interval m][power p]; out: (value, slope, curvature) per knot
+void quintic_coeffs_adjoint(const std::vector<double>& kn, const double* g, double* out) {
+    int n = (int)kn.size() - 1;
+    for (int m = 0; m < n; m++) {
+        double h = kn[m + 1] - kn[m];
+        double gw[6];
+        for (int b = 0; b < 6; b++) {
+            gw[b] = 0;
+            for (int p = 0; p < 6; p++) gw[b] += QB[b][p] * g[m * 6 + p];
+        }
+        out[3 * m] += gw[0];
+        out[3 * m + 1] += h * gw[1];
+        out[3 * m + 2] += h * h * gw[2];
+        out[3 * (m + 1) + 2] += h * h * gw[3];
+        out[3 * (m + 1) + 1] += h * gw[4];
+        out[3 * (m + 1)] += gw[5];
+    }
+}
+
 struct Scalars {
     double Dmin[3], Dmax[3], Q[3], alpha[3], A[3], B[3][3], beta[3][3], rho[3];
     double lam, gN[2], Fx[2], guard[2], sigma[3], eps[3], ljcut, ljsw, Sr[2], bmin[3], bmax[3], rstar[3], teps[3];
@@ -294,7 +359,7 @@ struct airebo_ctx {
     unsigned long long* counters = nullptr;   // 8
     int* derr = nullptr;                 // 8 ints
     int stride = 8;                      // REBO slots per atom (grows to MAXN)
-    int lj_chunk = 8, grid_per_sm = 8;   // launch shapes (airebo_autotune)
+    int lj_chunk = 8, bond_grid = 8, bstar_grid = 8;   // launch shapes (airebo_autotune)
     // batched systems (nsys = 0: one system with box L)
     int nsys = 0;
     std::vector<double> Lsys_h;
@@ -310,6 +375,7 @@ struct airebo_ctx {
     unsigned long long* maxd2 = nullptr;
     double* ke = nullptr;
     double* pg = nullptr;                // parameter gradients (6)
+    double* kg = nullptr;                // spline-coefficient gradients (KG_N)
     // pinned mirrors
     int* h_err = nullptr;
     unsigned long long* h_u64 = nullptr;
@@ -358,6 +424,7 @@ template <class R> airebo_status upload_params(airebo_handle h, Precision<R>& pr
     pr.hp.Ftab = pr.b.tables + 3 * 256;
     pr.hp.Ttab = pr.b.tables + 3 * 256 + 3 * NTRI_CELLS * 64;
     pr.hp.Tnz = pr.b.Tnz;
+    pr.hp.kg = nullptr;
     CK(cudaMemcpy(pr.b.P, &pr.hp, sizeof(DevParams<R>), cudaMemcpyHostToDevice));
     return AIREBO_OK;
 }
@@ -385,7 +452,7 @@ template <class R> airebo_status grow_map(airebo_handle h, Precision<R>& pr, int
 
 template <class R> void free_prec(Precision<R>& pr) {
     StepBuffers<R>& b = pr.b;
-    void* ps[] = {b.P, b.tables, b.Tnz, b.cnt, b.nj, b.nimg, b.dx, b.dy, b.dz, b.r, b.ir, b.w, b.dw, b.omw, b.nC, b.nH,
+    void* ps[] = {b.P, b.Pkg, b.tables, b.Tnz, b.cnt, b.nj, b.nimg, b.dx, b.dy, b.dz, b.r, b.ir, b.w, b.dw, b.omw, b.nC, b.nH,
                   b.map_cnt, b.map_key, b.map_wt, b.map_path};
     for (void* p : ps) if (p) cudaFree(p);
     b = StepBuffers<R>();
@@ -555,7 +622,8 @@ template <class R> StepArgs<R> make_args(airebo_handle h, Precision<R>& pr, cons
     a.bq2 = h->bq2; a.bq2_eps = h->bq2_eps; a.nbq2 = h->counts + 3;
     a.lj_next = h->counts + 7;
     a.lj_chunk = h->lj_chunk;
-    a.grid_per_sm = h->grid_per_sm;
+    a.bond_grid = h->bond_grid;
+    a.bstar_grid = h->bstar_grid;
     a.f = d_force; a.acc = h->acc; a.counters = h->counters; a.err = h->derr;
     a.virial = virial;
     a.sys = h->nsys ? h->d_sys : nullptr;
@@ -572,7 +640,8 @@ template <class R> StepArgs<R> make_args(airebo_handle h, Precision<R>& pr, cons
 // capacity flags are read by airebo_check), as needed for graph capture.
 template <class R>
 airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos, double* d_force, double* d_e4,
-                         double* d_w6, double* d_pgrad = nullptr, double* d_esys = nullptr, bool async = false) {
+                         double* d_w6, double* d_pgrad = nullptr, double* d_esys = nullptr, bool async = false,
+                         double* d_kg = nullptr) {
     for (int attempt = 0; attempt < 4; attempt++) {
         cudaStream_t s = h->stream;
         if (h->n) CK(cudaMemsetAsync(d_force, 0, sizeof(double) * 3 * h->n, s));
@@ -583,6 +652,16 @@ airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos,
         StepArgs<R> a = make_args<R>(h, pr, d_pos, d_force, d_w6 != nullptr);
         a.pgrad = d_pgrad;
         if (d_pgrad) CK(cudaMemsetAsync(d_pgrad, 0, sizeof(double) * 6, s));
+        if (d_kg) {
+            // a second device copy of the parameters that carries the gradient buffer
+            if (!pr.b.Pkg) CK(realloc_dev(pr.b.Pkg, 1));
+            DevParams<R> pk = pr.hp;
+            pk.kg = d_kg;
+            CK(cudaStreamSynchronize(s));
+            CK(cudaMemcpy(pr.b.Pkg, &pk, sizeof(DevParams<R>), cudaMemcpyHostToDevice));
+            CK(cudaMemsetAsync(d_kg, 0, sizeof(double) * KG_N, s));
+            a.P = pr.b.Pkg;
+        }
         if (d_esys) {
             a.eatom = h->eatom;
             if (h->n) CK(cudaMemsetAsync(h->eatom, 0, sizeof(double) * h->n, s));
@@ -634,7 +713,8 @@ airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos,
 }
 
 airebo_status compute_any(airebo_handle h, const double* d_pos, double* d_force, double* d_e4, double* d_w6,
-                          double* d_pgrad = nullptr, double* d_esys = nullptr, bool async = false) {
+                          double* d_pgrad = nullptr, double* d_esys = nullptr, bool async = false,
+                          double* d_kg = nullptr) {
     if (!h->built) return fail(h, AIREBO_ERR_STATE, "airebo_compute before airebo_neighbor");
     CK(cudaSetDevice(h->device));
     if (d_esys && (h->eatom_n < h->n || !h->eatom)) {
@@ -643,8 +723,8 @@ airebo_status compute_any(airebo_handle h, const double* d_pos, double* d_force,
         h->eatom_n = h->n;
     }
     if (h->opt.precision == AIREBO_MIXED)
-        return do_compute<float>(h, h->p32, d_pos, d_force, d_e4, d_w6, d_pgrad, d_esys, async);
-    return do_compute<double>(h, h->p64, d_pos, d_force, d_e4, d_w6, d_pgrad, d_esys, async);
+        return do_compute<float>(h, h->p32, d_pos, d_force, d_e4, d_w6, d_pgrad, d_esys, async, d_kg);
+    return do_compute<double>(h, h->p64, d_pos, d_force, d_e4, d_w6, d_pgrad, d_esys, async, d_kg);
 }
 
 airebo_status check_rebuild(airebo_handle h, const double* d_pos, int* flag) {
@@ -733,6 +813,7 @@ void airebo_destroy(airebo_handle h) {
     free_prec(h->p64);
     free_prec(h->p32);
     if (h->pg) cudaFree(h->pg);
+    if (h->kg) cudaFree(h->kg);
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->graph) cudaGraphDestroy(h->graph);
     {
@@ -1011,7 +1092,7 @@ airebo_status airebo_graph_launch(airebo_handle h) {
     return AIREBO_OK;
 }
 
-airebo_status airebo_autotune(airebo_handle h, const double* d_pos, double* d_force, int* out2) {
+airebo_status airebo_autotune(airebo_handle h, const double* d_pos, double* d_force, int* out3) {
     if (!h) return AIREBO_ERR_ARG;
     if (h->n > 0 && (!d_pos || !d_force)) return fail(h, AIREBO_ERR_ARG, "null position or force pointer");
     if (!h->built) return fail(h, AIREBO_ERR_STATE, "airebo_autotune before airebo_neighbor");
@@ -1021,47 +1102,63 @@ airebo_status airebo_autotune(airebo_handle h, const double* d_pos, double* d_fo
     if (st) return st;
     st = compute_any(h, d_pos, d_force, nullptr, nullptr);        // settle every capacity first
     if (st) return st;
+    // median over REPS evaluations of the kernel times k0..k1 (event indices)
+    const int REPS = 5;
+    auto timed = [&](double* med_a, double* med_b) -> airebo_status {
+        double ta[REPS], tb[REPS];
+        for (int rep = 0; rep < REPS; rep++) {
+            for (int k = 0; k < 8; k++) { h->kt_ms[k] = 0; h->kt_n[k] = 0; }
+            airebo_status s2 = compute_any(h, d_pos, d_force, nullptr, nullptr);
+            if (s2) return s2;
+            ta[rep] = h->kt_ms[4];                       // LJ
+            tb[rep] = h->kt_ms[1] + h->kt_ms[2];         // REBO + torsion
+            if (med_b) med_b[rep] = h->kt_ms[5];         // b* and its reverse
+        }
+        std::sort(ta, ta + REPS);
+        std::sort(tb, tb + REPS);
+        med_a[0] = ta[REPS / 2];
+        med_a[1] = tb[REPS / 2];
+        if (med_b) std::sort(med_b, med_b + REPS);
+        return AIREBO_OK;
+    };
     const int chunks[] = {2, 4, 8, 16, 32};
     const int grids[] = {4, 8, 16};
-    double best_lj = 1e300, best_b = 1e300;
-    int bc = h->lj_chunk, bg = h->grid_per_sm;
-    // the LJ chunk and the bond-kernel grid act on different kernels: tune each
-    for (int c : chunks) {
-        if (!h->opt.enable_lj) break;
-        h->lj_chunk = c;
-        double t = 0;
-        for (int rep = 0; rep < 3; rep++) {
-            for (int k = 0; k < 8; k++) { h->kt_ms[k] = 0; h->kt_n[k] = 0; }
-            st = compute_any(h, d_pos, d_force, nullptr, nullptr);
+    double best_lj = 1e300, best_bond = 1e300, best_bstar = 1e300;
+    int bc = h->lj_chunk, bg = h->bond_grid, bs = h->bstar_grid;
+    // the LJ chunk and the two grids act on different kernels: tune each
+    if (h->opt.enable_lj) {
+        for (int c : chunks) {
+            h->lj_chunk = c;
+            double m[2];
+            st = timed(m, nullptr);
             if (st) return st;
-            if (rep > 0) t += h->kt_ms[4];
+            if (m[0] < best_lj) { best_lj = m[0]; bc = c; }
         }
-        if (t < best_lj) { best_lj = t; bc = c; }
     }
     h->lj_chunk = bc;
     for (int g : grids) {
-        h->grid_per_sm = g;
-        double t = 0;
-        for (int rep = 0; rep < 3; rep++) {
-            for (int k = 0; k < 8; k++) { h->kt_ms[k] = 0; h->kt_n[k] = 0; }
-            st = compute_any(h, d_pos, d_force, nullptr, nullptr);
-            if (st) return st;
-            if (rep > 0) t += h->kt_ms[1] + h->kt_ms[2] + h->kt_ms[5];
-        }
-        if (t < best_b) { best_b = t; bg = g; }
+        h->bond_grid = g;
+        h->bstar_grid = g;
+        double m[2], tb[REPS];
+        st = timed(m, tb);
+        if (st) return st;
+        if (m[1] < best_bond) { best_bond = m[1]; bg = g; }
+        if (tb[REPS / 2] < best_bstar) { best_bstar = tb[REPS / 2]; bs = g; }
     }
-    h->grid_per_sm = bg;
+    h->bond_grid = bg;
+    h->bstar_grid = bs;
     airebo_set_timing(h, was_timing ? 1 : 0);
-    if (out2) { out2[0] = h->lj_chunk; out2[1] = h->grid_per_sm; }
+    if (out3) { out3[0] = h->lj_chunk; out3[1] = h->bond_grid; out3[2] = h->bstar_grid; }
     return AIREBO_OK;
 }
 
-airebo_status airebo_set_launch_shape(airebo_handle h, int lj_chunk, int grid_per_sm) {
+airebo_status airebo_set_launch_shape(airebo_handle h, int lj_chunk, int bond_grid, int bstar_grid) {
     if (!h) return AIREBO_ERR_ARG;
-    if (lj_chunk < 1 || lj_chunk > 64 || grid_per_sm < 1 || grid_per_sm > 32)
-        return fail(h, AIREBO_ERR_ARG, "launch shape out of range (lj_chunk 1..64, grid_per_sm 1..32)");
+    if (lj_chunk < 1 || lj_chunk > 64 || bond_grid < 1 || bond_grid > 32 || bstar_grid < 1 || bstar_grid > 32)
+        return fail(h, AIREBO_ERR_ARG, "launch shape out of range (lj_chunk 1..64, grids 1..32 blocks per SM)");
     h->lj_chunk = lj_chunk;
-    h->grid_per_sm = grid_per_sm;
+    h->bond_grid = bond_grid;
+    h->bstar_grid = bstar_grid;
     return AIREBO_OK;
 }
 
@@ -1077,6 +1174,32 @@ airebo_status airebo_param_grad(airebo_handle h, const double* d_pos, double* d_
     CK(cudaMemcpyAsync(h->h_acc, h->pg, sizeof(double) * 6, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     for (int k = 0; k < 6; k++) h_grad6[k] = h->h_acc[k];
+    return AIREBO_OK;
+}
+
+airebo_status airebo_knot_grad(airebo_handle h, const double* d_pos, double* d_force, double* d_energy4,
+                               double* h_grad, int64_t count) {
+    if (!h || !h_grad) return AIREBO_ERR_ARG;
+    if (count != AIREBO_KNOT_COUNT) return fail(h, AIREBO_ERR_ARG, "knot gradient needs AIREBO_KNOT_COUNT values");
+    if (h->n > 0 && (!d_pos || !d_force)) return fail(h, AIREBO_ERR_ARG, "null position or force pointer");
+    if (!h->built) return fail(h, AIREBO_ERR_STATE, "airebo_knot_grad before airebo_neighbor");
+    CK(cudaSetDevice(h->device));
+    if (!h->kg) CK(realloc_dev(h->kg, KG_N));
+    airebo_status st = compute_any(h, d_pos, d_force, d_energy4, nullptr, nullptr, nullptr, false, h->kg);
+    if (st) return st;
+    std::vector<double> g(KG_N, 0.0);
+    CK(cudaMemcpyAsync(g.data(), h->kg, sizeof(double) * KG_N, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    // parameter-file order: gC1, gC2, gH, P.CC, P.CH, P.HC, piRC.CC, piRC.CH, piRC.HH, Tij.CC
+    for (int64_t k = 0; k < count; k++) h_grad[k] = 0;
+    const Scalars& sc = h->sc;
+    double* o = h_grad;
+    quintic_coeffs_adjoint(sc.gC1k, g.data() + KG_GC1, o); o += 3 * sc.gC1k.size();
+    quintic_coeffs_adjoint(sc.gC2k, g.data() + KG_GC2, o); o += 3 * sc.gC2k.size();
+    quintic_coeffs_adjoint(sc.gHk, g.data() + KG_GH, o); o += 3 * sc.gHk.size();
+    for (int t = 0; t < 3; t++, o += 100) bicubic_coeffs_adjoint(g.data() + KG_P + t * 256, o);
+    for (int t = 0; t < 3; t++, o += 1800) tricubic_coeffs_adjoint(g.data() + KG_F + t * NTRI_CELLS * 64, o);
+    tricubic_coeffs_adjoint(g.data() + KG_T, o);
     return AIREBO_OK;
 }
 

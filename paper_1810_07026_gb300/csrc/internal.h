@@ -10,6 +10,7 @@ namespace airebo {
 // per-step device data of one precision R, all owned by the handle
 template <class R> struct StepBuffers {
     DevParams<R>* P = nullptr;        // device copy of the parameter struct
+    DevParams<R>* Pkg = nullptr;      // the same with the spline-gradient buffer set (knot gradients)
     R* tables = nullptr;              // P, pi^rc and T coefficients
     unsigned char* Tnz = nullptr;
     // short list
@@ -39,7 +40,8 @@ template <class R> struct StepArgs {
     int* bq2; double* bq2_eps; int* nbq2;  // b* pairs whose S_b is in its transition, and dE/db*
     int* lj_next;                          // work counter of the LJ kernel's warps
     int lj_chunk;                          // atoms a warp takes at a time (tuned)
-    int grid_per_sm;                       // blocks per SM of the grid-stride bond and b* kernels (tuned)
+    int bond_grid;                         // blocks per SM of the grid-stride REBO and torsion kernels (tuned)
+    int bstar_grid;                        // blocks per SM of the b* kernels (tuned)
     const int* sys;                        // batched systems: system of each atom (null: one system, box L)
     const double* Lsys;                    // batched systems: box of each system (3 per system)
     double* eatom;                         // nullable: energy of each atom's anchored terms

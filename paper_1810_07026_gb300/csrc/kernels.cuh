@@ -386,7 +386,8 @@ void launch_compute_impl(const StepArgs<R>& a, cudaStream_t s, int num_sms, cuda
     if (a.n == 0) return;
     int n = a.n;
     auto mark = [&](int k) { if (ev) cudaEventRecord(ev[k], s); };
-    int grid_bonds = num_sms * a.grid_per_sm;
+    int grid_bonds = num_sms * a.bond_grid;
+    int grid_bstar = num_sms * a.bstar_grid;
     mark(0);
     k_short_list<R><<<(n + 127) / 128, 128, 0, s>>>(a);
     mark(1);
@@ -405,8 +406,8 @@ void launch_compute_impl(const StepArgs<R>& a, cudaStream_t s, int num_sms, cuda
     }
     mark(5);
     if (a.lj_on) {
-        k_bstar<R><<<grid_bonds, 128, 0, s>>>(a);
-        k_bstar_rev<R><<<grid_bonds, 128, 0, s>>>(a);
+        k_bstar<R><<<grid_bstar, 128, 0, s>>>(a);
+        k_bstar_rev<R><<<grid_bstar, 128, 0, s>>>(a);
     }
     mark(6);
     k_finish_counters<R><<<1, 32, 0, s>>>(a);

@@ -128,7 +128,14 @@ template <class R> struct DevParams {
     const R* Ftab;                   // 3 tables (CC, CH, HH) x 128 cells x 64 coefficients
     const R* Ttab;                   // T_CC: 128 cells x 64 coefficients
     const unsigned char* Tnz;        // 1 where a T_CC cell has a nonzero coefficient
+    double* kg;                      // dE/d(power-basis coefficient) of every spline, or null (layout KG_*)
 };
+
+// Layout of the spline-coefficient gradient: the three angular splines
+// (5 intervals x 6 coefficients each), then the P, pi^rc and T tables in
+// their device layout.
+constexpr int KG_GC1 = 0, KG_GC2 = 30, KG_GH = 60, KG_P = 90, KG_F = KG_P + 3 * 256;
+constexpr int KG_T = KG_F + 3 * NTRI_CELLS * 64, KG_N = KG_T + NTRI_CELLS * 64;
 
 HD int pidx(int ti, int tj) { return ti + tj; }
 
@@ -275,6 +282,43 @@ HD R tricubic_cell(const R* a, R tx, R ty, R tz, bool clx, bool cly, bool clz, R
     return f;
 }
 
+// Gradient of a spline value with respect to its coefficients.  Every
+// spline here is linear in its power-basis coefficients, so d value / d a_m
+// is the monomial m at the (clamped) local coordinates; adj = dE/d value.
+template <class R> HD void kg_quintic(double* g, const Quintic<R>& q, R x, double adj) {
+    if (x < q.k[0]) x = q.k[0];
+    if (x > q.k[q.n]) x = q.k[q.n];
+    if (!(x == x)) x = q.k[0];
+    int m = 0;
+    while (m + 1 < q.n && x > q.k[m + 1]) m++;
+    double t = (double)((x - q.k[m]) * q.invh[m]), tp = 1.0;
+    for (int p = 0; p < 6; p++, tp *= t) atomic_add(g + m * 6 + p, adj * tp);
+}
+template <class R> HD void kg_bicubic(double* g, R x, R y, double adj) {
+    bool cx, cy;
+    clamp_arg<R>(x, R(0), R(4), cx);
+    clamp_arg<R>(y, R(0), R(4), cy);
+    int ix = clamp_cell((int)floor(x), 3);
+    int iy = clamp_cell((int)floor(y), 3);
+    double tx = (double)(x - R(ix)), ty = (double)(y - R(iy));
+    g += (ix * 4 + iy) * 16;
+    double xp = adj;
+    for (int p = 0; p < 4; p++, xp *= tx) {
+        double v = xp;
+        for (int q = 0; q < 4; q++, v *= ty) atomic_add(g + p * 4 + q, v);
+    }
+}
+template <class R> HD void kg_tricubic(double* g, R tx, R ty, R tz, double adj) {
+    double xp = adj;
+    for (int p = 0; p < 4; p++, xp *= (double)tx) {
+        double yp = xp;
+        for (int q = 0; q < 4; q++, yp *= (double)ty) {
+            double v = yp;
+            for (int r = 0; r < 4; r++, v *= (double)tz) atomic_add(g + (p * 4 + q) * 4 + r, v);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ neighbour data
 // Short REBO list of one step: slot s of atom i at index i * G.stride + s.
 template <class R> struct Graph {
@@ -351,6 +395,18 @@ HD R gfun(const DevParams<R>& P, int tc, R cs, R N, R& dg_dcos, R& dg_dN) {
     return quintic<R, D>(P.gH, cs, dg_dcos);
 }
 
+// the coefficient gradient of gfun with dE/dg = adj
+template <class R> HD void kg_gfun(const DevParams<R>& P, int tc, R cs, R N, double adj) {
+    if (tc == 0) {
+        R dQ;
+        R Qn = Sw<R>((N - P.gN0) * P.gNinv, dQ);
+        if (Qn != R(0)) kg_quintic<R>(P.kg + KG_GC2, P.gC2, cs, adj * (double)Qn);
+        if (Qn != R(1)) kg_quintic<R>(P.kg + KG_GC1, P.gC1, cs, adj * (1.0 - (double)Qn));
+        return;
+    }
+    kg_quintic<R>(P.kg + KG_GH, P.gH, cs, adj);
+}
+
 // e^lambda_jik, lambda = lam [(rho_kH - r_ik) - (rho_jH - r_ij)] for an H centre, else 1
 template <class R> HD R exp_lambda(const DevParams<R>& P, int tc, int tk, int to, R rck, R umag) {
     if (tc == 0) return R(1);
@@ -413,6 +469,10 @@ HD void side_reverse(const DevParams<R>& P, const Graph<R>& G, int c, int o, R u
     R dEdN = dEdN_direct + ac * s.dsum_dN;
     R dEdNC = dEdN + ac * s.dPdNC;
     R dEdNH = dEdN + ac * s.dPdNH;
+    if (P.kg && !(tc == 1 && to == 1)) {
+        int tab = (tc == 0 && to == 0) ? 0 : (tc == 0 ? 1 : 2);
+        kg_bicubic<R>(P.kg + KG_P + tab * 256, s.NC, s.NH, (double)ac);
+    }
     for (int a = 0; a < nc; a++) {
         int q = c * G.stride + a;
         int k = G.nj[q];
@@ -426,6 +486,7 @@ HD void side_reverse(const DevParams<R>& P, const Graph<R>& G, int c, int o, R u
         R dgc, dgN;
         R g = gfun<R, true>(P, tc, cs, s.N, dgc, dgN);
         R e = exp_lambda<R>(P, tc, tk, to, rck, umag);
+        if (P.kg) kg_gfun<R>(P, tc, cs, s.N, (double)(ac * w * e));
         // d E / d w_ck
         R dEdw = (tk == 0 ? dEdNC : dEdNH) + ac * g * e;
         R Fx = R(0), dFx = R(0);
@@ -577,8 +638,9 @@ HD R bond_order(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, R 
     R pirc = tricubic_cell<R, REV>(P.Ftab + (tab * NTRI_CELLS + cell) * 64, tx, ty, tz, clx, cly, clz, Fa, Fb, Fc);
     R dFdNi = swap ? Fb : Fa, dFdNj = swap ? Fa : Fb;
     // pi^dh (C-C only), skipped where the T_CC cell is identically zero
+    // (unless its coefficients' gradient is wanted)
     R pidh = 0, D = 0, Tv = 0, Ta = 0, Tb = 0, Tc = 0;
-    bool dih = (ti == 0 && tj == 0) && P.Tnz[cell];
+    bool dih = (ti == 0 && tj == 0) && (P.Tnz[cell] || (REV && P.kg));
     if (dih) {
         Tv = tricubic_cell<R, REV>(P.Ttab + cell * 64, tx, ty, tz, clx, cly, clz, Ta, Tb, Tc);
         R dummy = 0;
@@ -588,6 +650,10 @@ HD R bond_order(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, R 
     }
     R b = R(0.5) * (si.p + sj.p) + pirc + pidh;
     if (!REV) return b;
+    if (P.kg) {
+        kg_tricubic<R>(P.kg + KG_F + (tab * NTRI_CELLS + cell) * 64, tx, ty, tz, (double)eps);
+        if (dih) kg_tricubic<R>(P.kg + KG_T + cell * 64, tx, ty, tz, (double)(eps * D));
+    }
     R dEdNi = eps * (dFdNi + D * Ta);
     R dEdNj = eps * (dFdNj + D * Tb);
     R dEdNconj = eps * (Fc + D * Tc);

@@ -26,19 +26,21 @@ def test_autotune_keeps_result(torch_cuda, param_text, prec):
     pos = torch.tensor(pos0, device="cuda")
     ev.neighbor(pos, torch.tensor(types, device="cuda"), box)
     f0, e0, _ = ev.compute(pos)
-    chunk, grid = ev.autotune(pos)
-    assert chunk in (2, 4, 8, 16, 32) and grid in (4, 8, 16)
+    chunk, grid, bgrid = ev.autotune(pos)
+    assert chunk in (2, 4, 8, 16, 32) and grid in (4, 8, 16) and bgrid in (4, 8, 16)
     f1, e1, _ = ev.compute(pos)
     # any launch shape in range gives the same result
-    for c, g in ((1, 1), (3, 5), (64, 32)):
-        ev.set_launch_shape(c, g)
+    for c, g, b in ((1, 1, 1), (3, 5, 7), (64, 32, 32)):
+        ev.set_launch_shape(c, g, b)
         f2, e2, _ = ev.compute(pos)
         assert np.allclose(e2.cpu().numpy(), e0.cpu().numpy(), rtol=1e-12, atol=1e-9)
         assert (f2 - f0).abs().max().item() < 1e-9
     assert np.allclose(e1.cpu().numpy(), e0.cpu().numpy(), rtol=1e-12, atol=1e-9)
     assert (f1 - f0).abs().max().item() < 1e-9
     with pytest.raises(RuntimeError):
-        ev.set_launch_shape(0, 8)
+        ev.set_launch_shape(0, 8, 8)
     with pytest.raises(RuntimeError):
-        ev.set_launch_shape(8, 33)
+        ev.set_launch_shape(8, 33, 8)
+    with pytest.raises(RuntimeError):
+        ev.set_launch_shape(8, 8, 0)
     ev.close()
