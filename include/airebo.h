@@ -62,9 +62,14 @@ typedef struct {
     int enable_lj;        /* 1: LJ term (Alg. 3) */
     int enable_torsion;   /* 1: torsion term (Alg. 2) */
     int max_lj_nbrs;      /* initial long-list capacity per atom; 0 = from the density */
+    int bstar_screen;     /* FP64 only, 1 (default): b* enters the LJ term only through S_b,
+                             which is exactly 0 or 1 outside [b_min, b_max]; an FP32 b* decides
+                             those pairs when it lies more than 1e-3 outside the transition
+                             (FP32 b* errors measure below 1e-6), and the rest are evaluated in
+                             FP64.  0: every b* in FP64.  Results agree to rounding either way. */
 } airebo_options;
 
-/* Fill opts with the defaults: skin 1.0 A, FP64, all three terms on, auto capacity. */
+/* Fill opts with the defaults: skin 1.0 A, FP64, all three terms on, auto capacity, b* screen on. */
 void airebo_default_options(airebo_options* opts);
 
 /*
@@ -140,8 +145,10 @@ airebo_status airebo_nve_host(airebo_handle h, double* h_pos, double* h_vel, dou
 /*
  * Counters of the last compute (int64[8]): bonds, b* pairs, b* pairs with a
  * nonzero S_b derivative, LJ pairs within the cut-off evaluated in the pair
- * kernel, connectivity-map entries, list rebuilds, LJ list capacity, bond
- * order evaluations.  Synchronises.
+ * kernel, connectivity-map capacity, list rebuilds, LJ list capacity, b*
+ * pairs evaluated in the full-precision pass (the others were decided by the
+ * first pass: exactly in MIXED or with the screen off, by the FP32 screen in
+ * FP64).  Synchronises.
  */
 airebo_status airebo_counters(airebo_handle h, int64_t* out8);
 

@@ -35,7 +35,8 @@ class AireboError(RuntimeError):
 
 class Options(C.Structure):
     _fields_ = [("skin", C.c_double), ("precision", C.c_int), ("enable_rebo", C.c_int),
-                ("enable_lj", C.c_int), ("enable_torsion", C.c_int), ("max_lj_nbrs", C.c_int)]
+                ("enable_lj", C.c_int), ("enable_torsion", C.c_int), ("max_lj_nbrs", C.c_int),
+                ("bstar_screen", C.c_int)]
 
 
 _lib = None
@@ -109,14 +110,15 @@ class Airebo:
     (3, N) on the device (structure of arrays), types int8 (N,)."""
 
     def __init__(self, params: str | dict | None = None, precision: int = FP64, skin: float = 1.0,
-                 rebo: bool = True, lj: bool = True, torsion: bool = True, max_lj_nbrs: int = 0, stream=None):
+                 rebo: bool = True, lj: bool = True, torsion: bool = True, max_lj_nbrs: int = 0, stream=None,
+                 bstar_screen: bool = True):
         import torch
         self._torch = torch
         if params is None:
             params = inputs.make_params(0)
         if isinstance(params, dict):
             params = inputs.params_text(params)
-        opt = Options(skin, precision, int(rebo), int(lj), int(torsion), int(max_lj_nbrs))
+        opt = Options(skin, precision, int(rebo), int(lj), int(torsion), int(max_lj_nbrs), int(bstar_screen))
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -282,7 +284,7 @@ class Airebo:
     def counters(self) -> dict:
         out = np.zeros(8, dtype=np.int64)
         self._check(lib().airebo_counters(self._h, _np(out)))
-        names = ("bonds", "bstar", "bstar_dsb", "lj_in_cutoff", "map_cap", "list_builds", "lj_cap", "reserved")
+        names = ("bonds", "bstar", "bstar_dsb", "lj_in_cutoff", "map_cap", "list_builds", "lj_cap", "bstar_full")
         return dict(zip(names, out.tolist()))
 
     def export_lists(self, which: int, cap: int | None = None):

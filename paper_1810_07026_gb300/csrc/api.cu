@@ -286,6 +286,7 @@ bool fill_params(const Scalars& s, DevParams<R>& P, std::vector<R>& tables, std:
         P.Srhi2[p] = (R)(s.Sr[1] * sg * s.Sr[1] * sg);
         P.Srinv[p] = (R)(1.0 / ((s.Sr[1] - s.Sr[0]) * sg));
         P.bmin[p] = (R)s.bmin[p];
+        P.bmax[p] = (R)s.bmax[p];
         P.binv[p] = (R)(1.0 / (s.bmax[p] - s.bmin[p]));
         P.rstar[p] = (R)s.rstar[p];
         P.teps[p] = (R)s.teps[p];
@@ -353,7 +354,7 @@ struct airebo_ctx {
     // step scratch
     int2* bonds = nullptr; int2* ccbonds = nullptr; int bond_cap = 0;
     int4* bq = nullptr; int bq_cap = 0;
-    int* bq2 = nullptr; double* bq2_eps = nullptr;
+    int* bq2 = nullptr;
     int* counts = nullptr;               // [0] non-C-C bonds [2] C-C bonds [3] b* reverse queue [4..6] b* queue per species pair [7] LJ work counter
     double* acc = nullptr;               // 9 doubles
     unsigned long long* counters = nullptr;   // 8
@@ -429,6 +430,9 @@ template <class R> airebo_status upload_params(airebo_handle h, Precision<R>& pr
     return AIREBO_OK;
 }
 
+// the FP32 b* screen of the FP64 path (see k_bstar)
+bool screen_on(airebo_handle h);
+
 template <class R> airebo_status alloc_step(airebo_handle h, Precision<R>& pr, int n) {
     StepBuffers<R>& b = pr.b;
     size_t m = (size_t)n * h->stride;
@@ -439,6 +443,11 @@ template <class R> airebo_status alloc_step(airebo_handle h, Precision<R>& pr, i
     if (b.map_cap == 0) b.map_cap = 32;
     size_t mm = (size_t)n * b.map_cap;
     CK(realloc_dev(b.map_cnt, n)); CK(realloc_dev(b.map_key, mm)); CK(realloc_dev(b.map_wt, mm)); CK(realloc_dev(b.map_path, mm));
+    if (sizeof(R) == 8 && screen_on(h)) {
+        CK(realloc_dev(b.s_dx, m)); CK(realloc_dev(b.s_dy, m)); CK(realloc_dev(b.s_dz, m));
+        CK(realloc_dev(b.s_r, m)); CK(realloc_dev(b.s_ir, m)); CK(realloc_dev(b.s_w, m));
+        CK(realloc_dev(b.s_nC, n)); CK(realloc_dev(b.s_nH, n));
+    }
     return AIREBO_OK;
 }
 
@@ -453,12 +462,17 @@ template <class R> airebo_status grow_map(airebo_handle h, Precision<R>& pr, int
 template <class R> void free_prec(Precision<R>& pr) {
     StepBuffers<R>& b = pr.b;
     void* ps[] = {b.P, b.Pkg, b.tables, b.Tnz, b.cnt, b.nj, b.nimg, b.dx, b.dy, b.dz, b.r, b.ir, b.w, b.dw, b.omw, b.nC, b.nH,
-                  b.map_cnt, b.map_key, b.map_wt, b.map_path};
+                  b.map_cnt, b.map_key, b.map_wt, b.map_path,
+                  b.s_dx, b.s_dy, b.s_dz, b.s_r, b.s_ir, b.s_w, b.s_nC, b.s_nH};
     for (void* p : ps) if (p) cudaFree(p);
     b = StepBuffers<R>();
 }
 
 double max3(const double* v) { return std::max(v[0], std::max(v[1], v[2])); }
+
+bool screen_on(airebo_handle h) {
+    return h->opt.precision == AIREBO_FP64 && h->opt.bstar_screen != 0 && h->opt.enable_lj != 0;
+}
 
 airebo_status alloc_atoms(airebo_handle h, int n) {
     if (n <= h->n_alloc && h->n_alloc > 0) return AIREBO_OK;
@@ -476,7 +490,6 @@ airebo_status alloc_atoms(airebo_handle h, int n) {
     h->bq_cap = std::max(h->bq_cap, na * 4 + 1024);
     CK(realloc_dev(h->bq, 3 * (size_t)h->bq_cap));
     CK(realloc_dev(h->bq2, 3 * (size_t)h->bq_cap));
-    CK(realloc_dev(h->bq2_eps, 3 * (size_t)h->bq_cap));
     h->n_alloc = na;
     airebo_status st = h->opt.precision == AIREBO_MIXED ? alloc_step<float>(h, h->p32, na) : alloc_step<double>(h, h->p64, na);
     if (st) return st;
@@ -619,7 +632,22 @@ template <class R> StepArgs<R> make_args(airebo_handle h, Precision<R>& pr, cons
     a.bonds = h->bonds; a.nbonds = h->counts; a.bond_cap = h->bond_cap;
     a.ccbonds = h->ccbonds; a.nccbonds = h->counts + 2;
     a.bq = h->bq; a.nbq = h->counts + 4; a.bq_cap = h->bq_cap;
-    a.bq2 = h->bq2; a.bq2_eps = h->bq2_eps; a.nbq2 = h->counts + 3;
+    a.bq2 = h->bq2; a.nbq2 = h->counts + 3;
+    a.screen = false;
+    a.P32 = nullptr;
+    a.G32 = Graph<float>{};
+    a.s_dx = a.s_dy = a.s_dz = a.s_r = a.s_ir = a.s_w = a.s_nC = a.s_nH = nullptr;
+    if (sizeof(R) == 8 && screen_on(h) && b.s_dx) {
+        a.screen = true;
+        a.P32 = h->p32.b.P;
+        a.s_dx = b.s_dx; a.s_dy = b.s_dy; a.s_dz = b.s_dz; a.s_r = b.s_r; a.s_ir = b.s_ir; a.s_w = b.s_w;
+        a.s_nC = b.s_nC; a.s_nH = b.s_nH;
+        a.G32.n = h->n; a.G32.stride = h->stride; a.G32.type = h->types; a.G32.cnt = b.cnt; a.G32.nj = b.nj;
+        a.G32.nimg = b.nimg;
+        a.G32.dx = b.s_dx; a.G32.dy = b.s_dy; a.G32.dz = b.s_dz; a.G32.r = b.s_r; a.G32.ir = b.s_ir; a.G32.w = b.s_w;
+        a.G32.dw = nullptr; a.G32.omw = nullptr;        // the forward bond order reads neither
+        a.G32.nC = b.s_nC; a.G32.nH = b.s_nH;
+    }
     a.lj_next = h->counts + 7;
     a.lj_chunk = h->lj_chunk;
     a.bond_grid = h->bond_grid;
@@ -704,7 +732,6 @@ airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos,
             h->bq_cap = nq + nq / 4 + 1024;
             CK(realloc_dev(h->bq, 3 * (size_t)h->bq_cap));
             CK(realloc_dev(h->bq2, 3 * (size_t)h->bq_cap));
-            CK(realloc_dev(h->bq2_eps, 3 * (size_t)h->bq_cap));
             again = true;
         }
         if (!again) return AIREBO_OK;
@@ -771,6 +798,7 @@ void airebo_default_options(airebo_options* o) {
     o->enable_lj = 1;
     o->enable_torsion = 1;
     o->max_lj_nbrs = 0;
+    o->bstar_screen = 1;
 }
 
 airebo_status airebo_create(const char* params, const airebo_options* opts, void* stream, airebo_handle* out) {
@@ -794,6 +822,7 @@ airebo_status airebo_create(const char* params, const airebo_options* opts, void
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (ce != cudaSuccess) { delete h; return AIREBO_ERR_CUDA; }
     st = h->opt.precision == AIREBO_MIXED ? upload_params<float>(h, h->p32) : upload_params<double>(h, h->p64);
+    if (!st && screen_on(h)) st = upload_params<float>(h, h->p32);
     if (!st) {
         if (realloc_dev(h->counts, 8) || realloc_dev(h->acc, 9) || realloc_dev(h->counters, 8) ||
             realloc_dev(h->derr, 8) || realloc_dev(h->maxd2, 1) || realloc_dev(h->ke, 1) ||
@@ -821,7 +850,7 @@ void airebo_destroy(airebo_handle h) {
         for (void* p : bs) if (p) cudaFree(p);
     }
     void* ps[] = {h->types, h->cell_of, h->cell_count, h->cell_start, h->cell_fill, h->spos, h->swrap, h->lj, h->lj_cnt,
-                  h->im, h->im_cnt, h->xref, h->bonds, h->ccbonds, h->bq, h->bq2, h->bq2_eps, h->counts, h->acc, h->counters, h->derr, h->maxd2, h->ke,
+                  h->im, h->im_cnt, h->xref, h->bonds, h->ccbonds, h->bq, h->bq2, h->counts, h->acc, h->counters, h->derr, h->maxd2, h->ke,
                   h->hpos, h->hvel, h->hforce, h->he4, h->hw6};
     for (void* p : ps) if (p) cudaFree(p);
     for (int k = 0; k < 11; k++) if (h->ev[k]) cudaEventDestroy(h->ev[k]);
@@ -1223,6 +1252,10 @@ airebo_status airebo_set_lj_params(airebo_handle h, const double* eps3, const do
     h->sc = s;
     airebo_status st = h->opt.precision == AIREBO_MIXED ? upload_params<float>(h, h->p32) : upload_params<double>(h, h->p64);
     if (st) return st;
+    if (screen_on(h)) {
+        st = upload_params<float>(h, h->p32);
+        if (st) return st;
+    }
     if (sigma_changed) h->built = false;          // the LJ cut-off moved: the lists must be rebuilt
     return AIREBO_OK;
 }

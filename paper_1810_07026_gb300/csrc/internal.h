@@ -20,6 +20,9 @@ template <class R> struct StepBuffers {
     // connectivity map
     int map_cap = 0;
     int* map_cnt = nullptr; long long* map_key = nullptr; R* map_wt = nullptr; int* map_path = nullptr;
+    // FP32 copy of the short-list geometry for the b* screen (FP64 only)
+    float* s_dx = nullptr; float* s_dy = nullptr; float* s_dz = nullptr; float* s_r = nullptr; float* s_ir = nullptr;
+    float* s_w = nullptr; float* s_nC = nullptr; float* s_nH = nullptr;
 };
 
 // everything the compute kernels read, passed by value
@@ -37,7 +40,12 @@ template <class R> struct StepArgs {
     int2* bonds; int* nbonds; int bond_cap;   // bonds i<j that are not C-C
     int2* ccbonds; int* nccbonds;             // C-C bonds i<j, same capacity
     int4* bq; int* nbq; int bq_cap;
-    int* bq2; double* bq2_eps; int* nbq2;  // b* pairs whose S_b is in its transition, and dE/db*
+    int* bq2; int* nbq2;                   // b* pairs left to the full-precision pass
+    // b* screen (FP64): an FP32 b* decides S_b where it is certain
+    bool screen;
+    const DevParams<float>* P32;
+    Graph<float> G32;                      // reads the s_* arrays below
+    float* s_dx; float* s_dy; float* s_dz; float* s_r; float* s_ir; float* s_w; float* s_nC; float* s_nH;
     int* lj_next;                          // work counter of the LJ kernel's warps
     int lj_chunk;                          // atoms a warp takes at a time (tuned)
     int bond_grid;                         // blocks per SM of the grid-stride REBO and torsion kernels (tuned)
@@ -55,7 +63,11 @@ template <class R> struct StepArgs {
 };
 
 enum { ERR_SHORT = 0, ERR_MAP = 1, ERR_QUEUE = 2, ERR_NONFINITE = 3 };
-enum { CNT_BONDS = 0, CNT_BSTAR = 1, CNT_DSB = 2, CNT_LJ = 3, CNT_MAP = 4, CNT_BO = 7 };
+enum { CNT_BONDS = 0, CNT_BSTAR = 1, CNT_DSB = 2, CNT_LJ = 3, CNT_MAP = 4, CNT_BSTAR_FULL = 7 };
+
+// Half-width of the band around [b_min, b_max] inside which an FP32 b* does
+// not decide S_b.  Measured FP32-FP64 differences of b* stay below 1e-6.
+constexpr float BSTAR_SCREEN_MARGIN = 1e-3f;
 
 // launchers, one instantiation per precision (kernels_f64.cu, kernels_f32.cu)
 // ev (nullable): 7 events recorded before each of the 6 stages and after the last

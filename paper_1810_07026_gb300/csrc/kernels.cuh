@@ -109,6 +109,10 @@ __global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
             a.g_nj[q] = j; a.g_nimg[q] = img;
             a.g_dx[q] = (R)dx; a.g_dy[q] = (R)dy; a.g_dz[q] = (R)dz;
             a.g_r[q] = (R)r; a.g_ir[q] = (R)ir; a.g_w[q] = w; a.g_dw[q] = dw; a.g_omw[q] = omw;
+            if (a.screen) {
+                a.s_dx[q] = (float)dx; a.s_dy[q] = (float)dy; a.s_dz[q] = (float)dz;
+                a.s_r[q] = (float)r; a.s_ir[q] = (float)ir; a.s_w[q] = (float)w;
+            }
             // each bond once: i < j between like species, from the carbon for C-H,
             // so that the threads of a warp run the same code (species batches, Sec. 4.2)
             bool mine = (ti == tj) ? (j > i) : (ti == 0);
@@ -129,6 +133,10 @@ __global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
     a.g_cnt[i] = cnt < a.G.stride ? cnt : a.G.stride;
     a.g_nC[i] = nC;
     a.g_nH[i] = nH;
+    if (a.screen) {
+        a.s_nC[i] = (float)nC;
+        a.s_nH[i] = (float)nH;
+    }
 }
 
 // ------------------------------------------------------------------ REBO bonds
@@ -313,8 +321,28 @@ __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
 }
 
 // ------------------------------------------------------------------ b* pairs
-// Phase 1: every queued pair.  Pairs whose S_b is in its transition go to a
-// second queue, so that the reverse bond order runs compactly in phase 2.
+// Phase 1: every queued pair.  b* enters the energy only through S_b, which is
+// exactly 1 below b_min and 0 above b_max.  Where b* is clear of that
+// transition, phase 1 finishes the pair; the others go to a second queue, and
+// phase 2 evaluates them in one bond-order pass with its reverse.  In FP64 the
+// phase-1 b* is an FP32 evaluation, trusted only outside a band of
+// BSTAR_SCREEN_MARGIN around the transition (the screen).
+template <class R>
+__device__ __forceinline__ void bstar_load(const StepArgs<R>& a, int t, int& i, int& j, double& dx, double& dy,
+                                           double& dz, R& C, int& code) {
+    int4 q = a.bq[t];
+    i = q.x;
+    int2 ent = a.lj[(size_t)i * a.lj_cap + q.y];
+    j = ent.x;
+    load_disp(a.pos, a.n, box_of(a, i), i, j, ent.y, dx, dy, dz);
+    C = R(1);
+    code = -1;
+    if (q.z >= 0) {
+        C = a.M.wt[(size_t)i * a.M.cap + q.z];
+        code = a.M.path[(size_t)i * a.M.cap + q.z];
+    }
+}
+
 template <class R>
 __global__ void __launch_bounds__(128) k_bstar(StepArgs<R> a) {
     const DevParams<R>& P = *a.P;
@@ -325,51 +353,67 @@ __global__ void __launch_bounds__(128) k_bstar(StepArgs<R> a) {
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nq; u += gridDim.x * blockDim.x) {
         // the queue is kept per species pair (CC, CH, HH), so that warps are uniform
         int t = u < n0 ? u : (u < n0 + n1 ? a.bq_cap + (u - n0) : 2 * a.bq_cap + (u - n0 - n1));
-        int4 q = a.bq[t];
-        int i = q.x;
-        int2 ent = a.lj[(size_t)i * a.lj_cap + q.y];
-        int j = ent.x;
+        int i, j, code;
         double dx, dy, dz;
-        load_disp(a.pos, a.n, box_of(a, i), i, j, ent.y, dx, dy, dz);
+        R C;
+        bstar_load<R>(a, t, i, j, dx, dy, dz, C, code);
         R rx = (R)dx, ry = (R)dy, rz = (R)dz;
         R r2 = rx * rx + ry * ry + rz * rz;
-        R C = R(1);
-        int code = -1;
-        if (q.z >= 0) {
-            C = a.M.wt[(size_t)i * a.M.cap + q.z];
-            code = a.M.path[(size_t)i * a.M.cap + q.z];
+        int p = pidx(a.G.type[i], a.G.type[j]);
+        R Sb = R(0), dSb = R(1);
+        bool decided;
+        if (a.screen) {
+            const DevParams<float>& P32 = *a.P32;
+            float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+            float bs = bstar_value<float>(P32, a.G32, i, j, fx, fy, fz, fx * fx + fy * fy + fz * fz, sink);
+            bool below = bs < P32.bmin[p] - BSTAR_SCREEN_MARGIN;
+            bool above = bs > P32.bmax[p] + BSTAR_SCREEN_MARGIN;
+            decided = below || above;
+            Sb = below ? R(1) : R(0);
+            dSb = R(0);
+        } else {
+            R bs = bstar_value<R>(P, a.G, i, j, rx, ry, rz, r2, sink);
+            Sb = bstar_switch<R>(P, p, bs, dSb);
+            decided = dSb == R(0);
         }
-        R eps;
-        double e = bstar_pair<R>(P, a.G, i, j, rx, ry, rz, r2, C, code, sink, eps);
-        E += e;
-        if (a.eatom) atomicAdd(a.eatom + i, e);
-        if (eps != R(0)) {
+        if (decided) {
+            double e = bstar_finish<R>(P, a.G, i, j, rx, ry, rz, r2, C, code, Sb, R(0), sink);
+            E += e;
+            if (a.eatom) atomicAdd(a.eatom + i, e);
+        } else {
             int s = atomicAdd(a.nbq2, 1);
-            if (s < 3 * a.bq_cap) { a.bq2[s] = t; a.bq2_eps[s] = (double)eps; }
+            if (s < 3 * a.bq_cap) a.bq2[s] = t;
         }
     }
     block_accumulate<128>(E, sink.W, a.virial, a.acc + 1, a.acc + 3);
     if (a.pgrad) block_accumulate_g<128>(sink.G, a.pgrad);
 }
 
-// Phase 2: the force through b* for the pairs of the second queue.
+// Phase 2: the pairs of the second queue, b* and its gradient in one pass.
 template <class R>
 __global__ void __launch_bounds__(128) k_bstar_rev(StepArgs<R> a) {
     const DevParams<R>& P = *a.P;
     Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}, a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
+    double E = 0;
+    unsigned dsb_count = 0;
     int nq = min(*a.nbq2, 3 * a.bq_cap);
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nq; s += gridDim.x * blockDim.x) {
-        int4 q = a.bq[a.bq2[s]];
-        int i = q.x;
-        int2 ent = a.lj[(size_t)i * a.lj_cap + q.y];
-        int j = ent.x;
+        int i, j, code;
         double dx, dy, dz;
-        load_disp(a.pos, a.n, box_of(a, i), i, j, ent.y, dx, dy, dz);
+        R C;
+        bstar_load<R>(a, a.bq2[s], i, j, dx, dy, dz, C, code);
         R rx = (R)dx, ry = (R)dy, rz = (R)dz;
         R r2 = rx * rx + ry * ry + rz * rz;
-        bstar_reverse<R>(P, a.G, i, j, rx, ry, rz, r2, (R)a.bq2_eps[s], sink);
+        bool dsb;
+        double e = bstar_full<R>(P, a.G, i, j, rx, ry, rz, r2, C, code, sink, dsb);
+        dsb_count += dsb;
+        E += e;
+        if (a.eatom) atomicAdd(a.eatom + i, e);
     }
-    block_accumulate<128>(0.0, sink.W, a.virial, a.acc + 1, a.acc + 3);
+    unsigned c = __reduce_add_sync(0xffffffffu, dsb_count);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(a.counters + CNT_DSB, (unsigned long long)c);
+    block_accumulate<128>(E, sink.W, a.virial, a.acc + 1, a.acc + 3);
+    if (a.pgrad) block_accumulate_g<128>(sink.G, a.pgrad);
 }
 
 template <class R>
@@ -377,7 +421,7 @@ __global__ void k_finish_counters(StepArgs<R> a) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         a.counters[CNT_BONDS] = (unsigned long long)(*a.nbonds + *a.nccbonds);
         a.counters[CNT_BSTAR] = (unsigned long long)(a.nbq[0] + a.nbq[1] + a.nbq[2]);
-        a.counters[CNT_DSB] = (unsigned long long)*a.nbq2;
+        a.counters[CNT_BSTAR_FULL] = (unsigned long long)*a.nbq2;
     }
 }
 

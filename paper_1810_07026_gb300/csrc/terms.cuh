@@ -119,7 +119,7 @@ template <class R> struct DevParams {
     Quintic<R> gC1, gC2, gH;
     R guard0, guardinv;
     R sigma[3], sig2[3], eps4[3], rc2[3], swlo[3], swlo2[3], swinv[3], Srlo[3], Srhi[3], Srhi2[3], Srinv[3];
-    R bmin[3], binv[3], rstar[3];
+    R bmin[3], bmax[3], binv[3], rstar[3];
     R teps[3];
     int kind;                        // inter-molecular term: 0 Lennard-Jones (AIREBO), 1 Morse (AIREBO-M)
     R meps[3], malpha[3], mre[3];    // Morse well depth, stiffness, minimum
@@ -552,7 +552,7 @@ HD R dihedral_sum(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, 
         int k = G.nj[qa];
         if (k == j) continue;
         R ax = G.dx[qa], ay = G.dy[qa], az = G.dz[qa];
-        R inv_ra = G.ir[qa], wik = G.w[qa], dwik = G.dw[qa];
+        R inv_ra = G.ir[qa], wik = G.w[qa];
         R csi = (ux * ax + uy * ay + uz * az) * inv_u * inv_ra;
         R dsi;
         R si = guardf<R>(P, csi, dsi);
@@ -566,7 +566,7 @@ HD R dihedral_sum(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, 
             int l = G.nj[qb];
             if (l == i || l == k) continue;
             R bx = G.dx[qb], by = G.dy[qb], bz = G.dz[qb];
-            R inv_rb = G.ir[qb], wjl = G.w[qb], dwjl = G.dw[qb];
+            R inv_rb = G.ir[qb], wjl = G.w[qb];
             R csj = -(ux * bx + uy * by + uz * bz) * inv_u * inv_rb;
             R dsj;
             R sj = guardf<R>(P, csj, dsj);
@@ -578,6 +578,7 @@ HD R dihedral_sum(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, 
             R one_m = R(1) - cw * cw;
             D += one_m * wik * wjl * si * sj;
             if (!reverse) continue;
+            R dwik = G.dw[qa], dwjl = G.dw[qb];     // the forward pass reads no dw/dr
             R in2s = R(1) / n2s;
             R dcw = dEdD * R(-2) * cw * wik * wjl * si * sj;
             R dwi = dEdD * one_m * wjl * si * sj;
@@ -612,6 +613,14 @@ HD R dihedral_sum(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, 
     return D;
 }
 
+// The S_b switch of the LJ term evaluated inside a reverse bond order: the
+// forward pass gives b*, and the reverse pass then runs with
+// dE/db* = scale * dS_b/db* (zero outside the transition, which skips it).
+template <class R> struct BstarSwitch {
+    R bmin, binv, scale;     // in
+    R Sb, dSb;               // out: S_b(b*) and dS_b/db*
+};
+
 // b_ij with u standing for r_ij (inv_u = 1/|u|).  REV = false: the value only,
 // without any derivative work.  REV = true: also the reverse pass with
 // eps = dE/db, which applies the forces on all neighbours and returns the
@@ -621,7 +630,8 @@ HD R dihedral_sum(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, 
 template <class R, bool REV>
 HD R bond_order(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, R uy, R uz, R umag, R inv_u,
                 R eps, Sink& sink, R& gux, R& guy, R& guz, R& gumag,
-                double& fix, double& fiy, double& fiz, double& fjx, double& fjy, double& fjz) {
+                double& fix, double& fiy, double& fiz, double& fjx, double& fjy, double& fjz,
+                BstarSwitch<R>* bsw = nullptr) {
     Side<R> si, sj;
     side_forward<R, REV>(P, G, i, j, ux, uy, uz, inv_u, umag, si);
     side_forward<R, REV>(P, G, j, i, -ux, -uy, -uz, inv_u, umag, sj);
@@ -650,6 +660,13 @@ HD R bond_order(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, R 
     }
     R b = R(0.5) * (si.p + sj.p) + pirc + pidh;
     if (!REV) return b;
+    if (bsw) {
+        R dS;
+        bsw->Sb = Sw<R>((b - bsw->bmin) * bsw->binv, dS);
+        bsw->dSb = dS * bsw->binv;
+        eps = bsw->scale * bsw->dSb;
+        if (eps == R(0)) return b;      // no gradient flows through b* (nor to the spline knots)
+    }
     if (P.kg) {
         kg_tricubic<R>(P.kg + KG_F + (tab * NTRI_CELLS + cell) * 64, tx, ty, tz, (double)eps);
         if (dih) kg_tricubic<R>(P.kg + KG_T + cell * 64, tx, ty, tz, (double)(eps * D));
@@ -1057,12 +1074,12 @@ HD int lj_classify(const DevParams<R>& P, const PathMap<R>& M, int i, int p, int
 }
 
 // b* pair: (S_r S_b + 1 - S_r) C V for the pair i -> (j, image) with
-// displacement d; C and its path given.  Applies every force except the one
-// through db*, which is needed only where S_b is in its transition: then
-// eps_out = dE/db* != 0 and bstar_reverse applies it.
+// displacement d; C and its path given, and S_b(b*) with its derivative
+// already known.  Applies every force except the one through db*, which the
+// reverse bond order applies where dS_b != 0.
 template <class R>
-HD double bstar_pair(const DevParams<R>& P, const Graph<R>& G, int i, int j, R dx, R dy, R dz, R r2,
-                     R C, int path_code, Sink& sink, R& eps_out) {
+HD double bstar_finish(const DevParams<R>& P, const Graph<R>& G, int i, int j, R dx, R dy, R dz, R r2,
+                       R C, int path_code, R Sb, R dSb, Sink& sink) {
     int p = pidx(G.type[i], G.type[j]);
     R inv_r = rsqrt_(r2);
     R r = r2 * inv_r;
@@ -1071,20 +1088,11 @@ HD double bstar_pair(const DevParams<R>& P, const Graph<R>& G, int i, int j, R d
     R dSr;
     R Sr = Sw<R>((r - P.Srlo[p]) * P.Srinv[p], dSr);
     dSr *= P.Srinv[p];
-    R rs = P.rstar[p];
-    R ux = dx * inv_r * rs, uy = dy * inv_r * rs, uz = dz * inv_r * rs;
-    R gux = 0, guy = 0, guz = 0, gumag = 0;
-    double fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
-    R bs = bond_order<R, false>(P, G, i, j, ux, uy, uz, rs, R(1) / rs, R(0), sink, gux, guy, guz, gumag,
-                                fix, fiy, fiz, fjx, fjy, fjz);
-    R dSb;
-    R Sb = Sw<R>((bs - P.bmin[p]) * P.binv[p], dSb);
-    dSb *= P.binv[p];
     R factor = Sr * Sb + R(1) - Sr;
     R E = factor * C * V;
     R dEdr_r = (dSr * (Sb - R(1))) * C * V * inv_r + factor * C * dVr;   // (dE/dr)/r
     double gx = dEdr_r * dx, gy = dEdr_r * dy, gz = dEdr_r * dz;
-    eps_out = Sr * C * V * dSb;
+    double fix = 0, fiy = 0, fiz = 0;
     if (path_code >= 0) path_forces<R>(G, i, path_code, -factor * V, sink, fix, fiy, fiz);
     if (sink.pgrad) {
         R de, ds;
@@ -1103,30 +1111,64 @@ HD double bstar_pair(const DevParams<R>& P, const Graph<R>& G, int i, int j, R d
     return (double)E;
 }
 
-// the force through b* of a b* pair: eps = dE/db*
+// b* of the pair i -> (j, image) with displacement d: the bond order of
+// Eq. 4 at the fixed length r* along d (value only)
 template <class R>
-HD void bstar_reverse(const DevParams<R>& P, const Graph<R>& G, int i, int j, R dx, R dy, R dz, R r2, R eps,
-                      Sink& sink) {
+HD R bstar_value(const DevParams<R>& P, const Graph<R>& G, int i, int j, R dx, R dy, R dz, R r2, Sink& sink) {
     int p = pidx(G.type[i], G.type[j]);
     R inv_r = rsqrt_(r2);
     R rs = P.rstar[p];
     R ux = dx * inv_r * rs, uy = dy * inv_r * rs, uz = dz * inv_r * rs;
     R gux = 0, guy = 0, guz = 0, gumag = 0;
     double fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
-    bond_order<R, true>(P, G, i, j, ux, uy, uz, rs, R(1) / rs, eps, sink, gux, guy, guz, gumag,
-                        fix, fiy, fiz, fjx, fjy, fjz);
-    // u = r* d/|d|: only the direction of d carries a gradient
-    R ud = (gux * dx + guy * dy + guz * dz) * inv_r;
-    R sc = rs * inv_r;
-    double gx = sc * (gux - ud * dx * inv_r);
-    double gy = sc * (guy - ud * dy * inv_r);
-    double gz = sc * (guz - ud * dz * inv_r);
-    atomic_add(sink.f + i, fix + gx); atomic_add(sink.f + sink.n + i, fiy + gy); atomic_add(sink.f + 2 * sink.n + i, fiz + gz);
-    atomic_add(sink.f + j, fjx - gx); atomic_add(sink.f + sink.n + j, fjy - gy); atomic_add(sink.f + 2 * sink.n + j, fjz - gz);
-    if (sink.virial) {
-        sink.W[0] -= (double)dx * gx; sink.W[1] -= (double)dy * gy; sink.W[2] -= (double)dz * gz;
-        sink.W[3] -= (double)dx * gy; sink.W[4] -= (double)dx * gz; sink.W[5] -= (double)dy * gz;
+    return bond_order<R, false>(P, G, i, j, ux, uy, uz, rs, R(1) / rs, R(0), sink, gux, guy, guz, gumag,
+                                fix, fiy, fiz, fjx, fjy, fjz);
+}
+
+// S_b from b*: 1 below the transition, 0 above it
+template <class R> HD R bstar_switch(const DevParams<R>& P, int p, R bs, R& dSb) {
+    R dS;
+    R Sb = Sw<R>((bs - P.bmin[p]) * P.binv[p], dS);
+    dSb = dS * P.binv[p];
+    return Sb;
+}
+
+// The whole b* pair in one pass: b* and its reverse (where dS_b != 0) in one
+// bond-order evaluation, then the pair term.  Returns the energy; sets dsb
+// when dS_b != 0.
+template <class R>
+HD double bstar_full(const DevParams<R>& P, const Graph<R>& G, int i, int j, R dx, R dy, R dz, R r2,
+                     R C, int path_code, Sink& sink, bool& dsb) {
+    int p = pidx(G.type[i], G.type[j]);
+    R inv_r = rsqrt_(r2);
+    R r = r2 * inv_r;
+    R dVr;
+    R V = vlj<R>(P, p, r2, dVr);
+    R dSr;
+    R Sr = Sw<R>((r - P.Srlo[p]) * P.Srinv[p], dSr);
+    R rs = P.rstar[p];
+    R ux = dx * inv_r * rs, uy = dy * inv_r * rs, uz = dz * inv_r * rs;
+    R gux = 0, guy = 0, guz = 0, gumag = 0;
+    double fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
+    BstarSwitch<R> bsw{P.bmin[p], P.binv[p], Sr * C * V, R(0), R(0)};
+    bond_order<R, true>(P, G, i, j, ux, uy, uz, rs, R(1) / rs, R(0), sink, gux, guy, guz, gumag,
+                        fix, fiy, fiz, fjx, fjy, fjz, &bsw);
+    dsb = bsw.dSb != R(0);
+    if (dsb) {
+        // u = r* d/|d|: only the direction of d carries a gradient
+        R ud = (gux * dx + guy * dy + guz * dz) * inv_r;
+        R sc = rs * inv_r;
+        double gx = sc * (gux - ud * dx * inv_r);
+        double gy = sc * (guy - ud * dy * inv_r);
+        double gz = sc * (guz - ud * dz * inv_r);
+        atomic_add(sink.f + i, fix + gx); atomic_add(sink.f + sink.n + i, fiy + gy); atomic_add(sink.f + 2 * sink.n + i, fiz + gz);
+        atomic_add(sink.f + j, fjx - gx); atomic_add(sink.f + sink.n + j, fjy - gy); atomic_add(sink.f + 2 * sink.n + j, fjz - gz);
+        if (sink.virial) {
+            sink.W[0] -= (double)dx * gx; sink.W[1] -= (double)dy * gy; sink.W[2] -= (double)dz * gz;
+            sink.W[3] -= (double)dx * gy; sink.W[4] -= (double)dx * gz; sink.W[5] -= (double)dy * gz;
+        }
     }
+    return bstar_finish<R>(P, G, i, j, dx, dy, dz, r2, C, path_code, bsw.Sb, bsw.dSb, sink);
 }
 
 }  // namespace airebo

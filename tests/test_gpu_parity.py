@@ -88,6 +88,26 @@ def test_counters_match_oracle(A, oracle, param_text):
     assert g["lj_in_cutoff"] == c["lj_in_cutoff"]
 
 
+@pytest.mark.parametrize("case", ["pe1152", "hot300", "hot1000"])
+def test_bstar_screen(A, oracle, param_text, case):
+    """FP64 with the FP32 b* screen against FP64 without it and against the
+    oracle: the same energies and forces (S_b is exactly 0 or 1 wherever the
+    screen decides), and the screen leaves fewer pairs to the full pass."""
+    pos, types, box = CASES[case]()
+    e, f, w, c = oracle.compute(pos, types, box)
+    on, ev_on = gpu_eval(A, param_text, pos, types, box, bstar_screen=True)
+    off, ev_off = gpu_eval(A, param_text, pos, types, box, bstar_screen=False)
+    assert_close(on, (e, f, w), 1e-10, 1e-8, 1e-8)
+    assert_close(on, off, 1e-12, 1e-11, 1e-11)
+    g_on, g_off = ev_on.counters(), ev_off.counters()
+    assert g_on["bstar"] == g_off["bstar"] == c["bstar"]
+    assert g_on["bstar_dsb"] == g_off["bstar_dsb"] == c["bstar_dsb_nonzero"]
+    # without the screen the first pass decides exactly; with it, a superset
+    # of the transition pairs (those within the margin) is left over
+    assert g_off["bstar_full"] == g_off["bstar_dsb"]
+    assert g_on["bstar_dsb"] <= g_on["bstar_full"] <= g_on["bstar"]
+
+
 def as_set(cnt, j, img):
     out = set()
     for i in range(len(cnt)):
