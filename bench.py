@@ -392,8 +392,8 @@ def run_ours(args):
             "drift_eV_per_atom_step": r64["drift"],
             "list_builds_in_timed_region": r64["builds"],
             "launch_shape": {k: {"lj_atoms_per_claim": results[k]["shape"][0],
-                                 "bond_blocks_per_sm": results[k]["shape"][1],
-                                 "bstar_blocks_per_sm": results[k]["shape"][2]} for k in results},
+                                 "bond_waves": results[k]["shape"][1],
+                                 "bstar_waves": results[k]["shape"][2]} for k in results},
             "kernel_ms": {k: v[0] / max(1, v[1]) for k, v in kt.items()},
             "kernel_share": {k: v[0] / max(1e-9, sum(x[0] for x in kt.values())) for k, v in kt.items()},
             "roofline": roof,

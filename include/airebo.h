@@ -168,7 +168,8 @@ airebo_status airebo_export_lists(airebo_handle h, int which, int32_t* h_cnt, in
  * each launch.  airebo_set_timing(h, 1) starts (and zeroes) the record;
  * airebo_kernel_times fills ms[k] (total milliseconds) and launches[k] for
  * k = 0 short list, 1 REBO bonds, 2 torsion, 3 connectivity map, 4 LJ pairs,
- * 5 b* pairs, 6 neighbour build, 7 NVE half steps.  out arrays: 8 entries.
+ * 5 b* pairs (first pass), 6 neighbour build, 7 NVE half steps, 8 b* pairs
+ * (full-precision pass).  out arrays: 9 entries.
  */
 airebo_status airebo_set_timing(airebo_handle h, int on);
 airebo_status airebo_kernel_times(airebo_handle h, double* ms, int64_t* launches);
@@ -241,10 +242,11 @@ airebo_status airebo_graph_launch(airebo_handle h);
 /*
  * Pick the launch shapes for this handle's system by timing them with CUDA
  * events on the handle's stream: the number of atoms an LJ warp claims at a
- * time (2..32), and the blocks per SM of the grid-stride REBO/torsion kernels
- * and of the b* kernels (4, 8 or 16 each); each candidate is the median of 5
- * evaluations.  Runs about 45 evaluations at d_pos (d_force is overwritten).
- * out3 (nullable, host int[3]) receives (lj_chunk, bond_grid, bstar_grid).  A
+ * time (2..32), and the grids of the grid-stride REBO/torsion kernels and of
+ * the b* kernels, in waves of resident blocks (1, 2, 4 or 8 times the blocks
+ * that fit on all SMs at once); each candidate is the median of 5
+ * evaluations.  Runs about 50 evaluations at d_pos (d_force is overwritten).
+ * out3 (nullable, host int[3]) receives (lj_chunk, bond_waves, bstar_waves).  A
  * graph captured earlier keeps the shapes it was captured with.  Errors:
  * those of airebo_compute; AIREBO_ERR_STATE before airebo_neighbor.
  */
@@ -253,11 +255,11 @@ airebo_status airebo_autotune(airebo_handle h, const double* d_pos, double* d_fo
 /*
  * Set the launch shapes directly (for example to copy a tuned choice to
  * another handle of the same system): lj_chunk in 1..64 atoms per warp claim,
- * bond_grid and bstar_grid in 1..32 blocks per SM.  AIREBO_ERR_ARG outside
- * those ranges.  Results do not depend on the shapes beyond the order of
- * floating-point atomic additions.
+ * bond_waves and bstar_waves in 1..32 waves (default 8, 2, 2).
+ * AIREBO_ERR_ARG outside those ranges.  Results do not depend on the shapes
+ * beyond the order of floating-point atomic additions.
  */
-airebo_status airebo_set_launch_shape(airebo_handle h, int lj_chunk, int bond_grid, int bstar_grid);
+airebo_status airebo_set_launch_shape(airebo_handle h, int lj_chunk, int bond_waves, int bstar_waves);
 
 /*
  * Gradient of the total energy with respect to every spline knot datum of the

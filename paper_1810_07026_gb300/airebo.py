@@ -24,7 +24,7 @@ FP64, MIXED = 0, 1
 KNOT_BLOCKS = (("gC1.data", 18), ("gC2.data", 18), ("gH.data", 12), ("P.CC", 100), ("P.CH", 100), ("P.HC", 100),
                ("piRC.CC", 1800), ("piRC.CH", 1800), ("piRC.HH", 1800), ("Tij.CC", 1800))
 KNOT_COUNT = sum(c for _, c in KNOT_BLOCKS)
-KERNELS = ("short_list", "rebo", "torsion", "path_map", "lj", "bstar", "neighbor", "nve")
+KERNELS = ("short_list", "rebo", "torsion", "path_map", "lj", "bstar", "neighbor", "nve", "bstar_rev")
 
 
 class AireboError(RuntimeError):
@@ -196,8 +196,8 @@ class Airebo:
         self._check(lib().airebo_graph_capture(self._h, _ptr(pos), _ptr(force), _ptr(energy4), _ptr(energy_sys)))
 
     def autotune(self, pos, force=None):
-        """Time the launch shapes on this system; returns (LJ atoms per warp claim, REBO/torsion and b*
-        blocks per SM)."""
+        """Time the launch shapes on this system; returns (LJ atoms per warp claim, REBO/torsion waves,
+        b* waves)."""
         torch = self._torch
         pos = self._dev(pos, torch.float64)
         if force is None:
@@ -206,8 +206,8 @@ class Airebo:
         self._check(lib().airebo_autotune(self._h, _ptr(pos), _ptr(force), _np(out)))
         return int(out[0]), int(out[1]), int(out[2])
 
-    def set_launch_shape(self, lj_chunk, bond_grid, bstar_grid):
-        self._check(lib().airebo_set_launch_shape(self._h, int(lj_chunk), int(bond_grid), int(bstar_grid)))
+    def set_launch_shape(self, lj_chunk, bond_waves, bstar_waves):
+        self._check(lib().airebo_set_launch_shape(self._h, int(lj_chunk), int(bond_waves), int(bstar_waves)))
 
     def graph_launch(self):
         self._check(lib().airebo_graph_launch(self._h))
@@ -302,8 +302,8 @@ class Airebo:
         self._check(lib().airebo_set_timing(self._h, int(on)))
 
     def kernel_times(self) -> dict:
-        ms = np.zeros(8)
-        nl = np.zeros(8, dtype=np.int64)
+        ms = np.zeros(len(KERNELS))
+        nl = np.zeros(len(KERNELS), dtype=np.int64)
         self._check(lib().airebo_kernel_times(self._h, _np(ms), _np(nl)))
         return {k: (float(ms[i]), int(nl[i])) for i, k in enumerate(KERNELS)}
 

@@ -360,7 +360,7 @@ struct airebo_ctx {
     unsigned long long* counters = nullptr;   // 8
     int* derr = nullptr;                 // 8 ints
     int stride = 8;                      // REBO slots per atom (grows to MAXN)
-    int lj_chunk = 8, bond_grid = 8, bstar_grid = 8;   // launch shapes (airebo_autotune)
+    int lj_chunk = 8, bond_waves = 2, bstar_waves = 2;   // launch shapes (airebo_autotune)
     // batched systems (nsys = 0: one system with box L)
     int nsys = 0;
     std::vector<double> Lsys_h;
@@ -387,9 +387,9 @@ struct airebo_ctx {
     long long rebuilds = 0;
     // per-kernel timing
     bool timing = false;
-    cudaEvent_t ev[11] = {};
-    double kt_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    long long kt_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    cudaEvent_t ev[12] = {};             // 0..7 around the compute kernels, 8..11 neighbour build and NVE
+    double kt_ms[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    long long kt_n[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -581,15 +581,15 @@ airebo_status do_neighbor(airebo_handle h, const double* d_pos) {
         a.Lsys = h->nsys ? h->d_Lsys : nullptr;
         a.snc = h->d_snc; a.sreach = h->d_sreach; a.scw = h->d_scw; a.scell0 = h->d_scell0;
         CK(cudaMemsetAsync(h->derr, 0, sizeof(int) * 8, h->stream));
-        if (h->timing) CK(cudaEventRecord(h->ev[7], h->stream));
+        if (h->timing) CK(cudaEventRecord(h->ev[8], h->stream));
         launch_neighbor(a, h->stream, ncell);
         CK(cudaGetLastError());
-        if (h->timing) CK(cudaEventRecord(h->ev[8], h->stream));
+        if (h->timing) CK(cudaEventRecord(h->ev[9], h->stream));
         CK(cudaMemcpyAsync(h->h_err, h->derr, sizeof(int) * 8, cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
         if (h->timing && h->n) {
             float ms = 0;
-            CK(cudaEventElapsedTime(&ms, h->ev[7], h->ev[8]));
+            CK(cudaEventElapsedTime(&ms, h->ev[8], h->ev[9]));
             h->kt_ms[6] += ms;
             h->kt_n[6] += 1;
         }
@@ -650,8 +650,8 @@ template <class R> StepArgs<R> make_args(airebo_handle h, Precision<R>& pr, cons
     }
     a.lj_next = h->counts + 7;
     a.lj_chunk = h->lj_chunk;
-    a.bond_grid = h->bond_grid;
-    a.bstar_grid = h->bstar_grid;
+    a.bond_waves = h->bond_waves;
+    a.bstar_waves = h->bstar_waves;
     a.f = d_force; a.acc = h->acc; a.counters = h->counters; a.err = h->derr;
     a.virial = virial;
     a.sys = h->nsys ? h->d_sys : nullptr;
@@ -703,11 +703,13 @@ airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos,
         CK(cudaMemcpyAsync(h->h_u64, h->counts, sizeof(int) * 8, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (h->timing && h->n) {
-            bool ran[6] = {true, a.rebo, a.torsion, a.lj_on, a.lj_on, a.lj_on};
-            for (int k = 0; k < 6; k++) {
+            // slot k: events k -> k+1; the second b* kernel (events 6 -> 7) is slot 8
+            bool ran[7] = {true, a.rebo, a.torsion, a.lj_on, a.lj_on, a.lj_on, a.lj_on};
+            for (int k = 0; k < 7; k++) {
                 float ms = 0;
                 CK(cudaEventElapsedTime(&ms, h->ev[k], h->ev[k + 1]));
-                if (ran[k]) { h->kt_ms[k] += ms; h->kt_n[k] += 1; }
+                int slot = k == 6 ? 8 : k;
+                if (ran[k]) { h->kt_ms[slot] += ms; h->kt_n[slot] += 1; }
             }
         }
         if (h->h_err[ERR_NONFINITE]) return fail(h, AIREBO_ERR_NONFINITE, "non-finite position");
@@ -853,7 +855,7 @@ void airebo_destroy(airebo_handle h) {
                   h->im, h->im_cnt, h->xref, h->bonds, h->ccbonds, h->bq, h->bq2, h->counts, h->acc, h->counters, h->derr, h->maxd2, h->ke,
                   h->hpos, h->hvel, h->hforce, h->he4, h->hw6};
     for (void* p : ps) if (p) cudaFree(p);
-    for (int k = 0; k < 11; k++) if (h->ev[k]) cudaEventDestroy(h->ev[k]);
+    for (int k = 0; k < 12; k++) if (h->ev[k]) cudaEventDestroy(h->ev[k]);
     if (h->h_err) cudaFreeHost(h->h_err);
     if (h->h_u64) cudaFreeHost(h->h_u64);
     if (h->h_acc) cudaFreeHost(h->h_acc);
@@ -940,7 +942,7 @@ airebo_status airebo_nve(airebo_handle h, double* d_pos, double* d_vel, double* 
     auto read_pending = [&]() -> airebo_status {
         if (pending) {
             float ms = 0;
-            CK(cudaEventElapsedTime(&ms, h->ev[9], h->ev[10]));
+            CK(cudaEventElapsedTime(&ms, h->ev[10], h->ev[11]));
             h->kt_ms[7] += ms;
             h->kt_n[7] += 1;
             pending = false;
@@ -949,15 +951,15 @@ airebo_status airebo_nve(airebo_handle h, double* d_pos, double* d_vel, double* 
     };
     for (int step = 0; step < nsteps; step++) {
         CK(cudaMemsetAsync(h->maxd2, 0, sizeof(unsigned long long), s));
-        if (h->timing) CK(cudaEventRecord(h->ev[7], s));
+        if (h->timing) CK(cudaEventRecord(h->ev[8], s));
         launch_nve_half(d_pos, d_vel, d_force, h->types, h->n, dt, true, h->xref, h->maxd2, nullptr, s);
         CK(cudaGetLastError());
-        if (h->timing) CK(cudaEventRecord(h->ev[8], s));
+        if (h->timing) CK(cudaEventRecord(h->ev[9], s));
         CK(cudaMemcpyAsync(h->h_u64, h->maxd2, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (h->timing) {
             float ms = 0;
-            CK(cudaEventElapsedTime(&ms, h->ev[7], h->ev[8]));
+            CK(cudaEventElapsedTime(&ms, h->ev[8], h->ev[9]));
             h->kt_ms[7] += ms;
             h->kt_n[7] += 1;
             airebo_status st = read_pending();
@@ -974,15 +976,15 @@ airebo_status airebo_nve(airebo_handle h, double* d_pos, double* d_vel, double* 
         airebo_status st = compute_any(h, d_pos, d_force, nullptr, nullptr);
         if (st) return st;
         if (last) CK(cudaMemsetAsync(h->ke, 0, sizeof(double), s));
-        if (h->timing) CK(cudaEventRecord(h->ev[9], s));
+        if (h->timing) CK(cudaEventRecord(h->ev[10], s));
         launch_nve_half(d_pos, d_vel, d_force, h->types, h->n, dt, false, nullptr, nullptr, last ? h->ke : nullptr, s);
         CK(cudaGetLastError());
-        if (h->timing) { CK(cudaEventRecord(h->ev[10], s)); pending = true; }
+        if (h->timing) { CK(cudaEventRecord(h->ev[11], s)); pending = true; }
         if (last && d_energy4) k_nve_energy<<<1, 32, 0, s>>>(h->acc, h->ke, d_energy4, h->rebuilds);
     }
     CK(cudaGetLastError());
     if (pending) {
-        CK(cudaEventSynchronize(h->ev[10]));
+        CK(cudaEventSynchronize(h->ev[11]));
         airebo_status st = read_pending();
         if (st) return st;
     }
@@ -1136,12 +1138,12 @@ airebo_status airebo_autotune(airebo_handle h, const double* d_pos, double* d_fo
     auto timed = [&](double* med_a, double* med_b) -> airebo_status {
         double ta[REPS], tb[REPS];
         for (int rep = 0; rep < REPS; rep++) {
-            for (int k = 0; k < 8; k++) { h->kt_ms[k] = 0; h->kt_n[k] = 0; }
+            for (int k = 0; k < 9; k++) { h->kt_ms[k] = 0; h->kt_n[k] = 0; }
             airebo_status s2 = compute_any(h, d_pos, d_force, nullptr, nullptr);
             if (s2) return s2;
             ta[rep] = h->kt_ms[4];                       // LJ
             tb[rep] = h->kt_ms[1] + h->kt_ms[2];         // REBO + torsion
-            if (med_b) med_b[rep] = h->kt_ms[5];         // b* and its reverse
+            if (med_b) med_b[rep] = h->kt_ms[5] + h->kt_ms[8];   // both b* kernels
         }
         std::sort(ta, ta + REPS);
         std::sort(tb, tb + REPS);
@@ -1151,9 +1153,9 @@ airebo_status airebo_autotune(airebo_handle h, const double* d_pos, double* d_fo
         return AIREBO_OK;
     };
     const int chunks[] = {2, 4, 8, 16, 32};
-    const int grids[] = {4, 8, 16};
+    const int waves[] = {1, 2, 4, 8};
     double best_lj = 1e300, best_bond = 1e300, best_bstar = 1e300;
-    int bc = h->lj_chunk, bg = h->bond_grid, bs = h->bstar_grid;
+    int bc = h->lj_chunk, bg = h->bond_waves, bs = h->bstar_waves;
     // the LJ chunk and the two grids act on different kernels: tune each
     if (h->opt.enable_lj) {
         for (int c : chunks) {
@@ -1165,29 +1167,29 @@ airebo_status airebo_autotune(airebo_handle h, const double* d_pos, double* d_fo
         }
     }
     h->lj_chunk = bc;
-    for (int g : grids) {
-        h->bond_grid = g;
-        h->bstar_grid = g;
+    for (int g : waves) {
+        h->bond_waves = g;
+        h->bstar_waves = g;
         double m[2], tb[REPS];
         st = timed(m, tb);
         if (st) return st;
         if (m[1] < best_bond) { best_bond = m[1]; bg = g; }
         if (tb[REPS / 2] < best_bstar) { best_bstar = tb[REPS / 2]; bs = g; }
     }
-    h->bond_grid = bg;
-    h->bstar_grid = bs;
+    h->bond_waves = bg;
+    h->bstar_waves = bs;
     airebo_set_timing(h, was_timing ? 1 : 0);
-    if (out3) { out3[0] = h->lj_chunk; out3[1] = h->bond_grid; out3[2] = h->bstar_grid; }
+    if (out3) { out3[0] = h->lj_chunk; out3[1] = h->bond_waves; out3[2] = h->bstar_waves; }
     return AIREBO_OK;
 }
 
-airebo_status airebo_set_launch_shape(airebo_handle h, int lj_chunk, int bond_grid, int bstar_grid) {
+airebo_status airebo_set_launch_shape(airebo_handle h, int lj_chunk, int bond_waves, int bstar_waves) {
     if (!h) return AIREBO_ERR_ARG;
-    if (lj_chunk < 1 || lj_chunk > 64 || bond_grid < 1 || bond_grid > 32 || bstar_grid < 1 || bstar_grid > 32)
-        return fail(h, AIREBO_ERR_ARG, "launch shape out of range (lj_chunk 1..64, grids 1..32 blocks per SM)");
+    if (lj_chunk < 1 || lj_chunk > 64 || bond_waves < 1 || bond_waves > 32 || bstar_waves < 1 || bstar_waves > 32)
+        return fail(h, AIREBO_ERR_ARG, "launch shape out of range (lj_chunk 1..64, waves 1..32)");
     h->lj_chunk = lj_chunk;
-    h->bond_grid = bond_grid;
-    h->bstar_grid = bstar_grid;
+    h->bond_waves = bond_waves;
+    h->bstar_waves = bstar_waves;
     return AIREBO_OK;
 }
 
@@ -1307,15 +1309,15 @@ airebo_status airebo_set_timing(airebo_handle h, int on) {
     if (!h) return AIREBO_ERR_ARG;
     CK(cudaSetDevice(h->device));
     if (on && !h->ev[0])
-        for (int k = 0; k < 11; k++) CK(cudaEventCreate(&h->ev[k]));
+        for (int k = 0; k < 12; k++) CK(cudaEventCreate(&h->ev[k]));
     h->timing = on != 0;
-    for (int k = 0; k < 8; k++) { h->kt_ms[k] = 0; h->kt_n[k] = 0; }
+    for (int k = 0; k < 9; k++) { h->kt_ms[k] = 0; h->kt_n[k] = 0; }
     return AIREBO_OK;
 }
 
 airebo_status airebo_kernel_times(airebo_handle h, double* ms, int64_t* launches) {
     if (!h || !ms || !launches) return AIREBO_ERR_ARG;
-    for (int k = 0; k < 8; k++) { ms[k] = h->kt_ms[k]; launches[k] = h->kt_n[k]; }
+    for (int k = 0; k < 9; k++) { ms[k] = h->kt_ms[k]; launches[k] = h->kt_n[k]; }
     return AIREBO_OK;
 }
 

@@ -48,8 +48,8 @@ template <class R> struct StepArgs {
     float* s_dx; float* s_dy; float* s_dz; float* s_r; float* s_ir; float* s_w; float* s_nC; float* s_nH;
     int* lj_next;                          // work counter of the LJ kernel's warps
     int lj_chunk;                          // atoms a warp takes at a time (tuned)
-    int bond_grid;                         // blocks per SM of the grid-stride REBO and torsion kernels (tuned)
-    int bstar_grid;                        // blocks per SM of the b* kernels (tuned)
+    int bond_waves;                        // waves of resident blocks of the REBO and torsion kernels (tuned)
+    int bstar_waves;                       // waves of resident blocks of the b* kernels (tuned)
     const int* sys;                        // batched systems: system of each atom (null: one system, box L)
     const double* Lsys;                    // batched systems: box of each system (3 per system)
     double* eatom;                         // nullable: energy of each atom's anchored terms

@@ -198,17 +198,42 @@ template <class R> struct LjBuf {
     double dx[2][64], dy[2][64], dz[2][64];
     R r2[2][64];
     int jp[2][64];          // j | species pair << 30
+    int ia[2][64];          // the list's atom i
+};
+
+// Per-lane force (and energy) accumulator of the atom whose pairs the lane
+// last evaluated.  Batches run across atom boundaries, so a lane flushes it
+// with atomics when its next pair belongs to another atom.
+struct LaneAcc {
+    int own = -1;
+    double fx = 0, fy = 0, fz = 0, e = 0;
+    __device__ __forceinline__ void flush(double* f, int n, double* eatom) {
+        if (own >= 0) {
+            atomicAdd(f + own, fx); atomicAdd(f + n + own, fy); atomicAdd(f + 2 * n + own, fz);
+            if (eatom) atomicAdd(eatom + own, e);
+        }
+        fx = fy = fz = e = 0;
+    }
 };
 
 template <class R>
 __device__ __forceinline__ void lj_batch(const DevParams<R>& P, LjBuf<R>& B, int b, int lane, Sink& sink,
-                                         double& fix, double& fiy, double& fiz, double& E) {
+                                         LaneAcc& acc, double* eatom, double& E) {
     int jp = B.jp[b][lane];
     int j = jp & 0x3fffffff, p = (unsigned)jp >> 30;
+    int i = B.ia[b][lane];
+    if (i != acc.own) {
+        acc.flush(sink.f, sink.n, eatom);
+        acc.own = i;
+    }
+    double E0 = E;
     if (b == 0)
-        lj_eval_inner<R>(P, p, j, B.dx[b][lane], B.dy[b][lane], B.dz[b][lane], B.r2[b][lane], sink, fix, fiy, fiz, E);
+        lj_eval_inner<R>(P, p, j, B.dx[b][lane], B.dy[b][lane], B.dz[b][lane], B.r2[b][lane], sink,
+                         acc.fx, acc.fy, acc.fz, E);
     else
-        lj_eval_switch<R>(P, p, j, B.dx[b][lane], B.dy[b][lane], B.dz[b][lane], B.r2[b][lane], sink, fix, fiy, fiz, E);
+        lj_eval_switch<R>(P, p, j, B.dx[b][lane], B.dy[b][lane], B.dz[b][lane], B.r2[b][lane], sink,
+                          acc.fx, acc.fy, acc.fz, E);
+    if (eatom) acc.e += E - E0;
 }
 
 template <class R>
@@ -222,11 +247,15 @@ __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
     LjBuf<R>& B = bufs[threadIdx.x >> 5];
     unsigned lt = (1u << lane) - 1u;
     Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}, a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
+    LaneAcc acc;
     double E = 0;
     unsigned evaluated = 0;
     int n = a.n;
+    int cnt[2] = {0, 0};
     // warps take chunks of lj_chunk consecutive atoms from a global counter,
-    // which balances C and H atoms (different list lengths) across warps
+    // which balances C and H atoms (different list lengths) across warps; the
+    // compaction buffers carry over from atom to atom, so that only the last
+    // batch of a warp runs partly empty
     int chunk_end = 0;
     for (int i = 0;; i++) {
         if (i >= chunk_end) {
@@ -239,12 +268,9 @@ __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
         }
         double xi = a.pos[i], yi = a.pos[n + i], zi = a.pos[2 * n + i];
         int ti = a.G.type[i];
-        double fix = 0, fiy = 0, fiz = 0;
         int ne = a.lj_cnt[i];
         const int2* row = a.lj + (size_t)i * a.lj_cap;
         const double* L = box_of(a, i);
-        double E_before = E;
-        int cnt[2] = {0, 0};
         for (int base = 0; base < ne; base += 32) {
             int e = base + lane;
             int st = 0, j = 0, p = 0;
@@ -275,7 +301,10 @@ __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
                     int q = atomicAdd(a.nbq + p, 1);
                     if (q < a.bq_cap) a.bq[(size_t)p * a.bq_cap + q] = make_int4(i, e, mi, 0);
                 } else if (st == 4) {     // rare: 0 < C < 1 along a path
-                    lj_eval<R>(P, a.G, i, p, j, dx, dy, dz, C, code, sink, fix, fiy, fiz, E);
+                    double gx = 0, gy = 0, gz = 0, E0 = E;
+                    lj_eval<R>(P, a.G, i, p, j, dx, dy, dz, C, code, sink, gx, gy, gz, E);
+                    atomicAdd(a.f + i, gx); atomicAdd(a.f + n + i, gy); atomicAdd(a.f + 2 * n + i, gz);
+                    if (a.eatom) atomicAdd(a.eatom + i, E - E0);
                 }
             }
 #pragma unroll
@@ -284,36 +313,30 @@ __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
                 unsigned m = __ballot_sync(0xffffffffu, st == want);
                 if (st == want) {
                     int s = cnt[b] + __popc(m & lt);
-                    B.dx[b][s] = dx; B.dy[b][s] = dy; B.dz[b][s] = dz; B.r2[b][s] = r2; B.jp[b][s] = j | (p << 30);
+                    B.dx[b][s] = dx; B.dy[b][s] = dy; B.dz[b][s] = dz; B.r2[b][s] = r2;
+                    B.jp[b][s] = j | (p << 30); B.ia[b][s] = i;
                 }
                 cnt[b] += __popc(m);
                 __syncwarp();
                 if (cnt[b] >= 32) {
-                    lj_batch<R>(P, B, b, lane, sink, fix, fiy, fiz, E);
+                    lj_batch<R>(P, B, b, lane, sink, acc, a.eatom, E);
                     __syncwarp();
                     if (lane < cnt[b] - 32) {
                         int s = 32 + lane;
                         B.dx[b][lane] = B.dx[b][s]; B.dy[b][lane] = B.dy[b][s]; B.dz[b][lane] = B.dz[b][s];
-                        B.r2[b][lane] = B.r2[b][s]; B.jp[b][lane] = B.jp[b][s];
+                        B.r2[b][lane] = B.r2[b][s]; B.jp[b][lane] = B.jp[b][s]; B.ia[b][lane] = B.ia[b][s];
                     }
                     cnt[b] -= 32;
                     __syncwarp();
                 }
             }
         }
-#pragma unroll
-        for (int b = 0; b < 2; b++)
-            if (lane < cnt[b]) lj_batch<R>(P, B, b, lane, sink, fix, fiy, fiz, E);
-        __syncwarp();
-        fix = warp_sum(fix); fiy = warp_sum(fiy); fiz = warp_sum(fiz);
-        if (lane == 0) {
-            atomicAdd(a.f + i, fix); atomicAdd(a.f + n + i, fiy); atomicAdd(a.f + 2 * n + i, fiz);
-        }
-        if (a.eatom) {
-            double ei = warp_sum(E - E_before);
-            if (lane == 0) atomicAdd(a.eatom + i, ei);
-        }
     }
+    // the warp's last, partly filled batches
+#pragma unroll
+    for (int b = 0; b < 2; b++)
+        if (lane < cnt[b]) lj_batch<R>(P, B, b, lane, sink, acc, a.eatom, E);
+    acc.flush(a.f, n, a.eatom);
     unsigned ev = __reduce_add_sync(0xffffffffu, evaluated);
     if (lane == 0 && ev) atomicAdd(a.counters + CNT_LJ, (unsigned long long)ev);
     block_accumulate<LJ_THREADS>(E, sink.W, a.virial, a.acc + 1, a.acc + 3);
@@ -430,14 +453,22 @@ void launch_compute_impl(const StepArgs<R>& a, cudaStream_t s, int num_sms, cuda
     if (a.n == 0) return;
     int n = a.n;
     auto mark = [&](int k) { if (ev) cudaEventRecord(ev[k], s); };
-    int grid_bonds = num_sms * a.bond_grid;
-    int grid_bstar = num_sms * a.bstar_grid;
+    // grid-stride kernels launch whole waves: waves x resident blocks per SM x SMs
+    // (the occupancies are asked once; nothing but stream work during graph capture)
+    static int occ[4] = {-1, -1, -1, -1};
+    if (occ[0] < 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_rebo<R>, 128, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_torsion<R>, 128, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], k_bstar<R>, 128, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[3], k_bstar_rev<R>, 128, 0);
+    }
+    auto grid_of = [&](int k, int waves) { return num_sms * (occ[k] > 0 ? occ[k] : 1) * waves; };
     mark(0);
     k_short_list<R><<<(n + 127) / 128, 128, 0, s>>>(a);
     mark(1);
-    if (a.rebo) k_rebo<R><<<grid_bonds, 128, 0, s>>>(a);
+    if (a.rebo) k_rebo<R><<<grid_of(0, a.bond_waves), 128, 0, s>>>(a);
     mark(2);
-    if (a.torsion) k_torsion<R><<<grid_bonds, 128, 0, s>>>(a);
+    if (a.torsion) k_torsion<R><<<grid_of(1, a.bond_waves), 128, 0, s>>>(a);
     mark(3);
     if (a.lj_on) k_path_map<R><<<(n + 127) / 128, 128, 0, s>>>(a);
     mark(4);
@@ -449,11 +480,10 @@ void launch_compute_impl(const StepArgs<R>& a, cudaStream_t s, int num_sms, cuda
         k_lj<R><<<blocks < need ? blocks : need, LJ_THREADS, 0, s>>>(a);
     }
     mark(5);
-    if (a.lj_on) {
-        k_bstar<R><<<grid_bstar, 128, 0, s>>>(a);
-        k_bstar_rev<R><<<grid_bstar, 128, 0, s>>>(a);
-    }
+    if (a.lj_on) k_bstar<R><<<grid_of(2, a.bstar_waves), 128, 0, s>>>(a);
     mark(6);
+    if (a.lj_on) k_bstar_rev<R><<<grid_of(3, a.bstar_waves), 128, 0, s>>>(a);
+    mark(7);
     k_finish_counters<R><<<1, 32, 0, s>>>(a);
 }
 
