@@ -242,10 +242,10 @@ airebo_status airebo_graph_launch(airebo_handle h);
 /*
  * Pick the launch shapes for this handle's system by timing them with CUDA
  * events on the handle's stream: the number of atoms an LJ warp claims at a
- * time (2..32), and the grids of the grid-stride REBO/torsion kernels and of
- * the b* kernels, in waves of resident blocks (1, 2, 4 or 8 times the blocks
+ * time (2..16), and the grids of the grid-stride REBO/torsion kernels and of
+ * the b* kernels, in waves of resident blocks (2, 4, 8 or 16 times the blocks
  * that fit on all SMs at once); each candidate is the median of 5
- * evaluations.  Runs about 50 evaluations at d_pos (d_force is overwritten).
+ * evaluations.  Runs about 45 evaluations at d_pos (d_force is overwritten).
  * out3 (nullable, host int[3]) receives (lj_chunk, bond_waves, bstar_waves).  A
  * graph captured earlier keeps the shapes it was captured with.  Errors:
  * those of airebo_compute; AIREBO_ERR_STATE before airebo_neighbor.
@@ -255,7 +255,7 @@ airebo_status airebo_autotune(airebo_handle h, const double* d_pos, double* d_fo
 /*
  * Set the launch shapes directly (for example to copy a tuned choice to
  * another handle of the same system): lj_chunk in 1..64 atoms per warp claim,
- * bond_waves and bstar_waves in 1..32 waves (default 8, 2, 2).
+ * bond_waves and bstar_waves in 1..32 waves (defaults 4, 8, 8).
  * AIREBO_ERR_ARG outside those ranges.  Results do not depend on the shapes
  * beyond the order of floating-point atomic additions.
  */

@@ -360,7 +360,7 @@ struct airebo_ctx {
     unsigned long long* counters = nullptr;   // 8
     int* derr = nullptr;                 // 8 ints
     int stride = 8;                      // REBO slots per atom (grows to MAXN)
-    int lj_chunk = 8, bond_waves = 2, bstar_waves = 2;   // launch shapes (airebo_autotune)
+    int lj_chunk = 4, bond_waves = 8, bstar_waves = 8;   // launch shapes (airebo_autotune)
     // batched systems (nsys = 0: one system with box L)
     int nsys = 0;
     std::vector<double> Lsys_h;
@@ -1152,8 +1152,8 @@ airebo_status airebo_autotune(airebo_handle h, const double* d_pos, double* d_fo
         if (med_b) std::sort(med_b, med_b + REPS);
         return AIREBO_OK;
     };
-    const int chunks[] = {2, 4, 8, 16, 32};
-    const int waves[] = {1, 2, 4, 8};
+    const int chunks[] = {2, 4, 8, 16};
+    const int waves[] = {2, 4, 8, 16};
     double best_lj = 1e300, best_bond = 1e300, best_bstar = 1e300;
     int bc = h->lj_chunk, bg = h->bond_waves, bs = h->bstar_waves;
     // the LJ chunk and the two grids act on different kernels: tune each

@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
 
 // ------------------------------------------------------------------ REBO bonds
 template <class R>
-__global__ void __launch_bounds__(128) k_rebo(StepArgs<R> a) {
+__global__ void __launch_bounds__(128, 4) k_rebo(StepArgs<R> a) {
     const DevParams<R>& P = *a.P;
     Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}, a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
     double E = 0;
@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(128) k_bstar(StepArgs<R> a) {
 
 // Phase 2: the pairs of the second queue, b* and its gradient in one pass.
 template <class R>
-__global__ void __launch_bounds__(128) k_bstar_rev(StepArgs<R> a) {
+__global__ void __launch_bounds__(128, 4) k_bstar_rev(StepArgs<R> a) {
     const DevParams<R>& P = *a.P;
     Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}, a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
     double E = 0;
