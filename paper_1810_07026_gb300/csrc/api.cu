@@ -346,6 +346,7 @@ struct airebo_ctx {
     double cell_w[3] = {0, 0, 0};
     int *cell_of = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cell_fill = nullptr;
     float4* spos = nullptr;
+    float4* posf = nullptr;              // FP32 positions of the current step (LJ pair tests)
     char4* swrap = nullptr;
     // lists
     int2* lj = nullptr; int* lj_cnt = nullptr; int lj_cap = 0; size_t lj_alloc = 0;
@@ -480,6 +481,7 @@ airebo_status alloc_atoms(airebo_handle h, int n) {
     CK(realloc_dev(h->types, na));
     CK(realloc_dev(h->cell_of, na));
     CK(realloc_dev(h->spos, na));
+    CK(realloc_dev(h->posf, na));
     CK(realloc_dev(h->swrap, na));
     CK(realloc_dev(h->lj_cnt, na));
     CK(realloc_dev(h->im_cnt, na));
@@ -626,6 +628,7 @@ template <class R> StepArgs<R> make_args(airebo_handle h, Precision<R>& pr, cons
     a.g_r = b.r; a.g_ir = b.ir; a.g_w = b.w; a.g_dw = b.dw; a.g_omw = b.omw; a.g_nC = b.nC; a.g_nH = b.nH;
     a.M.cap = b.map_cap; a.M.cnt = b.map_cnt; a.M.key = b.map_key; a.M.wt = b.map_wt; a.M.path = b.map_path;
     a.pos = d_pos;
+    a.posf = h->posf;
     for (int d = 0; d < 3; d++) a.L[d] = h->L[d];
     a.lj = h->lj; a.lj_cnt = h->lj_cnt; a.lj_cap = h->lj_cap;
     a.im = h->im; a.im_cnt = h->im_cnt; a.im_cap = h->im_cap;
@@ -851,7 +854,7 @@ void airebo_destroy(airebo_handle h) {
         void* bs[] = {h->d_sys, h->d_snc, h->d_sreach, h->d_scell0, h->d_Lsys, h->d_scw, h->d_off, h->eatom};
         for (void* p : bs) if (p) cudaFree(p);
     }
-    void* ps[] = {h->types, h->cell_of, h->cell_count, h->cell_start, h->cell_fill, h->spos, h->swrap, h->lj, h->lj_cnt,
+    void* ps[] = {h->types, h->cell_of, h->cell_count, h->cell_start, h->cell_fill, h->spos, h->posf, h->swrap, h->lj, h->lj_cnt,
                   h->im, h->im_cnt, h->xref, h->bonds, h->ccbonds, h->bq, h->bq2, h->counts, h->acc, h->counters, h->derr, h->maxd2, h->ke,
                   h->hpos, h->hvel, h->hforce, h->he4, h->hw6};
     for (void* p : ps) if (p) cudaFree(p);

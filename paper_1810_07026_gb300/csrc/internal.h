@@ -34,6 +34,7 @@ template <class R> struct StepArgs {
     R* g_dx; R* g_dy; R* g_dz; R* g_r; R* g_ir; R* g_w; R* g_dw; R* g_omw; R* g_nC; R* g_nH;
     PathMap<R> M;
     const double* pos;
+    float4* posf;                          // FP32 copy of the positions (written by the short-list kernel)
     double L[3];
     const int2* lj; const int* lj_cnt; int lj_cap;
     const int2* im; const int* im_cnt; int im_cap;

@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
     int n = a.n;
     double xi = a.pos[i], yi = a.pos[n + i], zi = a.pos[2 * n + i];
     if (!isfinite(xi) || !isfinite(yi) || !isfinite(zi)) atomicMax(a.err + ERR_NONFINITE, 1);
+    a.posf[i] = make_float4((float)xi, (float)yi, (float)zi, 0.0f);      // the LJ kernel's pair tests
     int ti = a.G.type[i];
     int cnt = 0;
     R nC = 0, nH = 0;
@@ -194,11 +195,10 @@ constexpr int LJ_THREADS = 256;
 constexpr int LJ_WARPS = LJ_THREADS / 32;
 
 // two compaction buffers per warp: 0 = inner pairs, 1 = pairs in the cut-off switch
-template <class R> struct LjBuf {
-    double dx[2][64], dy[2][64], dz[2][64];
-    R r2[2][64];
+struct LjBuf {
     int jp[2][64];          // j | species pair << 30
     int ia[2][64];          // the list's atom i
+    int im[2][64];          // packed image of j
 };
 
 // Per-lane force (and energy) accumulator of the atom whose pairs the lane
@@ -216,37 +216,70 @@ struct LaneAcc {
     }
 };
 
+// FP64 displacement x_j + S L - x_i of a listed pair (minimum-image
+// arithmetic stays double); shift holds S L for |S| <= 4 of a single box
 template <class R>
-__device__ __forceinline__ void lj_batch(const DevParams<R>& P, LjBuf<R>& B, int b, int lane, Sink& sink,
-                                         LaneAcc& acc, double* eatom, double& E) {
+__device__ __forceinline__ void lj_disp(const StepArgs<R>& a, const double (*shift)[9], int i, int j, int img,
+                                        double& dx, double& dy, double& dz) {
+    int n = a.n;
+    dx = a.pos[j] - a.pos[i]; dy = a.pos[n + j] - a.pos[n + i]; dz = a.pos[2 * n + j] - a.pos[2 * n + i];
+    if (img != 0) {
+        int sx = img_x(img), sy = img_y(img), sz = img_z(img);
+        if (a.sys || sx < -4 || sx > 4 || sy < -4 || sy > 4 || sz < -4 || sz > 4) {
+            const double* L = box_of(a, i);
+            dx += sx * L[0]; dy += sy * L[1]; dz += sz * L[2];
+        } else {
+            dx += shift[0][sx + 4]; dy += shift[1][sy + 4]; dz += shift[2][sz + 4];
+        }
+    }
+}
+
+template <class R>
+__device__ __forceinline__ void lj_batch(const StepArgs<R>& a, const DevParams<R>& P, const double (*shift)[9],
+                                         LjBuf& B, int b, int lane, Sink& sink, LaneAcc& acc, double& E) {
     int jp = B.jp[b][lane];
     int j = jp & 0x3fffffff, p = (unsigned)jp >> 30;
     int i = B.ia[b][lane];
     if (i != acc.own) {
-        acc.flush(sink.f, sink.n, eatom);
+        acc.flush(sink.f, sink.n, a.eatom);
         acc.own = i;
     }
+    double dx, dy, dz;
+    lj_disp<R>(a, shift, i, j, B.im[b][lane], dx, dy, dz);
+    R rx = (R)dx, ry = (R)dy, rz = (R)dz;
+    R r2 = rx * rx + ry * ry + rz * rz;
     double E0 = E;
     if (b == 0)
-        lj_eval_inner<R>(P, p, j, B.dx[b][lane], B.dy[b][lane], B.dz[b][lane], B.r2[b][lane], sink,
-                         acc.fx, acc.fy, acc.fz, E);
+        lj_eval_inner<R>(P, p, j, dx, dy, dz, r2, sink, acc.fx, acc.fy, acc.fz, E);
     else
-        lj_eval_switch<R>(P, p, j, B.dx[b][lane], B.dy[b][lane], B.dz[b][lane], B.r2[b][lane], sink,
-                          acc.fx, acc.fy, acc.fz, E);
-    if (eatom) acc.e += E - E0;
+        lj_eval_switch<R>(P, p, j, dx, dy, dz, r2, sink, acc.fx, acc.fy, acc.fz, E);
+    if (a.eatom) acc.e += E - E0;
 }
 
+// Pair tests on FP32 positions.  An FP32 squared distance r2f differs from
+// the FP64 one by at most band (below); a test whose threshold lies within
+// band of r2f is redone on the FP64 displacement, so every pair is classified
+// exactly as the FP64 displacement classifies it.  Per component,
+// |dx_f - dx| <= 2^-22 (2 max|x_i| + 4 |S|max L + 48): the roundings of x_i,
+// x_j and S L to FP32 and of the two FP32 additions, with |x_j| <= |x_i| +
+// |dx| + |S L| and |dx| < 16 A for any listed pair, and a factor 2 to spare.
 template <class R>
 __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
     const DevParams<R>& P = *a.P;
     __shared__ double shift[3][9];                // image shifts S L for S in [-4, 4]
-    __shared__ LjBuf<R> bufs[LJ_WARPS];
+    __shared__ LjCuts<float> cutsf[3];            // thresholds in FP32, by species pair
+    __shared__ LjBuf bufs[LJ_WARPS];
     if (threadIdx.x < 27) shift[threadIdx.x / 9][threadIdx.x % 9] = (double)((int)(threadIdx.x % 9) - 4) * a.L[threadIdx.x / 9];
+    if (threadIdx.x < 3) {
+        int q = threadIdx.x;
+        cutsf[q] = LjCuts<float>{(float)P.rc2[q], (float)P.rpath2, (float)P.Srhi2[q], (float)P.swlo2[q]};
+    }
     __syncthreads();
     int lane = threadIdx.x & 31;
-    LjBuf<R>& B = bufs[threadIdx.x >> 5];
+    LjBuf& B = bufs[threadIdx.x >> 5];
     unsigned lt = (1u << lane) - 1u;
     Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}, a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
+    bool general = a.pgrad != nullptr;
     LaneAcc acc;
     double E = 0;
     unsigned evaluated = 0;
@@ -266,41 +299,55 @@ __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
             chunk_end = min(c + a.lj_chunk, n);
             i = c;
         }
-        double xi = a.pos[i], yi = a.pos[n + i], zi = a.pos[2 * n + i];
+        float4 pfi = a.posf[i];
         int ti = a.G.type[i];
         int ne = a.lj_cnt[i];
         const int2* row = a.lj + (size_t)i * a.lj_cap;
         const double* L = box_of(a, i);
+        float Lf[3] = {(float)L[0], (float)L[1], (float)L[2]};
+        float err0 = 2.0f * fmaxf(fabsf(pfi.x), fmaxf(fabsf(pfi.y), fabsf(pfi.z))) + 48.0f;
+        float Lmax = fmaxf(Lf[0], fmaxf(Lf[1], Lf[2]));
         for (int base = 0; base < ne; base += 32) {
             int e = base + lane;
-            int st = 0, j = 0, p = 0;
-            double dx = 0, dy = 0, dz = 0;
-            R r2 = R(0);
+            int st = 0, j = 0, p = 0, img = 0;
             if (e < ne) {
                 int2 ent = row[e];
                 j = ent.x;
-                int img = ent.y;
-                // displacement in FP64 (minimum-image arithmetic stays double)
-                dx = a.pos[j] - xi; dy = a.pos[n + j] - yi; dz = a.pos[2 * n + j] - zi;
+                img = ent.y;
+                float4 pj = a.posf[j];
+                float fx = pj.x - pfi.x, fy = pj.y - pfi.y, fz = pj.z - pfi.z;
+                float smax = 0.0f;
                 if (img != 0) {
                     int sx = img_x(img), sy = img_y(img), sz = img_z(img);
-                    if (a.sys || sx < -4 || sx > 4 || sy < -4 || sy > 4 || sz < -4 || sz > 4) {
-                        dx += sx * L[0]; dy += sy * L[1]; dz += sz * L[2];
-                    } else {
-                        dx += shift[0][sx + 4]; dy += shift[1][sy + 4]; dz += shift[2][sz + 4];
-                    }
+                    fx += (float)sx * Lf[0]; fy += (float)sy * Lf[1]; fz += (float)sz * Lf[2];
+                    smax = (float)max(abs(sx), max(abs(sy), abs(sz)));
                 }
-                R rx = (R)dx, ry = (R)dy, rz = (R)dz;
-                r2 = rx * rx + ry * ry + rz * rz;
+                float r2f = fx * fx + fy * fy + fz * fz;
                 p = pidx(ti, a.G.type[j]);
-                evaluated += lt_nonneg(r2, P.rc2[p]);
+                LjCuts<float> kf = cutsf[p];
+                float err = 2.3841858e-7f * (err0 + 4.0f * smax * Lmax);      // 2^-22 (...)
+                float band = err * (56.0f + 3.0f * err) + 1e-6f * r2f;
+                bool near = fabsf(r2f - kf.rc2) <= band || fabsf(r2f - kf.srhi2) <= band ||
+                            fabsf(r2f - kf.swlo2) <= band || fabsf(r2f - kf.rpath2) <= band;
                 R C;
                 int code, mi;
-                st = lj_classify<R>(P, a.M, i, p, j, img, r2, C, code, mi, a.pgrad != nullptr);
+                if (near) {                 // rare: decide on the FP64 displacement
+                    double dx, dy, dz;
+                    lj_disp<R>(a, shift, i, j, img, dx, dy, dz);
+                    R rx = (R)dx, ry = (R)dy, rz = (R)dz;
+                    R r2 = rx * rx + ry * ry + rz * rz;
+                    evaluated += lt_nonneg(r2, P.rc2[p]);
+                    st = lj_classify<R>(P, a.M, i, p, j, img, r2, C, code, mi, general);
+                } else {
+                    evaluated += r2f < kf.rc2;
+                    st = lj_classify_c<R, float>(P, a.M, i, j, img, r2f, kf, C, code, mi, general);
+                }
                 if (st == 2) {
                     int q = atomicAdd(a.nbq + p, 1);
                     if (q < a.bq_cap) a.bq[(size_t)p * a.bq_cap + q] = make_int4(i, e, mi, 0);
                 } else if (st == 4) {     // rare: 0 < C < 1 along a path
+                    double dx, dy, dz;
+                    lj_disp<R>(a, shift, i, j, img, dx, dy, dz);
                     double gx = 0, gy = 0, gz = 0, E0 = E;
                     lj_eval<R>(P, a.G, i, p, j, dx, dy, dz, C, code, sink, gx, gy, gz, E);
                     atomicAdd(a.f + i, gx); atomicAdd(a.f + n + i, gy); atomicAdd(a.f + 2 * n + i, gz);
@@ -313,18 +360,16 @@ __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
                 unsigned m = __ballot_sync(0xffffffffu, st == want);
                 if (st == want) {
                     int s = cnt[b] + __popc(m & lt);
-                    B.dx[b][s] = dx; B.dy[b][s] = dy; B.dz[b][s] = dz; B.r2[b][s] = r2;
-                    B.jp[b][s] = j | (p << 30); B.ia[b][s] = i;
+                    B.jp[b][s] = j | (p << 30); B.ia[b][s] = i; B.im[b][s] = img;
                 }
                 cnt[b] += __popc(m);
                 __syncwarp();
                 if (cnt[b] >= 32) {
-                    lj_batch<R>(P, B, b, lane, sink, acc, a.eatom, E);
+                    lj_batch<R>(a, P, shift, B, b, lane, sink, acc, E);
                     __syncwarp();
                     if (lane < cnt[b] - 32) {
                         int s = 32 + lane;
-                        B.dx[b][lane] = B.dx[b][s]; B.dy[b][lane] = B.dy[b][s]; B.dz[b][lane] = B.dz[b][s];
-                        B.r2[b][lane] = B.r2[b][s]; B.jp[b][lane] = B.jp[b][s]; B.ia[b][lane] = B.ia[b][s];
+                        B.jp[b][lane] = B.jp[b][s]; B.ia[b][lane] = B.ia[b][s]; B.im[b][lane] = B.im[b][s];
                     }
                     cnt[b] -= 32;
                     __syncwarp();
@@ -335,7 +380,7 @@ __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
     // the warp's last, partly filled batches
 #pragma unroll
     for (int b = 0; b < 2; b++)
-        if (lane < cnt[b]) lj_batch<R>(P, B, b, lane, sink, acc, a.eatom, E);
+        if (lane < cnt[b]) lj_batch<R>(a, P, shift, B, b, lane, sink, acc, E);
     acc.flush(a.f, n, a.eatom);
     unsigned ev = __reduce_add_sync(0xffffffffu, evaluated);
     if (lane == 0 && ev) atomicAdd(a.counters + CNT_LJ, (unsigned long long)ev);

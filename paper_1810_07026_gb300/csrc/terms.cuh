@@ -1051,26 +1051,39 @@ HD void lj_eval_switch(const DevParams<R>& P, int p, int j, double dx, double dy
 //   3: C = 1, no path, inside the cut-off switch, or any such Morse pair (lj_eval_switch);
 //   4: 0 < C < 1 along a path (lj_eval).
 // C, the path code and the map entry are returned.
-template <class R>
-HD int lj_classify(const DevParams<R>& P, const PathMap<R>& M, int i, int p, int j, int img, R r2,
-                   R& C, int& code, int& mi, bool general = false) {
+// The squared-distance thresholds of the pair tests for one species pair, in
+// the type T of the squared distance that is tested against them.
+template <class T> struct LjCuts {
+    T rc2, rpath2, srhi2, swlo2;
+};
+
+template <class R, class T>
+HD int lj_classify_c(const DevParams<R>& P, const PathMap<R>& M, int i, int j, int img, T r2, const LjCuts<T>& k,
+                     R& C, int& code, int& mi, bool general) {
     mi = -1; code = -1; C = R(1);
-    if (!lt_nonneg(r2, P.rc2[p])) return 0;
-    if (lt_nonneg(r2, P.rpath2)) {
+    if (!lt_nonneg(r2, k.rc2)) return 0;
+    if (lt_nonneg(r2, k.rpath2)) {
         long long key = map_key(j, img);
         int c = M.cnt[i];
-        const long long* k = M.key + (size_t)i * M.cap;
+        const long long* kk = M.key + (size_t)i * M.cap;
         for (int e = 0; e < c; e++)
-            if (k[e] == key) { mi = e; break; }
+            if (kk[e] == key) { mi = e; break; }
         if (mi >= 0) {
             C = M.wt[(size_t)i * M.cap + mi];
             if (!(C > R(0))) return 0;
             code = M.path[(size_t)i * M.cap + mi];
         }
     }
-    if (lt_nonneg(r2, P.Srhi2[p])) return 2;
+    if (lt_nonneg(r2, k.srhi2)) return 2;
     if (mi >= 0 || general) return 4;
-    return (P.kind != 0 || lt_nonneg(P.swlo2[p], r2)) ? 3 : 1;
+    return (P.kind != 0 || lt_nonneg(k.swlo2, r2)) ? 3 : 1;
+}
+
+template <class R>
+HD int lj_classify(const DevParams<R>& P, const PathMap<R>& M, int i, int p, int j, int img, R r2,
+                   R& C, int& code, int& mi, bool general = false) {
+    LjCuts<R> k{P.rc2[p], P.rpath2, P.Srhi2[p], P.swlo2[p]};
+    return lj_classify_c<R, R>(P, M, i, j, img, r2, k, C, code, mi, general);
 }
 
 // b* pair: (S_r S_b + 1 - S_r) C V for the pair i -> (j, image) with
