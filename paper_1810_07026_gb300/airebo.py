@@ -66,6 +66,7 @@ def lib():
             "airebo_set_timing": (I, [P, I]),
             "airebo_kernel_times": (I, [P, P, P]),
             "airebo_alu_peak": (I, [I, P]),
+            "airebo_math_check": (I, [P]),
             "airebo_param_grad": (I, [P, P, P, P, P]),
             "airebo_knot_grad": (I, [P, P, P, P, P, I64]),
             "airebo_set_lj_params": (I, [P, P, P]),
@@ -101,6 +102,15 @@ def alu_peak(precision: int = FP64) -> float:
     if st:
         raise AireboError(st, "alu peak probe failed")
     return out.value
+
+
+def math_check():
+    """(ulp difference of the kernels' 1/x from CUDA's correctly rounded one, same for 1/sqrt(x))."""
+    out = np.zeros(2, dtype=np.int64)
+    st = lib().airebo_math_check(_np(out))
+    if st:
+        raise AireboError(st, "math check failed")
+    return int(out[0]), int(out[1])
 
 
 class Airebo:

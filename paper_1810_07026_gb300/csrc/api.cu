@@ -1331,4 +1331,13 @@ airebo_status airebo_alu_peak(int precision, double* tflops) {
     return t > 0 ? AIREBO_OK : AIREBO_ERR_CUDA;
 }
 
+airebo_status airebo_math_check(int64_t* h_ulp2) {
+    if (!h_ulp2) return AIREBO_ERR_ARG;
+    long long o[2] = {0, 0};
+    if (math_check(o)) return AIREBO_ERR_CUDA;
+    h_ulp2[0] = o[0];
+    h_ulp2[1] = o[1];
+    return AIREBO_OK;
+}
+
 }  // extern "C"

@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
         int p = pidx(ti, tj);
         double dmax = (double)P.Dmax[p];
         if (!(r2 < dmax * dmax)) continue;
-        double ir = rsqrt(r2);
+        double ir = rsqrt_(r2);
         double r = r2 * ir;
         R dw, omw;
         R w = wfun_c<R>(P, p, (R)r, dw, omw);

@@ -47,4 +47,39 @@ double alu_peak(int fp64) {
     return cudaGetLastError() == cudaSuccess ? best : -1.0;
 }
 
+// Accuracy of the FP64 reciprocal and reciprocal square root of the kernels
+// (rcp_, rsqrt_) against CUDA's correctly rounded division and square root,
+// over x = 2^t, t uniform in [-30, 30) (a counter-based hash picks t).
+// out[0], out[1]: largest difference in units in the last place for 1/x and
+// 1/sqrt(x) (the latter's reference, 1 / sqrt(x) with two correct roundings,
+// is itself within 1 ulp).
+__global__ void k_math_check(unsigned long long* out, int n) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    unsigned long long h = (unsigned long long)k * 0x9E3779B97F4A7C15ull;
+    h ^= h >> 31; h *= 0xBF58476D1CE4E5B9ull; h ^= h >> 29;
+    double t = -30.0 + 60.0 * (double)(h >> 11) * (1.0 / 9007199254740992.0);
+    double x = exp2(t);
+    double r1 = rcp_(x), q1 = __ddiv_rn(1.0, x);
+    double r2 = rsqrt_(x), q2 = __ddiv_rn(1.0, __dsqrt_rn(x));
+    long long d1 = __double_as_longlong(r1) - __double_as_longlong(q1);
+    long long d2 = __double_as_longlong(r2) - __double_as_longlong(q2);
+    atomicMax(out + 0, (unsigned long long)(d1 < 0 ? -d1 : d1));
+    atomicMax(out + 1, (unsigned long long)(d2 < 0 ? -d2 : d2));
+}
+
+int math_check(long long* out2) {
+    unsigned long long* d = nullptr;
+    if (cudaMalloc(&d, 16) != cudaSuccess) return 1;
+    cudaMemset(d, 0, 16);
+    int n = 1 << 22;
+    k_math_check<<<(n + 255) / 256, 256>>>(d, n);
+    unsigned long long h[2] = {0, 0};
+    cudaError_t e = cudaMemcpy(h, d, 16, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    out2[0] = (long long)h[0];
+    out2[1] = (long long)h[1];
+    return (e == cudaSuccess && cudaGetLastError() == cudaSuccess) ? 0 : 1;
+}
+
 }  // namespace airebo

@@ -59,9 +59,19 @@ HD double neg_(double x) {
     return -x;
 #endif
 }
+// 1/sqrt(x) and 1/x in FP64 for positive, finite, normal x (every use here:
+// squared lengths and 1 + sum + P >= 0.95).  The hardware's approximate FP64
+// reciprocal (square root) is refined by one third-order Newton-Raphson step
+// (Householder's method): with y0 = (1 + d)/sqrt(x), e = 1 - x y0^2 and
+// y1 = y0 (1 + e/2 + 3e^2/8), the relative error becomes O(d^3); for 1/x,
+// e = 1 - x y0 and y1 = y0 (1 + e + e^2).  Checked against correctly rounded
+// results on the device (tests/test_gpu_math.py).
 HD double rsqrt_(double x) {
 #ifdef __CUDA_ARCH__
-    return rsqrt(x);
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    double e = fma(-(x * y), y, 1.0);
+    return fma(y * e, fma(0.375, e, 0.5), y);
 #else
     return 1.0 / std::sqrt(x);
 #endif
@@ -75,12 +85,23 @@ HD float rsqrt_(float x) {
 }
 HD double rcp_(double x) {
 #ifdef __CUDA_ARCH__
-    return __drcp_rn(x);
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    double e = fma(-x, y, 1.0);
+    return fma(y, fma(e, e, e), y);
 #else
     return 1.0 / x;
 #endif
 }
-HD float rcp_(float x) { return 1.0f / x; }
+HD float rcp_(float x) {
+#ifdef __CUDA_ARCH__
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+#else
+    return 1.0f / x;
+#endif
+}
 HD double sqrt_(double x) { return sqrt(x); }
 HD float sqrt_(float x) { return sqrtf(x); }
 HD double exp_(double x) { return exp(x); }
@@ -176,7 +197,7 @@ template <class R> HD R wfun_c(const DevParams<R>& P, int p, R r, R& dw, R& omw)
     R s, c;
     sincospi_(t, &s, &c);
     dw = R(-0.5 * M_PI) * s * P.Dinv[p];
-    omw = c > R(0) ? R(0.5) * s * s / (R(1) + c) : R(0.5) * (R(1) - c);
+    omw = c > R(0) ? R(0.5) * s * s * rcp_(R(1) + c) : R(0.5) * (R(1) - c);
     return R(0.5) * (R(1) + c);
 }
 
@@ -560,7 +581,7 @@ HD R dihedral_sum(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, 
         // n1 = u x a
         R n1x = uy * az - uz * ay, n1y = uz * ax - ux * az, n1z = ux * ay - uy * ax;
         R n1s = n1x * n1x + n1y * n1y + n1z * n1z;
-        R in1s = R(1) / n1s;
+        R in1s = rcp_(n1s);
         for (int b = 0; b < nj; b++) {
             int qb = j * G.stride + b;
             int l = G.nj[qb];
@@ -579,7 +600,7 @@ HD R dihedral_sum(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, 
             D += one_m * wik * wjl * si * sj;
             if (!reverse) continue;
             R dwik = G.dw[qa], dwjl = G.dw[qb];     // the forward pass reads no dw/dr
-            R in2s = R(1) / n2s;
+            R in2s = rcp_(n2s);
             R dcw = dEdD * R(-2) * cw * wik * wjl * si * sj;
             R dwi = dEdD * one_m * wjl * si * sj;
             R dwj = dEdD * one_m * wik * si * sj;
@@ -754,7 +775,7 @@ HD double torsion_bond(const DevParams<R>& P, const Graph<R>& G, int i, int slot
         if (si == R(0)) continue;
         R n1x = uy * az - uz * ay, n1y = uz * ax - ux * az, n1z = ux * ay - uy * ax;
         R n1s = n1x * n1x + n1y * n1y + n1z * n1z;
-        R in1s = R(1) / n1s;
+        R in1s = rcp_(n1s);
         for (int b = 0; b < nj; b++) {
             int qb = j * G.stride + b;
             int l = G.nj[qb];
@@ -1134,7 +1155,7 @@ HD R bstar_value(const DevParams<R>& P, const Graph<R>& G, int i, int j, R dx, R
     R ux = dx * inv_r * rs, uy = dy * inv_r * rs, uz = dz * inv_r * rs;
     R gux = 0, guy = 0, guz = 0, gumag = 0;
     double fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
-    return bond_order<R, false>(P, G, i, j, ux, uy, uz, rs, R(1) / rs, R(0), sink, gux, guy, guz, gumag,
+    return bond_order<R, false>(P, G, i, j, ux, uy, uz, rs, rcp_(rs), R(0), sink, gux, guy, guz, gumag,
                                 fix, fiy, fiz, fjx, fjy, fjz);
 }
 
@@ -1164,7 +1185,7 @@ HD double bstar_full(const DevParams<R>& P, const Graph<R>& G, int i, int j, R d
     R gux = 0, guy = 0, guz = 0, gumag = 0;
     double fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
     BstarSwitch<R> bsw{P.bmin[p], P.binv[p], Sr * C * V, R(0), R(0)};
-    bond_order<R, true>(P, G, i, j, ux, uy, uz, rs, R(1) / rs, R(0), sink, gux, guy, guz, gumag,
+    bond_order<R, true>(P, G, i, j, ux, uy, uz, rs, rcp_(rs), R(0), sink, gux, guy, guz, gumag,
                         fix, fiy, fiz, fjx, fjy, fjz, &bsw);
     dsb = bsw.dSb != R(0);
     if (dsb) {

@@ -1,0 +1,17 @@
+"""The FP64 reciprocal and reciprocal square root of the kernels (the
+hardware approximation refined by one third-order Newton-Raphson step)
+against CUDA's correctly rounded results on the device."""
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def test_rcp_rsqrt_within_two_ulp():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1810_07026_gb300 import build, airebo
+    build.build()
+    ulp_rcp, ulp_rsqrt = airebo.math_check()
+    assert ulp_rcp <= 1, ulp_rcp          # faithful: at most one rounding step from 1/x
+    assert ulp_rsqrt <= 2, ulp_rsqrt      # the reference 1/sqrt(x) is itself within 1 ulp
