@@ -165,6 +165,29 @@ __global__ void __launch_bounds__(128) k_build(NeighborArgs a, const int* cell_s
     if (nim > a.im_cap) atomicMax(a.err + 1, nim);
 }
 
+// Carbon neighbours first in each intermediate REBO row, so that the exact
+// REBO slots of every atom come out carbon-first too: the threads of a bond
+// kernel then meet the species of the neighbours k in the same slot order
+// and run the same branches.  (Two-pointer partition; rows are short.)
+__global__ void k_order_im(NeighborArgs a) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    int c = min(a.im_cnt[i], a.im_cap);
+    int2* row = a.im + (size_t)i * a.im_cap;
+    int lo = 0, hi = c - 1;
+    while (lo < hi) {
+        while (lo < hi && a.type[row[lo].x] == 0) lo++;
+        while (lo < hi && a.type[row[hi].x] != 0) hi--;
+        if (lo < hi) {
+            int2 t = row[lo];
+            row[lo] = row[hi];
+            row[hi] = t;
+            lo++;
+            hi--;
+        }
+    }
+}
+
 void launch_neighbor(NeighborArgs& a, cudaStream_t s, int ncell) {
     if (a.n == 0) return;
     cudaMemsetAsync(a.cell_count, 0, sizeof(int) * ncell, s);
@@ -173,6 +196,7 @@ void launch_neighbor(NeighborArgs& a, cudaStream_t s, int ncell) {
     k_scan<<<1, 1024, 0, s>>>(a.cell_count, a.cell_start, a.cell_fill, ncell);
     k_scatter<<<nb, 128, 0, s>>>(a);
     k_build<<<nb, 128, 0, s>>>(a, a.cell_start);
+    k_order_im<<<nb, 128, 0, s>>>(a);
 }
 
 // per-system energy: sum of the per-atom energies of each system's atoms

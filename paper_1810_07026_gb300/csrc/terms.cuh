@@ -355,6 +355,17 @@ template <class R> struct Graph {
     const R* nC; const R* nH;                // sum of w over C / H neighbours
 };
 
+// Slot of atom o among the REBO neighbours of c (MAXN when absent).  The
+// loops over N(c) \ {o} below run over the other slots by index, so that
+// threads whose atoms have equal neighbour counts run equal trip counts
+// instead of each skipping o at a different iteration.
+template <class R> HD int slot_of(const Graph<R>& G, int c, int o) {
+    int nc = G.cnt[c];
+    for (int a = 0; a < nc; a++)
+        if (G.nj[c * G.stride + a] == o) return a;
+    return MAXN;
+}
+
 // accumulation of forces (atomics) and the virial of one thread
 struct Sink {
     double* f;          // 3 x n, SoA
@@ -439,11 +450,13 @@ HD void side_forward(const DevParams<R>& P, const Graph<R>& G, int c, int o, R u
                      Side<R>& s) {
     int tc = G.type[c], to = G.type[o];
     int nc = G.cnt[c];
+    int so = slot_of<R>(G, c, o);
+    int m = nc - (so < MAXN);
     s.NC = 0; s.NH = 0; s.conj = 0;
-    for (int a = 0; a < nc; a++) {
+    for (int t = 0; t < m; t++) {
+        int a = t + (t >= so);
         int q = c * G.stride + a;
         int k = G.nj[q];
-        if (k == o) continue;
         R w = G.w[q];
         if (G.type[k] == 0) {
             s.NC += w;
@@ -456,10 +469,10 @@ HD void side_forward(const DevParams<R>& P, const Graph<R>& G, int c, int o, R u
     }
     s.N = s.NC + s.NH;
     s.sum = 0; s.dsum_dN = 0;
-    for (int a = 0; a < nc; a++) {
+    for (int t = 0; t < m; t++) {
+        int a = t + (t >= so);
         int q = c * G.stride + a;
         int k = G.nj[q];
-        if (k == o) continue;
         R cs = (ux * G.dx[q] + uy * G.dy[q] + uz * G.dz[q]) * inv_u * G.ir[q];
         cs = cs < R(-1) ? R(-1) : (cs > R(1) ? R(1) : cs);
         R dgc, dgN;
@@ -494,10 +507,12 @@ HD void side_reverse(const DevParams<R>& P, const Graph<R>& G, int c, int o, R u
         int tab = (tc == 0 && to == 0) ? 0 : (tc == 0 ? 1 : 2);
         kg_bicubic<R>(P.kg + KG_P + tab * 256, s.NC, s.NH, (double)ac);
     }
-    for (int a = 0; a < nc; a++) {
+    int so = slot_of<R>(G, c, o);
+    int m = nc - (so < MAXN);
+    for (int t = 0; t < m; t++) {
+        int a = t + (t >= so);
         int q = c * G.stride + a;
         int k = G.nj[q];
-        if (k == o) continue;
         int tk = G.type[k];
         R dxk = G.dx[q], dyk = G.dy[q], dzk = G.dz[q];
         R rck = G.r[q], inv_r = G.ir[q], w = G.w[q], dw = G.dw[q];
@@ -568,10 +583,12 @@ HD R dihedral_sum(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, 
                   double& fix, double& fiy, double& fiz, double& fjx, double& fjy, double& fjz) {
     R D = 0;
     int ni = G.cnt[i], nj = G.cnt[j];
-    for (int a = 0; a < ni; a++) {
+    int sj = slot_of<R>(G, i, j), si_ = slot_of<R>(G, j, i);
+    int mi = ni - (sj < MAXN), mj = nj - (si_ < MAXN);
+    for (int ta = 0; ta < mi; ta++) {
+        int a = ta + (ta >= sj);
         int qa = i * G.stride + a;
         int k = G.nj[qa];
-        if (k == j) continue;
         R ax = G.dx[qa], ay = G.dy[qa], az = G.dz[qa];
         R inv_ra = G.ir[qa], wik = G.w[qa];
         R csi = (ux * ax + uy * ay + uz * az) * inv_u * inv_ra;
@@ -582,10 +599,11 @@ HD R dihedral_sum(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, 
         R n1x = uy * az - uz * ay, n1y = uz * ax - ux * az, n1z = ux * ay - uy * ax;
         R n1s = n1x * n1x + n1y * n1y + n1z * n1z;
         R in1s = rcp_(n1s);
-        for (int b = 0; b < nj; b++) {
+        for (int tb = 0; tb < mj; tb++) {
+            int b = tb + (tb >= si_);
             int qb = j * G.stride + b;
             int l = G.nj[qb];
-            if (l == i || l == k) continue;
+            if (l == k) continue;              // a three-ring
             R bx = G.dx[qb], by = G.dy[qb], bz = G.dz[qb];
             R inv_rb = G.ir[qb], wjl = G.w[qb];
             R csj = -(ux * bx + uy * by + uz * bz) * inv_u * inv_rb;
@@ -762,10 +780,12 @@ HD double torsion_bond(const DevParams<R>& P, const Graph<R>& G, int i, int slot
     R gux = 0, guy = 0, guz = 0;
     double fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
     int ni = G.cnt[i], nj = G.cnt[j];
-    for (int a = 0; a < ni; a++) {
+    int sj = slot_of<R>(G, i, j), si_ = slot_of<R>(G, j, i);
+    int mi = ni - (sj < MAXN), mj = nj - (si_ < MAXN);
+    for (int ta = 0; ta < mi; ta++) {
+        int a = ta + (ta >= sj);
         int qa = i * G.stride + a;
         int k = G.nj[qa];
-        if (k == j) continue;
         R ax = G.dx[qa], ay = G.dy[qa], az = G.dz[qa];
         R wik = G.w[qa], dwik = G.dw[qa];
         R inv_ra = G.ir[qa];
@@ -776,10 +796,11 @@ HD double torsion_bond(const DevParams<R>& P, const Graph<R>& G, int i, int slot
         R n1x = uy * az - uz * ay, n1y = uz * ax - ux * az, n1z = ux * ay - uy * ax;
         R n1s = n1x * n1x + n1y * n1y + n1z * n1z;
         R in1s = rcp_(n1s);
-        for (int b = 0; b < nj; b++) {
+        for (int tb = 0; tb < mj; tb++) {
+            int b = tb + (tb >= si_);
             int qb = j * G.stride + b;
             int l = G.nj[qb];
-            if (l == i || l == k) continue;
+            if (l == k) continue;              // a three-ring
             R bx = G.dx[qb], by = G.dy[qb], bz = G.dz[qb];
             R wjl = G.w[qb], dwjl = G.dw[qb];
             R inv_rb = G.ir[qb];
