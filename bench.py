@@ -270,7 +270,7 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     results = {}
     forces = {}
-    runs = ((A.FP64, "fp64", True), (A.MIXED, "mixed", True), (A.FP64, "rebo_only", False))
+    runs = ((A.FP64, "fp64", True), (A.MIXED, "mixed", True), (A.DF64, "df64", True), (A.FP64, "rebo_only", False))
     for prec, name, full in runs:
         with torch.cuda.stream(stream):
             ev = A.Airebo(params, precision=prec, stream=stream, lj=full, torsion=full)
@@ -384,6 +384,13 @@ def run_ours(args):
                       "kernel_ms": {k: v[0] / max(1, v[1]) for k, v in mix_kt.items()},
                       "lj_achieved_fp32_frac": None if not mlj_n else
                       (flops_lj / (mlj_ms * 1e-3 / mlj_n) / 1e12) / peak32_nom},
+            "df64": {"value": replica_throughput(n, args.steps, ws, results["df64"]["ms"]), "unit": UNIT,
+                     "ms_per_step": results["df64"]["ms"] / args.steps,
+                     "dtype": "f64, LJ pair arithmetic in double-float (f32 pairs) with 64-bit fixed-point force sums",
+                     "max_abs_dF_vs_fp64": (forces["df64"] - forces["fp64"]).abs().max().item(),
+                     "max_rel_dF_vs_fp64": (forces["df64"] - forces["fp64"]).abs().max().item() / fscale,
+                     "drift_eV_per_atom_step": results["df64"]["drift"],
+                     "kernel_ms": {k: v[0] / max(1, v[1]) for k, v in results["df64"]["kt"].items()}},
             "batched": batched,
             "rebo_only": {"value": replica_throughput(n, args.steps, ws, results["rebo_only"]["ms"]),
                           "unit": UNIT, "ms_per_step": results["rebo_only"]["ms"] / args.steps,

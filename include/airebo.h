@@ -52,12 +52,23 @@ typedef enum {
     AIREBO_ERR_STATE = 6       /* call out of order, e.g. compute before neighbor */
 } airebo_status;
 
-enum { AIREBO_FP64 = 0, AIREBO_MIXED = 1 };
+/*
+ * Precisions.  AIREBO_FP64: every term in FP64.  AIREBO_MIXED: FP32 geometry,
+ * splines and bond order; FP64 positions, displacements, accumulation and
+ * integrator.  AIREBO_DF64: as AIREBO_FP64, except that the pair arithmetic
+ * of the Lennard-Jones pairs with C_ij = 1 and no b* runs in double-float
+ * (pairs of FP32 numbers, about 48 significant bits) on the FP32 pipe, from
+ * positions split on a 2^-12 A grid, with the pair forces summed in 64-bit
+ * fixed point (2^-40 eV/A) -- FP64-class results at FP32-pipe rates.  It
+ * needs every |coordinate| below 2000 A and pair forces below 4e6 eV/A
+ * (AIREBO_ERR_ARG / AIREBO_ERR_NONFINITE otherwise); the Morse form runs as
+ * AIREBO_FP64.
+ */
+enum { AIREBO_FP64 = 0, AIREBO_MIXED = 1, AIREBO_DF64 = 2 };
 
 typedef struct {
     double skin;          /* neighbour-list skin, Angstrom (default 1.0) */
-    int precision;        /* AIREBO_FP64, or AIREBO_MIXED: FP32 geometry, splines and bond
-                             order; FP64 positions, displacements, accumulation and integrator */
+    int precision;        /* AIREBO_FP64, AIREBO_MIXED or AIREBO_DF64 (see above) */
     int enable_rebo;      /* 1: REBO term (Alg. 1) */
     int enable_lj;        /* 1: LJ term (Alg. 3) */
     int enable_torsion;   /* 1: torsion term (Alg. 2) */

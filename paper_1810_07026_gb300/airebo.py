@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_PKG, "libairebo.so")
 
 OK, ERR_ARG, ERR_CUDA, ERR_CAPACITY, ERR_TIMEOUT, ERR_NONFINITE, ERR_STATE = range(7)
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_CAPACITY", 4: "ERR_TIMEOUT", 5: "ERR_NONFINITE", 6: "ERR_STATE"}
-FP64, MIXED = 0, 1
+FP64, MIXED, DF64 = 0, 1, 2
 # the spline knot data, in the order of the parameter file and of knot_grad()
 KNOT_BLOCKS = (("gC1.data", 18), ("gC2.data", 18), ("gH.data", 12), ("P.CC", 100), ("P.CH", 100), ("P.HC", 100),
                ("piRC.CC", 1800), ("piRC.CH", 1800), ("piRC.HH", 1800), ("Tij.CC", 1800))

@@ -347,6 +347,9 @@ struct airebo_ctx {
     int *cell_of = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cell_fill = nullptr;
     float4* spos = nullptr;
     float4* posf = nullptr;              // FP32 positions of the current step (LJ pair tests)
+    float4* pq_hi = nullptr;             // AIREBO_DF64: split positions and fixed-point LJ force sums
+    float4* pq_lo = nullptr;
+    unsigned long long* fix = nullptr;
     char4* swrap = nullptr;
     // lists
     int2* lj = nullptr; int* lj_cnt = nullptr; int lj_cap = 0; size_t lj_alloc = 0;
@@ -472,7 +475,12 @@ template <class R> void free_prec(Precision<R>& pr) {
 double max3(const double* v) { return std::max(v[0], std::max(v[1], v[2])); }
 
 bool screen_on(airebo_handle h) {
-    return h->opt.precision == AIREBO_FP64 && h->opt.bstar_screen != 0 && h->opt.enable_lj != 0;
+    return h->opt.precision != AIREBO_MIXED && h->opt.bstar_screen != 0 && h->opt.enable_lj != 0;
+}
+
+// the double-float LJ kernel (AIREBO_DF64, Lennard-Jones form only)
+bool df_on(airebo_handle h) {
+    return h->opt.precision == AIREBO_DF64 && h->opt.enable_lj != 0 && h->sc.kind == 0;
 }
 
 airebo_status alloc_atoms(airebo_handle h, int n) {
@@ -482,6 +490,11 @@ airebo_status alloc_atoms(airebo_handle h, int n) {
     CK(realloc_dev(h->cell_of, na));
     CK(realloc_dev(h->spos, na));
     CK(realloc_dev(h->posf, na));
+    if (h->opt.precision == AIREBO_DF64) {
+        CK(realloc_dev(h->pq_hi, na));
+        CK(realloc_dev(h->pq_lo, na));
+        CK(realloc_dev(h->fix, 3 * (size_t)na));
+    }
     CK(realloc_dev(h->swrap, na));
     CK(realloc_dev(h->lj_cnt, na));
     CK(realloc_dev(h->im_cnt, na));
@@ -629,6 +642,10 @@ template <class R> StepArgs<R> make_args(airebo_handle h, Precision<R>& pr, cons
     a.M.cap = b.map_cap; a.M.cnt = b.map_cnt; a.M.key = b.map_key; a.M.wt = b.map_wt; a.M.path = b.map_path;
     a.pos = d_pos;
     a.posf = h->posf;
+    bool df = sizeof(R) == 8 && df_on(h);
+    a.pq_hi = df ? h->pq_hi : nullptr;
+    a.pq_lo = df ? h->pq_lo : nullptr;
+    a.fix = df ? h->fix : nullptr;
     for (int d = 0; d < 3; d++) a.L[d] = h->L[d];
     a.lj = h->lj; a.lj_cnt = h->lj_cnt; a.lj_cap = h->lj_cap;
     a.im = h->im; a.im_cnt = h->im_cnt; a.im_cap = h->im_cap;
@@ -681,6 +698,7 @@ airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos,
         CK(cudaMemsetAsync(h->counts, 0, sizeof(int) * 8, s));
         CK(cudaMemsetAsync(h->derr, 0, sizeof(int) * 8, s));
         StepArgs<R> a = make_args<R>(h, pr, d_pos, d_force, d_w6 != nullptr);
+        if (a.fix && h->n) CK(cudaMemsetAsync(a.fix, 0, sizeof(unsigned long long) * 3 * h->n, s));
         a.pgrad = d_pgrad;
         if (d_pgrad) CK(cudaMemsetAsync(d_pgrad, 0, sizeof(double) * 6, s));
         if (d_kg) {
@@ -716,6 +734,9 @@ airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos,
             }
         }
         if (h->h_err[ERR_NONFINITE]) return fail(h, AIREBO_ERR_NONFINITE, "non-finite position");
+        if (h->h_err[ERR_DF] == 1) return fail(h, AIREBO_ERR_ARG, "AIREBO_DF64 needs every |coordinate| below 2000 A");
+        if (h->h_err[ERR_DF] == 2)
+            return fail(h, AIREBO_ERR_NONFINITE, "an LJ pair force beyond the fixed-point range (4e6 eV/A)");
         bool again = false;
         if (h->h_err[ERR_SHORT] > h->stride) {
             if (h->h_err[ERR_SHORT] > MAXN)
@@ -811,7 +832,8 @@ airebo_status airebo_create(const char* params, const airebo_options* opts, void
     *out = nullptr;
     airebo_handle h = new airebo_ctx();
     if (opts) h->opt = *opts; else airebo_default_options(&h->opt);
-    if (!(h->opt.skin >= 0.0) || (h->opt.precision != AIREBO_FP64 && h->opt.precision != AIREBO_MIXED)) {
+    if (!(h->opt.skin >= 0.0) ||
+        (h->opt.precision != AIREBO_FP64 && h->opt.precision != AIREBO_MIXED && h->opt.precision != AIREBO_DF64)) {
         delete h;
         return AIREBO_ERR_ARG;
     }
@@ -854,7 +876,7 @@ void airebo_destroy(airebo_handle h) {
         void* bs[] = {h->d_sys, h->d_snc, h->d_sreach, h->d_scell0, h->d_Lsys, h->d_scw, h->d_off, h->eatom};
         for (void* p : bs) if (p) cudaFree(p);
     }
-    void* ps[] = {h->types, h->cell_of, h->cell_count, h->cell_start, h->cell_fill, h->spos, h->posf, h->swrap, h->lj, h->lj_cnt,
+    void* ps[] = {h->types, h->cell_of, h->cell_count, h->cell_start, h->cell_fill, h->spos, h->posf, h->pq_hi, h->pq_lo, h->fix, h->swrap, h->lj, h->lj_cnt,
                   h->im, h->im_cnt, h->xref, h->bonds, h->ccbonds, h->bq, h->bq2, h->counts, h->acc, h->counters, h->derr, h->maxd2, h->ke,
                   h->hpos, h->hvel, h->hforce, h->he4, h->hw6};
     for (void* p : ps) if (p) cudaFree(p);

@@ -35,6 +35,8 @@ template <class R> struct StepArgs {
     PathMap<R> M;
     const double* pos;
     float4* posf;                          // FP32 copy of the positions (written by the short-list kernel)
+    float4* pq_hi; float4* pq_lo;          // double-float LJ (AIREBO_DF64): split positions
+    unsigned long long* fix;               // double-float LJ: fixed-point force sums (3 x n), null otherwise
     double L[3];
     const int2* lj; const int* lj_cnt; int lj_cap;
     const int2* im; const int* im_cnt; int im_cap;
@@ -63,7 +65,7 @@ template <class R> struct StepArgs {
     double* pgrad;        // nullable: dE/d eps[3], dE/d sigma[3] of the inter-molecular term
 };
 
-enum { ERR_SHORT = 0, ERR_MAP = 1, ERR_QUEUE = 2, ERR_NONFINITE = 3 };
+enum { ERR_SHORT = 0, ERR_MAP = 1, ERR_QUEUE = 2, ERR_NONFINITE = 3, ERR_DF = 4 };
 enum { CNT_BONDS = 0, CNT_BSTAR = 1, CNT_DSB = 2, CNT_LJ = 3, CNT_MAP = 4, CNT_BSTAR_FULL = 7 };
 
 // Half-width of the band around [b_min, b_max] inside which an FP32 b* does

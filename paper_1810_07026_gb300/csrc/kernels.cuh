@@ -14,8 +14,17 @@
 #pragma once
 
 #include "internal.h"
+#include "ff.cuh"
 
 namespace airebo {
+
+// hi/lo split of a double on the 2^-12 grid
+__device__ __forceinline__ void df_split(double v, float& h, float& l) {
+    double q = rint(v * 4096.0) * (1.0 / 4096.0);
+    h = (float)q;
+    l = (float)(v - q);
+}
+
 
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -84,6 +93,14 @@ __global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
     double xi = a.pos[i], yi = a.pos[n + i], zi = a.pos[2 * n + i];
     if (!isfinite(xi) || !isfinite(yi) || !isfinite(zi)) atomicMax(a.err + ERR_NONFINITE, 1);
     a.posf[i] = make_float4((float)xi, (float)yi, (float)zi, 0.0f);      // the LJ kernel's pair tests
+    if (a.fix) {                      // double-float LJ: hi on the 2^-12 grid, lo the rest
+        if (!(fabs(xi) < 2000.0 && fabs(yi) < 2000.0 && fabs(zi) < 2000.0)) atomicMax(a.err + ERR_DF, 1);
+        float4 h, l;
+        df_split(xi, h.x, l.x); df_split(yi, h.y, l.y); df_split(zi, h.z, l.z);
+        h.w = l.w = 0.0f;
+        a.pq_hi[i] = h;
+        a.pq_lo[i] = l;
+    }
     int ti = a.G.type[i];
     int cnt = 0;
     R nC = 0, nH = 0;
@@ -256,6 +273,99 @@ __device__ __forceinline__ void lj_batch(const StepArgs<R>& a, const DevParams<R
     if (a.eatom) acc.e += E - E0;
 }
 
+// ---- double-float evaluation of the compacted pairs (precision AIREBO_DF64)
+// Positions arrive split as hi + lo, hi rounded to a multiple of 2^-12 A (and
+// |x| < 2000 A, so that hi has at most 23 significant bits): the difference
+// of two such hi values, plus the same split of the image shift, is exact in
+// FP32, so the displacement keeps FP64-class accuracy.  Pair forces go to
+// 64-bit fixed-point sums (ff_to_fixed), added to the FP64 forces afterwards.
+struct DfParams {
+    ff sig2[3], eps4[3], swlo[3], swinv[3];
+};
+
+struct DfLaneAcc {
+    int own = -1;
+    ff fx{0.0f, 0.0f}, fy{0.0f, 0.0f}, fz{0.0f, 0.0f}, e{0.0f, 0.0f};
+    __device__ __forceinline__ void flush(unsigned long long* fix, int n, double* eatom) {
+        if (own >= 0) {
+            atomicAdd(fix + own, (unsigned long long)ff_to_fixed(fx));
+            atomicAdd(fix + n + own, (unsigned long long)ff_to_fixed(fy));
+            atomicAdd(fix + 2 * n + own, (unsigned long long)ff_to_fixed(fz));
+            if (eatom) atomicAdd(eatom + own, ff_to_double(e));
+        }
+        fx = fy = fz = e = ff{0.0f, 0.0f};
+    }
+};
+
+template <class R>
+__device__ __forceinline__ void lj_batch_df(const StepArgs<R>& a, const DfParams& D, const float (*sh)[9],
+                                            const float (*sl)[9], LjBuf& B, int b, int lane, DfLaneAcc& acc,
+                                            ff& E, ff* W) {
+    int jp = B.jp[b][lane];
+    int j = jp & 0x3fffffff, p = (unsigned)jp >> 30;
+    int i = B.ia[b][lane];
+    int img = B.im[b][lane];
+    if (i != acc.own) {
+        acc.flush(a.fix, a.n, a.eatom);
+        acc.own = i;
+    }
+    float4 hi = a.pq_hi[i], li = a.pq_lo[i], hj = a.pq_hi[j], lj = a.pq_lo[j];
+    float shx = 0.0f, shy = 0.0f, shz = 0.0f, slx = 0.0f, sly = 0.0f, slz = 0.0f;
+    if (img != 0) {
+        int sx = img_x(img), sy = img_y(img), sz = img_z(img);
+        if (a.sys || sx < -4 || sx > 4 || sy < -4 || sy > 4 || sz < -4 || sz > 4) {
+            const double* L = box_of(a, i);
+            df_split(sx * L[0], shx, slx); df_split(sy * L[1], shy, sly); df_split(sz * L[2], shz, slz);
+        } else {
+            shx = sh[0][sx + 4]; shy = sh[1][sy + 4]; shz = sh[2][sz + 4];
+            slx = sl[0][sx + 4]; sly = sl[1][sy + 4]; slz = sl[2][sz + 4];
+        }
+    }
+    // hi parts: exact (multiples of 2^-12 below 2^12 in magnitude); lo parts: rounded
+    ff dx = two_sum(__fsub_rn(__fadd_rn(hj.x, shx), hi.x), __fsub_rn(__fadd_rn(lj.x, slx), li.x));
+    ff dy = two_sum(__fsub_rn(__fadd_rn(hj.y, shy), hi.y), __fsub_rn(__fadd_rn(lj.y, sly), li.y));
+    ff dz = two_sum(__fsub_rn(__fadd_rn(hj.z, shz), hi.z), __fsub_rn(__fadd_rn(lj.z, slz), li.z));
+    ff r2 = ff_add(ff_add(ff_sqr(dx), ff_sqr(dy)), ff_sqr(dz));
+    ff v, c;
+    if (b == 0) {                 // C = 1, no path, r inside 2.7 sigma
+        ff ir2 = ff_rcp(r2);
+        ff s2 = ff_mul(D.sig2[p], ir2);
+        ff s6 = ff_mul(ff_sqr(s2), s2);
+        ff t = ff_mul(D.eps4[p], s6);                                   // 4 eps s6
+        v = ff_mul(t, ff_add_f(s6, -1.0f));                             // 4 eps (s12 - s6)
+        c = ff_mul(ff_mul(t, ff_add_f(ff_mul_f(s6, -12.0f), 6.0f)), ir2);   // (dV/dr) / r
+    } else {                      // inside the cut-off switch
+        ff ir = ff_rsqrt(r2);
+        ff ir2 = ff_sqr(ir);
+        ff s2 = ff_mul(D.sig2[p], ir2);
+        ff s6 = ff_mul(ff_sqr(s2), s2);
+        ff t = ff_mul(D.eps4[p], s6);
+        ff vv = ff_mul(t, ff_add_f(s6, -1.0f));
+        ff dvr = ff_mul(ff_mul(t, ff_add_f(ff_mul_f(s6, -12.0f), 6.0f)), ir2);
+        ff r = ff_mul(r2, ir);
+        ff x = ff_mul(ff_sub(r, D.swlo[p]), D.swinv[p]);                // > 0 in this class
+        ff so = ff_add_f(ff_neg(ff_mul(ff_sqr(x), ff_add_f(ff_mul_f(x, -2.0f), 3.0f))), 1.0f);
+        ff dso = ff_mul(ff_mul_f(ff_mul(x, ff_add_f(ff_neg(x), 1.0f)), -6.0f), D.swinv[p]);
+        v = ff_mul(vv, so);
+        c = ff_add(ff_mul(dvr, so), ff_mul(ff_mul(vv, dso), ir));
+    }
+    E = ff_add(E, v);
+    if (a.eatom) acc.e = ff_add(acc.e, v);
+    ff gx = ff_mul(c, dx), gy = ff_mul(c, dy), gz = ff_mul(c, dz);
+    acc.fx = ff_add(acc.fx, gx); acc.fy = ff_add(acc.fy, gy); acc.fz = ff_add(acc.fz, gz);
+    if (fabsf(gx.hi) < FIX_LIMIT && fabsf(gy.hi) < FIX_LIMIT && fabsf(gz.hi) < FIX_LIMIT) {
+        atomicAdd(a.fix + j, (unsigned long long)(-ff_to_fixed(gx)));
+        atomicAdd(a.fix + a.n + j, (unsigned long long)(-ff_to_fixed(gy)));
+        atomicAdd(a.fix + 2 * a.n + j, (unsigned long long)(-ff_to_fixed(gz)));
+    } else {
+        atomicMax(a.err + ERR_DF, 2);
+    }
+    if (a.virial) {
+        W[0] = ff_sub(W[0], ff_mul(dx, gx)); W[1] = ff_sub(W[1], ff_mul(dy, gy)); W[2] = ff_sub(W[2], ff_mul(dz, gz));
+        W[3] = ff_sub(W[3], ff_mul(dx, gy)); W[4] = ff_sub(W[4], ff_mul(dx, gz)); W[5] = ff_sub(W[5], ff_mul(dy, gz));
+    }
+}
+
 // Pair tests on FP32 positions.  An FP32 squared distance r2f differs from
 // the FP64 one by at most band (below); a test whose threshold lies within
 // band of r2f is redone on the FP64 displacement, so every pair is classified
@@ -263,16 +373,28 @@ __device__ __forceinline__ void lj_batch(const StepArgs<R>& a, const DevParams<R
 // |dx_f - dx| <= 2^-22 (2 max|x_i| + 4 |S|max L + 48): the roundings of x_i,
 // x_j and S L to FP32 and of the two FP32 additions, with |x_j| <= |x_i| +
 // |dx| + |S L| and |dx| < 16 A for any listed pair, and a factor 2 to spare.
-template <class R>
+template <class R, bool DF>
 __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
     const DevParams<R>& P = *a.P;
     __shared__ double shift[3][9];                // image shifts S L for S in [-4, 4]
     __shared__ LjCuts<float> cutsf[3];            // thresholds in FP32, by species pair
     __shared__ LjBuf bufs[LJ_WARPS];
-    if (threadIdx.x < 27) shift[threadIdx.x / 9][threadIdx.x % 9] = (double)((int)(threadIdx.x % 9) - 4) * a.L[threadIdx.x / 9];
+    __shared__ float shf[2][3][9];                // DF: split image shifts (hi, lo)
+    __shared__ DfParams dfp;
+    if (threadIdx.x < 27) {
+        double v = (double)((int)(threadIdx.x % 9) - 4) * a.L[threadIdx.x / 9];
+        shift[threadIdx.x / 9][threadIdx.x % 9] = v;
+        if (DF) df_split(v, shf[0][threadIdx.x / 9][threadIdx.x % 9], shf[1][threadIdx.x / 9][threadIdx.x % 9]);
+    }
     if (threadIdx.x < 3) {
         int q = threadIdx.x;
         cutsf[q] = LjCuts<float>{(float)P.rc2[q], (float)P.rpath2, (float)P.Srhi2[q], (float)P.swlo2[q]};
+        if (DF) {
+            dfp.sig2[q] = ff_from_double((double)P.sig2[q]);
+            dfp.eps4[q] = ff_from_double((double)P.eps4[q]);
+            dfp.swlo[q] = ff_from_double((double)P.swlo[q]);
+            dfp.swinv[q] = ff_from_double((double)P.swinv[q]);
+        }
     }
     __syncthreads();
     int lane = threadIdx.x & 31;
@@ -281,10 +403,18 @@ __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
     Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}, a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
     bool general = a.pgrad != nullptr;
     LaneAcc acc;
+    DfLaneAcc dacc;
+    ff Edf{0.0f, 0.0f};
+    ff Wdf[6] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
     double E = 0;
     unsigned evaluated = 0;
     int n = a.n;
     int cnt[2] = {0, 0};
+    // the pair arithmetic of one full (or, at the end, partial) batch
+    auto batch = [&](int b) {
+        if (DF) lj_batch_df<R>(a, dfp, shf[0], shf[1], B, b, lane, dacc, Edf, Wdf);
+        else lj_batch<R>(a, P, shift, B, b, lane, sink, acc, E);
+    };
     // warps take chunks of lj_chunk consecutive atoms from a global counter,
     // which balances C and H atoms (different list lengths) across warps; the
     // compaction buffers carry over from atom to atom, so that only the last
@@ -365,7 +495,7 @@ __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
                 cnt[b] += __popc(m);
                 __syncwarp();
                 if (cnt[b] >= 32) {
-                    lj_batch<R>(a, P, shift, B, b, lane, sink, acc, E);
+                    batch(b);
                     __syncwarp();
                     if (lane < cnt[b] - 32) {
                         int s = 32 + lane;
@@ -380,8 +510,15 @@ __global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
     // the warp's last, partly filled batches
 #pragma unroll
     for (int b = 0; b < 2; b++)
-        if (lane < cnt[b]) lj_batch<R>(a, P, shift, B, b, lane, sink, acc, E);
-    acc.flush(a.f, n, a.eatom);
+        if (lane < cnt[b]) batch(b);
+    if (DF) {
+        dacc.flush(a.fix, n, a.eatom);
+        E += ff_to_double(Edf);
+        if (a.virial)
+            for (int k = 0; k < 6; k++) sink.W[k] += ff_to_double(Wdf[k]);
+    } else {
+        acc.flush(a.f, n, a.eatom);
+    }
     unsigned ev = __reduce_add_sync(0xffffffffu, evaluated);
     if (lane == 0 && ev) atomicAdd(a.counters + CNT_LJ, (unsigned long long)ev);
     block_accumulate<LJ_THREADS>(E, sink.W, a.virial, a.acc + 1, a.acc + 3);
@@ -493,6 +630,14 @@ __global__ void k_finish_counters(StepArgs<R> a) {
     }
 }
 
+// the fixed-point LJ force sums of the double-float kernel into the FP64
+// forces (the sums are cleared before each evaluation)
+static __global__ void k_fix_add(unsigned long long* fix, double* f, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int d = 0; d < 3; d++) f[d * n + i] += (double)(long long)fix[d * n + i] * FIX_INV;
+}
+
 template <class R>
 void launch_compute_impl(const StepArgs<R>& a, cudaStream_t s, int num_sms, cudaEvent_t* ev) {
     if (a.n == 0) return;
@@ -518,11 +663,20 @@ void launch_compute_impl(const StepArgs<R>& a, cudaStream_t s, int num_sms, cuda
     if (a.lj_on) k_path_map<R><<<(n + 127) / 128, 128, 0, s>>>(a);
     mark(4);
     if (a.lj_on) {
-        static int per_sm = -1;            // asked once: nothing but stream work during graph capture
-        if (per_sm < 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lj<R>, LJ_THREADS, 0);
-        int blocks = num_sms * (per_sm > 0 ? per_sm : 1);
+        // asked once: nothing but stream work during graph capture
+        static int per_sm[2] = {-1, -1};
+        bool df = sizeof(R) == 8 && a.fix != nullptr;
         int need = (n + LJ_WARPS - 1) / LJ_WARPS;
-        k_lj<R><<<blocks < need ? blocks : need, LJ_THREADS, 0, s>>>(a);
+        if (df) {
+            if (per_sm[1] < 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_lj<R, true>, LJ_THREADS, 0);
+            int blocks = num_sms * (per_sm[1] > 0 ? per_sm[1] : 1);
+            k_lj<R, true><<<blocks < need ? blocks : need, LJ_THREADS, 0, s>>>(a);
+            k_fix_add<<<(n + 255) / 256, 256, 0, s>>>(a.fix, a.f, n);
+        } else {
+            if (per_sm[0] < 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_lj<R, false>, LJ_THREADS, 0);
+            int blocks = num_sms * (per_sm[0] > 0 ? per_sm[0] : 1);
+            k_lj<R, false><<<blocks < need ? blocks : need, LJ_THREADS, 0, s>>>(a);
+        }
     }
     mark(5);
     if (a.lj_on) k_bstar<R><<<grid_of(2, a.bstar_waves), 128, 0, s>>>(a);

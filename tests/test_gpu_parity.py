@@ -1,6 +1,7 @@
 """GPU path (through the C ABI) against the FP64 oracle, element by element.
 
-Tolerances (FP64 path): |dE| <= 1e-10 |E|, max|dF| <= 1e-8 max|F|,
+Tolerances (FP64 path, and the DF64 path whose LJ pair arithmetic runs in
+double-float): |dE| <= 1e-10 |E|, max|dF| <= 1e-8 max|F|,
 max|dW| <= 1e-8 max|W| -- the bar of the north star for a potential whose
 every term is evaluated in double precision (differences come only from the
 order of floating-point sums and from FP64 atomics).  Mixed path: FP32
@@ -67,6 +68,37 @@ def test_fp64_parity(A, oracle, param_text, case, term):
     e, f, w, _ = oracle.compute(pos, types, box, flags)
     got, _ = gpu_eval(A, param_text, pos, types, box, flags)
     assert_close(got, (e, f, w), 1e-10, 1e-8, 1e-8)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("term", ["all", "lj"])
+def test_df64_parity(A, oracle, param_text, case, term):
+    pos, types, box = CASES[case]()
+    flags = FLAGS[term]
+    e, f, w, _ = oracle.compute(pos, types, box, flags)
+    got, _ = gpu_eval(A, param_text, pos, types, box, flags, precision=A.DF64)
+    assert_close(got, (e, f, w), 1e-10, 1e-8, 1e-8)
+
+
+def test_df64_against_fp64_pe32k(A, param_text):
+    """DF64 against FP64 on the 32,640-atom PE: the LJ pair arithmetic in
+    double-float and its fixed-point force sums stay within 1e-11 of FP64."""
+    pos, types, box = inputs.workload("pe32k")
+    (e64, f64, w64), _ = gpu_eval(A, param_text, pos, types, box)
+    (edf, fdf, wdf), _ = gpu_eval(A, param_text, pos, types, box, precision=A.DF64)
+    assert abs(edf[0] - e64[0]) <= 1e-11 * abs(e64[0])
+    assert np.abs(fdf - f64).max() <= 1e-11 * np.abs(f64).max()
+    assert np.abs(wdf - w64).max() <= 1e-11 * np.abs(w64).max()
+
+
+def test_df64_coordinate_range(A, param_text):
+    pos, types, box = CASES["pe1152"]()
+    assert (2100.0 / box).max() < 120          # still a valid position for the list build
+    ev = A.Airebo(param_text, precision=A.DF64)
+    p = torch.tensor(pos + 2100.0, device="cuda")
+    ev.neighbor(p, torch.tensor(types, device="cuda"), box)
+    with pytest.raises(A.AireboError):
+        ev.compute(p)
 
 
 @pytest.mark.parametrize("case", list(CASES))
@@ -163,7 +195,7 @@ def test_pe1m_sampled_parity(A, oracle, param_text):
     """The bench's 1,044,480-atom polyethylene: sampled forces against the
     oracle's one-atom-at-a-time evaluation, plus zero net force."""
     pos, types, box = inputs.workload("pe1m")
-    for prec, tol in ((0, 1e-8), (A.MIXED, 1e-4)):
+    for prec, tol in ((0, 1e-8), (A.DF64, 1e-8), (A.MIXED, 1e-4)):
         (e4, f, _), _ = gpu_eval(A, param_text, pos, types, box, precision=prec, virial=False)
         rng = np.random.default_rng(3)
         atoms = np.concatenate([[0, len(types) - 1], rng.choice(len(types), 4, replace=False)])
@@ -251,6 +283,7 @@ def oracle_nve(oracle, pos, vel, types, box, dt, nsteps):
 @pytest.mark.parametrize("case,temp,precision,xtol,etol", [
     ("hot300", 2000.0, 0, 1e-8, 1e-9),
     ("pe1152", 600.0, 0, 1e-8, 1e-9),
+    ("pe1152", 600.0, 2, 1e-8, 1e-9),
     ("pe1152", 600.0, 1, 1e-4, 1e-5),
 ])
 def test_nve_against_oracle_trajectory(A, oracle, param_text, case, temp, precision, xtol, etol):
