@@ -60,7 +60,7 @@ typedef enum {
  * (pairs of FP32 numbers, about 48 significant bits) on the FP32 pipe, from
  * positions split on a 2^-12 A grid, with the pair forces summed in 64-bit
  * fixed point (2^-40 eV/A) -- FP64-class results at FP32-pipe rates.  It
- * needs every |coordinate| below 2000 A and pair forces below 4e6 eV/A
+ * needs every |coordinate| below 2000 A and pair forces below 1e6 eV/A
  * (AIREBO_ERR_ARG / AIREBO_ERR_NONFINITE otherwise); the Morse form runs as
  * AIREBO_FP64.
  */

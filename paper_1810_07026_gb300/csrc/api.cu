@@ -736,7 +736,7 @@ airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos,
         if (h->h_err[ERR_NONFINITE]) return fail(h, AIREBO_ERR_NONFINITE, "non-finite position");
         if (h->h_err[ERR_DF] == 1) return fail(h, AIREBO_ERR_ARG, "AIREBO_DF64 needs every |coordinate| below 2000 A");
         if (h->h_err[ERR_DF] == 2)
-            return fail(h, AIREBO_ERR_NONFINITE, "an LJ pair force beyond the fixed-point range (4e6 eV/A)");
+            return fail(h, AIREBO_ERR_NONFINITE, "an LJ pair force beyond the fixed-point range (1e6 eV/A)");
         bool again = false;
         if (h->h_err[ERR_SHORT] > h->stride) {
             if (h->h_err[ERR_SHORT] > MAXN)

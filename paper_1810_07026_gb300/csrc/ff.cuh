@@ -96,16 +96,30 @@ __device__ __forceinline__ ff ff_from_double(double x) {
 __device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
 
 // Fixed-point force accumulation: v * 2^FIX_BITS as a signed 64-bit integer.
-// hi * 2^40 is exact; lo * 2^40 is rounded to an integer, so each added value
-// carries an error below 2^-40 (about 1e-12 eV/A); integer sums are exact and
-// independent of the order of the atomic additions.
+// hi and lo are each scaled by 2^40 and rounded to an integer, so each added
+// value carries an error of at most 2^-40 (about 1e-12 eV/A); integer sums are
+// exact and independent of the order of the atomic additions.
 constexpr int FIX_BITS = 40;
 constexpr float FIX_SCALE = 1099511627776.0f;         // 2^40
 constexpr double FIX_INV = 1.0 / 1099511627776.0;      // 2^-40
-constexpr float FIX_LIMIT = 4.0e6f;                    // |v| below 2^22 keeps the sum far from 2^63
+constexpr float FIX_LIMIT = 1.0e6f;                    // |v| below 2^20: eight such terms stay below 2^63
 
-__device__ __forceinline__ long long ff_to_fixed(ff a) {
-    return __float2ll_rn(__fmul_rn(a.hi, FIX_SCALE)) + __float2ll_rn(__fmul_rn(a.lo, FIX_SCALE));
+// v * 2^FIX_BITS rounded to an integer (half away from zero), from the bits
+// of v with integer operations only: the float-to-64-bit-integer conversion
+// instruction shares the narrow FP64 pipe on this GPU.  For |v| < 2^22.
+__device__ __forceinline__ long long f2fix(float v) {
+    unsigned b = __float_as_uint(v);
+    int e = (int)((b >> 23) & 0xffu);
+    long long m = (long long)((b & 0x7fffffu) | 0x800000u);        // zero: m * 2^-110 rounds to 0
+    int sh = e - (127 + 23 - FIX_BITS);                              // v * 2^40 = m * 2^sh
+    long long up = m << (sh > 0 ? sh : 0);
+    int k = -sh;
+    k = k < 1 ? 1 : (k > 63 ? 63 : k);
+    long long dn = (m + (1ll << (k - 1))) >> k;
+    long long r = sh >= 0 ? up : dn;
+    return (b >> 31) ? -r : r;
 }
+
+__device__ __forceinline__ long long ff_to_fixed(ff a) { return f2fix(a.hi) + f2fix(a.lo); }
 
 }  // namespace airebo

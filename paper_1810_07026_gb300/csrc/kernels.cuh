@@ -285,15 +285,17 @@ struct DfParams {
 
 struct DfLaneAcc {
     int own = -1;
-    ff fx{0.0f, 0.0f}, fy{0.0f, 0.0f}, fz{0.0f, 0.0f}, e{0.0f, 0.0f};
+    long long fx = 0, fy = 0, fz = 0;            // fixed point, as the sums they go to
+    ff e{0.0f, 0.0f};
     __device__ __forceinline__ void flush(unsigned long long* fix, int n, double* eatom) {
         if (own >= 0) {
-            atomicAdd(fix + own, (unsigned long long)ff_to_fixed(fx));
-            atomicAdd(fix + n + own, (unsigned long long)ff_to_fixed(fy));
-            atomicAdd(fix + 2 * n + own, (unsigned long long)ff_to_fixed(fz));
+            atomicAdd(fix + own, (unsigned long long)fx);
+            atomicAdd(fix + n + own, (unsigned long long)fy);
+            atomicAdd(fix + 2 * n + own, (unsigned long long)fz);
             if (eatom) atomicAdd(eatom + own, ff_to_double(e));
         }
-        fx = fy = fz = e = ff{0.0f, 0.0f};
+        fx = fy = fz = 0;
+        e = ff{0.0f, 0.0f};
     }
 };
 
@@ -352,11 +354,12 @@ __device__ __forceinline__ void lj_batch_df(const StepArgs<R>& a, const DfParams
     E = ff_add(E, v);
     if (a.eatom) acc.e = ff_add(acc.e, v);
     ff gx = ff_mul(c, dx), gy = ff_mul(c, dy), gz = ff_mul(c, dz);
-    acc.fx = ff_add(acc.fx, gx); acc.fy = ff_add(acc.fy, gy); acc.fz = ff_add(acc.fz, gz);
     if (fabsf(gx.hi) < FIX_LIMIT && fabsf(gy.hi) < FIX_LIMIT && fabsf(gz.hi) < FIX_LIMIT) {
-        atomicAdd(a.fix + j, (unsigned long long)(-ff_to_fixed(gx)));
-        atomicAdd(a.fix + a.n + j, (unsigned long long)(-ff_to_fixed(gy)));
-        atomicAdd(a.fix + 2 * a.n + j, (unsigned long long)(-ff_to_fixed(gz)));
+        long long qx = ff_to_fixed(gx), qy = ff_to_fixed(gy), qz = ff_to_fixed(gz);
+        acc.fx += qx; acc.fy += qy; acc.fz += qz;
+        atomicAdd(a.fix + j, (unsigned long long)(-qx));
+        atomicAdd(a.fix + a.n + j, (unsigned long long)(-qy));
+        atomicAdd(a.fix + 2 * a.n + j, (unsigned long long)(-qz));
     } else {
         atomicMax(a.err + ERR_DF, 2);
     }

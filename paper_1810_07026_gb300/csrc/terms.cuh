@@ -946,6 +946,22 @@ HD int build_path_map(const Graph<R>& G, PathMap<R>& M, int i) {
             }
         }
     }
+    // keys ascending, so that the LJ pair test finds an entry by bisection
+    for (int e = 1; e < count; e++) {
+        long long kx = M.key[base + e];
+        R wx = M.wt[base + e];
+        int px = M.path[base + e];
+        int f = e;
+        while (f > 0 && M.key[base + f - 1] > kx) {
+            M.key[base + f] = M.key[base + f - 1];
+            M.wt[base + f] = M.wt[base + f - 1];
+            M.path[base + f] = M.path[base + f - 1];
+            f--;
+        }
+        M.key[base + f] = kx;
+        M.wt[base + f] = wx;
+        M.path[base + f] = px;
+    }
     M.cnt[i] = count;
     return overflow;
 }
@@ -1105,11 +1121,17 @@ HD int lj_classify_c(const DevParams<R>& P, const PathMap<R>& M, int i, int j, i
     mi = -1; code = -1; C = R(1);
     if (!lt_nonneg(r2, k.rc2)) return 0;
     if (lt_nonneg(r2, k.rpath2)) {
+        // bisection over i's keys (ascending); every lane of a warp looks in
+        // the same atom's map, so the trip counts agree
         long long key = map_key(j, img);
         int c = M.cnt[i];
         const long long* kk = M.key + (size_t)i * M.cap;
-        for (int e = 0; e < c; e++)
-            if (kk[e] == key) { mi = e; break; }
+        int lo = 0, hi = c;
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (kk[mid] < key) lo = mid + 1; else hi = mid;
+        }
+        if (lo < c && kk[lo] == key) mi = lo;
         if (mi >= 0) {
             C = M.wt[(size_t)i * M.cap + mi];
             if (!(C > R(0))) return 0;
