@@ -377,7 +377,7 @@ __device__ __forceinline__ void lj_batch_df(const StepArgs<R>& a, const DfParams
 // x_j and S L to FP32 and of the two FP32 additions, with |x_j| <= |x_i| +
 // |dx| + |S L| and |dx| < 16 A for any listed pair, and a factor 2 to spare.
 template <class R, bool DF>
-__global__ void __launch_bounds__(LJ_THREADS) k_lj(StepArgs<R> a) {
+__global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
     const DevParams<R>& P = *a.P;
     __shared__ double shift[3][9];                // image shifts S L for S in [-4, 4]
     __shared__ LjCuts<float> cutsf[3];            // thresholds in FP32, by species pair
