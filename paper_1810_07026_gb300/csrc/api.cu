@@ -447,6 +447,7 @@ template <class R> airebo_status alloc_step(airebo_handle h, Precision<R>& pr, i
     if (b.map_cap == 0) b.map_cap = 32;
     size_t mm = (size_t)n * b.map_cap;
     CK(realloc_dev(b.map_cnt, n)); CK(realloc_dev(b.map_key, mm)); CK(realloc_dev(b.map_wt, mm)); CK(realloc_dev(b.map_path, mm));
+    CK(realloc_dev(b.map_mask, 4 * (size_t)n));
     if (sizeof(R) == 8 && screen_on(h)) {
         CK(realloc_dev(b.s_dx, m)); CK(realloc_dev(b.s_dy, m)); CK(realloc_dev(b.s_dz, m));
         CK(realloc_dev(b.s_r, m)); CK(realloc_dev(b.s_ir, m)); CK(realloc_dev(b.s_w, m));
@@ -466,7 +467,7 @@ template <class R> airebo_status grow_map(airebo_handle h, Precision<R>& pr, int
 template <class R> void free_prec(Precision<R>& pr) {
     StepBuffers<R>& b = pr.b;
     void* ps[] = {b.P, b.Pkg, b.tables, b.Tnz, b.cnt, b.nj, b.nimg, b.dx, b.dy, b.dz, b.r, b.ir, b.w, b.dw, b.omw, b.nC, b.nH,
-                  b.map_cnt, b.map_key, b.map_wt, b.map_path,
+                  b.map_cnt, b.map_key, b.map_wt, b.map_path, b.map_mask,
                   b.s_dx, b.s_dy, b.s_dz, b.s_r, b.s_ir, b.s_w, b.s_nC, b.s_nH};
     for (void* p : ps) if (p) cudaFree(p);
     b = StepBuffers<R>();
@@ -640,6 +641,7 @@ template <class R> StepArgs<R> make_args(airebo_handle h, Precision<R>& pr, cons
     a.g_cnt = b.cnt; a.g_nj = b.nj; a.g_nimg = b.nimg; a.g_dx = b.dx; a.g_dy = b.dy; a.g_dz = b.dz;
     a.g_r = b.r; a.g_ir = b.ir; a.g_w = b.w; a.g_dw = b.dw; a.g_omw = b.omw; a.g_nC = b.nC; a.g_nH = b.nH;
     a.M.cap = b.map_cap; a.M.cnt = b.map_cnt; a.M.key = b.map_key; a.M.wt = b.map_wt; a.M.path = b.map_path;
+    a.M.mask = b.map_mask;
     a.pos = d_pos;
     a.posf = h->posf;
     bool df = sizeof(R) == 8 && df_on(h);

@@ -120,6 +120,15 @@ __device__ __forceinline__ long long f2fix(float v) {
     return (b >> 31) ? -r : r;
 }
 
-__device__ __forceinline__ long long ff_to_fixed(ff a) { return f2fix(a.hi) + f2fix(a.lo); }
+// hi + lo in fixed point.  lo * 2^40 is below 2^22 in magnitude unless the
+// value is beyond ~64 eV/A; then adding 1.5 * 2^23 rounds it to an integer in
+// the float's significand (the usual shift trick), two operations.
+__device__ __forceinline__ long long ff_to_fixed(ff a) {
+    float t = __fmul_rn(a.lo, FIX_SCALE);
+    long long lo;
+    if (fabsf(t) < 4194304.0f) lo = (long long)(__float_as_int(__fadd_rn(t, 12582912.0f)) - 0x4B400000);
+    else lo = f2fix(a.lo);
+    return f2fix(a.hi) + lo;
+}
 
 }  // namespace airebo

@@ -20,6 +20,7 @@ template <class R> struct StepBuffers {
     // connectivity map
     int map_cap = 0;
     int* map_cnt = nullptr; long long* map_key = nullptr; R* map_wt = nullptr; int* map_path = nullptr;
+    unsigned long long* map_mask = nullptr;   // 4 words per atom
     // FP32 copy of the short-list geometry for the b* screen (FP64 only)
     float* s_dx = nullptr; float* s_dy = nullptr; float* s_dz = nullptr; float* s_r = nullptr; float* s_ir = nullptr;
     float* s_w = nullptr; float* s_nC = nullptr; float* s_nH = nullptr;

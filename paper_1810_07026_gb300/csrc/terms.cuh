@@ -879,7 +879,11 @@ template <class R> struct PathMap {
     long long* key;      // [n * cap]
     R* wt;               // C = 1 - largest path weight
     int* path;
+    unsigned long long* mask;   // [n * 4]: bit map_bit(atom) set for every atom in the map (a filter)
 };
+
+// 256-bit membership filter of a map: an atom whose bit is clear is not in it
+HD int map_bit(int atom) { return (int)(((unsigned)atom * 2654435761u) >> 24); }
 
 // Ties: larger weight (smaller C), then the shorter path, then the smaller k,
 // then the smaller l.  The map stores C = 1 - weight, formed from the 1 - w of
@@ -896,6 +900,7 @@ template <class R>
 HD int build_path_map(const Graph<R>& G, PathMap<R>& M, int i) {
     int base = i * M.cap;
     int count = 0, overflow = 0;
+    unsigned long long mask[4] = {0, 0, 0, 0};
     auto insert = [&](int atom, int img, R c, int len, int k, int l, int code) {
         long long key = map_key(atom, img);
         for (int e = 0; e < count; e++) {
@@ -916,6 +921,8 @@ HD int build_path_map(const Graph<R>& G, PathMap<R>& M, int i) {
             M.wt[base + count] = c;
             M.path[base + count] = code;
             count++;
+            int bit = map_bit(atom);
+            mask[bit >> 6] |= 1ull << (bit & 63);
         } else {
             overflow++;
         }
@@ -946,23 +953,8 @@ HD int build_path_map(const Graph<R>& G, PathMap<R>& M, int i) {
             }
         }
     }
-    // keys ascending, so that the LJ pair test finds an entry by bisection
-    for (int e = 1; e < count; e++) {
-        long long kx = M.key[base + e];
-        R wx = M.wt[base + e];
-        int px = M.path[base + e];
-        int f = e;
-        while (f > 0 && M.key[base + f - 1] > kx) {
-            M.key[base + f] = M.key[base + f - 1];
-            M.wt[base + f] = M.wt[base + f - 1];
-            M.path[base + f] = M.path[base + f - 1];
-            f--;
-        }
-        M.key[base + f] = kx;
-        M.wt[base + f] = wx;
-        M.path[base + f] = px;
-    }
     M.cnt[i] = count;
+    for (int w = 0; w < 4; w++) M.mask[4 * i + w] = mask[w];
     return overflow;
 }
 
@@ -1121,17 +1113,15 @@ HD int lj_classify_c(const DevParams<R>& P, const PathMap<R>& M, int i, int j, i
     mi = -1; code = -1; C = R(1);
     if (!lt_nonneg(r2, k.rc2)) return 0;
     if (lt_nonneg(r2, k.rpath2)) {
-        // bisection over i's keys (ascending); every lane of a warp looks in
-        // the same atom's map, so the trip counts agree
-        long long key = map_key(j, img);
-        int c = M.cnt[i];
-        const long long* kk = M.key + (size_t)i * M.cap;
-        int lo = 0, hi = c;
-        while (lo < hi) {
-            int mid = (lo + hi) >> 1;
-            if (kk[mid] < key) lo = mid + 1; else hi = mid;
+        // the filter rules most non-members out without touching the keys
+        int bit = map_bit(j);
+        if ((M.mask[4 * i + (bit >> 6)] >> (bit & 63)) & 1ull) {
+            long long key = map_key(j, img);
+            int c = M.cnt[i];
+            const long long* kk = M.key + (size_t)i * M.cap;
+            for (int e = 0; e < c; e++)
+                if (kk[e] == key) { mi = e; break; }
         }
-        if (lo < c && kk[lo] == key) mi = lo;
         if (mi >= 0) {
             C = M.wt[(size_t)i * M.cap + mi];
             if (!(C > R(0))) return 0;
