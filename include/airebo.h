@@ -55,14 +55,19 @@ typedef enum {
 /*
  * Precisions.  AIREBO_FP64: every term in FP64.  AIREBO_MIXED: FP32 geometry,
  * splines and bond order; FP64 positions, displacements, accumulation and
- * integrator.  AIREBO_DF64: as AIREBO_FP64, except that the pair arithmetic
+ * integrator -- except that the Lennard-Jones pairs with C_ij = 1 and no b*
+ * take their displacement from the split positions below (exact to about
+ * 1e-11 A before its one rounding to FP32) and sum their pair forces in 64-bit
+ * fixed point and their energy in double-float, so that they need no FP64
+ * instruction.  AIREBO_DF64: as AIREBO_FP64, except that the pair arithmetic
  * of the Lennard-Jones pairs with C_ij = 1 and no b* runs in double-float
  * (pairs of FP32 numbers, about 48 significant bits) on the FP32 pipe, from
  * positions split on a 2^-12 A grid, with the pair forces summed in 64-bit
  * fixed point (2^-40 eV/A) -- FP64-class results at FP32-pipe rates.  It
  * needs every |coordinate| below 2000 A and pair forces below 1e6 eV/A
- * (AIREBO_ERR_ARG / AIREBO_ERR_NONFINITE otherwise); the Morse form runs as
- * AIREBO_FP64.
+ * (AIREBO_ERR_ARG / AIREBO_ERR_NONFINITE otherwise), as does AIREBO_MIXED;
+ * with the Morse form both run their LJ pairs as before the split (FP64
+ * displacements and FP64 sums).
  */
 enum { AIREBO_FP64 = 0, AIREBO_MIXED = 1, AIREBO_DF64 = 2 };
 

@@ -479,9 +479,11 @@ bool screen_on(airebo_handle h) {
     return h->opt.precision != AIREBO_MIXED && h->opt.bstar_screen != 0 && h->opt.enable_lj != 0;
 }
 
-// the double-float LJ kernel (AIREBO_DF64, Lennard-Jones form only)
+// the LJ kernel on split positions with fixed-point force sums: double-float
+// pair arithmetic (AIREBO_DF64) or FP32 pair arithmetic (AIREBO_MIXED);
+// Lennard-Jones form only
 bool df_on(airebo_handle h) {
-    return h->opt.precision == AIREBO_DF64 && h->opt.enable_lj != 0 && h->sc.kind == 0;
+    return h->opt.precision != AIREBO_FP64 && h->opt.enable_lj != 0 && h->sc.kind == 0;
 }
 
 airebo_status alloc_atoms(airebo_handle h, int n) {
@@ -491,7 +493,7 @@ airebo_status alloc_atoms(airebo_handle h, int n) {
     CK(realloc_dev(h->cell_of, na));
     CK(realloc_dev(h->spos, na));
     CK(realloc_dev(h->posf, na));
-    if (h->opt.precision == AIREBO_DF64) {
+    if (h->opt.precision != AIREBO_FP64) {
         CK(realloc_dev(h->pq_hi, na));
         CK(realloc_dev(h->pq_lo, na));
         CK(realloc_dev(h->fix, 3 * (size_t)na));
@@ -644,7 +646,7 @@ template <class R> StepArgs<R> make_args(airebo_handle h, Precision<R>& pr, cons
     a.M.mask = b.map_mask;
     a.pos = d_pos;
     a.posf = h->posf;
-    bool df = sizeof(R) == 8 && df_on(h);
+    bool df = df_on(h);
     a.pq_hi = df ? h->pq_hi : nullptr;
     a.pq_lo = df ? h->pq_lo : nullptr;
     a.fix = df ? h->fix : nullptr;
@@ -736,7 +738,8 @@ airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos,
             }
         }
         if (h->h_err[ERR_NONFINITE]) return fail(h, AIREBO_ERR_NONFINITE, "non-finite position");
-        if (h->h_err[ERR_DF] == 1) return fail(h, AIREBO_ERR_ARG, "AIREBO_DF64 needs every |coordinate| below 2000 A");
+        if (h->h_err[ERR_DF] == 1)
+            return fail(h, AIREBO_ERR_ARG, "AIREBO_DF64 and AIREBO_MIXED need every |coordinate| below 2000 A");
         if (h->h_err[ERR_DF] == 2)
             return fail(h, AIREBO_ERR_NONFINITE, "an LJ pair force beyond the fixed-point range (1e6 eV/A)");
         bool again = false;

@@ -369,6 +369,77 @@ __device__ __forceinline__ void lj_batch_df(const StepArgs<R>& a, const DfParams
     }
 }
 
+// Mixed precision with the same split positions: the double-float
+// displacement (FP64-class) rounded once to FP32, the pair term in FP32, and
+// the pair forces summed in 64-bit fixed point, the energy and virial in
+// double-float -- no FP64 instruction per pair.
+template <class R>
+__device__ __forceinline__ void lj_batch_mx(const StepArgs<R>& a, const DevParams<R>& P, const float (*sh)[9],
+                                            const float (*sl)[9], LjBuf& B, int b, int lane, DfLaneAcc& acc,
+                                            ff& E, ff* W) {
+    int jp = B.jp[b][lane];
+    int j = jp & 0x3fffffff, p = (unsigned)jp >> 30;
+    int i = B.ia[b][lane];
+    int img = B.im[b][lane];
+    if (i != acc.own) {
+        acc.flush(a.fix, a.n, a.eatom);
+        acc.own = i;
+    }
+    float4 hi = a.pq_hi[i], li = a.pq_lo[i], hj = a.pq_hi[j], lj = a.pq_lo[j];
+    float shx = 0.0f, shy = 0.0f, shz = 0.0f, slx = 0.0f, sly = 0.0f, slz = 0.0f;
+    if (img != 0) {
+        int sx = img_x(img), sy = img_y(img), sz = img_z(img);
+        if (a.sys || sx < -4 || sx > 4 || sy < -4 || sy > 4 || sz < -4 || sz > 4) {
+            const double* L = box_of(a, i);
+            df_split(sx * L[0], shx, slx); df_split(sy * L[1], shy, sly); df_split(sz * L[2], shz, slz);
+        } else {
+            shx = sh[0][sx + 4]; shy = sh[1][sy + 4]; shz = sh[2][sz + 4];
+            slx = sl[0][sx + 4]; sly = sl[1][sy + 4]; slz = sl[2][sz + 4];
+        }
+    }
+    float rx = __fadd_rn(__fsub_rn(__fadd_rn(hj.x, shx), hi.x), __fsub_rn(__fadd_rn(lj.x, slx), li.x));
+    float ry = __fadd_rn(__fsub_rn(__fadd_rn(hj.y, shy), hi.y), __fsub_rn(__fadd_rn(lj.y, sly), li.y));
+    float rz = __fadd_rn(__fsub_rn(__fadd_rn(hj.z, shz), hi.z), __fsub_rn(__fadd_rn(lj.z, slz), li.z));
+    float r2 = rx * rx + ry * ry + rz * rz;
+    float v, c;
+    float sig2 = (float)P.sig2[p], e4 = (float)P.eps4[p];
+    if (b == 0) {
+        float ir2 = rcp_(r2);
+        float s2 = sig2 * ir2;
+        float s6 = s2 * s2 * s2;
+        v = e4 * (s6 * s6 - s6);
+        c = e4 * (6.0f * s6 - 12.0f * s6 * s6) * ir2;
+    } else {
+        float ir = rsqrt_(r2);
+        float ir2 = ir * ir;
+        float s2 = sig2 * ir2;
+        float s6 = s2 * s2 * s2;
+        float vv = e4 * (s6 * s6 - s6);
+        float dvr = e4 * (-12.0f * s6 * s6 + 6.0f * s6) * ir2;
+        float t = (r2 * ir - (float)P.swlo[p]) * (float)P.swinv[p];
+        float so = 1.0f - t * t * (3.0f - 2.0f * t);
+        float dso = -6.0f * t * (1.0f - t) * (float)P.swinv[p];
+        v = vv * so;
+        c = dvr * so + vv * dso * ir;
+    }
+    E = ff_add_f(E, v);
+    if (a.eatom) acc.e = ff_add_f(acc.e, v);
+    float gx = c * rx, gy = c * ry, gz = c * rz;
+    if (fabsf(gx) < FIX_LIMIT && fabsf(gy) < FIX_LIMIT && fabsf(gz) < FIX_LIMIT) {
+        long long qx = f2fix(gx), qy = f2fix(gy), qz = f2fix(gz);
+        acc.fx += qx; acc.fy += qy; acc.fz += qz;
+        atomicAdd(a.fix + j, (unsigned long long)(-qx));
+        atomicAdd(a.fix + a.n + j, (unsigned long long)(-qy));
+        atomicAdd(a.fix + 2 * a.n + j, (unsigned long long)(-qz));
+    } else {
+        atomicMax(a.err + ERR_DF, 2);
+    }
+    if (a.virial) {
+        W[0] = ff_add_f(W[0], -rx * gx); W[1] = ff_add_f(W[1], -ry * gy); W[2] = ff_add_f(W[2], -rz * gz);
+        W[3] = ff_add_f(W[3], -rx * gy); W[4] = ff_add_f(W[4], -rx * gz); W[5] = ff_add_f(W[5], -ry * gz);
+    }
+}
+
 // Pair tests on FP32 positions.  An FP32 squared distance r2f differs from
 // the FP64 one by at most band (below); a test whose threshold lies within
 // band of r2f is redone on the FP64 displacement, so every pair is classified
@@ -415,8 +486,12 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
     int cnt[2] = {0, 0};
     // the pair arithmetic of one full (or, at the end, partial) batch
     auto batch = [&](int b) {
-        if (DF) lj_batch_df<R>(a, dfp, shf[0], shf[1], B, b, lane, dacc, Edf, Wdf);
-        else lj_batch<R>(a, P, shift, B, b, lane, sink, acc, E);
+        if constexpr (DF) {
+            if constexpr (sizeof(R) == 8) lj_batch_df<R>(a, dfp, shf[0], shf[1], B, b, lane, dacc, Edf, Wdf);
+            else lj_batch_mx<R>(a, P, shf[0], shf[1], B, b, lane, dacc, Edf, Wdf);
+        } else {
+            lj_batch<R>(a, P, shift, B, b, lane, sink, acc, E);
+        }
     };
     // warps take chunks of lj_chunk consecutive atoms from a global counter,
     // which balances C and H atoms (different list lengths) across warps; the
@@ -668,7 +743,7 @@ void launch_compute_impl(const StepArgs<R>& a, cudaStream_t s, int num_sms, cuda
     if (a.lj_on) {
         // asked once: nothing but stream work during graph capture
         static int per_sm[2] = {-1, -1};
-        bool df = sizeof(R) == 8 && a.fix != nullptr;
+        bool df = a.fix != nullptr;
         int need = (n + LJ_WARPS - 1) / LJ_WARPS;
         if (df) {
             if (per_sm[1] < 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_lj<R, true>, LJ_THREADS, 0);
