@@ -92,18 +92,15 @@ __global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
     int n = a.n;
     double xi = a.pos[i], yi = a.pos[n + i], zi = a.pos[2 * n + i];
     if (!isfinite(xi) || !isfinite(yi) || !isfinite(zi)) atomicMax(a.err + ERR_NONFINITE, 1);
-    // FP32 position and species for the LJ kernel's pair tests; with split
-    // positions (fixed-point LJ sums) the FP32 position is the hi part
-    if (a.fix) {
+    // FP32 position and species for the LJ kernel's pair tests
+    a.posf[i] = make_float4((float)xi, (float)yi, (float)zi, __int_as_float((int)a.G.type[i]));
+    if (a.fix) {                      // double-float LJ: hi on the 2^-12 grid, lo the rest
         if (!(fabs(xi) < 2000.0 && fabs(yi) < 2000.0 && fabs(zi) < 2000.0)) atomicMax(a.err + ERR_DF, 1);
         float4 h, l;
         df_split(xi, h.x, l.x); df_split(yi, h.y, l.y); df_split(zi, h.z, l.z);
-        h.w = __int_as_float((int)a.G.type[i]);
-        l.w = 0.0f;
-        a.posf[i] = h;
+        h.w = l.w = 0.0f;
+        a.pq_hi[i] = h;
         a.pq_lo[i] = l;
-    } else {
-        a.posf[i] = make_float4((float)xi, (float)yi, (float)zi, __int_as_float((int)a.G.type[i]));
     }
     int ti = a.G.type[i];
     int cnt = 0;
@@ -220,7 +217,6 @@ struct LjBuf {
     int jp[2][64];          // j | species pair << 30
     int ia[2][64];          // the list's atom i
     int im[2][64];          // packed image of j
-    float hx[2][64], hy[2][64], hz[2][64];   // split positions: the exact hi part of the displacement
 };
 
 // Per-lane force (and energy) accumulator of the atom whose pairs the lane
@@ -316,23 +312,22 @@ __device__ __forceinline__ void lj_batch_df(const StepArgs<R>& a, const DfParams
         acc.flush(a.fix, a.n, a.eatom);
         acc.own = i;
     }
-    float4 li = a.pq_lo[i], lj = a.pq_lo[j];
-    float slx = 0.0f, sly = 0.0f, slz = 0.0f;
+    float4 hi = a.pq_hi[i], li = a.pq_lo[i], hj = a.pq_hi[j], lj = a.pq_lo[j];
+    float shx = 0.0f, shy = 0.0f, shz = 0.0f, slx = 0.0f, sly = 0.0f, slz = 0.0f;
     if (img != 0) {
         int sx = img_x(img), sy = img_y(img), sz = img_z(img);
         if (a.sys || sx < -4 || sx > 4 || sy < -4 || sy > 4 || sz < -4 || sz > 4) {
             const double* L = box_of(a, i);
-            float h;
-            df_split(sx * L[0], h, slx); df_split(sy * L[1], h, sly); df_split(sz * L[2], h, slz);
+            df_split(sx * L[0], shx, slx); df_split(sy * L[1], shy, sly); df_split(sz * L[2], shz, slz);
         } else {
+            shx = sh[0][sx + 4]; shy = sh[1][sy + 4]; shz = sh[2][sz + 4];
             slx = sl[0][sx + 4]; sly = sl[1][sy + 4]; slz = sl[2][sz + 4];
         }
     }
-    float hx = B.hx[b][lane], hy = B.hy[b][lane], hz = B.hz[b][lane];
-    // hi parts: exact (formed in the pair test); lo parts: rounded
-    ff dx = two_sum(hx, __fsub_rn(__fadd_rn(lj.x, slx), li.x));
-    ff dy = two_sum(hy, __fsub_rn(__fadd_rn(lj.y, sly), li.y));
-    ff dz = two_sum(hz, __fsub_rn(__fadd_rn(lj.z, slz), li.z));
+    // hi parts: exact (multiples of 2^-12 below 2^12 in magnitude); lo parts: rounded
+    ff dx = two_sum(__fsub_rn(__fadd_rn(hj.x, shx), hi.x), __fsub_rn(__fadd_rn(lj.x, slx), li.x));
+    ff dy = two_sum(__fsub_rn(__fadd_rn(hj.y, shy), hi.y), __fsub_rn(__fadd_rn(lj.y, sly), li.y));
+    ff dz = two_sum(__fsub_rn(__fadd_rn(hj.z, shz), hi.z), __fsub_rn(__fadd_rn(lj.z, slz), li.z));
     ff r2 = ff_add(ff_add(ff_sqr(dx), ff_sqr(dy)), ff_sqr(dz));
     ff v, c;
     if (b == 0) {                 // C = 1, no path, r inside 2.7 sigma
@@ -391,22 +386,21 @@ __device__ __forceinline__ void lj_batch_mx(const StepArgs<R>& a, const DevParam
         acc.flush(a.fix, a.n, a.eatom);
         acc.own = i;
     }
-    float4 li = a.pq_lo[i], lj = a.pq_lo[j];
-    float slx = 0.0f, sly = 0.0f, slz = 0.0f;
+    float4 hi = a.pq_hi[i], li = a.pq_lo[i], hj = a.pq_hi[j], lj = a.pq_lo[j];
+    float shx = 0.0f, shy = 0.0f, shz = 0.0f, slx = 0.0f, sly = 0.0f, slz = 0.0f;
     if (img != 0) {
         int sx = img_x(img), sy = img_y(img), sz = img_z(img);
         if (a.sys || sx < -4 || sx > 4 || sy < -4 || sy > 4 || sz < -4 || sz > 4) {
             const double* L = box_of(a, i);
-            float h;
-            df_split(sx * L[0], h, slx); df_split(sy * L[1], h, sly); df_split(sz * L[2], h, slz);
+            df_split(sx * L[0], shx, slx); df_split(sy * L[1], shy, sly); df_split(sz * L[2], shz, slz);
         } else {
+            shx = sh[0][sx + 4]; shy = sh[1][sy + 4]; shz = sh[2][sz + 4];
             slx = sl[0][sx + 4]; sly = sl[1][sy + 4]; slz = sl[2][sz + 4];
         }
     }
-    float hx = B.hx[b][lane], hy = B.hy[b][lane], hz = B.hz[b][lane];
-    float rx = __fadd_rn(hx, __fsub_rn(__fadd_rn(lj.x, slx), li.x));
-    float ry = __fadd_rn(hy, __fsub_rn(__fadd_rn(lj.y, sly), li.y));
-    float rz = __fadd_rn(hz, __fsub_rn(__fadd_rn(lj.z, slz), li.z));
+    float rx = __fadd_rn(__fsub_rn(__fadd_rn(hj.x, shx), hi.x), __fsub_rn(__fadd_rn(lj.x, slx), li.x));
+    float ry = __fadd_rn(__fsub_rn(__fadd_rn(hj.y, shy), hi.y), __fsub_rn(__fadd_rn(lj.y, sly), li.y));
+    float rz = __fadd_rn(__fsub_rn(__fadd_rn(hj.z, shz), hi.z), __fsub_rn(__fadd_rn(lj.z, slz), li.z));
     float r2 = rx * rx + ry * ry + rz * rz;
     float v, c;
     float sig2 = (float)P.sig2[p], e4 = (float)P.eps4[p];
@@ -525,47 +519,23 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
         for (int base = 0; base < ne; base += 32) {
             int e = base + lane;
             int st = 0, j = 0, p = 0, img = 0;
-            float fx = 0.0f, fy = 0.0f, fz = 0.0f;
             if (e < ne) {
                 int2 ent = row[e];
                 j = ent.x;
                 img = ent.y;
                 float4 pj = a.posf[j];
+                float fx = pj.x - pfi.x, fy = pj.y - pfi.y, fz = pj.z - pfi.z;
                 float smax = 0.0f;
-                if (DF) {             // hi parts on the 2^-12 grid: this difference is exact
-                    float shx = 0.0f, shy = 0.0f, shz = 0.0f;
-                    if (img != 0) {
-                        int sx = img_x(img), sy = img_y(img), sz = img_z(img);
-                        if (a.sys || sx < -4 || sx > 4 || sy < -4 || sy > 4 || sz < -4 || sz > 4) {
-                            float l;
-                            df_split(sx * L[0], shx, l); df_split(sy * L[1], shy, l); df_split(sz * L[2], shz, l);
-                        } else {
-                            shx = shf[0][0][sx + 4]; shy = shf[0][1][sy + 4]; shz = shf[0][2][sz + 4];
-                        }
-                    }
-                    fx = __fsub_rn(__fadd_rn(pj.x, shx), pfi.x);
-                    fy = __fsub_rn(__fadd_rn(pj.y, shy), pfi.y);
-                    fz = __fsub_rn(__fadd_rn(pj.z, shz), pfi.z);
-                } else {
-                    fx = pj.x - pfi.x; fy = pj.y - pfi.y; fz = pj.z - pfi.z;
-                    if (img != 0) {
-                        int sx = img_x(img), sy = img_y(img), sz = img_z(img);
-                        fx += (float)sx * Lf[0]; fy += (float)sy * Lf[1]; fz += (float)sz * Lf[2];
-                        smax = (float)max(abs(sx), max(abs(sy), abs(sz)));
-                    }
+                if (img != 0) {
+                    int sx = img_x(img), sy = img_y(img), sz = img_z(img);
+                    fx += (float)sx * Lf[0]; fy += (float)sy * Lf[1]; fz += (float)sz * Lf[2];
+                    smax = (float)max(abs(sx), max(abs(sy), abs(sz)));
                 }
                 float r2f = fx * fx + fy * fy + fz * fz;
                 p = pidx(ti, __float_as_int(pj.w));
                 LjCuts<float> kf = cutsf[p];
-                // split positions: |dx - dx_hi| <= 3 * 2^-13 per component (the lo parts
-                // and the shift's), so |r2f - r2| <= 3.7e-4 (2 sqrt(3) 16 + 1.1e-3) + rounding
-                float band;
-                if (DF) {
-                    band = 0.025f + 1e-6f * r2f;
-                } else {
-                    float err = 2.3841858e-7f * (err0 + 4.0f * smax * Lmax);      // 2^-22 (...)
-                    band = err * (56.0f + 3.0f * err) + 1e-6f * r2f;
-                }
+                float err = 2.3841858e-7f * (err0 + 4.0f * smax * Lmax);      // 2^-22 (...)
+                float band = err * (56.0f + 3.0f * err) + 1e-6f * r2f;
                 bool near = fabsf(r2f - kf.rc2) <= band || fabsf(r2f - kf.srhi2) <= band ||
                             fabsf(r2f - kf.swlo2) <= band || fabsf(r2f - kf.rpath2) <= band;
                 R C;
@@ -600,7 +570,6 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
                 if (st == want) {
                     int s = cnt[b] + __popc(m & lt);
                     B.jp[b][s] = j | (p << 30); B.ia[b][s] = i; B.im[b][s] = img;
-                    if (DF) { B.hx[b][s] = fx; B.hy[b][s] = fy; B.hz[b][s] = fz; }
                 }
                 cnt[b] += __popc(m);
                 __syncwarp();
@@ -610,7 +579,6 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
                     if (lane < cnt[b] - 32) {
                         int s = 32 + lane;
                         B.jp[b][lane] = B.jp[b][s]; B.ia[b][lane] = B.ia[b][s]; B.im[b][lane] = B.im[b][s];
-                        if (DF) { B.hx[b][lane] = B.hx[b][s]; B.hy[b][lane] = B.hy[b][s]; B.hz[b][lane] = B.hz[b][s]; }
                     }
                     cnt[b] -= 32;
                     __syncwarp();
