@@ -347,8 +347,7 @@ struct airebo_ctx {
     int *cell_of = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cell_fill = nullptr;
     float4* spos = nullptr;
     float4* posf = nullptr;              // FP32 positions of the current step (LJ pair tests)
-    float4* pq_hi = nullptr;             // AIREBO_DF64: split positions and fixed-point LJ force sums
-    float4* pq_lo = nullptr;
+    float4* pq_lo = nullptr;             // split positions (lo parts) and fixed-point LJ force sums
     unsigned long long* fix = nullptr;
     char4* swrap = nullptr;
     // lists
@@ -499,7 +498,6 @@ airebo_status alloc_atoms(airebo_handle h, int n) {
     CK(realloc_dev(h->spos, na));
     CK(realloc_dev(h->posf, na));
     if (h->opt.precision != AIREBO_FP64) {
-        CK(realloc_dev(h->pq_hi, na));
         CK(realloc_dev(h->pq_lo, na));
         CK(realloc_dev(h->fix, 3 * (size_t)na));
     }
@@ -652,7 +650,6 @@ template <class R> StepArgs<R> make_args(airebo_handle h, Precision<R>& pr, cons
     a.pos = d_pos;
     a.posf = h->posf;
     bool df = df_on(h);
-    a.pq_hi = df ? h->pq_hi : nullptr;
     a.pq_lo = df ? h->pq_lo : nullptr;
     a.fix = df ? h->fix : nullptr;
     for (int d = 0; d < 3; d++) a.L[d] = h->L[d];
@@ -886,7 +883,7 @@ void airebo_destroy(airebo_handle h) {
         void* bs[] = {h->d_sys, h->d_snc, h->d_sreach, h->d_scell0, h->d_Lsys, h->d_scw, h->d_off, h->eatom};
         for (void* p : bs) if (p) cudaFree(p);
     }
-    void* ps[] = {h->types, h->cell_of, h->cell_count, h->cell_start, h->cell_fill, h->spos, h->posf, h->pq_hi, h->pq_lo, h->fix, h->swrap, h->lj, h->lj_cnt,
+    void* ps[] = {h->types, h->cell_of, h->cell_count, h->cell_start, h->cell_fill, h->spos, h->posf, h->pq_lo, h->fix, h->swrap, h->lj, h->lj_cnt,
                   h->im, h->im_cnt, h->xref, h->bonds, h->ccbonds, h->bq, h->bq2, h->counts, h->acc, h->counters, h->derr, h->maxd2, h->ke,
                   h->hpos, h->hvel, h->hforce, h->he4, h->hw6};
     for (void* p : ps) if (p) cudaFree(p);

@@ -36,7 +36,7 @@ template <class R> struct StepArgs {
     PathMap<R> M;
     const double* pos;
     float4* posf;                          // FP32 copy of the positions (written by the short-list kernel)
-    float4* pq_hi; float4* pq_lo;          // double-float LJ (AIREBO_DF64): split positions
+    float4* pq_lo;                         // split positions: the lo parts (posf holds the hi parts)
     unsigned long long* fix;               // double-float LJ: fixed-point force sums (3 x n), null otherwise
     double L[3];
     const int2* lj; const int* lj_cnt; int lj_cap;

@@ -92,15 +92,19 @@ __global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
     int n = a.n;
     double xi = a.pos[i], yi = a.pos[n + i], zi = a.pos[2 * n + i];
     if (!isfinite(xi) || !isfinite(yi) || !isfinite(zi)) atomicMax(a.err + ERR_NONFINITE, 1);
-    // FP32 position and species for the LJ kernel's pair tests
-    a.posf[i] = make_float4((float)xi, (float)yi, (float)zi, __int_as_float((int)a.G.type[i]));
-    if (a.fix) {                      // double-float LJ: hi on the 2^-12 grid, lo the rest
+    // FP32 position and species for the LJ kernel's pair tests; with split
+    // positions (fixed-point LJ sums) the FP32 position is the hi part, on the
+    // 2^-12 A grid, and pq_lo holds the rest
+    if (a.fix) {
         if (!(fabs(xi) < 2000.0 && fabs(yi) < 2000.0 && fabs(zi) < 2000.0)) atomicMax(a.err + ERR_DF, 1);
         float4 h, l;
         df_split(xi, h.x, l.x); df_split(yi, h.y, l.y); df_split(zi, h.z, l.z);
-        h.w = l.w = 0.0f;
-        a.pq_hi[i] = h;
+        h.w = __int_as_float((int)a.G.type[i]);
+        l.w = 0.0f;
+        a.posf[i] = h;
         a.pq_lo[i] = l;
+    } else {
+        a.posf[i] = make_float4((float)xi, (float)yi, (float)zi, __int_as_float((int)a.G.type[i]));
     }
     int ti = a.G.type[i];
     int cnt = 0;
@@ -312,7 +316,7 @@ __device__ __forceinline__ void lj_batch_df(const StepArgs<R>& a, const DfParams
         acc.flush(a.fix, a.n, a.eatom);
         acc.own = i;
     }
-    float4 hi = a.pq_hi[i], li = a.pq_lo[i], hj = a.pq_hi[j], lj = a.pq_lo[j];
+    float4 hi = a.posf[i], li = a.pq_lo[i], hj = a.posf[j], lj = a.pq_lo[j];
     float shx = 0.0f, shy = 0.0f, shz = 0.0f, slx = 0.0f, sly = 0.0f, slz = 0.0f;
     if (img != 0) {
         int sx = img_x(img), sy = img_y(img), sz = img_z(img);
@@ -386,7 +390,7 @@ __device__ __forceinline__ void lj_batch_mx(const StepArgs<R>& a, const DevParam
         acc.flush(a.fix, a.n, a.eatom);
         acc.own = i;
     }
-    float4 hi = a.pq_hi[i], li = a.pq_lo[i], hj = a.pq_hi[j], lj = a.pq_lo[j];
+    float4 hi = a.posf[i], li = a.pq_lo[i], hj = a.posf[j], lj = a.pq_lo[j];
     float shx = 0.0f, shy = 0.0f, shz = 0.0f, slx = 0.0f, sly = 0.0f, slz = 0.0f;
     if (img != 0) {
         int sx = img_x(img), sy = img_y(img), sz = img_z(img);
@@ -524,18 +528,43 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
                 j = ent.x;
                 img = ent.y;
                 float4 pj = a.posf[j];
-                float fx = pj.x - pfi.x, fy = pj.y - pfi.y, fz = pj.z - pfi.z;
+                float fx, fy, fz;
                 float smax = 0.0f;
-                if (img != 0) {
-                    int sx = img_x(img), sy = img_y(img), sz = img_z(img);
-                    fx += (float)sx * Lf[0]; fy += (float)sy * Lf[1]; fz += (float)sz * Lf[2];
-                    smax = (float)max(abs(sx), max(abs(sy), abs(sz)));
+                if (DF) {             // hi parts on the 2^-12 grid: this difference is exact
+                    float shx = 0.0f, shy = 0.0f, shz = 0.0f;
+                    if (img != 0) {
+                        int sx = img_x(img), sy = img_y(img), sz = img_z(img);
+                        if (a.sys || sx < -4 || sx > 4 || sy < -4 || sy > 4 || sz < -4 || sz > 4) {
+                            float l;
+                            df_split(sx * L[0], shx, l); df_split(sy * L[1], shy, l); df_split(sz * L[2], shz, l);
+                        } else {
+                            shx = shf[0][0][sx + 4]; shy = shf[0][1][sy + 4]; shz = shf[0][2][sz + 4];
+                        }
+                    }
+                    fx = __fsub_rn(__fadd_rn(pj.x, shx), pfi.x);
+                    fy = __fsub_rn(__fadd_rn(pj.y, shy), pfi.y);
+                    fz = __fsub_rn(__fadd_rn(pj.z, shz), pfi.z);
+                } else {
+                    fx = pj.x - pfi.x; fy = pj.y - pfi.y; fz = pj.z - pfi.z;
+                    if (img != 0) {
+                        int sx = img_x(img), sy = img_y(img), sz = img_z(img);
+                        fx += (float)sx * Lf[0]; fy += (float)sy * Lf[1]; fz += (float)sz * Lf[2];
+                        smax = (float)max(abs(sx), max(abs(sy), abs(sz)));
+                    }
                 }
                 float r2f = fx * fx + fy * fy + fz * fz;
                 p = pidx(ti, __float_as_int(pj.w));
                 LjCuts<float> kf = cutsf[p];
-                float err = 2.3841858e-7f * (err0 + 4.0f * smax * Lmax);      // 2^-22 (...)
-                float band = err * (56.0f + 3.0f * err) + 1e-6f * r2f;
+                // with split positions |dx - dx_hi| <= 3 * 2^-13 per component (the lo
+                // parts and the shift's), so |r2f - r2| <= 3.7e-4 (2 sqrt(3) 16 + 1.1e-3)
+                // plus the rounding of r2f
+                float band;
+                if (DF) {
+                    band = 0.025f + 1e-6f * r2f;
+                } else {
+                    float err = 2.3841858e-7f * (err0 + 4.0f * smax * Lmax);      // 2^-22 (...)
+                    band = err * (56.0f + 3.0f * err) + 1e-6f * r2f;
+                }
                 bool near = fabsf(r2f - kf.rc2) <= band || fabsf(r2f - kf.srhi2) <= band ||
                             fabsf(r2f - kf.swlo2) <= band || fabsf(r2f - kf.rpath2) <= band;
                 R C;
