@@ -45,6 +45,11 @@ TEMP = 300.0
 # Algorithmic FP64 work per unit, in flops (FMA = 2); see the roofline notes in the design doc.
 FLOPS_LJ_PAIR = 44        # displacement with image (9), r^2 (5), sqrt, 1/r, (s/r)^6, V, dV/dr, force, sums (30)
 FLOPS_LJ_TEST = 14        # displacement and r^2 of a pair that is tested but not evaluated (C = 0, or queued for b*)
+# DRAM bytes (read + write) per atom of one k_lj<double> launch, measured by ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum) on the 261,120-atom PE with
+# the same kernel: 687.4 MB per launch.  The traffic is the list read, whose
+# length per atom the density fixes, so it scales with the atom count.
+LJ_DRAM_BYTES_PER_ATOM = 687.4e6 / 261120
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 FP64_FMA_PER_SM_CLK = 2   # 1.25 TFLOP/s nominal FP64 = 152 SMs x 2 FMA x 2 flop x 2.07 GHz
@@ -365,14 +370,16 @@ def run_ours(args):
         mix_kt = results["mixed"]["kt"]
         mlj_ms, mlj_n = mix_kt["lj"]
         roof = {"kernel": "k_lj<double>", "bound": "alu", "achieved": achieved, "peak": peak64_nom,
-                "unit": "TFLOP/s", "frac": (achieved / peak64_nom) if achieved else None, "traffic": None,
+                "unit": "TFLOP/s", "frac": (achieved / peak64_nom) if achieved else None,
+                "traffic": LJ_DRAM_BYTES_PER_ATOM * n if args.workload.startswith("pe") else None,
+                "traffic_unit": "bytes per launch (ncu, 261,120-atom PE, scaled by atoms)",
                 "peak_kind": "FP64 nominal from SM count x FMA units x max clock; measured FMA probe beside it",
                 "peak_measured": peak64_meas,
                 "flops_per_launch": flops_lj, "avg_launch_ms": lj_avg_s * 1e3,
                 "dominant_kernel": dom}
         # kernels of one NVE step: 2 half kicks, short list, REBO, torsion, map,
-        # LJ, b*, b* reverse, counters, energy write; 4 more per list rebuild
-        launches = 11 * args.steps + 4 * r64["builds"]
+        # LJ, b*, b* reverse, counters, energy write; 5 more per list rebuild
+        launches = 11 * args.steps + 5 * r64["builds"]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r64["ms"] / args.steps, "higher_is_better": True,

@@ -370,6 +370,7 @@ struct airebo_ctx {
     std::vector<long long> off_h;
     int *d_sys = nullptr, *d_snc = nullptr, *d_sreach = nullptr, *d_scell0 = nullptr;
     double *d_Lsys = nullptr, *d_scw = nullptr;
+    float4* d_Lhl = nullptr;             // per system: box edges split as hi (2^-12 grid) + lo
     long long* d_off = nullptr;
     double* eatom = nullptr;
     int eatom_n = 0;
@@ -651,6 +652,7 @@ template <class R> StepArgs<R> make_args(airebo_handle h, Precision<R>& pr, cons
     a.posf = h->posf;
     bool df = df_on(h);
     a.pq_lo = df ? h->pq_lo : nullptr;
+    a.Lhl = h->d_Lhl;
     a.fix = df ? h->fix : nullptr;
     for (int d = 0; d < 3; d++) a.L[d] = h->L[d];
     a.lj = h->lj; a.lj_cnt = h->lj_cnt; a.lj_cap = h->lj_cap;
@@ -800,6 +802,25 @@ airebo_status check_rebuild(airebo_handle h, const double* d_pos, int* flag) {
     return AIREBO_OK;
 }
 
+// the split (hi on the 2^-12 A grid, lo the rest) of every system's box edges,
+// for the image shifts of the LJ kernel on split positions
+airebo_status upload_Lhl(airebo_handle h, const double* boxes, int nsys) {
+    std::vector<float4> v(2 * (size_t)nsys);
+    for (int s = 0; s < nsys; s++) {
+        float hi[3], lo[3];
+        for (int d = 0; d < 3; d++) {
+            double q = std::rint(boxes[3 * s + d] * 4096.0) / 4096.0;
+            hi[d] = (float)q;
+            lo[d] = (float)(boxes[3 * s + d] - q);
+        }
+        v[2 * s] = make_float4(hi[0], hi[1], hi[2], 0.0f);
+        v[2 * s + 1] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+    }
+    CK(realloc_dev(h->d_Lhl, v.size()));
+    CK(cudaMemcpy(h->d_Lhl, v.data(), sizeof(float4) * v.size(), cudaMemcpyHostToDevice));
+    return AIREBO_OK;
+}
+
 airebo_status set_system(airebo_handle h, const int8_t* d_types, int64_t n, const double* box, bool types_on_host) {
     if (n < 0 || n > (1LL << 30)) return fail(h, AIREBO_ERR_ARG, "atom count out of range");
     if (!box) return fail(h, AIREBO_ERR_ARG, "box is null");
@@ -814,6 +835,8 @@ airebo_status set_system(airebo_handle h, const int8_t* d_types, int64_t n, cons
     CK(realloc_dev(h->d_off, 2));
     CK(cudaMemcpy(h->d_off, h->off_h.data(), sizeof(long long) * 2, cudaMemcpyHostToDevice));
     for (int d = 0; d < 3; d++) h->L[d] = box[d];
+    st = upload_Lhl(h, box, 1);
+    if (st) return st;
     if (n) CK(cudaMemcpyAsync(h->types, d_types, n, types_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->stream));
     return AIREBO_OK;
 }
@@ -880,7 +903,7 @@ void airebo_destroy(airebo_handle h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->graph) cudaGraphDestroy(h->graph);
     {
-        void* bs[] = {h->d_sys, h->d_snc, h->d_sreach, h->d_scell0, h->d_Lsys, h->d_scw, h->d_off, h->eatom};
+        void* bs[] = {h->d_sys, h->d_snc, h->d_sreach, h->d_scell0, h->d_Lsys, h->d_scw, h->d_off, h->eatom, h->d_Lhl};
         for (void* p : bs) if (p) cudaFree(p);
     }
     void* ps[] = {h->types, h->cell_of, h->cell_count, h->cell_start, h->cell_fill, h->spos, h->posf, h->pq_lo, h->fix, h->swrap, h->lj, h->lj_cnt,
@@ -1095,6 +1118,8 @@ airebo_status airebo_neighbor_batch(airebo_handle h, const double* d_pos, const 
     CK(cudaMemcpy(h->d_sys, sys.data(), sizeof(int) * sys.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(h->d_Lsys, h_boxes, sizeof(double) * 3 * nsys, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(h->d_off, h->off_h.data(), sizeof(long long) * (nsys + 1), cudaMemcpyHostToDevice));
+    st = upload_Lhl(h, h_boxes, nsys);
+    if (st) return st;
     return do_neighbor(h, d_pos);
 }
 

@@ -37,6 +37,7 @@ template <class R> struct StepArgs {
     const double* pos;
     float4* posf;                          // FP32 copy of the positions (written by the short-list kernel)
     float4* pq_lo;                         // split positions: the lo parts (posf holds the hi parts)
+    const float4* Lhl;                     // per system: box edges split as hi + lo (2 float4)
     unsigned long long* fix;               // double-float LJ: fixed-point force sums (3 x n), null otherwise
     double L[3];
     const int2* lj; const int* lj_cnt; int lj_cap;

@@ -304,6 +304,27 @@ struct DfLaneAcc {
     }
 };
 
+// Image shift S L of a split-position pair as hi + lo: from the table of the
+// single box for |S| <= 4, from the system's split box edges for |S| <= 1
+// (hi times -1, 0 or 1 stays exact), else split here in FP64 (tiny boxes)
+template <class R>
+__device__ __forceinline__ void shift_split(const StepArgs<R>& a, const float (*sh)[9], const float (*sl)[9],
+                                            int i, int img, float* h, float* l) {
+    int s3[3] = {img_x(img), img_y(img), img_z(img)};
+    bool small = s3[0] >= -1 && s3[0] <= 1 && s3[1] >= -1 && s3[1] <= 1 && s3[2] >= -1 && s3[2] <= 1;
+    if (!a.sys && s3[0] >= -4 && s3[0] <= 4 && s3[1] >= -4 && s3[1] <= 4 && s3[2] >= -4 && s3[2] <= 4) {
+        for (int d = 0; d < 3; d++) { h[d] = sh[d][s3[d] + 4]; l[d] = sl[d][s3[d] + 4]; }
+    } else if (small) {
+        int sy = a.sys[i];
+        float4 bh = a.Lhl[2 * sy], bl = a.Lhl[2 * sy + 1];
+        h[0] = (float)s3[0] * bh.x; h[1] = (float)s3[1] * bh.y; h[2] = (float)s3[2] * bh.z;
+        l[0] = (float)s3[0] * bl.x; l[1] = (float)s3[1] * bl.y; l[2] = (float)s3[2] * bl.z;
+    } else {
+        const double* L = box_of(a, i);
+        for (int d = 0; d < 3; d++) df_split(s3[d] * L[d], h[d], l[d]);
+    }
+}
+
 template <class R>
 __device__ __forceinline__ void lj_batch_df(const StepArgs<R>& a, const DfParams& D, const float (*sh)[9],
                                             const float (*sl)[9], LjBuf& B, int b, int lane, DfLaneAcc& acc,
@@ -319,14 +340,9 @@ __device__ __forceinline__ void lj_batch_df(const StepArgs<R>& a, const DfParams
     float4 hi = a.posf[i], li = a.pq_lo[i], hj = a.posf[j], lj = a.pq_lo[j];
     float shx = 0.0f, shy = 0.0f, shz = 0.0f, slx = 0.0f, sly = 0.0f, slz = 0.0f;
     if (img != 0) {
-        int sx = img_x(img), sy = img_y(img), sz = img_z(img);
-        if (a.sys || sx < -4 || sx > 4 || sy < -4 || sy > 4 || sz < -4 || sz > 4) {
-            const double* L = box_of(a, i);
-            df_split(sx * L[0], shx, slx); df_split(sy * L[1], shy, sly); df_split(sz * L[2], shz, slz);
-        } else {
-            shx = sh[0][sx + 4]; shy = sh[1][sy + 4]; shz = sh[2][sz + 4];
-            slx = sl[0][sx + 4]; sly = sl[1][sy + 4]; slz = sl[2][sz + 4];
-        }
+        float h[3], l[3];
+        shift_split<R>(a, sh, sl, i, img, h, l);
+        shx = h[0]; shy = h[1]; shz = h[2]; slx = l[0]; sly = l[1]; slz = l[2];
     }
     // hi parts: exact (multiples of 2^-12 below 2^12 in magnitude); lo parts: rounded
     ff dx = two_sum(__fsub_rn(__fadd_rn(hj.x, shx), hi.x), __fsub_rn(__fadd_rn(lj.x, slx), li.x));
@@ -393,14 +409,9 @@ __device__ __forceinline__ void lj_batch_mx(const StepArgs<R>& a, const DevParam
     float4 hi = a.posf[i], li = a.pq_lo[i], hj = a.posf[j], lj = a.pq_lo[j];
     float shx = 0.0f, shy = 0.0f, shz = 0.0f, slx = 0.0f, sly = 0.0f, slz = 0.0f;
     if (img != 0) {
-        int sx = img_x(img), sy = img_y(img), sz = img_z(img);
-        if (a.sys || sx < -4 || sx > 4 || sy < -4 || sy > 4 || sz < -4 || sz > 4) {
-            const double* L = box_of(a, i);
-            df_split(sx * L[0], shx, slx); df_split(sy * L[1], shy, sly); df_split(sz * L[2], shz, slz);
-        } else {
-            shx = sh[0][sx + 4]; shy = sh[1][sy + 4]; shz = sh[2][sz + 4];
-            slx = sl[0][sx + 4]; sly = sl[1][sy + 4]; slz = sl[2][sz + 4];
-        }
+        float h[3], l[3];
+        shift_split<R>(a, sh, sl, i, img, h, l);
+        shx = h[0]; shy = h[1]; shz = h[2]; slx = l[0]; sly = l[1]; slz = l[2];
     }
     float rx = __fadd_rn(__fsub_rn(__fadd_rn(hj.x, shx), hi.x), __fsub_rn(__fadd_rn(lj.x, slx), li.x));
     float ry = __fadd_rn(__fsub_rn(__fadd_rn(hj.y, shy), hi.y), __fsub_rn(__fadd_rn(lj.y, sly), li.y));
@@ -533,13 +544,9 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
                 if (DF) {             // hi parts on the 2^-12 grid: this difference is exact
                     float shx = 0.0f, shy = 0.0f, shz = 0.0f;
                     if (img != 0) {
-                        int sx = img_x(img), sy = img_y(img), sz = img_z(img);
-                        if (a.sys || sx < -4 || sx > 4 || sy < -4 || sy > 4 || sz < -4 || sz > 4) {
-                            float l;
-                            df_split(sx * L[0], shx, l); df_split(sy * L[1], shy, l); df_split(sz * L[2], shz, l);
-                        } else {
-                            shx = shf[0][0][sx + 4]; shy = shf[0][1][sy + 4]; shz = shf[0][2][sz + 4];
-                        }
+                        float h[3], l[3];
+                        shift_split<R>(a, shf[0], shf[1], i, img, h, l);
+                        shx = h[0]; shy = h[1]; shz = h[2];
                     }
                     fx = __fsub_rn(__fadd_rn(pj.x, shx), pfi.x);
                     fy = __fsub_rn(__fadd_rn(pj.y, shy), pfi.y);
