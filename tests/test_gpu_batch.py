@@ -29,7 +29,7 @@ def systems():
     return out, pos, types, offsets, boxes
 
 
-@pytest.mark.parametrize("precision,etol,ftol", [(0, 1e-10, 1e-8), (1, 1e-5, 1e-4)])
+@pytest.mark.parametrize("precision,etol,ftol", [(0, 1e-10, 1e-8), (1, 1e-5, 1e-4), (2, 1e-10, 1e-8)])
 def test_batched_systems_match_oracle(A, param_text, precision, etol, ftol):
     sysl, pos, types, offsets, boxes = systems()
     ev = A.Airebo(param_text, precision=precision)
@@ -48,11 +48,12 @@ def test_batched_systems_match_oracle(A, param_text, precision, etol, ftol):
     assert abs(e.sum() - e4[0].item()) <= 1e-12 * abs(e4[0].item())
 
 
-def test_graph_and_async_reproduce_sync(A, param_text):
+@pytest.mark.parametrize("precision", [1, 2])
+def test_graph_and_async_reproduce_sync(A, param_text, precision):
     sysl, pos, types, offsets, boxes = systems()
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        ev = A.Airebo(param_text, precision=A.MIXED, stream=stream)
+        ev = A.Airebo(param_text, precision=precision, stream=stream)
         p = torch.tensor(pos, device="cuda")
         ev.neighbor_batch(p, torch.tensor(types, device="cuda"), offsets, boxes)
         f0, e0 = ev.compute_batch(p)

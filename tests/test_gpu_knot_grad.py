@@ -102,6 +102,18 @@ def test_knot_grad_all_blocks_and_largest_components(A, case):
             o += c
 
 
+def test_knot_grad_same_in_df64(A, case):
+    """The knots enter only through bond orders, which run in FP64 in both
+    precisions: DF64's gradient equals FP64's up to summation order."""
+    params, pos, types, box, g, *_ = case
+    ev = A.Airebo(inputs.params_text(params), precision=A.DF64)
+    p = torch.tensor(pos, device="cuda")
+    ev.neighbor(p, torch.tensor(types, device="cuda"), box)
+    _, _, g2 = ev.knot_grad(p)
+    ev.close()
+    assert np.abs(g2 - g).max() <= 1e-10 * np.abs(g).max()
+
+
 def test_knot_grad_count_checked(A, case):
     params, pos, types, box, *_ = case
     ev = A.Airebo(inputs.params_text(params))
