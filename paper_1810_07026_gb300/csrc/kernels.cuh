@@ -78,9 +78,13 @@ __device__ __forceinline__ const double* box_of(const StepArgs<R>& a, int i) {
 
 __device__ __forceinline__ void load_disp(const double* pos, int n, const double* L, int i, int j, int img,
                                           double& dx, double& dy, double& dz) {
-    dx = pos[j] + img_x(img) * L[0] - pos[i];
-    dy = pos[n + j] + img_y(img) * L[1] - pos[n + i];
-    dz = pos[2 * n + j] + img_z(img) * L[2] - pos[2 * n + i];
+    if (img == 0) {
+        dx = pos[j] - pos[i]; dy = pos[n + j] - pos[n + i]; dz = pos[2 * n + j] - pos[2 * n + i];
+    } else {
+        dx = pos[j] + img_x(img) * L[0] - pos[i];
+        dy = pos[n + j] + img_y(img) * L[1] - pos[n + i];
+        dz = pos[2 * n + j] + img_z(img) * L[2] - pos[2 * n + i];
+    }
 }
 
 // ------------------------------------------------------------------ short list
@@ -115,9 +119,14 @@ __global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
     for (int e = 0; e < ne; e++) {
         int2 ent = row[e];
         int j = ent.x, img = ent.y;
-        double dx = a.pos[j] + img_x(img) * L[0] - xi;
-        double dy = a.pos[n + j] + img_y(img) * L[1] - yi;
-        double dz = a.pos[2 * n + j] + img_z(img) * L[2] - zi;
+        double dx, dy, dz;
+        if (img == 0) {               // most entries: no image, three FP64 operations
+            dx = a.pos[j] - xi; dy = a.pos[n + j] - yi; dz = a.pos[2 * n + j] - zi;
+        } else {
+            dx = a.pos[j] + img_x(img) * L[0] - xi;
+            dy = a.pos[n + j] + img_y(img) * L[1] - yi;
+            dz = a.pos[2 * n + j] + img_z(img) * L[2] - zi;
+        }
         double r2 = dx * dx + dy * dy + dz * dz;
         int tj = a.G.type[j];
         int p = pidx(ti, tj);
