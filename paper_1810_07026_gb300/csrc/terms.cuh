@@ -106,6 +106,21 @@ HD double sqrt_(double x) { return sqrt(x); }
 HD float sqrt_(float x) { return sqrtf(x); }
 HD double exp_(double x) { return exp(x); }
 HD float exp_(float x) { return expf(x); }
+// t == 0 (either sign) by the bit pattern: an integer test, no FP64 compare
+HD bool is_zero(double t) {
+#ifdef __CUDA_ARCH__
+    return (__double_as_longlong(t) << 1) == 0;
+#else
+    return t == 0.0;
+#endif
+}
+HD bool is_zero(float t) {
+#ifdef __CUDA_ARCH__
+    return (__float_as_int(t) << 1) == 0;
+#else
+    return t == 0.0f;
+#endif
+}
 HD void sincospi_(double t, double* s, double* c) {
 #ifdef __CUDA_ARCH__
     sincospi(t, s, c);
@@ -248,6 +263,11 @@ template <class R, bool D = true> HD R bicubic(const R* tab, R x, R y, R& fx, R&
     int iy = clamp_cell((int)floor(y), 3);
     R tx = x - R(ix), ty = y - R(iy);
     const R* a = tab + (ix * 4 + iy) * 16;
+    if (is_zero(tx) && is_zero(ty)) {        // at a knot (integer N^C, N^H): the corner coefficients
+        fx = (D && !cx) ? a[4] : R(0);
+        fy = (D && !cy) ? a[1] : R(0);
+        return a[0];
+    }
     R f = 0, dx = 0, dy = 0;
     for (int p = 3; p >= 0; p--) {
         const R* c = a + p * 4;
@@ -277,6 +297,12 @@ template <class R> HD int tri_cell_index(R& x, R& y, R& z, bool& clx, bool& cly,
 }
 template <class R, bool D = true>
 HD R tricubic_cell(const R* a, R tx, R ty, R tz, bool clx, bool cly, bool clz, R& fx, R& fy, R& fz) {
+    if (is_zero(tx) && is_zero(ty) && is_zero(tz)) {   // at a knot: the corner coefficients
+        fx = (D && !clx) ? a[16] : R(0);
+        fy = (D && !cly) ? a[4] : R(0);
+        fz = (D && !clz) ? a[1] : R(0);
+        return a[0];
+    }
     R f = 0, dx = 0, dy = 0, dz = 0;
     for (int p = 3; p >= 0; p--) {
         R cp = 0, cpy = 0, cpz = 0;
