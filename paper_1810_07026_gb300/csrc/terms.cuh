@@ -21,6 +21,7 @@
 
 #include <cstdint>
 #include <cmath>
+#include <cstring>
 
 #ifdef __CUDACC__
 #define HD __host__ __device__ __forceinline__
@@ -186,11 +187,47 @@ HD bool lt_nonneg(double a, double b) {
 }
 HD bool lt_nonneg(float a, float b) { return a < b; }
 
+// Ordered comparisons of FP64 values as 64-bit integers: the sign-magnitude
+// bit pattern turned into two's complement orders like the values (-0 maps
+// to 0; a NaN sorts beyond the infinity of its sign).  Comparisons are
+// frequent in the splines, switches and clamps of the bond order, and an FP64
+// compare takes an FP64-pipe issue; these take integer operations.  FP32
+// values compare natively.
+HD long long okey(double x) {
+#ifdef __CUDA_ARCH__
+    long long b = __double_as_longlong(x);
+#else
+    long long b;
+    memcpy(&b, &x, sizeof(b));
+#endif
+    return b < 0 ? -(b & 0x7fffffffffffffffLL) : b;
+}
+HD bool lt_(double a, double b) {
+#ifdef __CUDA_ARCH__
+    return okey(a) < okey(b);
+#else
+    return a < b;
+#endif
+}
+HD bool lt_(float a, float b) { return a < b; }
+template <class R> HD bool gt_(R a, R b) { return lt_(b, a); }
+template <class R> HD bool le_(R a, R b) { return !lt_(b, a); }
+template <class R> HD bool ge_(R a, R b) { return !lt_(a, b); }
+// clamp to [lo, hi]; for FP64 a NaN ends at one of the ends (its key lies
+// beyond the infinities), for FP32 at lo
+template <class R> HD R clamp_(R x, R lo, R hi, bool& cl) {
+    cl = false;
+    if (lt_(x, lo)) { x = lo; cl = true; }
+    if (gt_(x, hi)) { x = hi; cl = true; }
+    if (sizeof(R) == 4 && !(x == x)) { x = lo; cl = true; }
+    return x;
+}
+
 // ------------------------------------------------------------------ switches
 // S(t) = 1 for t <= 0, 0 for t >= 1, (1 + cos pi t)/2 between; dS = dS/dt
 template <class R> HD R Sw(R t, R& dS) {
-    if (t <= R(0)) { dS = R(0); return R(1); }
-    if (t >= R(1)) { dS = R(0); return R(0); }
+    if (le_(t, R(0))) { dS = R(0); return R(1); }
+    if (ge_(t, R(1))) { dS = R(0); return R(0); }
     R s, c;
     sincospi_(t, &s, &c);
     dS = R(-0.5 * M_PI) * s;
@@ -207,24 +244,22 @@ template <class R> HD R wfun(const DevParams<R>& P, int p, R r, R& dw) {
 // so that C_ij = 1 - w keeps its relative precision when w is close to 1
 template <class R> HD R wfun_c(const DevParams<R>& P, int p, R r, R& dw, R& omw) {
     R t = (r - P.Dmin[p]) * P.Dinv[p];
-    if (t <= R(0)) { dw = R(0); omw = R(0); return R(1); }
-    if (t >= R(1)) { dw = R(0); omw = R(1); return R(0); }
+    if (le_(t, R(0))) { dw = R(0); omw = R(0); return R(1); }
+    if (ge_(t, R(1))) { dw = R(0); omw = R(1); return R(0); }
     R s, c;
     sincospi_(t, &s, &c);
     dw = R(-0.5 * M_PI) * s * P.Dinv[p];
-    omw = c > R(0) ? R(0.5) * s * s * rcp_(R(1) + c) : R(0.5) * (R(1) - c);
+    omw = gt_(c, R(0)) ? R(0.5) * s * s * rcp_(R(1) + c) : R(0.5) * (R(1) - c);
     return R(0.5) * (R(1) + c);
 }
 
 // ------------------------------------------------------------------ splines
 // D = true: value and derivative(s); D = false: value only
 template <class R, bool D = true> HD R quintic(const Quintic<R>& q, R x, R& dfdx) {
-    bool cl = false;
-    if (x < q.k[0]) { x = q.k[0]; cl = true; }
-    if (x > q.k[q.n]) { x = q.k[q.n]; cl = true; }
-    if (!(x == x)) { x = q.k[0]; cl = true; }
+    bool cl;
+    x = clamp_<R>(x, q.k[0], q.k[q.n], cl);
     int m = 0;
-    while (m + 1 < q.n && x > q.k[m + 1]) m++;
+    while (m + 1 < q.n && gt_(x, q.k[m + 1])) m++;
     R t = (x - q.k[m]) * q.invh[m];
     const R* a = q.a[m];
     R f = a[5];
@@ -246,12 +281,8 @@ template <class R, bool D = true> HD R quintic(const Quintic<R>& q, R x, R& dfdx
     return f;
 }
 
-template <class R> HD void clamp_arg(R& x, R lo, R hi, bool& cl) {
-    cl = false;
-    if (x < lo) { x = lo; cl = true; }
-    if (x > hi) { x = hi; cl = true; }
-    if (!(x == x)) { x = lo; cl = true; }      // NaN: keep every table index in range
-}
+// clamp a spline argument (a NaN too: every table index stays in range)
+template <class R> HD void clamp_arg(R& x, R lo, R hi, bool& cl) { x = clamp_<R>(x, lo, hi, cl); }
 HD int clamp_cell(int c, int hi) { return c < 0 ? 0 : (c > hi ? hi : c); }
 
 // bicubic on the integer grid [0,4]^2, 16 power-basis coefficients per cell
@@ -333,11 +364,10 @@ HD R tricubic_cell(const R* a, R tx, R ty, R tz, bool clx, bool cly, bool clz, R
 // spline here is linear in its power-basis coefficients, so d value / d a_m
 // is the monomial m at the (clamped) local coordinates; adj = dE/d value.
 template <class R> HD void kg_quintic(double* g, const Quintic<R>& q, R x, double adj) {
-    if (x < q.k[0]) x = q.k[0];
-    if (x > q.k[q.n]) x = q.k[q.n];
-    if (!(x == x)) x = q.k[0];
+    bool cl;
+    x = clamp_<R>(x, q.k[0], q.k[q.n], cl);
     int m = 0;
-    while (m + 1 < q.n && x > q.k[m + 1]) m++;
+    while (m + 1 < q.n && gt_(x, q.k[m + 1])) m++;
     double t = (double)((x - q.k[m]) * q.invh[m]), tp = 1.0;
     for (int p = 0; p < 6; p++, tp *= t) atomic_add(g + m * 6 + p, adj * tp);
 }
@@ -439,8 +469,8 @@ HD R gfun(const DevParams<R>& P, int tc, R cs, R N, R& dg_dcos, R& dg_dN) {
     if (tc == 0) {
         R dQ;
         R Qn = Sw<R>((N - P.gN0) * P.gNinv, dQ);
-        if (Qn == R(1)) return quintic<R, D>(P.gC2, cs, dg_dcos);
-        if (Qn == R(0)) return quintic<R, D>(P.gC1, cs, dg_dcos);
+        if (ge_(Qn, R(1))) return quintic<R, D>(P.gC2, cs, dg_dcos);
+        if (le_(Qn, R(0))) return quintic<R, D>(P.gC1, cs, dg_dcos);
         R d1, d2;
         R G = quintic<R, D>(P.gC1, cs, d1);
         R gam = quintic<R, D>(P.gC2, cs, d2);
@@ -458,8 +488,8 @@ template <class R> HD void kg_gfun(const DevParams<R>& P, int tc, R cs, R N, dou
     if (tc == 0) {
         R dQ;
         R Qn = Sw<R>((N - P.gN0) * P.gNinv, dQ);
-        if (Qn != R(0)) kg_quintic<R>(P.kg + KG_GC2, P.gC2, cs, adj * (double)Qn);
-        if (Qn != R(1)) kg_quintic<R>(P.kg + KG_GC1, P.gC1, cs, adj * (1.0 - (double)Qn));
+        if (!is_zero(Qn)) kg_quintic<R>(P.kg + KG_GC2, P.gC2, cs, adj * (double)Qn);
+        if (lt_(Qn, R(1))) kg_quintic<R>(P.kg + KG_GC1, P.gC1, cs, adj * (1.0 - (double)Qn));
         return;
     }
     kg_quintic<R>(P.kg + KG_GH, P.gH, cs, adj);
@@ -500,7 +530,8 @@ HD void side_forward(const DevParams<R>& P, const Graph<R>& G, int c, int o, R u
         int q = c * G.stride + a;
         int k = G.nj[q];
         R cs = (ux * G.dx[q] + uy * G.dy[q] + uz * G.dz[q]) * inv_u * G.ir[q];
-        cs = cs < R(-1) ? R(-1) : (cs > R(1) ? R(1) : cs);
+        bool clc;
+        cs = clamp_<R>(cs, R(-1), R(1), clc);
         R dgc, dgN;
         R g = gfun<R, D>(P, tc, cs, s.N, dgc, dgN);
         R e = exp_lambda<R>(P, tc, G.type[k], to, G.r[q], umag);
@@ -543,8 +574,8 @@ HD void side_reverse(const DevParams<R>& P, const Graph<R>& G, int c, int o, R u
         R dxk = G.dx[q], dyk = G.dy[q], dzk = G.dz[q];
         R rck = G.r[q], inv_r = G.ir[q], w = G.w[q], dw = G.dw[q];
         R cs_raw = (ux * dxk + uy * dyk + uz * dzk) * inv_u * inv_r;
-        bool cl = cs_raw < R(-1) || cs_raw > R(1);
-        R cs = cs_raw < R(-1) ? R(-1) : (cs_raw > R(1) ? R(1) : cs_raw);
+        bool cl;
+        R cs = clamp_<R>(cs_raw, R(-1), R(1), cl);
         R dgc, dgN;
         R g = gfun<R, true>(P, tc, cs, s.N, dgc, dgN);
         R e = exp_lambda<R>(P, tc, tk, to, rck, umag);
@@ -576,7 +607,7 @@ HD void side_reverse(const DevParams<R>& P, const Graph<R>& G, int c, int o, R u
         guz += a1 * dzk - a3 * uz;
         sink.half(k, dxk, dyk, dzk, gxk, gyk, gzk, fcx, fcy, fcz);
         // conjugation: x_ck = sum_{m in N(k), m != c} w_km
-        if (tk == 0 && dFx != R(0) && dEdconj != R(0)) {
+        if (tk == 0 && !is_zero(dFx) && !is_zero(dEdconj)) {
             R coef = dEdconj * w * dFx;
             int nk = G.cnt[k];
             for (int b = 0; b < nk; b++) {
@@ -584,7 +615,7 @@ HD void side_reverse(const DevParams<R>& P, const Graph<R>& G, int c, int o, R u
                 int m = G.nj[qq];
                 if (m == c) continue;
                 R dwm = G.dw[qq];
-                if (dwm == R(0)) continue;
+                if (is_zero(dwm)) continue;
                 R t = coef * dwm * G.ir[qq];
                 sink.pair(k, m, G.dx[qq], G.dy[qq], G.dz[qq], t * G.dx[qq], t * G.dy[qq], t * G.dz[qq]);
             }
@@ -594,10 +625,11 @@ HD void side_reverse(const DevParams<R>& P, const Graph<R>& G, int c, int o, R u
 
 // angle guard of the dihedral sums: 1 unless |cos| is within the guard band of 1
 template <class R> HD R guardf(const DevParams<R>& P, R cs, R& dgd) {
-    R a = cs < R(0) ? -cs : cs;
+    bool neg = lt_(cs, R(0));
+    R a = neg ? -cs : cs;
     R dS;
     R g = Sw<R>((a - P.guard0) * P.guardinv, dS);
-    dgd = dS * P.guardinv * (cs < R(0) ? R(-1) : R(1));
+    dgd = dS * P.guardinv * (neg ? R(-1) : R(1));
     return g;
 }
 
@@ -620,7 +652,7 @@ HD R dihedral_sum(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, 
         R csi = (ux * ax + uy * ay + uz * az) * inv_u * inv_ra;
         R dsi;
         R si = guardf<R>(P, csi, dsi);
-        if (si == R(0)) continue;
+        if (is_zero(si)) continue;
         // n1 = u x a
         R n1x = uy * az - uz * ay, n1y = uz * ax - ux * az, n1z = ux * ay - uy * ax;
         R n1s = n1x * n1x + n1y * n1y + n1z * n1z;
@@ -635,7 +667,7 @@ HD R dihedral_sum(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, 
             R csj = -(ux * bx + uy * by + uz * bz) * inv_u * inv_rb;
             R dsj;
             R sj = guardf<R>(P, csj, dsj);
-            if (sj == R(0)) continue;
+            if (is_zero(sj)) continue;
             R n2x = uy * bz - uz * by, n2y = uz * bx - ux * bz, n2z = ux * by - uy * bx;
             R n2s = n2x * n2x + n2y * n2y + n2z * n2z;
             R inv12 = rsqrt_(n1s * n2s);
@@ -730,7 +762,7 @@ HD R bond_order(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, R 
         bsw->Sb = Sw<R>((b - bsw->bmin) * bsw->binv, dS);
         bsw->dSb = dS * bsw->binv;
         eps = bsw->scale * bsw->dSb;
-        if (eps == R(0)) return b;      // no gradient flows through b* (nor to the spline knots)
+        if (is_zero(eps)) return b;     // no gradient flows through b* (nor to the spline knots)
     }
     if (P.kg) {
         kg_tricubic<R>(P.kg + KG_F + (tab * NTRI_CELLS + cell) * 64, tx, ty, tz, (double)eps);
@@ -818,7 +850,7 @@ HD double torsion_bond(const DevParams<R>& P, const Graph<R>& G, int i, int slot
         R csi = (ux * ax + uy * ay + uz * az) * inv_u * inv_ra;
         R dsi;
         R si = guardf<R>(P, csi, dsi);
-        if (si == R(0)) continue;
+        if (is_zero(si)) continue;
         R n1x = uy * az - uz * ay, n1y = uz * ax - ux * az, n1z = ux * ay - uy * ax;
         R n1s = n1x * n1x + n1y * n1y + n1z * n1z;
         R in1s = rcp_(n1s);
@@ -833,7 +865,7 @@ HD double torsion_bond(const DevParams<R>& P, const Graph<R>& G, int i, int slot
             R csj = -(ux * bx + uy * by + uz * bz) * inv_u * inv_rb;
             R dsj;
             R sj = guardf<R>(P, csj, dsj);
-            if (sj == R(0)) continue;
+            if (is_zero(sj)) continue;
             R n2x = uy * bz - uz * by, n2y = uz * bx - ux * bz, n2z = ux * by - uy * bx;
             R n2s = n2x * n2x + n2y * n2y + n2z * n2z;
             R inv12 = rsqrt_(n1s * n2s);
@@ -996,7 +1028,7 @@ HD void path_forces(const Graph<R>& G, int i, int code, R dEdw, Sink& sink, doub
     R w[3], dw[3];
     for (int s = 0; s < len; s++) { w[s] = G.w[q[s]]; dw[s] = G.dw[q[s]]; }
     for (int s = 0; s < len; s++) {
-        if (dw[s] == R(0)) continue;
+        if (is_zero(dw[s])) continue;
         R other = R(1);
         for (int t = 0; t < len; t++) if (t != s) other *= w[t];
         R c = dEdw * other * dw[s] * G.ir[q[s]];
@@ -1026,7 +1058,7 @@ template <class R> HD R vlj(const DevParams<R>& P, int p, R r2, R& dVr) {
         dvr = R(2) * P.malpha[p] * P.meps[p] * e * (R(1) - e) * ir;
     }
     R t = (r - P.swlo[p]) * P.swinv[p];
-    t = t > R(0) ? t : R(0);
+    t = gt_(t, R(0)) ? t : R(0);
     R so = R(1) - t * t * (R(3) - R(2) * t);
     R dso = R(-6) * t * (R(1) - t) * P.swinv[p];
     dVr = dvr * so + v * dso * ir;
@@ -1038,7 +1070,7 @@ template <class R> HD R vlj(const DevParams<R>& P, int p, R r2, R& dVr) {
 template <class R> HD void vlj_param_grad(const DevParams<R>& P, int p, R r, R& dV_deps, R& dV_dsig) {
     R sg = P.sigma[p];
     R t = (r - P.swlo[p]) * P.swinv[p];
-    t = t > R(0) ? t : R(0);
+    t = gt_(t, R(0)) ? t : R(0);
     R so = R(1) - t * t * (R(3) - R(2) * t);
     R dso_dt = R(-6) * t * (R(1) - t);
     R dt_dsig = t > R(0) ? -r * P.swinv[p] / sg : R(0);        // t = (r/sigma - 2.7)/0.3
@@ -1150,7 +1182,7 @@ HD int lj_classify_c(const DevParams<R>& P, const PathMap<R>& M, int i, int j, i
         }
         if (mi >= 0) {
             C = M.wt[(size_t)i * M.cap + mi];
-            if (!(C > R(0))) return 0;
+            if (!gt_(C, R(0))) return 0;
             code = M.path[(size_t)i * M.cap + mi];
         }
     }
@@ -1246,7 +1278,7 @@ HD double bstar_full(const DevParams<R>& P, const Graph<R>& G, int i, int j, R d
     BstarSwitch<R> bsw{P.bmin[p], P.binv[p], Sr * C * V, R(0), R(0)};
     bond_order<R, true>(P, G, i, j, ux, uy, uz, rs, rcp_(rs), R(0), sink, gux, guy, guz, gumag,
                         fix, fiy, fiz, fjx, fjy, fjz, &bsw);
-    dsb = bsw.dSb != R(0);
+    dsb = !is_zero(bsw.dSb);
     if (dsb) {
         // u = r* d/|d|: only the direction of d carries a gradient
         R ud = (gux * dx + guy * dy + guz * dz) * inv_r;
