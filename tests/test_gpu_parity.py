@@ -346,9 +346,10 @@ def test_nve_pe32k_1000_steps_energy(A, param_text, precision):
 
 
 @pytest.mark.parametrize("case", ["hot300", "pe1152", "diamond216"])
-@pytest.mark.parametrize("precision,etol,ftol", [(0, 1e-10, 1e-8), (1, 1e-5, 1e-4)])
+@pytest.mark.parametrize("precision,etol,ftol", [(0, 1e-10, 1e-8), (1, 1e-5, 1e-4), (2, 1e-10, 1e-8)])
 def test_morse_parity(A, case, precision, etol, ftol):
-    """AIREBO-M: the Morse inter-molecular term, GPU against the oracle."""
+    """AIREBO-M: the Morse inter-molecular term, GPU against the oracle (with
+    the Morse form DF64 and mixed run their LJ pairs without the split)."""
     from oracle.oracle import Oracle
     text = inputs.params_text(inputs.make_params(0, morse=True))
     pos, types, box = CASES[case]()
