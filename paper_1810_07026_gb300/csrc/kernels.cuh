@@ -404,7 +404,7 @@ __device__ __noinline__ void lj_batch_df(const StepArgs<R>& a, const DfParams& D
 // the pair forces summed in 64-bit fixed point, the energy and virial in
 // double-float -- no FP64 instruction per pair.
 template <class R>
-__device__ __noinline__ void lj_batch_mx(const StepArgs<R>& a, const DevParams<R>& P, const float (*sh)[9],
+__device__ __forceinline__ void lj_batch_mx(const StepArgs<R>& a, const DevParams<R>& P, const float (*sh)[9],
                                             const float (*sl)[9], LjBuf& B, int b, int lane, DfLaneAcc& acc,
                                             ff& E, ff* W) {
     int jp = B.jp[b][lane];
