@@ -317,7 +317,7 @@ struct DfLaneAcc {
 // single box for |S| <= 4, from the system's split box edges for |S| <= 1
 // (hi times -1, 0 or 1 stays exact), else split here in FP64 (tiny boxes)
 template <class R>
-__device__ __noinline__ void shift_split(const StepArgs<R>& a, const float (*sh)[9], const float (*sl)[9],
+__device__ __forceinline__ void shift_split(const StepArgs<R>& a, const float (*sh)[9], const float (*sl)[9],
                                             int i, int img, float* h, float* l) {
     int s3[3] = {img_x(img), img_y(img), img_z(img)};
     bool small = s3[0] >= -1 && s3[0] <= 1 && s3[1] >= -1 && s3[1] <= 1 && s3[2] >= -1 && s3[2] <= 1;

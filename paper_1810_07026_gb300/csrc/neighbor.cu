@@ -96,7 +96,9 @@ __global__ void k_scatter(NeighborArgs a) {
         xw[d] = (float)(x - w * g.L[d]);
         wr[d] = (int)w;
     }
-    a.spos[slot] = make_float4(xw[0], xw[1], xw[2], __int_as_float(i));
+    // the fourth word: the atom and its species (bit 30), so that the list
+    // build reads one float4 per tested candidate
+    a.spos[slot] = make_float4(xw[0], xw[1], xw[2], __int_as_float(i | ((a.type[i] == 1 ? 1 : 0) << 30)));
     a.swrap[slot] = make_char4((char)wr[0], (char)wr[1], (char)wr[2], (char)(a.type[i] == 1 ? 1 : 0));
 }
 
@@ -105,7 +107,7 @@ __global__ void __launch_bounds__(128) k_build(NeighborArgs a, const int* cell_s
     if (s >= a.n) return;
     float4 pi = a.spos[s];
     char4 wi = a.swrap[s];
-    int i = __float_as_int(pi.w);
+    int i = __float_as_int(pi.w) & 0x3fffffff;
     int ti = wi.w;
     Grid g = grid_of(a, i);
     int cell = a.cell_of[i] - g.cell0;
@@ -115,20 +117,36 @@ __global__ void __launch_bounds__(128) k_build(NeighborArgs a, const int* cell_s
         lj2[t] = a.lj_rc[ti + t] * a.lj_rc[ti + t];
         im2[t] = a.im_rc[ti + t] * a.im_rc[ti + t];
     }
+    // cells farther than the largest cut-off from this atom are skipped: the
+    // squared distance from the atom to a stencil cell's box, per dimension
+    float rmax2 = fmaxf(fmaxf(lj2[0], lj2[1]), fmaxf(im2[0], im2[1]));
     float Lf[3] = {(float)g.L[0], (float)g.L[1], (float)g.L[2]};
+    float cwf[3] = {(float)g.cw[0], (float)g.cw[1], (float)g.cw[2]};
     int nlj = 0, nim = 0;
     int2* ljrow = a.lj + (size_t)i * a.lj_cap;
     int2* imrow = a.im + (size_t)i * a.im_cap;
+    // distance from the atom to the slab [q w, (q + 1) w) of stencil cell q (margin 2e-3 A)
+    auto slab = [&](int q, int d, float p) {
+        float lo = q * cwf[d] - p, hi = lo + cwf[d];
+        float e = lo > 0.0f ? lo : (hi < 0.0f ? -hi : 0.0f);
+        e = fmaxf(e - 2e-3f, 0.0f);
+        return e * e;
+    };
     for (int ox = -g.reach[0]; ox <= g.reach[0]; ox++) {
         int qx = ci[0] + ox;
+        float ex = slab(qx, 0, pi.x);
+        if (ex >= rmax2) continue;
         int sx = qx >= 0 ? qx / g.nc[0] : -((-qx + g.nc[0] - 1) / g.nc[0]);
         int cx = qx - sx * g.nc[0];
         for (int oy = -g.reach[1]; oy <= g.reach[1]; oy++) {
             int qy = ci[1] + oy;
+            float ey = ex + slab(qy, 1, pi.y);
+            if (ey >= rmax2) continue;
             int sy = qy >= 0 ? qy / g.nc[1] : -((-qy + g.nc[1] - 1) / g.nc[1]);
             int cy = qy - sy * g.nc[1];
             for (int oz = -g.reach[2]; oz <= g.reach[2]; oz++) {
                 int qz = ci[2] + oz;
+                if (ey + slab(qz, 2, pi.z) >= rmax2) continue;
                 int sz = qz >= 0 ? qz / g.nc[2] : -((-qz + g.nc[2] - 1) / g.nc[2]);
                 int cz = qz - sz * g.nc[2];
                 int c = g.cell0 + (cx * g.nc[1] + cy) * g.nc[2] + cz;
@@ -138,10 +156,11 @@ __global__ void __launch_bounds__(128) k_build(NeighborArgs a, const int* cell_s
                     float4 pj = a.spos[t];
                     float dx = pj.x + shx, dy = pj.y + shy, dz = pj.z + shz;
                     float r2 = dx * dx + dy * dy + dz * dz;
-                    char4 wj = a.swrap[t];
-                    int tj = wj.w;
+                    int jt = __float_as_int(pj.w);
+                    int tj = jt >> 30;
                     if (r2 >= lj2[tj]) continue;
-                    int j = __float_as_int(pj.w);
+                    int j = jt & 0x3fffffff;
+                    char4 wj = a.swrap[t];
                     int Sx = sx - wj.x + wi.x, Sy = sy - wj.y + wi.y, Sz = sz - wj.z + wi.z;
                     bool self = (j == i);
                     if (self && Sx == 0 && Sy == 0 && Sz == 0) continue;
