@@ -27,6 +27,7 @@ import os
 import platform
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -42,7 +43,7 @@ WORKLOAD = "pe1m"
 DT = 0.5
 TEMP = 300.0
 
-# Algorithmic FP64 work per unit, in flops (FMA = 2); see the roofline notes in the design doc.
+# Algorithmic FP64 work per unit, in flops (FMA = 2).
 FLOPS_LJ_PAIR = 44        # displacement with image (9), r^2 (5), sqrt, 1/r, (s/r)^6, V, dV/dr, force, sums (30)
 FLOPS_LJ_TEST = 14        # displacement and r^2 of a pair that is tested but not evaluated (C = 0, or queued for b*)
 # DRAM bytes (read + write) per atom of one k_lj<double> launch, measured by ncu
@@ -54,6 +55,17 @@ SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 FP64_FMA_PER_SM_CLK = 2   # 1.25 TFLOP/s nominal FP64 = 152 SMs x 2 FMA x 2 flop x 2.07 GHz
 FP32_FMA_PER_SM_CLK = 128
+
+
+def hbm_peak():
+    """HBM bandwidth in GB/s: the measured copy rate of these GPUs when the
+    measurement file sits beside this script, else an earlier measurement."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
 
 
 def peaks_nominal():
@@ -97,7 +109,7 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"airebo_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -377,6 +389,10 @@ def run_ours(args):
                 "peak_measured": peak64_meas,
                 "flops_per_launch": flops_lj, "avg_launch_ms": lj_avg_s * 1e3,
                 "dominant_kernel": dom}
+        if roof["traffic"]:
+            hbm, hbm_kind = hbm_peak()
+            gbs = roof["traffic"] / lj_avg_s / 1e9
+            roof["hbm"] = {"achieved_gbs": gbs, "peak_gbs": hbm, "peak_kind": hbm_kind, "frac": gbs / hbm}
         # kernels of one NVE step: 2 half kicks, short list, REBO, torsion, map,
         # LJ, b*, b* reverse, counters, energy write; 5 more per list rebuild
         launches = 11 * args.steps + 5 * r64["builds"]

@@ -2,9 +2,9 @@
 
 Tolerances (FP64 path, and the DF64 path whose LJ pair arithmetic runs in
 double-float): |dE| <= 1e-10 |E|, max|dF| <= 1e-8 max|F|,
-max|dW| <= 1e-8 max|W| -- the bar of the north star for a potential whose
-every term is evaluated in double precision (differences come only from the
-order of floating-point sums and from FP64 atomics).  Mixed path: FP32
+max|dW| <= 1e-8 max|W| -- the bar for a potential whose every term is
+evaluated in double precision (differences come only from the order of
+floating-point sums and from FP64 atomics).  Mixed path: FP32
 geometry/splines/bond order against FP64 gives about 1e-6 relative per term;
 the test allows |dE| <= 1e-5 |E| and max|dF| <= 1e-4 max|F|.
 """
