@@ -15,7 +15,7 @@ working set (~3 GB of lists, 50 MB of positions and forces) is larger than the
 L2, so no flush is needed.  Per-kernel times come from CUDA events the library
 records around each launch during the same timed region.
 
---impl reference times the CPU oracle (the reference arm of this build) on a
+--impl reference times the plain FP64 CPU oracle on a
 bounded sample of the same workload on the host cores.
 """
 from __future__ import annotations
