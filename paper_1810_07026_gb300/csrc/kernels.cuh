@@ -334,6 +334,14 @@ __device__ __forceinline__ void shift_split(const StepArgs<R>& a, const float (*
     }
 }
 
+// the same as a called function: the double-float kernel is sensitive to its
+// code size (instruction-cache stalls)
+template <class R>
+__device__ __noinline__ void shift_split_call(const StepArgs<R>& a, const float (*sh)[9], const float (*sl)[9],
+                                              int i, int img, float* h, float* l) {
+    shift_split<R>(a, sh, sl, i, img, h, l);
+}
+
 template <class R>
 __device__ __noinline__ void lj_batch_df(const StepArgs<R>& a, const DfParams& D, const float (*sh)[9],
                                             const float (*sl)[9], LjBuf& B, int b, int lane, DfLaneAcc& acc,
@@ -350,7 +358,7 @@ __device__ __noinline__ void lj_batch_df(const StepArgs<R>& a, const DfParams& D
     float shx = 0.0f, shy = 0.0f, shz = 0.0f, slx = 0.0f, sly = 0.0f, slz = 0.0f;
     if (img != 0) {
         float h[3], l[3];
-        shift_split<R>(a, sh, sl, i, img, h, l);
+        shift_split_call<R>(a, sh, sl, i, img, h, l);
         shx = h[0]; shy = h[1]; shz = h[2]; slx = l[0]; sly = l[1]; slz = l[2];
     }
     // hi parts: exact (multiples of 2^-12 below 2^12 in magnitude); lo parts: rounded
@@ -554,7 +562,8 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
                     float shx = 0.0f, shy = 0.0f, shz = 0.0f;
                     if (img != 0) {
                         float h[3], l[3];
-                        shift_split<R>(a, shf[0], shf[1], i, img, h, l);
+                        if (sizeof(R) == 8) shift_split_call<R>(a, shf[0], shf[1], i, img, h, l);
+                        else shift_split<R>(a, shf[0], shf[1], i, img, h, l);
                         shx = h[0]; shy = h[1]; shz = h[2];
                     }
                     fx = __fsub_rn(__fadd_rn(pj.x, shx), pfi.x);
