@@ -961,7 +961,10 @@ HD int build_path_map(const Graph<R>& G, PathMap<R>& M, int i) {
     unsigned long long mask[4] = {0, 0, 0, 0};
     auto insert = [&](int atom, int img, R c, int len, int k, int l, int code) {
         long long key = map_key(atom, img);
-        for (int e = 0; e < count; e++) {
+        int bit = map_bit(atom);
+        // the filter rules out most repeats without a scan (chains reach each atom once)
+        bool seen = (mask[bit >> 6] >> (bit & 63)) & 1ull;
+        for (int e = 0; seen && e < count; e++) {
             if (M.key[base + e] == key) {
                 int p0 = M.path[base + e];
                 int k0 = path_len(p0) >= 2 ? G.nj[i * G.stride + path_a(p0)] : -1;
@@ -979,7 +982,6 @@ HD int build_path_map(const Graph<R>& G, PathMap<R>& M, int i) {
             M.wt[base + count] = c;
             M.path[base + count] = code;
             count++;
-            int bit = map_bit(atom);
             mask[bit >> 6] |= 1ull << (bit & 63);
         } else {
             overflow++;
