@@ -201,12 +201,13 @@ airebo_status airebo_alu_peak(int precision, double* tflops);
 /*
  * Accuracy check of the FP64 reciprocal and reciprocal square root the
  * kernels use (a hardware approximation refined by one third-order Newton
- * step): h_ulp2 (host int64[2]) receives the largest difference, in units in
+ * step): h_ulp4 (host int64[4]) receives the largest difference, in units in
  * the last place, from CUDA's correctly rounded 1/x and from 1/sqrt(x) over
- * 4M values of x spread over [2^-30, 2^30) on the current device.  A
+ * 4M values of x spread over [2^-30, 2^30) on the current device, then the
+ * same for the hardware approximations without the Newton step.  A
  * diagnostic; the paper has no counterpart.
  */
-airebo_status airebo_math_check(int64_t* h_ulp2);
+airebo_status airebo_math_check(int64_t* h_ulp4);
 
 /*
  * Energy and forces as airebo_compute, plus the gradient of the energy with

@@ -105,12 +105,13 @@ def alu_peak(precision: int = FP64) -> float:
 
 
 def math_check():
-    """(ulp difference of the kernels' 1/x from CUDA's correctly rounded one, same for 1/sqrt(x))."""
-    out = np.zeros(2, dtype=np.int64)
+    """ulp differences from CUDA's correctly rounded results: the kernels' 1/x and 1/sqrt(x), then
+    the hardware approximations alone."""
+    out = np.zeros(4, dtype=np.int64)
     st = lib().airebo_math_check(_np(out))
     if st:
         raise AireboError(st, "math check failed")
-    return int(out[0]), int(out[1])
+    return tuple(int(v) for v in out)
 
 
 class Airebo:

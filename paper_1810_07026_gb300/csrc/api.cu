@@ -1385,12 +1385,11 @@ airebo_status airebo_alu_peak(int precision, double* tflops) {
     return t > 0 ? AIREBO_OK : AIREBO_ERR_CUDA;
 }
 
-airebo_status airebo_math_check(int64_t* h_ulp2) {
-    if (!h_ulp2) return AIREBO_ERR_ARG;
-    long long o[2] = {0, 0};
+airebo_status airebo_math_check(int64_t* h_ulp4) {
+    if (!h_ulp4) return AIREBO_ERR_ARG;
+    long long o[4] = {0, 0, 0, 0};
     if (math_check(o)) return AIREBO_ERR_CUDA;
-    h_ulp2[0] = o[0];
-    h_ulp2[1] = o[1];
+    for (int k = 0; k < 4; k++) h_ulp4[k] = o[k];
     return AIREBO_OK;
 }
 

@@ -112,7 +112,7 @@ void launch_system_energy(const double* eatom, const long long* offsets, int nsy
 void launch_nve_half(double* pos, double* vel, const double* f, const int8_t* type, int n, double dt,
                      bool drift, const double* xref, unsigned long long* maxdisp2_bits, double* ke, cudaStream_t s);
 double alu_peak(int fp64);
-int math_check(long long* out2);
+int math_check(long long* out4);
 void launch_max_disp(const double* pos, const double* xref, int n, unsigned long long* maxdisp2_bits, cudaStream_t s);
 
 }  // namespace airebo

@@ -52,7 +52,8 @@ double alu_peak(int fp64) {
 // over x = 2^t, t uniform in [-30, 30) (a counter-based hash picks t).
 // out[0], out[1]: largest difference in units in the last place for 1/x and
 // 1/sqrt(x) (the latter's reference, 1 / sqrt(x) with two correct roundings,
-// is itself within 1 ulp).
+// is itself within 1 ulp); out[2], out[3]: the same for the hardware
+// approximations alone.
 __global__ void k_math_check(unsigned long long* out, int n) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -66,19 +67,26 @@ __global__ void k_math_check(unsigned long long* out, int n) {
     long long d2 = __double_as_longlong(r2) - __double_as_longlong(q2);
     atomicMax(out + 0, (unsigned long long)(d1 < 0 ? -d1 : d1));
     atomicMax(out + 1, (unsigned long long)(d2 < 0 ? -d2 : d2));
+    // the hardware approximations alone, before the Newton step
+    double a1, a2;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(a1) : "d"(x));
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(a2) : "d"(x));
+    long long d3 = __double_as_longlong(a1) - __double_as_longlong(q1);
+    long long d4 = __double_as_longlong(a2) - __double_as_longlong(q2);
+    atomicMax(out + 2, (unsigned long long)(d3 < 0 ? -d3 : d3));
+    atomicMax(out + 3, (unsigned long long)(d4 < 0 ? -d4 : d4));
 }
 
-int math_check(long long* out2) {
+int math_check(long long* out4) {
     unsigned long long* d = nullptr;
-    if (cudaMalloc(&d, 16) != cudaSuccess) return 1;
-    cudaMemset(d, 0, 16);
+    if (cudaMalloc(&d, 32) != cudaSuccess) return 1;
+    cudaMemset(d, 0, 32);
     int n = 1 << 22;
     k_math_check<<<(n + 255) / 256, 256>>>(d, n);
-    unsigned long long h[2] = {0, 0};
-    cudaError_t e = cudaMemcpy(h, d, 16, cudaMemcpyDeviceToHost);
+    unsigned long long h[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpy(h, d, 32, cudaMemcpyDeviceToHost);
     cudaFree(d);
-    out2[0] = (long long)h[0];
-    out2[1] = (long long)h[1];
+    for (int k = 0; k < 4; k++) out4[k] = (long long)h[k];
     return (e == cudaSuccess && cudaGetLastError() == cudaSuccess) ? 0 : 1;
 }
 

@@ -12,6 +12,7 @@ def test_rcp_rsqrt_within_two_ulp():
         pytest.skip("no CUDA device")
     from paper_1810_07026_gb300 import build, airebo
     build.build()
-    ulp_rcp, ulp_rsqrt = airebo.math_check()
+    ulp_rcp, ulp_rsqrt, raw_rcp, raw_rsqrt = airebo.math_check()
+    print(f"ulp: 1/x {ulp_rcp}, 1/sqrt(x) {ulp_rsqrt}; hardware approximations alone {raw_rcp}, {raw_rsqrt}")
     assert ulp_rcp <= 1, ulp_rcp          # faithful: at most one rounding step from 1/x
     assert ulp_rsqrt <= 2, ulp_rsqrt      # the reference 1/sqrt(x) is itself within 1 ulp
