@@ -225,16 +225,12 @@ __global__ void __launch_bounds__(128) k_path_map(StepArgs<R> a) {
 constexpr int LJ_THREADS = 256;
 constexpr int LJ_WARPS = LJ_THREADS / 32;
 
-// compaction buffers per warp: class 0 = inner pairs, 1 = pairs in the cut-off
-// switch; in FP64, classes 2 and 3 are the same with a periodic image (only
-// their batches spend FP64 additions on the image shift)
-template <int NC> struct LjBufT {
-    int jp[NC][64];         // j | species pair << 30
-    int ia[NC][64];         // the list's atom i
-    int im[NC][64];         // packed image of j
+// two compaction buffers per warp: 0 = inner pairs, 1 = pairs in the cut-off switch
+struct LjBuf {
+    int jp[2][64];          // j | species pair << 30
+    int ia[2][64];          // the list's atom i
+    int im[2][64];          // packed image of j
 };
-using LjBuf = LjBufT<4>;      // FP64: four classes
-using LjBuf2 = LjBufT<2>;     // split positions: two classes
 
 // Per-lane force (and energy) accumulator of the atom whose pairs the lane
 // last evaluated.  Batches run across atom boundaries, so a lane flushes it
@@ -280,16 +276,11 @@ __device__ __forceinline__ void lj_batch(const StepArgs<R>& a, const DevParams<R
         acc.own = i;
     }
     double dx, dy, dz;
-    if (b & 2) {
-        lj_disp<R>(a, shift, i, j, B.im[b][lane], dx, dy, dz);
-    } else {
-        int n = a.n;
-        dx = a.pos[j] - a.pos[i]; dy = a.pos[n + j] - a.pos[n + i]; dz = a.pos[2 * n + j] - a.pos[2 * n + i];
-    }
+    lj_disp<R>(a, shift, i, j, B.im[b][lane], dx, dy, dz);
     R rx = (R)dx, ry = (R)dy, rz = (R)dz;
     R r2 = rx * rx + ry * ry + rz * rz;
     double E0 = E;
-    if ((b & 1) == 0)
+    if (b == 0)
         lj_eval_inner<R>(P, p, j, dx, dy, dz, r2, sink, acc.fx, acc.fy, acc.fz, E);
     else
         lj_eval_switch<R>(P, p, j, dx, dy, dz, r2, sink, acc.fx, acc.fy, acc.fz, E);
@@ -353,7 +344,7 @@ __device__ __noinline__ void shift_split_call(const StepArgs<R>& a, const float 
 
 template <class R>
 __device__ __noinline__ void lj_batch_df(const StepArgs<R>& a, const DfParams& D, const float (*sh)[9],
-                                            const float (*sl)[9], LjBuf2& B, int b, int lane, DfLaneAcc& acc,
+                                            const float (*sl)[9], LjBuf& B, int b, int lane, DfLaneAcc& acc,
                                             ff& E, ff* W) {
     int jp = B.jp[b][lane];
     int j = jp & 0x3fffffff, p = (unsigned)jp >> 30;
@@ -422,7 +413,7 @@ __device__ __noinline__ void lj_batch_df(const StepArgs<R>& a, const DfParams& D
 // double-float -- no FP64 instruction per pair.
 template <class R>
 __device__ __forceinline__ void lj_batch_mx(const StepArgs<R>& a, const DevParams<R>& P, const float (*sh)[9],
-                                            const float (*sl)[9], LjBuf2& B, int b, int lane, DfLaneAcc& acc,
+                                            const float (*sl)[9], LjBuf& B, int b, int lane, DfLaneAcc& acc,
                                             ff& E, ff* W) {
     int jp = B.jp[b][lane];
     int j = jp & 0x3fffffff, p = (unsigned)jp >> 30;
@@ -494,8 +485,7 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
     const DevParams<R>& P = *a.P;
     __shared__ double shift[3][9];                // image shifts S L for S in [-4, 4]
     __shared__ LjCuts<float> cutsf[3];            // thresholds in FP32, by species pair
-    using Buf = LjBufT<DF ? 2 : 4>;
-    __shared__ Buf bufs[LJ_WARPS];
+    __shared__ LjBuf bufs[LJ_WARPS];
     __shared__ float shf[2][3][9];                // DF: split image shifts (hi, lo)
     __shared__ DfParams dfp;
     if (threadIdx.x < 27) {
@@ -515,7 +505,7 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
     }
     __syncthreads();
     int lane = threadIdx.x & 31;
-    Buf& B = bufs[threadIdx.x >> 5];
+    LjBuf& B = bufs[threadIdx.x >> 5];
     unsigned lt = (1u << lane) - 1u;
     Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}, a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
     bool general = a.pgrad != nullptr;
@@ -526,8 +516,7 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
     double E = 0;
     unsigned evaluated = 0;
     int n = a.n;
-    constexpr int NCLS = DF ? 2 : 4;
-    int cnt[4] = {0, 0, 0, 0};
+    int cnt[2] = {0, 0};
     // the pair arithmetic of one full (or, at the end, partial) batch
     auto batch = [&](int b) {
         if constexpr (DF) {
@@ -628,11 +617,11 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
                     if (a.eatom) atomicAdd(a.eatom + i, E - E0);
                 }
             }
-            int cls = (st == 1 || st == 3) ? (st == 3) + ((!DF && img != 0) ? 2 : 0) : -1;
 #pragma unroll
-            for (int b = 0; b < NCLS; b++) {
-                unsigned m = __ballot_sync(0xffffffffu, cls == b);
-                if (cls == b) {
+            for (int b = 0; b < 2; b++) {
+                int want = b == 0 ? 1 : 3;
+                unsigned m = __ballot_sync(0xffffffffu, st == want);
+                if (st == want) {
                     int s = cnt[b] + __popc(m & lt);
                     B.jp[b][s] = j | (p << 30); B.ia[b][s] = i; B.im[b][s] = img;
                 }
@@ -652,8 +641,8 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
         }
     }
     // the warp's last, partly filled batches
-#pragma unroll 1
-    for (int b = 0; b < NCLS; b++)
+#pragma unroll
+    for (int b = 0; b < 2; b++)
         if (lane < cnt[b]) batch(b);
     if (DF) {
         dacc.flush(a.fix, n, a.eatom);
