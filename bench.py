@@ -155,6 +155,13 @@ class Clocks:
 
 def cpu_model():
     try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip() + f", {os.cpu_count()} logical CPUs"
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
         for line in open("/proc/cpuinfo"):
             if line.lower().startswith(("model name", "cpu model")):
                 return line.split(":", 1)[1].strip()
@@ -373,6 +380,9 @@ def run_ours(args):
     if rank == 0:
         # algorithmic work from the oracle's term counters on a bounded sample
         cpu_rate, nth, sample, per, cpu_dt = oracle_sample(pos0, types, box, target_s=12.0)
+        cpu1_rate, _, sample1, _, cpu1_dt = oracle_sample(pos0, types, box, target_s=4.0, threads=1)
+        from oracle import oracle as O
+        O.set_threads(nth)
         pairs_eval = per["lj_in_cutoff"] - per["lj_c_zero"] - per["bstar"]
         pairs_test = per["lj_c_zero"] + per["bstar"]
         flops_lj = n * (FLOPS_LJ_PAIR * pairs_eval + FLOPS_LJ_TEST * pairs_test)
@@ -430,7 +440,10 @@ def run_ours(args):
             "peaks_TFLOPs": {"fp64_nominal": peak64_nom, "fp64_measured": peak64_meas,
                              "fp32_nominal": peak32_nom, "fp32_measured": peak32_meas},
             "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": nth, "kind": "oracle", "sample": sample,
-                             "cpu": cpu_model(), "seconds": cpu_dt},
+                             "cpu": cpu_model(), "seconds": cpu_dt,
+                             "single_thread": {"value": cpu1_rate, "cores": 1, "sample": sample1,
+                                               "seconds": cpu1_dt}},
+            "counters_fp64_last_step": {k: v for k, v in r64["counters"].items() if k != "list_builds"},
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": r64["clocks"],
