@@ -342,7 +342,7 @@ __device__ __noinline__ void shift_split_call(const StepArgs<R>& a, const float 
     shift_split<R>(a, sh, sl, i, img, h, l);
 }
 
-template <class R>
+template <class R, bool EXTRA>
 __device__ __noinline__ void lj_batch_df(const StepArgs<R>& a, const DfParams& D, const float (*sh)[9],
                                             const float (*sl)[9], LjBuf& B, int b, int lane, DfLaneAcc& acc,
                                             ff& E, ff* W) {
@@ -401,7 +401,7 @@ __device__ __noinline__ void lj_batch_df(const StepArgs<R>& a, const DfParams& D
     } else {
         atomicMax(a.err + ERR_DF, 2);
     }
-    if (a.virial) {
+    if (EXTRA && a.virial) {
         W[0] = ff_sub(W[0], ff_mul(dx, gx)); W[1] = ff_sub(W[1], ff_mul(dy, gy)); W[2] = ff_sub(W[2], ff_mul(dz, gz));
         W[3] = ff_sub(W[3], ff_mul(dx, gy)); W[4] = ff_sub(W[4], ff_mul(dx, gz)); W[5] = ff_sub(W[5], ff_mul(dy, gz));
     }
@@ -411,7 +411,7 @@ __device__ __noinline__ void lj_batch_df(const StepArgs<R>& a, const DfParams& D
 // displacement (FP64-class) rounded once to FP32, the pair term in FP32, and
 // the pair forces summed in 64-bit fixed point, the energy and virial in
 // double-float -- no FP64 instruction per pair.
-template <class R>
+template <class R, bool EXTRA>
 __device__ __forceinline__ void lj_batch_mx(const StepArgs<R>& a, const DevParams<R>& P, const float (*sh)[9],
                                             const float (*sl)[9], LjBuf& B, int b, int lane, DfLaneAcc& acc,
                                             ff& E, ff* W) {
@@ -467,7 +467,7 @@ __device__ __forceinline__ void lj_batch_mx(const StepArgs<R>& a, const DevParam
     } else {
         atomicMax(a.err + ERR_DF, 2);
     }
-    if (a.virial) {
+    if (EXTRA && a.virial) {
         W[0] = ff_add_f(W[0], -rx * gx); W[1] = ff_add_f(W[1], -ry * gy); W[2] = ff_add_f(W[2], -rz * gz);
         W[3] = ff_add_f(W[3], -rx * gy); W[4] = ff_add_f(W[4], -rx * gz); W[5] = ff_add_f(W[5], -ry * gz);
     }
@@ -480,7 +480,11 @@ __device__ __forceinline__ void lj_batch_mx(const StepArgs<R>& a, const DevParam
 // |dx_f - dx| <= 2^-22 (2 max|x_i| + 4 |S|max L + 48): the roundings of x_i,
 // x_j and S L to FP32 and of the two FP32 additions, with |x_j| <= |x_i| +
 // |dx| + |S L| and |dx| < 16 A for any listed pair, and a factor 2 to spare.
-template <class R, bool DF>
+//
+// EXTRA: the virial or the parameter gradient is wanted.  The instance without
+// them keeps no accumulators for them in registers (they cost the mixed
+// instance its spill-free register budget).
+template <class R, bool DF, bool EXTRA>
 __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
     const DevParams<R>& P = *a.P;
     __shared__ double shift[3][9];                // image shifts S L for S in [-4, 4]
@@ -507,8 +511,8 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
     int lane = threadIdx.x & 31;
     LjBuf& B = bufs[threadIdx.x >> 5];
     unsigned lt = (1u << lane) - 1u;
-    Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}, a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
-    bool general = a.pgrad != nullptr;
+    Sink sink{a.f, a.n, EXTRA && a.virial, {0, 0, 0, 0, 0, 0}, EXTRA && a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
+    bool general = EXTRA && a.pgrad != nullptr;
     LaneAcc acc;
     DfLaneAcc dacc;
     ff Edf{0.0f, 0.0f};
@@ -520,8 +524,8 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
     // the pair arithmetic of one full (or, at the end, partial) batch
     auto batch = [&](int b) {
         if constexpr (DF) {
-            if constexpr (sizeof(R) == 8) lj_batch_df<R>(a, dfp, shf[0], shf[1], B, b, lane, dacc, Edf, Wdf);
-            else lj_batch_mx<R>(a, P, shf[0], shf[1], B, b, lane, dacc, Edf, Wdf);
+            if constexpr (sizeof(R) == 8) lj_batch_df<R, EXTRA>(a, dfp, shf[0], shf[1], B, b, lane, dacc, Edf, Wdf);
+            else lj_batch_mx<R, EXTRA>(a, P, shf[0], shf[1], B, b, lane, dacc, Edf, Wdf);
         } else {
             lj_batch<R>(a, P, shift, B, b, lane, sink, acc, E);
         }
@@ -647,15 +651,15 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
     if (DF) {
         dacc.flush(a.fix, n, a.eatom);
         E += ff_to_double(Edf);
-        if (a.virial)
+        if (EXTRA && a.virial)
             for (int k = 0; k < 6; k++) sink.W[k] += ff_to_double(Wdf[k]);
     } else {
         acc.flush(a.f, n, a.eatom);
     }
     unsigned ev = __reduce_add_sync(0xffffffffu, evaluated);
     if (lane == 0 && ev) atomicAdd(a.counters + CNT_LJ, (unsigned long long)ev);
-    block_accumulate<LJ_THREADS>(E, sink.W, a.virial, a.acc + 1, a.acc + 3);
-    if (a.pgrad) block_accumulate_g<LJ_THREADS>(sink.G, a.pgrad);
+    block_accumulate<LJ_THREADS>(E, sink.W, EXTRA && a.virial, a.acc + 1, a.acc + 3);
+    if (EXTRA && a.pgrad) block_accumulate_g<LJ_THREADS>(sink.G, a.pgrad);
 }
 
 // ------------------------------------------------------------------ b* pairs
@@ -797,18 +801,20 @@ void launch_compute_impl(const StepArgs<R>& a, cudaStream_t s, int num_sms, cuda
     mark(4);
     if (a.lj_on) {
         // asked once: nothing but stream work during graph capture
-        static int per_sm[2] = {-1, -1};
+        static int per_sm[4] = {-1, -1, -1, -1};
         bool df = a.fix != nullptr;
+        bool extra = a.virial || a.pgrad != nullptr;
         int need = (n + LJ_WARPS - 1) / LJ_WARPS;
+        auto launch = [&](auto kernel, int slot) {
+            if (per_sm[slot] < 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[slot], kernel, LJ_THREADS, 0);
+            int blocks = num_sms * (per_sm[slot] > 0 ? per_sm[slot] : 1);
+            kernel<<<blocks < need ? blocks : need, LJ_THREADS, 0, s>>>(a);
+        };
         if (df) {
-            if (per_sm[1] < 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_lj<R, true>, LJ_THREADS, 0);
-            int blocks = num_sms * (per_sm[1] > 0 ? per_sm[1] : 1);
-            k_lj<R, true><<<blocks < need ? blocks : need, LJ_THREADS, 0, s>>>(a);
+            if (extra) launch(k_lj<R, true, true>, 3); else launch(k_lj<R, true, false>, 2);
             k_fix_add<<<(n + 255) / 256, 256, 0, s>>>(a.fix, a.f, n);
         } else {
-            if (per_sm[0] < 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_lj<R, false>, LJ_THREADS, 0);
-            int blocks = num_sms * (per_sm[0] > 0 ? per_sm[0] : 1);
-            k_lj<R, false><<<blocks < need ? blocks : need, LJ_THREADS, 0, s>>>(a);
+            if (extra) launch(k_lj<R, false, true>, 1); else launch(k_lj<R, false, false>, 0);
         }
     }
     mark(5);

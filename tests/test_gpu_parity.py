@@ -140,6 +140,28 @@ def test_bstar_screen(A, oracle, param_text, case):
     assert g_on["bstar_dsb"] <= g_on["bstar_full"] <= g_on["bstar"]
 
 
+@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("case", ["diamond216", "pe1152", "hot1000"])
+def test_without_virial(A, oracle, param_text, case, precision):
+    """An evaluation that asks for no virial runs the LJ kernel instance without
+    virial (or parameter-gradient) accumulators: the same energies and forces
+    as with the virial on the same handle, and the oracle's within the
+    precision's tolerances."""
+    pos, types, box = CASES[case]()
+    got, ev = gpu_eval(A, param_text, pos, types, box, precision=precision, virial=False)
+    p = torch.tensor(pos, device="cuda")
+    f2, e2, w2 = ev.compute(p, virial=True)
+    torch.cuda.synchronize()
+    with_w = (e2.cpu().numpy(), f2.cpu().numpy(), w2.cpu().numpy())
+    assert_close(got, with_w, 1e-12, 1e-11)
+    e, f, w, _ = oracle.compute(pos, types, box)
+    if precision == 1:
+        assert_close(got, (e, f, w), 1e-5, 1e-4)
+    else:
+        assert_close(got, (e, f, w), 1e-10, 1e-8)
+    ev.close()
+
+
 def as_set(cnt, j, img):
     out = set()
     for i in range(len(cnt)):
