@@ -172,10 +172,12 @@ __global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
 }
 
 // ------------------------------------------------------------------ REBO bonds
-template <class R>
+// EXTRA (here and in the torsion and b* kernels): the virial or the parameter
+// gradient is wanted; the instances without them hold no accumulators for them.
+template <class R, bool EXTRA>
 __global__ void __launch_bounds__(128, 4) k_rebo(StepArgs<R> a) {
     const DevParams<R>& P = *a.P;
-    Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}, a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
+    Sink sink{a.f, a.n, EXTRA && a.virial, {0, 0, 0, 0, 0, 0}, EXTRA && a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
     double E = 0;
     int ncc = min(*a.nccbonds, a.bond_cap);
     int nb = ncc + min(*a.nbonds, a.bond_cap);
@@ -185,14 +187,14 @@ __global__ void __launch_bounds__(128, 4) k_rebo(StepArgs<R> a) {
         E += e;
         if (a.eatom) atomicAdd(a.eatom + bd.x, e);
     }
-    block_accumulate<128>(E, sink.W, a.virial, a.acc + 0, a.acc + 3);
+    block_accumulate<128>(E, sink.W, EXTRA && a.virial, a.acc + 0, a.acc + 3);
 }
 
 // ------------------------------------------------------------------ torsion
-template <class R>
+template <class R, bool EXTRA>
 __global__ void __launch_bounds__(128) k_torsion(StepArgs<R> a) {
     const DevParams<R>& P = *a.P;
-    Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}, a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
+    Sink sink{a.f, a.n, EXTRA && a.virial, {0, 0, 0, 0, 0, 0}, EXTRA && a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
     double E = 0;
     int nb = *a.nccbonds;
     if (nb > a.bond_cap) nb = a.bond_cap;
@@ -202,7 +204,7 @@ __global__ void __launch_bounds__(128) k_torsion(StepArgs<R> a) {
         E += e;
         if (a.eatom && e != 0.0) atomicAdd(a.eatom + bd.x, e);
     }
-    block_accumulate<128>(E, sink.W, a.virial, a.acc + 2, a.acc + 3);
+    block_accumulate<128>(E, sink.W, EXTRA && a.virial, a.acc + 2, a.acc + 3);
 }
 
 // ------------------------------------------------------------------ connectivity map
@@ -685,10 +687,10 @@ __device__ __forceinline__ void bstar_load(const StepArgs<R>& a, int t, int& i, 
     }
 }
 
-template <class R>
+template <class R, bool EXTRA>
 __global__ void __launch_bounds__(128) k_bstar(StepArgs<R> a) {
     const DevParams<R>& P = *a.P;
-    Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}, a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
+    Sink sink{a.f, a.n, EXTRA && a.virial, {0, 0, 0, 0, 0, 0}, EXTRA && a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
     double E = 0;
     int n0 = min(a.nbq[0], a.bq_cap), n1 = min(a.nbq[1], a.bq_cap), n2 = min(a.nbq[2], a.bq_cap);
     int nq = n0 + n1 + n2;
@@ -727,15 +729,15 @@ __global__ void __launch_bounds__(128) k_bstar(StepArgs<R> a) {
             if (s < 3 * a.bq_cap) a.bq2[s] = t;
         }
     }
-    block_accumulate<128>(E, sink.W, a.virial, a.acc + 1, a.acc + 3);
-    if (a.pgrad) block_accumulate_g<128>(sink.G, a.pgrad);
+    block_accumulate<128>(E, sink.W, EXTRA && a.virial, a.acc + 1, a.acc + 3);
+    if (EXTRA && a.pgrad) block_accumulate_g<128>(sink.G, a.pgrad);
 }
 
 // Phase 2: the pairs of the second queue, b* and its gradient in one pass.
-template <class R>
+template <class R, bool EXTRA>
 __global__ void __launch_bounds__(128, 4) k_bstar_rev(StepArgs<R> a) {
     const DevParams<R>& P = *a.P;
-    Sink sink{a.f, a.n, a.virial, {0, 0, 0, 0, 0, 0}, a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
+    Sink sink{a.f, a.n, EXTRA && a.virial, {0, 0, 0, 0, 0, 0}, EXTRA && a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
     double E = 0;
     unsigned dsb_count = 0;
     int nq = min(*a.nbq2, 3 * a.bq_cap);
@@ -754,8 +756,8 @@ __global__ void __launch_bounds__(128, 4) k_bstar_rev(StepArgs<R> a) {
     }
     unsigned c = __reduce_add_sync(0xffffffffu, dsb_count);
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(a.counters + CNT_DSB, (unsigned long long)c);
-    block_accumulate<128>(E, sink.W, a.virial, a.acc + 1, a.acc + 3);
-    if (a.pgrad) block_accumulate_g<128>(sink.G, a.pgrad);
+    block_accumulate<128>(E, sink.W, EXTRA && a.virial, a.acc + 1, a.acc + 3);
+    if (EXTRA && a.pgrad) block_accumulate_g<128>(sink.G, a.pgrad);
 }
 
 template <class R>
@@ -782,20 +784,35 @@ void launch_compute_impl(const StepArgs<R>& a, cudaStream_t s, int num_sms, cuda
     auto mark = [&](int k) { if (ev) cudaEventRecord(ev[k], s); };
     // grid-stride kernels launch whole waves: waves x resident blocks per SM x SMs
     // (the occupancies are asked once; nothing but stream work during graph capture)
-    static int occ[4] = {-1, -1, -1, -1};
+    bool extra = a.virial || a.pgrad != nullptr;
+    static int occ_all[2][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}};
+    int* occ = occ_all[extra];
     if (occ[0] < 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_rebo<R>, 128, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_torsion<R>, 128, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], k_bstar<R>, 128, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[3], k_bstar_rev<R>, 128, 0);
+        if (extra) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_rebo<R, true>, 128, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_torsion<R, true>, 128, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], k_bstar<R, true>, 128, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[3], k_bstar_rev<R, true>, 128, 0);
+        } else {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_rebo<R, false>, 128, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_torsion<R, false>, 128, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], k_bstar<R, false>, 128, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[3], k_bstar_rev<R, false>, 128, 0);
+        }
     }
     auto grid_of = [&](int k, int waves) { return num_sms * (occ[k] > 0 ? occ[k] : 1) * waves; };
     mark(0);
     k_short_list<R><<<(n + 127) / 128, 128, 0, s>>>(a);
     mark(1);
-    if (a.rebo) k_rebo<R><<<grid_of(0, a.bond_waves), 128, 0, s>>>(a);
+    if (a.rebo) {
+        if (extra) k_rebo<R, true><<<grid_of(0, a.bond_waves), 128, 0, s>>>(a);
+        else k_rebo<R, false><<<grid_of(0, a.bond_waves), 128, 0, s>>>(a);
+    }
     mark(2);
-    if (a.torsion) k_torsion<R><<<grid_of(1, a.bond_waves), 128, 0, s>>>(a);
+    if (a.torsion) {
+        if (extra) k_torsion<R, true><<<grid_of(1, a.bond_waves), 128, 0, s>>>(a);
+        else k_torsion<R, false><<<grid_of(1, a.bond_waves), 128, 0, s>>>(a);
+    }
     mark(3);
     if (a.lj_on) k_path_map<R><<<(n + 127) / 128, 128, 0, s>>>(a);
     mark(4);
@@ -803,7 +820,6 @@ void launch_compute_impl(const StepArgs<R>& a, cudaStream_t s, int num_sms, cuda
         // asked once: nothing but stream work during graph capture
         static int per_sm[4] = {-1, -1, -1, -1};
         bool df = a.fix != nullptr;
-        bool extra = a.virial || a.pgrad != nullptr;
         int need = (n + LJ_WARPS - 1) / LJ_WARPS;
         auto launch = [&](auto kernel, int slot) {
             if (per_sm[slot] < 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[slot], kernel, LJ_THREADS, 0);
@@ -818,9 +834,15 @@ void launch_compute_impl(const StepArgs<R>& a, cudaStream_t s, int num_sms, cuda
         }
     }
     mark(5);
-    if (a.lj_on) k_bstar<R><<<grid_of(2, a.bstar_waves), 128, 0, s>>>(a);
+    if (a.lj_on) {
+        if (extra) k_bstar<R, true><<<grid_of(2, a.bstar_waves), 128, 0, s>>>(a);
+        else k_bstar<R, false><<<grid_of(2, a.bstar_waves), 128, 0, s>>>(a);
+    }
     mark(6);
-    if (a.lj_on) k_bstar_rev<R><<<grid_of(3, a.bstar_waves), 128, 0, s>>>(a);
+    if (a.lj_on) {
+        if (extra) k_bstar_rev<R, true><<<grid_of(3, a.bstar_waves), 128, 0, s>>>(a);
+        else k_bstar_rev<R, false><<<grid_of(3, a.bstar_waves), 128, 0, s>>>(a);
+    }
     mark(7);
     k_finish_counters<R><<<1, 32, 0, s>>>(a);
 }
