@@ -210,6 +210,17 @@ airebo_status airebo_alu_peak(int precision, double* tflops);
 airebo_status airebo_math_check(int64_t* h_ulp4);
 
 /*
+ * Accuracy check of the double-float operations of the AIREBO_DF64 torsion
+ * kernel on the current device, against FP64 on the same (exactly
+ * representable) inputs over 4M seeded operands +-m 2^t (m in [1, 2), t in
+ * [-20, 20)): h_err8 (host double[8]) receives the largest error of a + b
+ * relative to |a| + |b|; of a * b, a / b, 1/a and 1/sqrt(|a|) relative; of
+ * sin(pi t) and cos(pi t) for t in [0, 2) absolute (against CUDA's FP64
+ * sincospi); and of the conversion from double, relative.  A diagnostic.
+ */
+airebo_status airebo_dd_check(double* h_err8);
+
+/*
  * Energy and forces as airebo_compute, plus the gradient of the energy with
  * respect to the parameters of the inter-molecular term (Sec. 2.1.2):
  * h_grad6 (host double[6]) = dE/d epsilon[CC, CH, HH] (lj.epsilon, or

@@ -67,6 +67,7 @@ def lib():
             "airebo_kernel_times": (I, [P, P, P]),
             "airebo_alu_peak": (I, [I, P]),
             "airebo_math_check": (I, [P]),
+            "airebo_dd_check": (I, [P]),
             "airebo_param_grad": (I, [P, P, P, P, P]),
             "airebo_knot_grad": (I, [P, P, P, P, P, I64]),
             "airebo_set_lj_params": (I, [P, P, P]),
@@ -102,6 +103,16 @@ def alu_peak(precision: int = FP64) -> float:
     if st:
         raise AireboError(st, "alu peak probe failed")
     return out.value
+
+
+def dd_check():
+    """Largest errors of the double-float operations (add relative to |a|+|b|; mul, div, rcp, rsqrt
+    relative; sin(pi t), cos(pi t) absolute; conversion from double relative)."""
+    out = np.zeros(8, dtype=np.float64)
+    st = lib().airebo_dd_check(_np(out))
+    if st:
+        raise AireboError(st, "double-float check failed")
+    return dict(zip(("add", "mul", "div", "rcp", "rsqrt", "sinpi", "cospi", "from_double"), out.tolist()))
 
 
 def math_check():

@@ -336,6 +336,7 @@ struct airebo_ctx {
     Scalars sc;
     Precision<double> p64;
     Precision<float> p32;
+    Precision<dd> pdd;        // AIREBO_DF64: the parameters in double-float (torsion kernel)
     // system
     int n = 0, n_alloc = 0;
     double L[3] = {0, 0, 0};
@@ -482,6 +483,15 @@ constexpr int CELL_DIV = 2;
 
 bool screen_on(airebo_handle h) {
     return h->opt.precision != AIREBO_MIXED && h->opt.bstar_screen != 0 && h->opt.enable_lj != 0;
+}
+
+// the parameter sets of the handle's precision: its own, the FP32 one of the
+// b* screen, and for AIREBO_DF64 the double-float one of the torsion kernel
+airebo_status upload_own_params(airebo_handle h) {
+    airebo_status st = h->opt.precision == AIREBO_MIXED ? upload_params<float>(h, h->p32) : upload_params<double>(h, h->p64);
+    if (!st && screen_on(h)) st = upload_params<float>(h, h->p32);
+    if (!st && h->opt.precision == AIREBO_DF64) st = upload_params<dd>(h, h->pdd);
+    return st;
 }
 
 // the LJ kernel on split positions with fixed-point force sums: double-float
@@ -642,6 +652,7 @@ template <class R> StepArgs<R> make_args(airebo_handle h, Precision<R>& pr, cons
     StepBuffers<R>& b = pr.b;
     a.n = h->n;
     a.P = b.P;
+    a.Pdd = h->opt.precision == AIREBO_DF64 ? h->pdd.b.P : nullptr;
     a.G.n = h->n; a.G.stride = h->stride; a.G.type = h->types; a.G.cnt = b.cnt; a.G.nj = b.nj; a.G.nimg = b.nimg;
     a.G.dx = b.dx; a.G.dy = b.dy; a.G.dz = b.dz; a.G.r = b.r; a.G.ir = b.ir; a.G.w = b.w; a.G.dw = b.dw; a.G.omw = b.omw; a.G.nC = b.nC; a.G.nH = b.nH;
     a.g_cnt = b.cnt; a.g_nj = b.nj; a.g_nimg = b.nimg; a.g_dx = b.dx; a.g_dy = b.dy; a.g_dz = b.dz;
@@ -878,8 +889,7 @@ airebo_status airebo_create(const char* params, const airebo_options* opts, void
     cudaError_t ce = cudaGetDevice(&h->device);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (ce != cudaSuccess) { delete h; return AIREBO_ERR_CUDA; }
-    st = h->opt.precision == AIREBO_MIXED ? upload_params<float>(h, h->p32) : upload_params<double>(h, h->p64);
-    if (!st && screen_on(h)) st = upload_params<float>(h, h->p32);
+    st = upload_own_params(h);
     if (!st) {
         if (realloc_dev(h->counts, 8) || realloc_dev(h->acc, 9) || realloc_dev(h->counters, 8) ||
             realloc_dev(h->derr, 8) || realloc_dev(h->maxd2, 1) || realloc_dev(h->ke, 1) ||
@@ -898,6 +908,7 @@ void airebo_destroy(airebo_handle h) {
     if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
     free_prec(h->p64);
     free_prec(h->p32);
+    free_prec(h->pdd);
     if (h->pg) cudaFree(h->pg);
     if (h->kg) cudaFree(h->kg);
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
@@ -1309,12 +1320,8 @@ airebo_status airebo_set_lj_params(airebo_handle h, const double* eps3, const do
     CK(cudaSetDevice(h->device));
     CK(cudaStreamSynchronize(h->stream));
     h->sc = s;
-    airebo_status st = h->opt.precision == AIREBO_MIXED ? upload_params<float>(h, h->p32) : upload_params<double>(h, h->p64);
+    airebo_status st = upload_own_params(h);
     if (st) return st;
-    if (screen_on(h)) {
-        st = upload_params<float>(h, h->p32);
-        if (st) return st;
-    }
     if (sigma_changed) h->built = false;          // the LJ cut-off moved: the lists must be rebuilt
     return AIREBO_OK;
 }
@@ -1390,6 +1397,12 @@ airebo_status airebo_math_check(int64_t* h_ulp4) {
     long long o[4] = {0, 0, 0, 0};
     if (math_check(o)) return AIREBO_ERR_CUDA;
     for (int k = 0; k < 4; k++) h_ulp4[k] = o[k];
+    return AIREBO_OK;
+}
+
+airebo_status airebo_dd_check(double* h_err8) {
+    if (!h_err8) return AIREBO_ERR_ARG;
+    if (dd_check(h_err8)) return AIREBO_ERR_CUDA;
     return AIREBO_OK;
 }
 

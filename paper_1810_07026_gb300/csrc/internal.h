@@ -30,6 +30,7 @@ template <class R> struct StepBuffers {
 template <class R> struct StepArgs {
     int n;
     const DevParams<R>* P;
+    const DevParams<dd>* Pdd;              // AIREBO_DF64: the parameters in double-float (torsion), null otherwise
     Graph<R> G;
     int* g_cnt; int* g_nj; int* g_nimg;
     R* g_dx; R* g_dy; R* g_dz; R* g_r; R* g_ir; R* g_w; R* g_dw; R* g_omw; R* g_nC; R* g_nH;
@@ -113,6 +114,7 @@ void launch_nve_half(double* pos, double* vel, const double* f, const int8_t* ty
                      bool drift, const double* xref, unsigned long long* maxdisp2_bits, double* ke, cudaStream_t s);
 double alu_peak(int fp64);
 int math_check(long long* out4);
+int dd_check(double* out8);
 void launch_max_disp(const double* pos, const double* xref, int n, unsigned long long* maxdisp2_bits, cudaStream_t s);
 
 }  // namespace airebo

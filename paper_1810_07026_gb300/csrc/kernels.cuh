@@ -13,6 +13,8 @@
 //   bstar       : one thread per queued pair: b*, S_b, forces (Alg. 3)
 #pragma once
 
+#include <type_traits>
+
 #include "internal.h"
 #include "ff.cuh"
 
@@ -201,6 +203,26 @@ __global__ void __launch_bounds__(128) k_torsion(StepArgs<R> a) {
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
         int2 bd = a.ccbonds[b];
         double e = torsion_bond<R>(P, a.G, bd.x, bd.y, sink);
+        E += e;
+        if (a.eatom && e != 0.0) atomicAdd(a.eatom + bd.x, e);
+    }
+    block_accumulate<128>(E, sink.W, EXTRA && a.virial, a.acc + 2, a.acc + 3);
+}
+
+// The torsion term in double-float on the FP64 short list (AIREBO_DF64): the
+// term is short arithmetic on data the list already holds, which the FP32 pipe
+// runs about three times faster than the FP64 pipe at FP64-class accuracy.
+template <bool EXTRA>
+__global__ void __launch_bounds__(128) k_torsion_dd(StepArgs<double> a) {
+    const DevParams<dd>& P = *a.Pdd;
+    GraphAs<dd, double> G(a.G);
+    Sink sink{a.f, a.n, EXTRA && a.virial, {0, 0, 0, 0, 0, 0}, false, {0, 0, 0, 0, 0, 0}};
+    double E = 0;
+    int nb = *a.nccbonds;
+    if (nb > a.bond_cap) nb = a.bond_cap;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        int2 bd = a.ccbonds[b];
+        double e = torsion_bond<dd>(P, G, bd.x, bd.y, sink);
         E += e;
         if (a.eatom && e != 0.0) atomicAdd(a.eatom + bd.x, e);
     }
@@ -810,8 +832,22 @@ void launch_compute_impl(const StepArgs<R>& a, cudaStream_t s, int num_sms, cuda
     }
     mark(2);
     if (a.torsion) {
-        if (extra) k_torsion<R, true><<<grid_of(1, a.bond_waves), 128, 0, s>>>(a);
-        else k_torsion<R, false><<<grid_of(1, a.bond_waves), 128, 0, s>>>(a);
+        bool dd_torsion = false;
+        if constexpr (std::is_same<R, double>::value) {
+            if (a.Pdd) {
+                static int occ_dd[2] = {-1, -1};
+                int& o = occ_dd[extra];
+                if (o < 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, extra ? k_torsion_dd<true> : k_torsion_dd<false>, 128, 0);
+                int g = num_sms * (o > 0 ? o : 1) * a.bond_waves;
+                if (extra) k_torsion_dd<true><<<g, 128, 0, s>>>(a);
+                else k_torsion_dd<false><<<g, 128, 0, s>>>(a);
+                dd_torsion = true;
+            }
+        }
+        if (!dd_torsion) {
+            if (extra) k_torsion<R, true><<<grid_of(1, a.bond_waves), 128, 0, s>>>(a);
+            else k_torsion<R, false><<<grid_of(1, a.bond_waves), 128, 0, s>>>(a);
+        }
     }
     mark(3);
     if (a.lj_on) k_path_map<R><<<(n + 127) / 128, 128, 0, s>>>(a);

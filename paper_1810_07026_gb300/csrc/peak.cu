@@ -1,5 +1,8 @@
 // FMA throughput probe: the ALU roofline denominator of the FP64 and mixed
-// paths, measured on the device the library runs on.
+// paths, measured on the device the library runs on; accuracy checks of the
+// FP64 reciprocals and of the double-float operations.
+#include <cstring>
+
 #include "internal.h"
 
 namespace airebo {
@@ -75,6 +78,62 @@ __global__ void k_math_check(unsigned long long* out, int n) {
     long long d4 = __double_as_longlong(a2) - __double_as_longlong(q2);
     atomicMax(out + 2, (unsigned long long)(d3 < 0 ? -d3 : d3));
     atomicMax(out + 3, (unsigned long long)(d4 < 0 ? -d4 : d4));
+}
+
+// Accuracy of the double-float operations (dd.cuh) against FP64 on the same
+// inputs, whose hi + lo sums are exact in FP64.  Operands a, b = +-m 2^t with
+// m uniform in [1, 2), t uniform in [-20, 20) (counter-based hash), split into
+// dd; t in [0, 2) for sin/cos of pi t.  out (as the bits of non-negative
+// doubles, so that atomicMax orders them): the largest error of a + b
+// relative to |a| + |b|; of a * b, a / b, 1 / a, 1 / sqrt(|a|) relative to
+// the exact-input FP64 result; of sin(pi t) and cos(pi t) absolute; of the
+// conversion from double relative.
+__device__ __forceinline__ double dd_rand(unsigned long long k, int salt, double lo, double hi) {
+    unsigned long long h = (k * 2 + salt) * 0x9E3779B97F4A7C15ull;
+    h ^= h >> 31; h *= 0xBF58476D1CE4E5B9ull; h ^= h >> 29;
+    return lo + (hi - lo) * (double)(h >> 11) * (1.0 / 9007199254740992.0);
+}
+__global__ void k_dd_check(unsigned long long* out, int n) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    auto pick = [&](int salt) {
+        double m = dd_rand(k, salt, 1.0, 2.0) * (dd_rand(k, salt + 7, 0.0, 1.0) < 0.5 ? -1.0 : 1.0);
+        return m * exp2(floor(dd_rand(k, salt + 13, -20.0, 20.0)));
+    };
+    double x = pick(1), y = pick(2);
+    dd a(x), b(y);
+    double ea = (double)a, eb = (double)b;             // the exact values of the operands
+    double t = dd_rand(k, 5, 0.0, 2.0);
+    dd u(t);
+    double eu = (double)u;
+    double err[8];
+    err[0] = fabs((double)(a + b) - (ea + eb)) / (fabs(ea) + fabs(eb));
+    err[1] = fabs((double)(a * b) / (ea * eb) - 1.0);
+    err[2] = fabs((double)(a / b) / (ea / eb) - 1.0);
+    err[3] = fabs((double)rcp_(a) * ea - 1.0);
+    dd aa = a.hi < 0.0f ? -a : a;
+    err[4] = fabs((double)rsqrt_(aa) * sqrt(fabs(ea)) - 1.0);
+    dd s, c;
+    sincospi_(u, &s, &c);
+    double rs, rc;
+    sincospi(eu, &rs, &rc);
+    err[5] = fabs((double)s - rs);
+    err[6] = fabs((double)c - rc);
+    err[7] = fabs(ea / x - 1.0);
+    for (int q = 0; q < 8; q++) atomicMax(out + q, (unsigned long long)__double_as_longlong(err[q]));
+}
+
+int dd_check(double* out8) {
+    unsigned long long* d = nullptr;
+    if (cudaMalloc(&d, 64) != cudaSuccess) return 1;
+    cudaMemset(d, 0, 64);
+    int n = 1 << 22;
+    k_dd_check<<<(n + 255) / 256, 256>>>(d, n);
+    unsigned long long h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    cudaError_t e = cudaMemcpy(h, d, 64, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    for (int k = 0; k < 8; k++) memcpy(out8 + k, h + k, 8);
+    return (e == cudaSuccess && cudaGetLastError() == cudaSuccess) ? 0 : 1;
 }
 
 int math_check(long long* out4) {

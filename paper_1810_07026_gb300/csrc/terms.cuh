@@ -15,8 +15,9 @@
 // F_b -= g, F_a += g and adds -v (x) g to the virial.
 //
 // R is the arithmetic type of the geometry, splines and bond order (double
-// for the FP64 path, float for the mixed path); forces, energies and virial
-// are always accumulated in double.
+// for the FP64 path, float for the mixed path, the double-float dd of dd.cuh
+// for the DF64 path); forces, energies and virial are always accumulated in
+// double.
 #pragma once
 
 #include <cstdint>
@@ -103,6 +104,8 @@ HD float rcp_(float x) {
     return 1.0f / x;
 #endif
 }
+HD double floor_(double x) { return floor(x); }
+HD float floor_(float x) { return floorf(x); }
 HD double sqrt_(double x) { return sqrt(x); }
 HD float sqrt_(float x) { return sqrtf(x); }
 HD double exp_(double x) { return exp(x); }
@@ -136,6 +139,14 @@ HD void sincospi_(float t, float* s, float* c) {
     *s = (float)std::sin(M_PI * (double)t); *c = (float)std::cos(M_PI * (double)t);
 #endif
 }
+
+}  // namespace airebo
+
+#ifdef __CUDACC__
+#include "dd.cuh"          // the double-float value type (R = dd: AIREBO_DF64)
+#endif
+
+namespace airebo {
 
 // ------------------------------------------------------------------ parameters
 template <class R> struct Quintic {
@@ -290,8 +301,8 @@ template <class R, bool D = true> HD R bicubic(const R* tab, R x, R y, R& fx, R&
     bool cx, cy;
     clamp_arg<R>(x, R(0), R(4), cx);
     clamp_arg<R>(y, R(0), R(4), cy);
-    int ix = clamp_cell((int)floor(x), 3);
-    int iy = clamp_cell((int)floor(y), 3);
+    int ix = clamp_cell((int)floor_(x), 3);
+    int iy = clamp_cell((int)floor_(y), 3);
     R tx = x - R(ix), ty = y - R(iy);
     const R* a = tab + (ix * 4 + iy) * 16;
     if (is_zero(tx) && is_zero(ty)) {        // at a knot (integer N^C, N^H): the corner coefficients
@@ -320,9 +331,9 @@ template <class R> HD int tri_cell_index(R& x, R& y, R& z, bool& clx, bool& cly,
     clamp_arg<R>(x, R(0), R(4), clx);
     clamp_arg<R>(y, R(0), R(4), cly);
     clamp_arg<R>(z, R(1), R(9), clz);
-    int ix = clamp_cell((int)floor(x), 3);
-    int iy = clamp_cell((int)floor(y), 3);
-    int iz = clamp_cell((int)floor(z - R(1)), 7);
+    int ix = clamp_cell((int)floor_(x), 3);
+    int iy = clamp_cell((int)floor_(y), 3);
+    int iz = clamp_cell((int)floor_(z - R(1)), 7);
     tx = x - R(ix); ty = y - R(iy); tz = z - R(1) - R(iz);
     return (ix * 4 + iy) * 8 + iz;
 }
@@ -375,8 +386,8 @@ template <class R> HD void kg_bicubic(double* g, R x, R y, double adj) {
     bool cx, cy;
     clamp_arg<R>(x, R(0), R(4), cx);
     clamp_arg<R>(y, R(0), R(4), cy);
-    int ix = clamp_cell((int)floor(x), 3);
-    int iy = clamp_cell((int)floor(y), 3);
+    int ix = clamp_cell((int)floor_(x), 3);
+    int iy = clamp_cell((int)floor_(y), 3);
     double tx = (double)(x - R(ix)), ty = (double)(y - R(iy));
     g += (ix * 4 + iy) * 16;
     double xp = adj;
@@ -411,11 +422,27 @@ template <class R> struct Graph {
     const R* nC; const R* nH;                // sum of w over C / H neighbours
 };
 
+// The short REBO list of one precision read in another arithmetic type: the
+// torsion term of the DF64 path runs in double-float on the FP64 list.
+template <class R, class S> struct ConvArray {
+    const S* p;
+    HD R operator[](size_t i) const { return R(p[i]); }
+};
+template <class R, class S> struct GraphAs {
+    int n, stride;
+    const int8_t* type;
+    const int* cnt; const int* nj; const int* nimg;
+    ConvArray<R, S> dx, dy, dz, r, ir, w, dw, omw, nC, nH;
+    HD explicit GraphAs(const Graph<S>& g)
+        : n(g.n), stride(g.stride), type(g.type), cnt(g.cnt), nj(g.nj), nimg(g.nimg), dx{g.dx}, dy{g.dy}, dz{g.dz},
+          r{g.r}, ir{g.ir}, w{g.w}, dw{g.dw}, omw{g.omw}, nC{g.nC}, nH{g.nH} {}
+};
+
 // Slot of atom o among the REBO neighbours of c (MAXN when absent).  The
 // loops over N(c) \ {o} below run over the other slots by index, so that
 // threads whose atoms have equal neighbour counts run equal trip counts
 // instead of each skipping o at a different iteration.
-template <class R> HD int slot_of(const Graph<R>& G, int c, int o) {
+template <class GT> HD int slot_of(const GT& G, int c, int o) {
     int nc = G.cnt[c];
     for (int a = 0; a < nc; a++)
         if (G.nj[c * G.stride + a] == o) return a;
@@ -438,6 +465,15 @@ struct Sink {
             W[3] -= vx * gy; W[4] -= vx * gz; W[5] -= vy * gz;
         }
     }
+#ifdef __CUDACC__
+    // the same from double-float vectors
+    HD void pair(int a, int b, dd vx, dd vy, dd vz, dd gx, dd gy, dd gz) {
+        pair(a, b, (double)vx, (double)vy, (double)vz, (double)gx, (double)gy, (double)gz);
+    }
+    HD void half(int b, dd vx, dd vy, dd vz, dd gx, dd gy, dd gz, double& fax, double& fay, double& faz) {
+        half(b, (double)vx, (double)vy, (double)vz, (double)gx, (double)gy, (double)gz, fax, fay, faz);
+    }
+#endif
     // gradient on the vector from a to b, where the force on a is kept by the caller
     HD void half(int b, double vx, double vy, double vz, double gx, double gy, double gz,
                  double& fax, double& fay, double& faz) {
@@ -506,7 +542,7 @@ HD void side_forward(const DevParams<R>& P, const Graph<R>& G, int c, int o, R u
                      Side<R>& s) {
     int tc = G.type[c], to = G.type[o];
     int nc = G.cnt[c];
-    int so = slot_of<R>(G, c, o);
+    int so = slot_of(G, c, o);
     int m = nc - (so < MAXN);
     s.NC = 0; s.NH = 0; s.conj = 0;
     for (int t = 0; t < m; t++) {
@@ -564,7 +600,7 @@ HD void side_reverse(const DevParams<R>& P, const Graph<R>& G, int c, int o, R u
         int tab = (tc == 0 && to == 0) ? 0 : (tc == 0 ? 1 : 2);
         kg_bicubic<R>(P.kg + KG_P + tab * 256, s.NC, s.NH, (double)ac);
     }
-    int so = slot_of<R>(G, c, o);
+    int so = slot_of(G, c, o);
     int m = nc - (so < MAXN);
     for (int t = 0; t < m; t++) {
         int a = t + (t >= so);
@@ -641,7 +677,7 @@ HD R dihedral_sum(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, 
                   double& fix, double& fiy, double& fiz, double& fjx, double& fjy, double& fjz) {
     R D = 0;
     int ni = G.cnt[i], nj = G.cnt[j];
-    int sj = slot_of<R>(G, i, j), si_ = slot_of<R>(G, j, i);
+    int sj = slot_of(G, i, j), si_ = slot_of(G, j, i);
     int mi = ni - (sj < MAXN), mj = nj - (si_ < MAXN);
     for (int ta = 0; ta < mi; ta++) {
         int a = ta + (ta >= sj);
@@ -814,7 +850,7 @@ HD double rebo_bond(const DevParams<R>& P, const Graph<R>& G, int i, int slot, S
     R e = dEdr * ir;
     gux += e * ux; guy += e * uy; guz += e * uz;
     // vector u runs from i to j
-    double gx = gux, gy = guy, gz = guz;
+    double gx = (double)gux, gy = (double)guy, gz = (double)guz;
     atomic_add(sink.f + i, fix + gx); atomic_add(sink.f + sink.n + i, fiy + gy); atomic_add(sink.f + 2 * sink.n + i, fiz + gz);
     atomic_add(sink.f + j, fjx - gx); atomic_add(sink.f + sink.n + j, fjy - gy); atomic_add(sink.f + 2 * sink.n + j, fjz - gz);
     if (sink.virial) {
@@ -826,8 +862,8 @@ HD double rebo_bond(const DevParams<R>& P, const Graph<R>& G, int i, int slot, S
 
 // ------------------------------------------------------------------ torsion (Alg. 2)
 // omega is the dihedral angle with trans = pi; cos^2(omega/2) = (1 + cos omega)/2
-template <class R>
-HD double torsion_bond(const DevParams<R>& P, const Graph<R>& G, int i, int slot, Sink& sink) {
+template <class R, class GT>
+HD double torsion_bond(const DevParams<R>& P, const GT& G, int i, int slot, Sink& sink) {
     int q = i * G.stride + slot;
     int j = G.nj[q];
     R ux = G.dx[q], uy = G.dy[q], uz = G.dz[q];
@@ -838,7 +874,7 @@ HD double torsion_bond(const DevParams<R>& P, const Graph<R>& G, int i, int slot
     R gux = 0, guy = 0, guz = 0;
     double fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
     int ni = G.cnt[i], nj = G.cnt[j];
-    int sj = slot_of<R>(G, i, j), si_ = slot_of<R>(G, j, i);
+    int sj = slot_of(G, i, j), si_ = slot_of(G, j, i);
     int mi = ni - (sj < MAXN), mj = nj - (si_ < MAXN);
     for (int ta = 0; ta < mi; ta++) {
         int a = ta + (ta >= sj);
@@ -910,7 +946,7 @@ HD double torsion_bond(const DevParams<R>& P, const Graph<R>& G, int i, int slot
         }
     }
     if (!any) return 0.0;
-    double gx = gux, gy = guy, gz = guz;
+    double gx = (double)gux, gy = (double)guy, gz = (double)guz;
     atomic_add(sink.f + i, fix + gx); atomic_add(sink.f + sink.n + i, fiy + gy); atomic_add(sink.f + 2 * sink.n + i, fiz + gz);
     atomic_add(sink.f + j, fjx - gx); atomic_add(sink.f + sink.n + j, fjy - gy); atomic_add(sink.f + 2 * sink.n + j, fjz - gz);
     if (sink.virial) {
@@ -1218,7 +1254,7 @@ HD double bstar_finish(const DevParams<R>& P, const Graph<R>& G, int i, int j, R
     R factor = Sr * Sb + R(1) - Sr;
     R E = factor * C * V;
     R dEdr_r = (dSr * (Sb - R(1))) * C * V * inv_r + factor * C * dVr;   // (dE/dr)/r
-    double gx = dEdr_r * dx, gy = dEdr_r * dy, gz = dEdr_r * dz;
+    double gx = (double)(dEdr_r * dx), gy = (double)(dEdr_r * dy), gz = (double)(dEdr_r * dz);
     double fix = 0, fiy = 0, fiz = 0;
     if (path_code >= 0) path_forces<R>(G, i, path_code, -factor * V, sink, fix, fiy, fiz);
     if (sink.pgrad) {
@@ -1285,9 +1321,9 @@ HD double bstar_full(const DevParams<R>& P, const Graph<R>& G, int i, int j, R d
         // u = r* d/|d|: only the direction of d carries a gradient
         R ud = (gux * dx + guy * dy + guz * dz) * inv_r;
         R sc = rs * inv_r;
-        double gx = sc * (gux - ud * dx * inv_r);
-        double gy = sc * (guy - ud * dy * inv_r);
-        double gz = sc * (guz - ud * dz * inv_r);
+        double gx = (double)(sc * (gux - ud * dx * inv_r));
+        double gy = (double)(sc * (guy - ud * dy * inv_r));
+        double gz = (double)(sc * (guz - ud * dz * inv_r));
         atomic_add(sink.f + i, fix + gx); atomic_add(sink.f + sink.n + i, fiy + gy); atomic_add(sink.f + 2 * sink.n + i, fiz + gz);
         atomic_add(sink.f + j, fjx - gx); atomic_add(sink.f + sink.n + j, fjy - gy); atomic_add(sink.f + 2 * sink.n + j, fjz - gz);
         if (sink.virial) {
