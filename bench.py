@@ -419,7 +419,7 @@ def run_ours(args):
                       (flops_lj / (mlj_ms * 1e-3 / mlj_n) / 1e12) / peak32_nom},
             "df64": {"value": replica_throughput(n, args.steps, ws, results["df64"]["ms"]), "unit": UNIT,
                      "ms_per_step": results["df64"]["ms"] / args.steps,
-                     "dtype": "f64, LJ pair arithmetic in double-float (f32 pairs) with 64-bit fixed-point force sums",
+                     "dtype": "f64; LJ pair and torsion arithmetic in double-float (f32 pairs), LJ forces in 64-bit fixed point",
                      "max_abs_dF_vs_fp64": (forces["df64"] - forces["fp64"]).abs().max().item(),
                      "max_rel_dF_vs_fp64": (forces["df64"] - forces["fp64"]).abs().max().item() / fscale,
                      "drift_eV_per_atom_step": results["df64"]["drift"],

@@ -63,7 +63,8 @@ typedef enum {
  * of the Lennard-Jones pairs with C_ij = 1 and no b* runs in double-float
  * (pairs of FP32 numbers, about 48 significant bits) on the FP32 pipe, from
  * positions split on a 2^-12 A grid, with the pair forces summed in 64-bit
- * fixed point (2^-40 eV/A) -- FP64-class results at FP32-pipe rates.  It
+ * fixed point (2^-40 eV/A), and the torsion term runs in double-float on the
+ * FP64 short list -- FP64-class results at FP32-pipe rates.  It
  * needs every |coordinate| below 2000 A and pair forces below 1e6 eV/A
  * (AIREBO_ERR_ARG / AIREBO_ERR_NONFINITE otherwise), as does AIREBO_MIXED;
  * with the Morse form both run their LJ pairs as before the split (FP64
