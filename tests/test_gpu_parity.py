@@ -71,8 +71,10 @@ def test_fp64_parity(A, oracle, param_text, case, term):
 
 
 @pytest.mark.parametrize("case", list(CASES))
-@pytest.mark.parametrize("term", ["all", "lj"])
+@pytest.mark.parametrize("term", list(FLAGS))
 def test_df64_parity(A, oracle, param_text, case, term):
+    """DF64 (LJ pair and torsion arithmetic in double-float) against the
+    oracle, term by term, at the FP64 tolerances."""
     pos, types, box = CASES[case]()
     flags = FLAGS[term]
     e, f, w, _ = oracle.compute(pos, types, box, flags)
@@ -81,8 +83,9 @@ def test_df64_parity(A, oracle, param_text, case, term):
 
 
 def test_df64_against_fp64_pe32k(A, param_text):
-    """DF64 against FP64 on the 32,640-atom PE: the LJ pair arithmetic in
-    double-float and its fixed-point force sums stay within 1e-11 of FP64."""
+    """DF64 against FP64 on the 32,640-atom PE: the LJ pair and torsion
+    arithmetic in double-float and the fixed-point LJ force sums stay within
+    1e-11 of FP64."""
     pos, types, box = inputs.workload("pe32k")
     (e64, f64, w64), _ = gpu_eval(A, param_text, pos, types, box)
     (edf, fdf, wdf), _ = gpu_eval(A, param_text, pos, types, box, precision=A.DF64)
