@@ -89,18 +89,17 @@ __device__ __forceinline__ void load_disp(const double* pos, int n, const double
     }
 }
 
-// ------------------------------------------------------------------ short list
+// ------------------------------------------------------------------ FP32 positions
+// FP32 position and species of every atom for the FP32 pre-tests of the
+// short-list and LJ kernels; with split positions (fixed-point LJ sums) the
+// FP32 position is the hi part, on the 2^-12 A grid, and pq_lo holds the rest.
 template <class R>
-__global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
+__global__ void __launch_bounds__(128) k_posf(StepArgs<R> a) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
-    const DevParams<R>& P = *a.P;
     int n = a.n;
     double xi = a.pos[i], yi = a.pos[n + i], zi = a.pos[2 * n + i];
     if (!isfinite(xi) || !isfinite(yi) || !isfinite(zi)) atomicMax(a.err + ERR_NONFINITE, 1);
-    // FP32 position and species for the LJ kernel's pair tests; with split
-    // positions (fixed-point LJ sums) the FP32 position is the hi part, on the
-    // 2^-12 A grid, and pq_lo holds the rest
     if (a.fix) {
         if (!(fabs(xi) < 2000.0 && fabs(yi) < 2000.0 && fabs(zi) < 2000.0)) atomicMax(a.err + ERR_DF, 1);
         float4 h, l;
@@ -112,15 +111,57 @@ __global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
     } else {
         a.posf[i] = make_float4((float)xi, (float)yi, (float)zi, __int_as_float((int)a.G.type[i]));
     }
+}
+
+// ------------------------------------------------------------------ short list
+// Most entries of the intermediate list lie beyond D_max (in hydrocarbons
+// about 12 of 14): an FP32 distance on the FP32 positions rules those out
+// without FP64 instructions.  Per component the FP32 displacement f differs
+// from the FP64 one d by at most e = 2^-22 (2 |x_i| + 4 |S| L + 8) (the
+// roundings of x_i, x_j, S L and of the FP32 additions, with |x_j| <= |x_i| +
+// |d| + |S| L and a factor of about 2 to spare), plus 2^-11 for split
+// positions (hi parts on the 2^-12 grid).  Then |r2f - r2| <= e (2 sum |f_c|
+// + 3 e) plus the rounding of r2f, and an entry with r2f beyond D_max^2 by
+// more than that is beyond D_max in FP64 too.  The others take the exact FP64
+// test.
+template <class R>
+__global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const DevParams<R>& P = *a.P;
+    int n = a.n;
+    double xi = a.pos[i], yi = a.pos[n + i], zi = a.pos[2 * n + i];
+    float4 pfi = a.posf[i];
+    float err0 = 2.3841858e-7f * (2.0f * fmaxf(fabsf(pfi.x), fmaxf(fabsf(pfi.y), fabsf(pfi.z))) + 8.0f) +
+                 (a.fix ? 4.8828125e-4f : 0.0f);
     int ti = a.G.type[i];
     int cnt = 0;
     R nC = 0, nH = 0;
     int ne = a.im_cnt[i];
     const int2* row = a.im + (size_t)i * a.im_cap;
     const double* L = box_of(a, i);
+    float Lf[3] = {(float)L[0], (float)L[1], (float)L[2]};
+    float Lmax = fmaxf(Lf[0], fmaxf(Lf[1], Lf[2]));
     for (int e = 0; e < ne; e++) {
         int2 ent = row[e];
         int j = ent.x, img = ent.y;
+        float4 pj = a.posf[j];
+        int tj = __float_as_int(pj.w);
+        int p = pidx(ti, tj);
+        {
+            float fx = pj.x - pfi.x, fy = pj.y - pfi.y, fz = pj.z - pfi.z;
+            float err = err0;
+            if (img != 0) {
+                int sx = img_x(img), sy = img_y(img), sz = img_z(img);
+                fx += (float)sx * Lf[0]; fy += (float)sy * Lf[1]; fz += (float)sz * Lf[2];
+                err += 9.5367432e-7f * (float)max(abs(sx), max(abs(sy), abs(sz))) * Lmax;    // 2^-22 4 |S| L
+            }
+            // |r2f - r2| <= sum_c |f_c - d_c| (2 |f_c| + |f_c - d_c|) + rounding
+            float r2f = fx * fx + fy * fy + fz * fz;
+            float band = err * (2.0f * (fabsf(fx) + fabsf(fy) + fabsf(fz)) + 3.0f * err) + 1e-6f * r2f;
+            float dmf = (float)P.Dmax[p];
+            if (r2f > dmf * dmf * 1.000001f + band) continue;
+        }
         double dx, dy, dz;
         if (img == 0) {               // most entries: no image, three FP64 operations
             dx = a.pos[j] - xi; dy = a.pos[n + j] - yi; dz = a.pos[2 * n + j] - zi;
@@ -130,8 +171,6 @@ __global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
             dz = a.pos[2 * n + j] + img_z(img) * L[2] - zi;
         }
         double r2 = dx * dx + dy * dy + dz * dz;
-        int tj = a.G.type[j];
-        int p = pidx(ti, tj);
         double dmax = (double)P.Dmax[p];
         if (!(r2 < dmax * dmax)) continue;
         double ir = rsqrt_(r2);
@@ -824,6 +863,7 @@ void launch_compute_impl(const StepArgs<R>& a, cudaStream_t s, int num_sms, cuda
     }
     auto grid_of = [&](int k, int waves) { return num_sms * (occ[k] > 0 ? occ[k] : 1) * waves; };
     mark(0);
+    k_posf<R><<<(n + 127) / 128, 128, 0, s>>>(a);
     k_short_list<R><<<(n + 127) / 128, 128, 0, s>>>(a);
     mark(1);
     if (a.rebo) {
