@@ -15,9 +15,9 @@
 // F_b -= g, F_a += g and adds -v (x) g to the virial.
 //
 // R is the arithmetic type of the geometry, splines and bond order (double
-// for the FP64 path, float for the mixed path, the double-float dd of dd.cuh
-// for the DF64 path); forces, energies and virial are always accumulated in
-// double.
+// for the FP64 path, float for the mixed path, and the double-float dd of
+// dd.cuh for the torsion term of the DF64 path); forces, energies and virial
+// are always accumulated in double.
 #pragma once
 
 #include <cstdint>
@@ -143,7 +143,7 @@ HD void sincospi_(float t, float* s, float* c) {
 }  // namespace airebo
 
 #ifdef __CUDACC__
-#include "dd.cuh"          // the double-float value type (R = dd: AIREBO_DF64)
+#include "dd.cuh"          // the double-float value type (R = dd: the DF64 torsion term)
 #endif
 
 namespace airebo {
