@@ -749,7 +749,10 @@ __device__ __forceinline__ void bstar_load(const StepArgs<R>& a, int t, int& i, 
 }
 
 template <class R, bool EXTRA>
-__global__ void __launch_bounds__(128) k_bstar(StepArgs<R> a) {
+// 64 registers (8 blocks of 128 per SM): this pass waits mostly on the
+// gathers of the FP32 screen, and twice the warps of the compiler's own
+// choice (80 registers) hide more of them (1.12 -> 1.03 ms at 1M PE, FP64)
+__global__ void __launch_bounds__(128, 8) k_bstar(StepArgs<R> a) {
     const DevParams<R>& P = *a.P;
     Sink sink{a.f, a.n, EXTRA && a.virial, {0, 0, 0, 0, 0, 0}, EXTRA && a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
     double E = 0;
