@@ -57,28 +57,41 @@ __global__ void k_bin(NeighborArgs a) {
 }
 
 // exclusive scan of the cell counts, one block
-__global__ void k_scan(const int* count, int* start, int* fill, int ncell) {
-    __shared__ int part[1024];
-    int t = threadIdx.x;
-    int per = (ncell + 1023) / 1024;
-    int lo = t * per, hi = min(lo + per, ncell);
-    int s = 0;
-    for (int c = lo; c < hi; c++) s += count[c];
-    part[t] = s;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        int v = t >= o ? part[t - o] : 0;
+// Exclusive scan of the cell counts into the cell starts (and the fill
+// cursors), by one block over tiles of 1024 cells: coalesced loads, a
+// shuffle scan in each warp, then over the warps' sums, and a running carry.
+__global__ void __launch_bounds__(1024) k_scan(const int* count, int* start, int* fill, int ncell) {
+    __shared__ int wsum[32];
+    int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    int carry = 0;
+    for (int base = 0; base < ncell; base += 1024) {
+        int c = base + t;
+        int v = c < ncell ? count[c] : 0;
+        int x = v;                                   // inclusive scan within the warp
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
         __syncthreads();
-        part[t] += v;
+        if (w == 0) {                                // inclusive scan of the 32 warp sums
+            int y = wsum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                int z = __shfl_up_sync(0xffffffffu, y, o);
+                if (lane >= o) y += z;
+            }
+            wsum[lane] = y;
+        }
         __syncthreads();
+        int excl = carry + (w > 0 ? wsum[w - 1] : 0) + x - v;
+        if (c < ncell) {
+            start[c] = excl;
+            fill[c] = excl;
+        }
+        carry += wsum[31];
+        __syncthreads();                             // wsum is rewritten by the next tile
     }
-    int run = part[t] - s;
-    for (int c = lo; c < hi; c++) {
-        start[c] = run;
-        fill[c] = run;
-        run += count[c];
-    }
-    if (t == 1023) start[ncell] = part[1023];
+    if (t == 0) start[ncell] = carry;
 }
 
 __global__ void k_scatter(NeighborArgs a) {
