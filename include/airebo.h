@@ -282,9 +282,11 @@ airebo_status airebo_graph_launch(airebo_handle h);
  * Pick the launch shapes for this handle's system by timing them with CUDA
  * events on the handle's stream: the number of atoms an LJ warp claims at a
  * time (2..16), and the grids of the grid-stride REBO/torsion kernels and of
- * the b* kernels, in waves of resident blocks (2, 4, 8 or 16 times the blocks
- * that fit on all SMs at once); each candidate is the median of 5
- * evaluations.  Runs about 45 evaluations at d_pos (d_force is overwritten).
+ * the b* kernels, in waves of resident blocks (2, 4, 8, 16 or 32 times the
+ * blocks that fit on all SMs at once); each candidate is the median of 5
+ * evaluations.  Runs about 50 evaluations at d_pos (d_force is overwritten).
+ * Untuned handles start at (2, 16, 16), the shapes tuned on a 1M-atom
+ * polyethylene in FP64.
  * out3 (nullable, host int[3]) receives (lj_chunk, bond_waves, bstar_waves).  A
  * graph captured earlier keeps the shapes it was captured with.  Errors:
  * those of airebo_compute; AIREBO_ERR_STATE before airebo_neighbor.

@@ -364,7 +364,9 @@ struct airebo_ctx {
     unsigned long long* counters = nullptr;   // 8
     int* derr = nullptr;                 // 8 ints
     int stride = 8;                      // REBO slots per atom (grows to MAXN)
-    int lj_chunk = 4, bond_waves = 8, bstar_waves = 8;   // launch shapes (airebo_autotune)
+    // launch shapes (airebo_autotune); the defaults are the tuned shapes of the
+    // 1M-atom PE in FP64 (grids of one b* pair or bond per thread at that size)
+    int lj_chunk = 2, bond_waves = 16, bstar_waves = 16;
     // batched systems (nsys = 0: one system with box L)
     int nsys = 0;
     std::vector<double> Lsys_h;
@@ -554,9 +556,12 @@ airebo_status do_neighbor(airebo_handle h, const double* d_pos) {
     rlj += 2e-3;
     int ncell = 1;
     double rho_max = 0;
+    // without the long list the cut-off is the REBO one: half of it would make
+    // cells of less than one atom, whose per-cell work outweighs the pruning
+    int div = h->opt.enable_lj ? CELL_DIV : 1;
     if (h->nsys == 0) {
         for (int d = 0; d < 3; d++) {
-            h->nc[d] = std::max(1, (int)std::floor(h->L[d] * CELL_DIV / rlj));
+            h->nc[d] = std::max(1, (int)std::floor(h->L[d] * div / rlj));
             h->cell_w[d] = h->L[d] / h->nc[d];
             h->reach[d] = (int)std::ceil(rlj / h->cell_w[d]);
             ncell *= h->nc[d];
@@ -571,7 +576,7 @@ airebo_status do_neighbor(airebo_handle h, const double* d_pos) {
             int cs = 1;
             for (int d = 0; d < 3; d++) {
                 double L = h->Lsys_h[3 * s + d];
-                nc[3 * s + d] = std::max(1, (int)std::floor(L * CELL_DIV / rlj));
+                nc[3 * s + d] = std::max(1, (int)std::floor(L * div / rlj));
                 cw[3 * s + d] = L / nc[3 * s + d];
                 reach[3 * s + d] = (int)std::ceil(rlj / cw[3 * s + d]);
                 cs *= nc[3 * s + d];
@@ -1221,7 +1226,7 @@ airebo_status airebo_autotune(airebo_handle h, const double* d_pos, double* d_fo
         return AIREBO_OK;
     };
     const int chunks[] = {2, 4, 8, 16};
-    const int waves[] = {2, 4, 8, 16};
+    const int waves[] = {2, 4, 8, 16, 32};
     double best_lj = 1e300, best_bond = 1e300, best_bstar = 1e300;
     int bc = h->lj_chunk, bg = h->bond_waves, bs = h->bstar_waves;
     // the LJ chunk and the two grids act on different kernels: tune each
