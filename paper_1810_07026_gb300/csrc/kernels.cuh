@@ -1,16 +1,24 @@
 // Compute kernels of one step (templated on the arithmetic type R).
 //
+//   posf        : one thread per atom: FP32 (or split hi + lo) positions for
+//                 the FP32 pre-tests
 //   short_list  : exact REBO neighbours (r < Dmax_ij) from the intermediate
 //                 list, w and dw/dr, N^C, N^H per atom, the i<j bond list
 //                 (Sec. 4.1: rebuilt every step from a list with a skin)
 //   rebo        : one thread per bond: b_ij forward + reverse, E = f_R + b f_A (Alg. 1)
-//   torsion     : one thread per C-C bond (Alg. 2)
+//   torsion     : one thread per C-C bond (Alg. 2); torsion_dd the same in
+//                 double-float for AIREBO_DF64
 //   path_map    : one thread per atom: connectivity map over <= 3 bonds, the
 //                 reverse of the per-pair C_ij search (Sec. 4.3)
-//   lj          : one warp per atom i, lanes over its half list: cut-off test,
-//                 C_ij lookup, V^LJ, forces; pairs with S_r != 0 are queued
-//                 for b* (the deferred batch of Sec. 4.3)
-//   bstar       : one thread per queued pair: b*, S_b, forces (Alg. 3)
+//   lj          : persistent warps over chunks of atoms, lanes over an atom's
+//                 half list: cut-off test, C_ij lookup, then the live pairs
+//                 compacted into batches of 32 for V^LJ and forces; pairs
+//                 with S_r != 0 are queued for b* (the deferred batch of Sec. 4.3)
+//   bstar       : one thread per queued pair: b*, S_b, forces (Alg. 3), in
+//                 two passes (pairs whose S_b is exactly 0 or 1, then the rest)
+//
+// Kernels with an EXTRA template flag have an instance without virial and
+// parameter-gradient accumulators, used whenever neither is asked for.
 #pragma once
 
 #include <type_traits>
