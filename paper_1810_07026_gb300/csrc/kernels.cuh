@@ -806,8 +806,10 @@ __global__ void __launch_bounds__(128, 8) k_bstar(StepArgs<R> a) {
 }
 
 // Phase 2: the pairs of the second queue, b* and its gradient in one pass.
+// The FP32 (mixed) instance at 5 blocks per SM (0.655 -> 0.613 ms at 1M PE);
+// the FP64 one is best at 4 (3.0 ms; 3 and 5 blocks: 3.6 and 3.1 ms).
 template <class R, bool EXTRA>
-__global__ void __launch_bounds__(128, 4) k_bstar_rev(StepArgs<R> a) {
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 4) k_bstar_rev(StepArgs<R> a) {
     const DevParams<R>& P = *a.P;
     Sink sink{a.f, a.n, EXTRA && a.virial, {0, 0, 0, 0, 0, 0}, EXTRA && a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
     double E = 0;
