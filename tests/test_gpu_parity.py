@@ -331,6 +331,39 @@ def test_nve_against_oracle_trajectory(A, oracle, param_text, case, temp, precis
     assert abs(e4[1] - ke_o) <= etol * 10 * abs(ke_o)
 
 
+@pytest.mark.parametrize("precision", [0, 2])
+def test_trace_rerun_frames(A, oracle, param_text, precision):
+    """Trace dump and rerun: the oracle drives a hot reactive NVE run (2000 K,
+    bonds forming and breaking) and records 20 frames; the GPU path then
+    evaluates every recorded frame on its own, so both see identical inputs,
+    and each frame's energy and forces must match the oracle's."""
+    pos, types, box = CASES["hot300"]()
+    vel = inputs.velocities(types, 2000.0, seed=9)
+    m = np.where(types == 0, 12.011, 1.008)
+    dt = 0.5
+    x, v = pos.copy(), vel.copy()
+    e, f, _, _ = oracle.compute(x, types, box)
+    frames = []
+    for _ in range(20):
+        v += 0.5 * dt * f / m / inputs.MVV2E
+        x += dt * v
+        e, f, _, _ = oracle.compute(x, types, box)
+        v += 0.5 * dt * f / m / inputs.MVV2E
+        frames.append((x.copy(), e.copy(), f.copy()))
+    ev = A.Airebo(param_text, precision=precision, skin=0.1)
+    t = torch.tensor(types, device="cuda")
+    for k, (xk, ek, fk) in enumerate(frames):
+        p = torch.tensor(xk, device="cuda")
+        ev.neighbor(p, t, box)
+        fg, eg, _ = ev.compute(p)
+        torch.cuda.synchronize()
+        eg = eg.cpu().numpy()
+        fg = fg.cpu().numpy()
+        assert abs(eg[0] - ek[0]) <= 1e-10 * abs(ek[0]), (k, eg, ek)
+        assert np.abs(fg - fk).max() <= 1e-8 * np.abs(fk).max(), (k, np.abs(fg - fk).max())
+    ev.close()
+
+
 def test_nve_energy_conservation(A, param_text):
     pos, types, box = inputs.diamond()
     vel = inputs.velocities(types, 1000.0, seed=3)
