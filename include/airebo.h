@@ -48,7 +48,7 @@ typedef enum {
     AIREBO_ERR_CUDA = 2,       /* a CUDA runtime call failed (text in airebo_last_error) */
     AIREBO_ERR_CAPACITY = 3,   /* more than 16 REBO neighbours on an atom (twice the bound of Sec. 4.3) */
     AIREBO_ERR_TIMEOUT = 4,    /* reserved: a bounded device-side wait gave up */
-    AIREBO_ERR_NONFINITE = 5,  /* a position is NaN or infinite */
+    AIREBO_ERR_NONFINITE = 5,  /* a position is NaN or infinite, or two atoms closer than 1e-6 A */
     AIREBO_ERR_STATE = 6       /* call out of order, e.g. compute before neighbor */
 } airebo_status;
 

@@ -757,7 +757,9 @@ airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos,
                 if (ran[k]) { h->kt_ms[slot] += ms; h->kt_n[slot] += 1; }
             }
         }
-        if (h->h_err[ERR_NONFINITE]) return fail(h, AIREBO_ERR_NONFINITE, "non-finite position");
+        if (h->h_err[ERR_NONFINITE] == 1) return fail(h, AIREBO_ERR_NONFINITE, "non-finite position");
+        if (h->h_err[ERR_NONFINITE] == 2)
+            return fail(h, AIREBO_ERR_NONFINITE, "two atoms closer than 1e-6 A (overlapping atoms)");
         if (h->h_err[ERR_DF] == 1)
             return fail(h, AIREBO_ERR_ARG, "AIREBO_DF64 and AIREBO_MIXED need every |coordinate| below 2000 A");
         if (h->h_err[ERR_DF] == 2)
@@ -1159,7 +1161,9 @@ airebo_status airebo_check(airebo_handle h) {
     CK(cudaMemcpyAsync(h->h_u64, h->counts, sizeof(int) * 8, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     const int* cn = (const int*)h->h_u64;
-    if (h->h_err[ERR_NONFINITE]) return fail(h, AIREBO_ERR_NONFINITE, "non-finite position");
+    if (h->h_err[ERR_NONFINITE])
+        return fail(h, AIREBO_ERR_NONFINITE, h->h_err[ERR_NONFINITE] == 2 ? "two atoms closer than 1e-6 A (overlapping atoms)"
+                                                                           : "non-finite position");
     if (h->h_err[ERR_SHORT] > h->stride || h->h_err[ERR_MAP] ||
         std::max(cn[4], std::max(cn[5], cn[6])) > h->bq_cap)
         return fail(h, AIREBO_ERR_CAPACITY, "a scratch capacity was exceeded; run airebo_compute once to grow it");

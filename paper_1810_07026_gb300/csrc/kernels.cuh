@@ -181,6 +181,8 @@ __global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
         double r2 = dx * dx + dy * dy + dz * dz;
         double dmax = (double)P.Dmax[p];
         if (!(r2 < dmax * dmax)) continue;
+        // two atoms at (nearly) one point: every term diverges there
+        if (!(r2 > 1e-12)) { atomicMax(a.err + ERR_NONFINITE, 2); continue; }
         double ir = rsqrt_(r2);
         double r = r2 * ir;
         R dw, omw;

@@ -261,6 +261,13 @@ def test_errors(A, param_text):
     with pytest.raises(A.AireboError) as ex:
         ev.compute(bad)
     assert ex.value.status == A.ERR_NONFINITE
+    # two atoms at one point
+    ov = p.clone()
+    ov[:, 7] = ov[:, 3]
+    ev.neighbor(ov, t, box)
+    with pytest.raises(A.AireboError) as ex:
+        ev.compute(ov)
+    assert ex.value.status == A.ERR_NONFINITE and "overlapping" in str(ex.value)
     # more than 16 REBO neighbours: a cluster of 20 carbons within 2 A of each other
     rng = np.random.default_rng(0)
     cl = rng.uniform(-0.5, 0.5, (3, 20)) + 10.0
