@@ -371,6 +371,38 @@ def test_trace_rerun_frames(A, oracle, param_text, precision):
     ev.close()
 
 
+def test_nve_resume_from_checkpoint(A, param_text, tmp_path):
+    """Ten NVE steps in one run equal five steps, a checkpoint file, and five
+    more steps on a fresh handle built from the file (to the order of the
+    atomic sums)."""
+    from paper_1810_07026_gb300 import checkpoint
+    pos, types, box = CASES["pe1152"]()
+    vel = inputs.velocities(types, 600.0, seed=6)
+    t = torch.tensor(types, device="cuda")
+
+    def run(p0, v0, steps):
+        ev = A.Airebo(param_text)
+        p = torch.tensor(p0, device="cuda")
+        v = torch.tensor(v0, device="cuda")
+        ev.neighbor(p, t, box)
+        f, _, _ = ev.compute(p)
+        e4 = ev.nve(p, v, f, 0.5, steps)
+        torch.cuda.synchronize()
+        ev.close()
+        return p.cpu().numpy(), v.cpu().numpy(), e4.cpu().numpy()
+
+    x10, v10, e10 = run(pos, vel, 10)
+    x5, v5, _ = run(pos, vel, 5)
+    f = tmp_path / "md.npz"
+    checkpoint.save(str(f), x5, v5, types, box, 5)
+    s = checkpoint.load(str(f))
+    assert s["step"] == 5
+    xr, vr, er = run(s["pos"], s["vel"], 5)
+    assert np.abs(xr - x10).max() < 1e-10
+    assert np.abs(vr - v10).max() < 1e-10
+    assert abs(er[2] - e10[2]) <= 1e-10 * abs(e10[2])
+
+
 def test_nve_energy_conservation(A, param_text):
     pos, types, box = inputs.diamond()
     vel = inputs.velocities(types, 1000.0, seed=3)
