@@ -6,8 +6,14 @@ drift, the displacement check that triggers a list rebuild (binning, LJ half
 list, REBO intermediate list) when an atom moved more than skin/2, the exact
 REBO list, REBO bonds with the bond order, torsion, the connectivity map, the
 LJ pairs, the deferred b* pairs, and the second half kick.  `value` is the
-FP64 path; the mixed path (FP32 geometry/splines/bond order, FP64
-accumulation) is reported beside it with its max |dF| against FP64.
+FP64 path (every term in FP64, b* included); the mixed path (FP32
+geometry/splines/bond order, FP64 accumulation), the DF64 path and the FP64
+path with the optional FP32 b* screen are reported beside it with their max
+|dF| against FP64.  The energy drift of the FP64 and mixed paths is the
+least-squares slope of the total energy over 200 NVE steps after the timed
+region, at the bench's dt = 0.5 fs and again from the same state at 0.25 fs
+(a few hydrogen atoms of this noisy start run hot, and their close collisions
+need the shorter step).
 
 Timing: W untimed warm-up steps, then K steps bracketed by a barrier and
 torch.cuda.synchronize(), timed with CUDA events on the library's stream; the
@@ -42,6 +48,7 @@ UNIT = "atom-steps/s"
 WORKLOAD = "pe1m"
 DT = 0.5
 TEMP = 300.0
+DRIFT_STEPS = 200         # NVE steps after the timed region whose total energy is fitted for the drift
 
 # Algorithmic FP64 work per unit, in flops (FMA = 2).
 FLOPS_LJ_PAIR = 44        # displacement with image (9), r^2 (5), sqrt, 1/r, (s/r)^6, V, dV/dr, force, sums (30)
@@ -192,6 +199,16 @@ def oracle_sample(pos, types, box, target_s, threads=None):
     return na / dt, nth, sample, per, dt
 
 
+def drift_fit(etot, n_atoms):
+    """Least-squares slope of the total energy per atom over consecutive NVE
+    steps (eV/atom/step) and its spread (max - min, eV/atom)."""
+    e = np.asarray(etot, dtype=np.float64) / n_atoms
+    k = np.arange(len(e), dtype=np.float64)
+    slope = float(np.polyfit(k, e, 1)[0]) if len(e) > 1 else 0.0
+    return {"slope_eV_per_atom_step": slope, "spread_eV_per_atom": float(e.max() - e.min()), "steps": len(e),
+            "method": "least-squares slope of E_total/N over consecutive NVE steps after the timed region"}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -265,11 +282,73 @@ def run_batched(args, A, params, dev, stream):
         e1.record(stream)
         e1.synchronize()
         ms_loop = e0.elapsed_time(e1) / args.steps
+        # MD: K velocity-Verlet steps of every system (rebuilds decided on the
+        # device) in one graph launch, against K airebo_nve steps of each
+        # per-system handle in turn (the host decides each rebuild)
+        K = 10
+        vel0 = inputs.velocities(T, 300.0, seed=3)
+        md = A.Airebo(params, precision=A.MIXED, stream=stream)
+        pm = pos.clone()
+        vm = torch.tensor(vel0, device=dev)
+        md.neighbor_batch(pm, typ, O, B)
+        fm = torch.zeros_like(pm)
+        reps = max(1, args.steps // 5)
+        recaptures = 0
+        p_init, v_init = pm.clone(), vm.clone()
+        for attempt in range(3):
+            # a capacity exceeded during the replays: start again from the
+            # first state with a new capture (which grows every capacity)
+            pm.copy_(p_init)
+            vm.copy_(v_init)
+            md.graph_capture_nve(pm, vm, fm, DT, K)
+            md.graph_launch()
+            try:
+                md.check()
+            except A.AireboError as ex:
+                if ex.status != A.ERR_CAPACITY:
+                    raise
+                recaptures += 1
+                continue
+            stream.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                md.graph_launch()
+            e1.record(stream)
+            e1.synchronize()
+            try:
+                md.check()
+            except A.AireboError as ex:
+                if ex.status != A.ERR_CAPACITY:
+                    raise
+                recaptures += 1
+                continue
+            break
+        ms_md_graph = e0.elapsed_time(e1) / (reps * K)
+        md.close()
+        vs = [torch.tensor(vel0[:, O[s]:O[s + 1]], device=dev) for s in range(len(B))]
+        fs = []
+        for h, p in zip(hs, ps):
+            fs.append(h.compute(p)[0])
+        for h, p, v, f in zip(hs, ps, vs, fs):
+            h.nve(p, v, f, DT, 1)
+        stream.synchronize()
+        e0.record(stream)
+        for h, p, v, f in zip(hs, ps, vs, fs):
+            h.nve(p, v, f, DT, K)
+        e1.record(stream)
+        e1.synchronize()
+        ms_md_loop = e0.elapsed_time(e1) / K
         for h in hs:
             h.close()
     return {"systems": len(B), "atoms": nat, "dtype": "mixed", "unit": "atom-evaluations/s",
             "graph": nat / (ms_graph * 1e-3), "graph_ms": ms_graph,
             "loop": nat / (ms_loop * 1e-3), "loop_ms": ms_loop, "speedup": ms_loop / ms_graph,
+            "md": {"unit": "atom-steps/s", "steps_per_graph_launch": K, "recaptures": recaptures,
+                   "graph": nat / (ms_md_graph * 1e-3), "graph_ms_per_step": ms_md_graph,
+                   "loop": nat / (ms_md_loop * 1e-3), "loop_ms_per_step": ms_md_loop,
+                   "speedup": ms_md_loop / ms_md_graph,
+                   "what": "velocity-Verlet steps (dt 0.5 fs, 300 K) of all systems, list rebuilds decided on the "
+                           "device, as one CUDA graph of 10 steps; loop: airebo_nve on each system's own handle"},
             "workload": "amorphous C:H boxes 200-8000 atoms, H/C 0.5-2.0, 0.9 g/cm^3, relaxed 200 SD steps"}
 
 
@@ -294,10 +373,12 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     results = {}
     forces = {}
-    runs = ((A.FP64, "fp64", True), (A.MIXED, "mixed", True), (A.DF64, "df64", True), (A.FP64, "rebo_only", False))
-    for prec, name, full in runs:
+    # name, precision, all terms, FP32 b* screen (an option, off in the headline FP64 run)
+    runs = ((A.FP64, "fp64", True, False), (A.FP64, "fp64_bstar_screen", True, True), (A.MIXED, "mixed", True, False),
+            (A.DF64, "df64", True, False), (A.FP64, "rebo_only", False, False))
+    for prec, name, full, screen in runs:
         with torch.cuda.stream(stream):
-            ev = A.Airebo(params, precision=prec, stream=stream, lj=full, torsion=full)
+            ev = A.Airebo(params, precision=prec, stream=stream, lj=full, torsion=full, bstar_screen=screen)
             pos = torch.tensor(pos0, device=dev)
             vel = torch.tensor(vel0, device=dev)
             t = torch.tensor(types, device=dev)
@@ -305,7 +386,7 @@ def run_ours(args):
             shape = ev.autotune(pos)
             f, e4, _ = ev.compute(pos)
             forces[name] = f.clone()
-            e_start = ev.nve(pos, vel, f, DT, 1)
+            ev.nve(pos, vel, f, DT, 1)
             for _ in range(max(0, args.warmup - 1)):
                 ev.nve(pos, vel, f, DT, 1)
             builds0 = ev.counters()["list_builds"]
@@ -332,12 +413,26 @@ def run_ours(args):
             kt = ev.kernel_times()
             ev.set_timing(False)
             builds = ev.counters()["list_builds"] - builds0
-            e_end = ev.nve(pos, vel, f, DT, 1).cpu().numpy()
-            e_beg = e_start.cpu().numpy()
+            counters = ev.counters()
+            drift = None
+            if name in ("fp64", "mixed") and args.drift_steps > 1:
+                # from the state after the timed steps: dt = 0.5 fs (the bench's step),
+                # then again from that state at dt = 0.25 fs
+                p0, v0 = pos.clone(), vel.clone()
+                drift = {}
+                mass = torch.tensor(inputs.masses(types), device=dev)
+                for dt in (DT, 0.5 * DT):
+                    pos.copy_(p0)
+                    vel.copy_(v0)
+                    ev.neighbor(pos, t, box)
+                    ev.compute(pos, f)
+                    etot = [ev.nve(pos, vel, f, dt, 1)[2].clone() for _ in range(args.drift_steps)]
+                    fit = drift_fit(torch.stack(etot).cpu().numpy(), n)
+                    fit["hottest_atom_KE_eV"] = float((0.5 * inputs.MVV2E * (mass * vel * vel).sum(0)).max().item())
+                    drift[f"dt_{dt:g}fs"] = fit
             ms = max_over_ranks(ms, dist, dev)
-            results[name] = dict(ms=ms, kt=kt, clocks=ck, shape=shape, builds=builds, counters=ev.counters(),
-                                 drift=(e_end[2] - e_beg[2]) / (args.steps + args.warmup + 1) / n,
-                                 etot=float(e_end[2]))
+            results[name] = dict(ms=ms, kt=kt, clocks=ck, shape=shape, builds=builds, counters=counters,
+                                 drift=drift)
             ev.close()
     # mixed against FP64 at the same (initial) positions
     df = (forces["mixed"] - forces["fp64"]).abs().max().item()
@@ -416,7 +511,7 @@ def run_ours(args):
             "config": config_of(args.workload, n, ws),
             "mixed": {"value": mixed_value, "unit": UNIT, "ms_per_step": results["mixed"]["ms"] / args.steps,
                       "max_abs_dF_vs_fp64": df, "max_rel_dF_vs_fp64": df / fscale,
-                      "drift_eV_per_atom_step": results["mixed"]["drift"],
+                      "drift": results["mixed"]["drift"],
                       "kernel_ms": {k: v[0] / max(1, v[1]) for k, v in mix_kt.items()},
                       "lj_achieved_fp32_frac": None if not mlj_n else
                       (flops_lj / (mlj_ms * 1e-3 / mlj_n) / 1e12) / peak32_nom},
@@ -425,14 +520,19 @@ def run_ours(args):
                      "dtype": "f64; LJ pair and torsion arithmetic in double-float (f32 pairs), LJ forces in 64-bit fixed point",
                      "max_abs_dF_vs_fp64": (forces["df64"] - forces["fp64"]).abs().max().item(),
                      "max_rel_dF_vs_fp64": (forces["df64"] - forces["fp64"]).abs().max().item() / fscale,
-                     "drift_eV_per_atom_step": results["df64"]["drift"],
                      "kernel_ms": {k: v[0] / max(1, v[1]) for k, v in results["df64"]["kt"].items()}},
+            "fp64_bstar_screen": {
+                "value": replica_throughput(n, args.steps, ws, results["fp64_bstar_screen"]["ms"]), "unit": UNIT,
+                "ms_per_step": results["fp64_bstar_screen"]["ms"] / args.steps,
+                "dtype": "f64 except that an FP32 b* decides S_b in {0, 1} outside a 1e-3 margin (measured, not proven)",
+                "max_abs_dF_vs_fp64": (forces["fp64_bstar_screen"] - forces["fp64"]).abs().max().item(),
+                "kernel_ms": {k: v[0] / max(1, v[1]) for k, v in results["fp64_bstar_screen"]["kt"].items()}},
             "batched": batched,
             "rebo_only": {"value": replica_throughput(n, args.steps, ws, results["rebo_only"]["ms"]),
                           "unit": UNIT, "ms_per_step": results["rebo_only"]["ms"] / args.steps,
                           "dtype": "f64", "terms": "REBO (Alg. 1) only, no LJ or torsion, no long list",
                           "kernel_ms": {k: v[0] / max(1, v[1]) for k, v in results["rebo_only"]["kt"].items()}},
-            "drift_eV_per_atom_step": r64["drift"],
+            "drift": r64["drift"],
             "list_builds_in_timed_region": r64["builds"],
             "launch_shape": {k: {"lj_atoms_per_claim": results[k]["shape"][0],
                                  "bond_waves": results[k]["shape"][1],
@@ -465,6 +565,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-batch", dest="batch", action="store_false",
                     help="leave out the batched-ensemble comparison (profiler captures)")
+    ap.add_argument("--drift-steps", dest="drift_steps", type=int, default=DRIFT_STEPS,
+                    help="NVE steps after the timed region whose energy slope is reported (FP64 and mixed)")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(inputs.WORKLOADS),
                     help="pe1m is the benchmark; the smaller ones exist for profiler captures")
     args = ap.parse_args()

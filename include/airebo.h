@@ -79,14 +79,16 @@ typedef struct {
     int enable_lj;        /* 1: LJ term (Alg. 3) */
     int enable_torsion;   /* 1: torsion term (Alg. 2) */
     int max_lj_nbrs;      /* initial long-list capacity per atom; 0 = from the density */
-    int bstar_screen;     /* FP64 only, 1 (default): b* enters the LJ term only through S_b,
-                             which is exactly 0 or 1 outside [b_min, b_max]; an FP32 b* decides
-                             those pairs when it lies more than 1e-3 outside the transition
-                             (FP32 b* errors measure below 1e-6), and the rest are evaluated in
-                             FP64.  0: every b* in FP64.  Results agree to rounding either way. */
+    int bstar_screen;     /* 0 (default): every b* in FP64 (AIREBO_FP64, AIREBO_DF64).  1: a
+                             faster FP64 path that is not strictly FP64: b* enters the LJ term only
+                             through S_b, which is exactly 0 or 1 outside [b_min, b_max], and an
+                             FP32 b* decides those pairs when it lies more than 1e-3 outside the
+                             transition; the rest are evaluated in FP64.  The margin rests on
+                             measured FP32 b* errors (below 1e-6 on the test systems), not on a
+                             proven bound.  Ignored by AIREBO_MIXED. */
 } airebo_options;
 
-/* Fill opts with the defaults: skin 1.0 A, FP64, all three terms on, auto capacity, b* screen on. */
+/* Fill opts with the defaults: skin 1.0 A, FP64, all three terms on, auto capacity, b* screen off. */
 void airebo_default_options(airebo_options* opts);
 
 /*
@@ -118,24 +120,32 @@ airebo_status airebo_neighbor(airebo_handle h, const double* d_pos, const int8_t
                               const double* box);
 
 /*
- * Energy and forces at d_pos (same atoms as the last airebo_neighbor; the
- * lists stay valid while no atom has moved more than skin/2 since it).
- * d_force: device double[3][n], overwritten.  d_energy4 (device double[4])
- * and d_virial6 (device double[6]) may be NULL; the virial is only computed
- * when d_virial6 is given.  Synchronises the stream once to check capacity
- * flags, and regrows and recomputes when a scratch capacity was exceeded.
+ * Energy and forces at d_pos (Sec. 2: positions in, F_i = -grad_i V out, with
+ * the energy of Sec. 2.1; same atoms as the last airebo_neighbor; the lists
+ * stay valid while no atom has moved more than skin/2 since it).
+ * d_force: device double[3][n], overwritten.  d_energy4 (device double[4]),
+ * d_virial6 (device double[6]) and d_energy_per_atom (device double[n]) may
+ * be NULL; the virial is only computed when d_virial6 is given.  Per-atom
+ * energies split every term evenly between the two atoms that define it: a
+ * REBO bond i-j (Alg. 1) and a torsion term around the bond i-j (Alg. 2)
+ * give half to i and half to j, an LJ pair i-j (Alg. 3, b* included) half to
+ * each, so they do not depend on the atom numbering and sum to the total.
+ * Synchronises the stream once to check capacity flags, and regrows and
+ * recomputes when a scratch capacity was exceeded.
  */
 airebo_status airebo_compute(airebo_handle h, const double* d_pos, double* d_force, double* d_energy4,
-                             double* d_virial6);
+                             double* d_virial6, double* d_energy_per_atom);
 
 /*
  * Same as airebo_compute with host buffers: copies h_pos to the device, runs
  * the neighbour build when needed (first call, new n or box, or an atom moved
- * more than skin/2), computes, and copies forces, energies and virial back.
+ * more than skin/2), computes, and copies forces, energies, virial and
+ * per-atom energies (h_energy_per_atom, host double[n], nullable) back.
  * h_types/box are read on the first call and whenever n changes.
  */
 airebo_status airebo_compute_host(airebo_handle h, const double* h_pos, const int8_t* h_types, int64_t n,
-                                  const double* box, double* h_force, double* h_energy4, double* h_virial6);
+                                  const double* box, double* h_force, double* h_energy4, double* h_virial6,
+                                  double* h_energy_per_atom);
 
 /* *out_flag = 1 if some atom moved more than skin/2 since the last neighbour build. */
 airebo_status airebo_needs_rebuild(airebo_handle h, const double* d_pos, int* out_flag);
@@ -153,6 +163,37 @@ airebo_status airebo_needs_rebuild(airebo_handle h, const double* d_pos, int* ou
  */
 airebo_status airebo_nve(airebo_handle h, double* d_pos, double* d_vel, double* d_force, double dt, int nsteps,
                          double* d_energy4);
+
+/*
+ * The NVE step of airebo_nve with no host synchronisation: every step is
+ * enqueued on the handle's stream, and the rebuild decision is taken on the
+ * device -- a kernel compares the largest displacement since the last build
+ * with skin/2 and gates the kernels of the list build, which then run or
+ * return at once.  The cell grid and every capacity are those of the last
+ * synchronous airebo_neighbor / airebo_compute (a build may not grow them):
+ * an overflow, a non-finite position or a range error is recorded on the
+ * device and reported by airebo_check, which the caller must call after the
+ * steps (the results of steps after an overflow are not valid).  d_energy4
+ * (nullable) as in airebo_nve; its fourth value counts the builds run by the
+ * host and by the device.  Errors: AIREBO_ERR_STATE before airebo_neighbor,
+ * AIREBO_ERR_ARG for a bad dt or step count.
+ */
+airebo_status airebo_nve_async(airebo_handle h, double* d_pos, double* d_vel, double* d_force, double dt, int nsteps,
+                               double* d_energy4);
+
+/*
+ * Capture nsteps steps of airebo_nve_async into the handle's CUDA graph
+ * (replacing any graph captured before), after a synchronous evaluation at
+ * d_pos that grows every scratch capacity, with headroom for the steps ahead
+ * (lists rebuilt at d_pos with a quarter more room per atom, 16 REBO slots
+ * per atom, a quarter more connectivity-map entries and b* queue), and writes
+ * the forces at d_pos to d_force.  Each airebo_graph_launch then runs nsteps MD steps, rebuilds
+ * included, in one launch; call airebo_check after launches.  The handle must
+ * have been created on a non-default stream; a synchronous airebo_neighbor
+ * (new atoms, box or capacities) needs a new capture.
+ */
+airebo_status airebo_graph_capture_nve(airebo_handle h, double* d_pos, double* d_vel, double* d_force, double dt,
+                                       int nsteps, double* d_energy4);
 
 /* The NVE step with host buffers: copy in, nsteps steps, copy positions,
  * velocities, forces and d_energy4's four values back. */
@@ -224,7 +265,9 @@ airebo_status airebo_dd_check(double* h_err8);
 
 /*
  * Energy and forces as airebo_compute, plus the gradient of the energy with
- * respect to the parameters of the inter-molecular term (Sec. 2.1.2):
+ * respect to the parameters of the inter-molecular term (Sec. 2.1.2, the
+ * E^LJ of Alg. 3; the spline knot data of the bond order, Sec. 2.1.3, have
+ * their own call, airebo_knot_grad):
  * h_grad6 (host double[6]) = dE/d epsilon[CC, CH, HH] (lj.epsilon, or
  * morse.epsilon for the Morse form), dE/d sigma[CC, CH, HH] (lj.sigma, which
  * also sets the switch and cut-off radii).  Slower than airebo_compute: every
@@ -260,9 +303,14 @@ airebo_status airebo_compute_batch(airebo_handle h, const double* d_pos, double*
 /*
  * Enqueue one evaluation without any host synchronisation or capacity growth
  * (d_energy4, d_energy_sys nullable; per-system energies need one earlier
- * synchronous evaluation that wanted them).  Capacity flags are read by
- * airebo_check, which synchronises and returns AIREBO_ERR_CAPACITY if a
- * scratch capacity was exceeded (run airebo_compute once, then retry).
+ * synchronous evaluation that wanted them).  Capacity and error flags are
+ * read by airebo_check, which synchronises and returns what airebo_compute
+ * would have returned for the same evaluation: AIREBO_ERR_NONFINITE for a
+ * non-finite position, overlapping atoms or an LJ pair force beyond the
+ * fixed-point range, AIREBO_ERR_ARG for a coordinate beyond 2000 A in
+ * AIREBO_MIXED / AIREBO_DF64 (each found condition is named in
+ * airebo_last_error), else AIREBO_ERR_CAPACITY if a scratch capacity was
+ * exceeded (run airebo_compute once, then retry).
  */
 airebo_status airebo_compute_async(airebo_handle h, const double* d_pos, double* d_force, double* d_energy4,
                                    double* d_energy_sys);
@@ -326,6 +374,16 @@ airebo_status airebo_knot_grad(airebo_handle h, const double* d_pos, double* d_f
                                double* h_grad, int64_t count);
 
 /*
+ * Replace every spline knot datum of the handle's parameter set (the data
+ * whose gradient airebo_knot_grad returns, Sec. 2.1.3), in the same order and
+ * layout; the knot abscissae and all scalars stay.  The spline coefficients
+ * are rebuilt and uploaded; the lists stay valid.  count must equal
+ * AIREBO_KNOT_COUNT; AIREBO_ERR_ARG for a wrong count or a non-finite value
+ * (the handle then keeps its old data).  Synchronises.
+ */
+airebo_status airebo_set_knots(airebo_handle h, const double* h_knots, int64_t count);
+
+/*
  * Rebuild check that allocates no device memory (the paper has no
  * counterpart: it is a service for callers that cannot call cudaMalloc, such
  * as code running inside a framework that owns all device memory, or code
@@ -337,9 +395,10 @@ airebo_status airebo_knot_grad(airebo_handle h, const double* d_pos, double* d_f
  * Its scratch is a fixed 64 KB array inside the library image, held by every
  * GPU that loads the library until exit, so n is limited to 2,097,152 atoms
  * (larger n returns AIREBO_ERR_ARG).  The first call on a device looks up the
- * array's device address (set-up); make that first call before any stream
- * capture.  All calls share the array: calls whose kernels overlap on the GPU
- * race and must be serialised by the caller.
+ * array's device address (set-up), and looks it up again after the device's
+ * context was replaced (cudaDeviceReset); make that first call before any
+ * stream capture.  All calls share the array: calls whose kernels overlap on
+ * the GPU race and must be serialised by the caller.
  */
 airebo_status airebo_needs_rebuild_noalloc(const double* d_pos, const double* d_ref, int64_t n, double skin,
                                            void* stream, int* h_flag, double* h_max_disp);

@@ -725,9 +725,12 @@ int oracle_threads() {
 // energy4 = total, REBO, LJ, torsion (over the evaluated terms).
 // need (nullable): atoms whose REBO neighbour sets are needed by the anchored
 // terms (all atoms when null).
+// eatom (nullable, n doubles): per-atom energies, each term (a REBO bond, the
+// torsion term of a C-C bond, an LJ pair) split evenly between the two atoms
+// i and j that define it.
 int oracle_compute_masked(void* h, int64_t n, const double* pos, const int8_t* types, const double* box,
                           int flags, const char* anchor, const char* sel, const char* need, double* force,
-                          double* energy4, double* virial6, int64_t* counters) {
+                          double* energy4, double* virial6, int64_t* counters, double* eatom) {
     Oracle* o = (Oracle*)h;
     o->sys.n = n; o->sys.x = pos; o->sys.t = types;
     for (int d = 0; d < 3; d++) o->sys.L[d] = box[d];
@@ -735,10 +738,12 @@ int oracle_compute_masked(void* h, int64_t n, const double* pos, const int8_t* t
     std::vector<char> selv;
     if (sel) selv.assign(sel, sel + n);
     if (force) std::fill(force, force + 3 * n, 0.0);
+    if (eatom) std::fill(eatom, eatom + n, 0.0);
     double E[4] = {0, 0, 0, 0}, W[6] = {0, 0, 0, 0, 0, 0};
     int64_t cnt[N_COUNTERS] = {0};
     int nthr = oracle_threads();
     std::vector<std::vector<double>> fthr(nthr, std::vector<double>(force ? 3 * n : 0, 0.0));
+    std::vector<std::vector<double>> ethr(nthr, std::vector<double>(eatom ? n : 0, 0.0));
 #pragma omp parallel
     {
         int tid = 0;
@@ -749,6 +754,10 @@ int oracle_compute_masked(void* h, int64_t n, const double* pos, const int8_t* t
         double Et[4] = {0, 0, 0, 0};
         int64_t ct[N_COUNTERS] = {0};
         TermCtx T; T.sys = &o->sys;
+        double* ea = eatom ? ethr[tid].data() : nullptr;
+        auto split = [&](int64_t a, int64_t b, double e) {
+            if (ea) { ea[a] += 0.5 * e; ea[b] += 0.5 * e; }
+        };
 #pragma omp for schedule(dynamic, 16)
         for (int64_t i = 0; i < n; i++) {
             if (anchor && !anchor[i]) continue;
@@ -757,6 +766,7 @@ int oracle_compute_masked(void* h, int64_t n, const double* pos, const int8_t* t
                     if (nb.j <= i) continue;
                     V e = o->rebo_term(T, i, nb, ct);
                     Et[1] += e.v;
+                    split(i, nb.j, e.v);
                     backprop(T, e, acc);
                 }
             if (flags & 4)
@@ -764,6 +774,7 @@ int oracle_compute_masked(void* h, int64_t n, const double* pos, const int8_t* t
                     if (nb.j <= i || types[i] != 0 || types[nb.j] != 0) continue;
                     V e = o->torsion_term(T, i, nb, ct);
                     Et[3] += e.v;
+                    split(i, nb.j, e.v);
                     backprop(T, e, acc);
                 }
             if (flags & 2)
@@ -772,6 +783,7 @@ int oracle_compute_masked(void* h, int64_t n, const double* pos, const int8_t* t
                     V e = o->lj_term(T, i, nb, ct, &dsb);
                     if (dsb) ct[N_BSTAR_DSB]++;
                     Et[2] += e.v;
+                    split(i, nb.j, e.v);
                     backprop(T, e, acc);
                 }
         }
@@ -785,6 +797,9 @@ int oracle_compute_masked(void* h, int64_t n, const double* pos, const int8_t* t
     if (force)
         for (int t = 0; t < nthr; t++)
             for (int64_t k = 0; k < 3 * n; k++) force[k] += fthr[t][k];
+    if (eatom)
+        for (int t = 0; t < nthr; t++)
+            for (int64_t k = 0; k < n; k++) eatom[k] += ethr[t][k];
     E[0] = E[1] + E[2] + E[3];
     if (energy4) for (int k = 0; k < 4; k++) energy4[k] = E[k];
     if (virial6) for (int k = 0; k < 6; k++) virial6[k] = W[k];
@@ -794,8 +809,9 @@ int oracle_compute_masked(void* h, int64_t n, const double* pos, const int8_t* t
 }
 
 int oracle_compute(void* h, int64_t n, const double* pos, const int8_t* types, const double* box, int flags,
-                   double* force, double* energy4, double* virial6, int64_t* counters) {
-    return oracle_compute_masked(h, n, pos, types, box, flags, nullptr, nullptr, nullptr, force, energy4, virial6, counters);
+                   double* force, double* energy4, double* virial6, int64_t* counters, double* eatom) {
+    return oracle_compute_masked(h, n, pos, types, box, flags, nullptr, nullptr, nullptr, force, energy4, virial6,
+                                 counters, eatom);
 }
 
 // REBO neighbour sets (r < Dmax) as flat arrays; returns the total count, or

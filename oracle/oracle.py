@@ -43,9 +43,9 @@ def lib():
         L.oracle_threads.restype = C.c_int
         L.oracle_set_threads.argtypes = [C.c_int]
         L.oracle_compute_masked.restype = C.c_int
-        L.oracle_compute_masked.argtypes = [P, C.c_int64, P, P, P, C.c_int, P, P, P, P, P, P, P]
+        L.oracle_compute_masked.argtypes = [P, C.c_int64, P, P, P, C.c_int, P, P, P, P, P, P, P, P]
         L.oracle_compute.restype = C.c_int
-        L.oracle_compute.argtypes = [P, C.c_int64, P, P, P, C.c_int, P, P, P, P]
+        L.oracle_compute.argtypes = [P, C.c_int64, P, P, P, C.c_int, P, P, P, P, P]
         for f in (L.oracle_rebo_neighbors, L.oracle_lj_pairs):
             f.restype = C.c_int64
             f.argtypes = [P, C.c_int64, P, P, P, C.c_int64, P, P, P]
@@ -82,15 +82,20 @@ class Oracle:
         assert pos.shape[0] == 3 and pos.shape[1] == types.shape[0]
         return pos, types, box
 
-    def compute(self, pos, types, box, flags=FLAG_ALL, forces=True):
-        """Energy (total, REBO, LJ, torsion), forces (3, N), virial (6,), counters."""
+    def compute(self, pos, types, box, flags=FLAG_ALL, forces=True, per_atom=False):
+        """Energy (total, REBO, LJ, torsion), forces (3, N), virial (6,), counters; with
+        per_atom=True also the per-atom energies (N,), each term split evenly between its i and j."""
         pos, types, box = self._sys(pos, types, box)
         n = types.shape[0]
         f = np.zeros((3, n)) if forces else None
         e = np.zeros(4)
         w = np.zeros(6)
         c = np.zeros(16, dtype=np.int64)
-        lib().oracle_compute(self._h, n, _ptr(pos), _ptr(types), _ptr(box), flags, _ptr(f), _ptr(e), _ptr(w), _ptr(c))
+        ea = np.zeros(n) if per_atom else None
+        lib().oracle_compute(self._h, n, _ptr(pos), _ptr(types), _ptr(box), flags, _ptr(f), _ptr(e), _ptr(w), _ptr(c),
+                             _ptr(ea))
+        if per_atom:
+            return e, f, w, dict(zip(COUNTERS, c.tolist())), ea
         return e, f, w, dict(zip(COUNTERS, c.tolist()))
 
     def energy(self, pos, types, box, flags=FLAG_ALL):
@@ -121,7 +126,7 @@ class Oracle:
         f = np.zeros((3, n))
         c = np.zeros(16, dtype=np.int64)
         lib().oracle_compute_masked(self._h, n, _ptr(pos), _ptr(types), _ptr(box), flags, _ptr(anchor), _ptr(sel),
-                                    _ptr(need), _ptr(f), None, None, _ptr(c))
+                                    _ptr(need), _ptr(f), None, None, _ptr(c), None)
         if counters:
             return f[:, atoms], dict(zip(COUNTERS, c.tolist()))
         return f[:, atoms]
@@ -141,7 +146,7 @@ class Oracle:
         e = np.zeros(4)
         c = np.zeros(16, dtype=np.int64)
         lib().oracle_compute_masked(self._h, n, _ptr(pos), _ptr(types), _ptr(box), flags, _ptr(anchor), None,
-                                    _ptr(need), _ptr(f), _ptr(e), None, _ptr(c))
+                                    _ptr(need), _ptr(f), _ptr(e), None, _ptr(c), None)
         return e, f, dict(zip(COUNTERS, c.tolist())), int(anchor.sum())
 
     def _pairs(self, fn, pos, types, box, cap=None):

@@ -56,8 +56,8 @@ def lib():
             "airebo_destroy": (None, [P]),
             "airebo_last_error": (C.c_char_p, [P]),
             "airebo_neighbor": (I, [P, P, P, I64, P]),
-            "airebo_compute": (I, [P, P, P, P, P]),
-            "airebo_compute_host": (I, [P, P, P, I64, P, P, P, P]),
+            "airebo_compute": (I, [P, P, P, P, P, P]),
+            "airebo_compute_host": (I, [P, P, P, I64, P, P, P, P, P]),
             "airebo_needs_rebuild": (I, [P, P, P]),
             "airebo_nve": (I, [P, P, P, P, D, I, P]),
             "airebo_nve_host": (I, [P, P, P, P, D, I, P]),
@@ -79,6 +79,9 @@ def lib():
             "airebo_graph_launch": (I, [P]),
             "airebo_autotune": (I, [P, P, P, P]),
             "airebo_set_launch_shape": (I, [P, I, I, I]),
+            "airebo_set_knots": (I, [P, P, I64]),
+            "airebo_nve_async": (I, [P, P, P, P, D, I, P]),
+            "airebo_graph_capture_nve": (I, [P, P, P, P, D, I, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -133,7 +136,7 @@ class Airebo:
 
     def __init__(self, params: str | dict | None = None, precision: int = FP64, skin: float = 1.0,
                  rebo: bool = True, lj: bool = True, torsion: bool = True, max_lj_nbrs: int = 0, stream=None,
-                 bstar_screen: bool = True):
+                 bstar_screen: bool = False):
         import torch
         self._torch = torch
         if params is None:
@@ -152,6 +155,8 @@ class Airebo:
         self._h = h
         self.n = None
         self.precision = precision
+        self.skin = float(skin)
+        self.params_text = params
 
     def close(self):
         if getattr(self, "_h", None):
@@ -234,15 +239,19 @@ class Airebo:
     def graph_launch(self):
         self._check(lib().airebo_graph_launch(self._h))
 
-    def compute(self, pos, force=None, virial=False):
-        """Forces (3, N), energies (total, REBO, LJ, torsion) and the virial (or None)."""
+    def compute(self, pos, force=None, virial=False, per_atom=False):
+        """Forces (3, N), energies (total, REBO, LJ, torsion) and the virial (or None); with
+        per_atom=True also the per-atom energies (N,) as a fourth value."""
         torch = self._torch
         pos = self._dev(pos, torch.float64)
         if force is None:
             force = torch.empty_like(pos)
         e4 = torch.empty(4, dtype=torch.float64, device=self.device)
         w6 = torch.empty(6, dtype=torch.float64, device=self.device) if virial else None
-        self._check(lib().airebo_compute(self._h, _ptr(pos), _ptr(force), _ptr(e4), _ptr(w6)))
+        ea = torch.empty(pos.shape[1], dtype=torch.float64, device=self.device) if per_atom else None
+        self._check(lib().airebo_compute(self._h, _ptr(pos), _ptr(force), _ptr(e4), _ptr(w6), _ptr(ea)))
+        if per_atom:
+            return force, e4, w6, ea
         return force, e4, w6
 
     def param_grad(self, pos, force=None):
@@ -273,6 +282,11 @@ class Airebo:
         sg = None if sigma is None else np.ascontiguousarray(np.asarray(sigma, dtype=np.float64).reshape(3))
         self._check(lib().airebo_set_lj_params(self._h, _np(e), _np(sg)))
 
+    def set_knots(self, knots):
+        """Replace all KNOT_COUNT spline knot data (the order of knot_grad())."""
+        k = np.ascontiguousarray(np.asarray(knots, dtype=np.float64).reshape(-1))
+        self._check(lib().airebo_set_knots(self._h, _np(k), k.size))
+
     def needs_rebuild(self, pos) -> bool:
         flag = C.c_int(0)
         self._check(lib().airebo_needs_rebuild(self._h, _ptr(pos), C.byref(flag)))
@@ -284,7 +298,21 @@ class Airebo:
         self._check(lib().airebo_nve(self._h, _ptr(pos), _ptr(vel), _ptr(force), dt, nsteps, _ptr(e4)))
         return e4
 
-    def compute_host(self, pos, types, box, virial=False):
+    def nve_async(self, pos, vel, force, dt: float, nsteps: int, energy4=None):
+        """Enqueue nsteps NVE steps with the rebuild decided on the device (no host
+        synchronisation); call check() afterwards.  Returns the energy buffer."""
+        e4 = energy4 if energy4 is not None else self._torch.empty(4, dtype=self._torch.float64, device=self.device)
+        self._check(lib().airebo_nve_async(self._h, _ptr(pos), _ptr(vel), _ptr(force), dt, nsteps, _ptr(e4)))
+        return e4
+
+    def graph_capture_nve(self, pos, vel, force, dt: float, nsteps: int, energy4=None):
+        """Capture nsteps asynchronous NVE steps as this handle's graph; graph_launch() replays
+        them.  Returns the energy buffer the graph writes (PE, KE, total, list builds)."""
+        e4 = energy4 if energy4 is not None else self._torch.empty(4, dtype=self._torch.float64, device=self.device)
+        self._check(lib().airebo_graph_capture_nve(self._h, _ptr(pos), _ptr(vel), _ptr(force), dt, nsteps, _ptr(e4)))
+        return e4
+
+    def compute_host(self, pos, types, box, virial=False, per_atom=False):
         pos = np.ascontiguousarray(pos, dtype=np.float64)
         types = np.ascontiguousarray(types, dtype=np.int8)
         b = np.ascontiguousarray(np.asarray(box, dtype=np.float64).reshape(3))
@@ -292,8 +320,12 @@ class Airebo:
         f = np.zeros((3, n))
         e4 = np.zeros(4)
         w6 = np.zeros(6) if virial else None
-        self._check(lib().airebo_compute_host(self._h, _np(pos), _np(types), n, _np(b), _np(f), _np(e4), _np(w6)))
+        ea = np.zeros(n) if per_atom else None
+        self._check(lib().airebo_compute_host(self._h, _np(pos), _np(types), n, _np(b), _np(f), _np(e4), _np(w6),
+                                              _np(ea)))
         self.n = n
+        if per_atom:
+            return f, e4, w6, ea
         return f, e4, w6
 
     def nve_host(self, pos, vel, force, dt: float, nsteps: int):
@@ -331,45 +363,62 @@ class Airebo:
 
 
 class AireboEnergy:
-    """Differentiable AIREBO energy: ``E = AireboEnergy.apply(pos, eps, sigma, evaluator)``.
+    """Differentiable AIREBO energy:
+    ``E = AireboEnergy.apply(pos, eps, sigma, evaluator, knots=None)``.
 
-    The backward pass is the library's own force computation (F = -dE/dx),
-    and, when eps or sigma (the three per-species-pair values of the
-    inter-molecular term) require gradients, its hand-written dE/d(eps, sigma).
-    eps and sigma are pushed to the evaluator before the evaluation; the
-    neighbour lists are rebuilt when needed."""
+    The backward pass is the library's own force computation (F = -dE/dx);
+    when eps or sigma (the three per-species-pair values of the
+    inter-molecular term) require gradients, its hand-written dE/d(eps, sigma)
+    (airebo_param_grad); when knots (a tensor of KNOT_COUNT spline knot data,
+    the order of knot_grad()) is given and requires a gradient, its
+    hand-written dE/d(knots) (airebo_knot_grad).  eps, sigma and knots are
+    pushed to the evaluator before the evaluation; the neighbour lists are
+    rebuilt each time."""
 
     _fn = None
 
     @classmethod
-    def apply(cls, pos, eps, sigma, evaluator):
+    def apply(cls, pos, eps, sigma, evaluator, knots=None):
         if cls._fn is None:
             import torch
 
             class _F(torch.autograd.Function):
                 @staticmethod
-                def forward(ctx, pos, eps, sigma, ev):
-                    e_np = eps.detach().cpu().numpy()
-                    s_np = sigma.detach().cpu().numpy()
-                    ev.set_lj_params(e_np, s_np)
+                def forward(ctx, pos, eps, sigma, knots, ev):
+                    ev.set_lj_params(eps.detach().cpu().numpy(), sigma.detach().cpu().numpy())
+                    if knots is not None:
+                        ev.set_knots(knots.detach().cpu().numpy())
                     ev.neighbor(pos.detach(), ev._types, ev.box)
                     need_p = ctx.needs_input_grad[1] or ctx.needs_input_grad[2]
+                    need_k = knots is not None and ctx.needs_input_grad[3]
                     if need_p:
                         f, e4, g = ev.param_grad(pos.detach())
                         gt = torch.tensor(g, dtype=torch.float64, device=pos.device)
                     else:
                         f, e4, _ = ev.compute(pos.detach())
                         gt = torch.zeros(6, dtype=torch.float64, device=pos.device)
-                    ctx.save_for_backward(f, gt)
+                    gk = None
+                    if need_k:
+                        _, _, g = ev.knot_grad(pos.detach())
+                        gk = torch.tensor(g, dtype=torch.float64, device=knots.device)
+                    ctx.has_knots = knots is not None
+                    ctx.save_for_backward(f, gt, gk)
                     return e4[0].clone()
 
                 @staticmethod
                 def backward(ctx, gE):
-                    f, gt = ctx.saved_tensors
-                    return -f * gE, gt[:3] * gE, gt[3:] * gE, None
+                    f, gt, gk = ctx.saved_tensors
+                    gknots = gk * gE if (ctx.has_knots and gk is not None) else None
+                    return -f * gE, gt[:3] * gE, gt[3:] * gE, gknots, None
 
             cls._fn = _F
-        return cls._fn.apply(pos, eps, sigma, evaluator)
+        return cls._fn.apply(pos, eps, sigma, knots, evaluator)
+
+
+def knot_vector(params: dict):
+    """The KNOT_COUNT spline knot data of a parameter set, in the order of
+    knot_grad() and set_knots()."""
+    return np.concatenate([np.asarray(params[name], dtype=np.float64).ravel() for name, _ in KNOT_BLOCKS])
 
 
 def _addr(a):

@@ -382,6 +382,15 @@ struct airebo_ctx {
     cudaGraphExec_t gexec = nullptr;
     unsigned long long* maxd2 = nullptr;
     double* ke = nullptr;
+    // asynchronous MD step: the device's rebuild decision, its count of the
+    // builds it ran, the sticky error flags of those builds (read and cleared
+    // by airebo_check), and the arguments of the last synchronous build
+    int* gate = nullptr;
+    long long* d_builds = nullptr;
+    int* nerr = nullptr;
+    NeighborArgs nargs{};
+    int nargs_ncell = 0;
+    bool nargs_ok = false;
     double* pg = nullptr;                // parameter gradients (6)
     double* kg = nullptr;                // spline-coefficient gradients (KG_N)
     // pinned mirrors
@@ -541,6 +550,7 @@ airebo_status ensure_lists(airebo_handle h) {
 
 airebo_status do_neighbor(airebo_handle h, const double* d_pos) {
     const Scalars& s = h->sc;
+    h->nargs_ok = false;            // the saved build arguments may point at buffers about to change
     double rlj = 0, rim = 0;
     NeighborArgs a{};
     bool with_lj = h->opt.enable_lj != 0;
@@ -640,6 +650,9 @@ airebo_status do_neighbor(airebo_handle h, const double* d_pos) {
             if (h->n) CK(cudaMemcpyAsync(h->xref, d_pos, sizeof(double) * 3 * h->n, cudaMemcpyDeviceToDevice, h->stream));
             h->built = true;
             h->rebuilds++;
+            h->nargs = a;
+            h->nargs_ncell = ncell;
+            h->nargs_ok = true;
             return AIREBO_OK;
         }
     }
@@ -650,6 +663,27 @@ __global__ void k_finalize(const double* acc, double* e4, double* w6) {
     int t = threadIdx.x;
     if (e4 && t < 4) e4[t] = t == 0 ? acc[0] + acc[1] + acc[2] : acc[t - 1];
     if (w6 && t < 6) w6[t] = acc[3 + t];
+}
+
+// The status of the device error flags of the last evaluation (h->h_err):
+// non-finite positions, overlapping atoms, and the range limits of the split
+// positions and fixed-point sums of AIREBO_MIXED / AIREBO_DF64.  Every
+// condition found is named in the message; the status is that of the first.
+airebo_status device_errors(airebo_handle h) {
+    int nf = h->h_err[ERR_NONFINITE], df = h->h_err[ERR_DF];
+    if (!nf && !df) return AIREBO_OK;
+    std::string msg;
+    airebo_status st = AIREBO_OK;
+    auto add = [&](airebo_status s2, const char* m) {
+        if (!msg.empty()) msg += "; ";
+        msg += m;
+        if (st == AIREBO_OK) st = s2;
+    };
+    if (nf & NONFINITE_POS) add(AIREBO_ERR_NONFINITE, "non-finite position");
+    if (nf & NONFINITE_OVERLAP) add(AIREBO_ERR_NONFINITE, "two atoms closer than 1e-6 A (overlapping atoms)");
+    if (df & DF_RANGE) add(AIREBO_ERR_ARG, "AIREBO_DF64 and AIREBO_MIXED need every |coordinate| below 2000 A");
+    if (df & DF_FORCE) add(AIREBO_ERR_NONFINITE, "an LJ pair force beyond the fixed-point range (1e6 eV/A)");
+    return fail(h, st, msg);
 }
 
 template <class R> StepArgs<R> make_args(airebo_handle h, Precision<R>& pr, const double* d_pos, double* d_force, bool virial) {
@@ -707,20 +741,24 @@ template <class R> StepArgs<R> make_args(airebo_handle h, Precision<R>& pr, cons
     return a;
 }
 
-// One evaluation.  eatom: per-atom energies wanted (summed per system into
-// d_esys).  async: enqueue only (no host synchronisation, no regrowth; the
-// capacity flags are read by airebo_check), as needed for graph capture.
+// One evaluation.  d_esys: per-system energies wanted (sums of the per-atom
+// energies); d_eatom: per-atom energies wanted in the caller's buffer (also
+// the source of d_esys then).  async: enqueue only (no host synchronisation,
+// no regrowth; the capacity flags are read by airebo_check), as needed for
+// graph capture.
 template <class R>
 airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos, double* d_force, double* d_e4,
                          double* d_w6, double* d_pgrad = nullptr, double* d_esys = nullptr, bool async = false,
-                         double* d_kg = nullptr) {
+                         double* d_kg = nullptr, double* d_eatom = nullptr) {
     for (int attempt = 0; attempt < 4; attempt++) {
         cudaStream_t s = h->stream;
         if (h->n) CK(cudaMemsetAsync(d_force, 0, sizeof(double) * 3 * h->n, s));
         CK(cudaMemsetAsync(h->acc, 0, sizeof(double) * 9, s));
         CK(cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * 8, s));
         CK(cudaMemsetAsync(h->counts, 0, sizeof(int) * 8, s));
-        CK(cudaMemsetAsync(h->derr, 0, sizeof(int) * 8, s));
+        // an asynchronous evaluation keeps the flags of earlier ones: they stay
+        // set until airebo_check reads and clears them
+        if (!async) CK(cudaMemsetAsync(h->derr, 0, sizeof(int) * 8, s));
         StepArgs<R> a = make_args<R>(h, pr, d_pos, d_force, d_w6 != nullptr);
         if (a.fix && h->n) CK(cudaMemsetAsync(a.fix, 0, sizeof(unsigned long long) * 3 * h->n, s));
         a.pgrad = d_pgrad;
@@ -735,14 +773,14 @@ airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos,
             CK(cudaMemsetAsync(d_kg, 0, sizeof(double) * KG_N, s));
             a.P = pr.b.Pkg;
         }
-        if (d_esys) {
-            a.eatom = h->eatom;
-            if (h->n) CK(cudaMemsetAsync(h->eatom, 0, sizeof(double) * h->n, s));
+        if (d_esys || d_eatom) {
+            a.eatom = d_eatom ? d_eatom : h->eatom;
+            if (h->n) CK(cudaMemsetAsync(a.eatom, 0, sizeof(double) * h->n, s));
         }
         launch_compute<R>(a, s, h->num_sms, (h->timing && !async) ? h->ev : nullptr);
         CK(cudaGetLastError());
         if (d_e4 || d_w6) k_finalize<<<1, 32, 0, s>>>(h->acc, d_e4, d_w6);
-        if (d_esys) launch_system_energy(h->eatom, h->d_off, std::max(h->nsys, 1), d_esys, s);
+        if (d_esys) launch_system_energy(a.eatom, h->d_off, std::max(h->nsys, 1), d_esys, s);
         if (async) return AIREBO_OK;
         CK(cudaMemcpyAsync(h->h_err, h->derr, sizeof(int) * 8, cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(h->h_u64, h->counts, sizeof(int) * 8, cudaMemcpyDeviceToHost, s));
@@ -757,13 +795,7 @@ airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos,
                 if (ran[k]) { h->kt_ms[slot] += ms; h->kt_n[slot] += 1; }
             }
         }
-        if (h->h_err[ERR_NONFINITE] == 1) return fail(h, AIREBO_ERR_NONFINITE, "non-finite position");
-        if (h->h_err[ERR_NONFINITE] == 2)
-            return fail(h, AIREBO_ERR_NONFINITE, "two atoms closer than 1e-6 A (overlapping atoms)");
-        if (h->h_err[ERR_DF] == 1)
-            return fail(h, AIREBO_ERR_ARG, "AIREBO_DF64 and AIREBO_MIXED need every |coordinate| below 2000 A");
-        if (h->h_err[ERR_DF] == 2)
-            return fail(h, AIREBO_ERR_NONFINITE, "an LJ pair force beyond the fixed-point range (1e6 eV/A)");
+        if (airebo_status st = device_errors(h)) return st;
         bool again = false;
         if (h->h_err[ERR_SHORT] > h->stride) {
             if (h->h_err[ERR_SHORT] > MAXN)
@@ -794,17 +826,17 @@ airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos,
 
 airebo_status compute_any(airebo_handle h, const double* d_pos, double* d_force, double* d_e4, double* d_w6,
                           double* d_pgrad = nullptr, double* d_esys = nullptr, bool async = false,
-                          double* d_kg = nullptr) {
+                          double* d_kg = nullptr, double* d_eatom = nullptr) {
     if (!h->built) return fail(h, AIREBO_ERR_STATE, "airebo_compute before airebo_neighbor");
     CK(cudaSetDevice(h->device));
-    if (d_esys && (h->eatom_n < h->n || !h->eatom)) {
+    if (d_esys && !d_eatom && (h->eatom_n < h->n || !h->eatom)) {
         if (async) return fail(h, AIREBO_ERR_STATE, "per-system energies need one synchronous evaluation first");
         CK(realloc_dev(h->eatom, std::max(h->n, 1)));
         h->eatom_n = h->n;
     }
     if (h->opt.precision == AIREBO_MIXED)
-        return do_compute<float>(h, h->p32, d_pos, d_force, d_e4, d_w6, d_pgrad, d_esys, async, d_kg);
-    return do_compute<double>(h, h->p64, d_pos, d_force, d_e4, d_w6, d_pgrad, d_esys, async, d_kg);
+        return do_compute<float>(h, h->p32, d_pos, d_force, d_e4, d_w6, d_pgrad, d_esys, async, d_kg, d_eatom);
+    return do_compute<double>(h, h->p64, d_pos, d_force, d_e4, d_w6, d_pgrad, d_esys, async, d_kg, d_eatom);
 }
 
 airebo_status check_rebuild(airebo_handle h, const double* d_pos, int* flag) {
@@ -872,7 +904,7 @@ void airebo_default_options(airebo_options* o) {
     o->enable_lj = 1;
     o->enable_torsion = 1;
     o->max_lj_nbrs = 0;
-    o->bstar_screen = 1;
+    o->bstar_screen = 0;
 }
 
 airebo_status airebo_create(const char* params, const airebo_options* opts, void* stream, airebo_handle* out) {
@@ -900,6 +932,9 @@ airebo_status airebo_create(const char* params, const airebo_options* opts, void
     if (!st) {
         if (realloc_dev(h->counts, 8) || realloc_dev(h->acc, 9) || realloc_dev(h->counters, 8) ||
             realloc_dev(h->derr, 8) || realloc_dev(h->maxd2, 1) || realloc_dev(h->ke, 1) ||
+            realloc_dev(h->gate, 1) || realloc_dev(h->d_builds, 1) || realloc_dev(h->nerr, 4) ||
+            cudaMemset(h->derr, 0, sizeof(int) * 8) || cudaMemset(h->d_builds, 0, sizeof(long long)) ||
+            cudaMemset(h->nerr, 0, sizeof(int) * 4) ||
             cudaMallocHost((void**)&h->h_err, sizeof(int) * 8) || cudaMallocHost((void**)&h->h_u64, sizeof(unsigned long long) * 8) ||
             cudaMallocHost((void**)&h->h_acc, sizeof(double) * 16))
             st = AIREBO_ERR_CUDA;
@@ -926,6 +961,7 @@ void airebo_destroy(airebo_handle h) {
     }
     void* ps[] = {h->types, h->cell_of, h->cell_count, h->cell_start, h->cell_fill, h->spos, h->posf, h->pq_lo, h->fix, h->swrap, h->lj, h->lj_cnt,
                   h->im, h->im_cnt, h->xref, h->bonds, h->ccbonds, h->bq, h->bq2, h->counts, h->acc, h->counters, h->derr, h->maxd2, h->ke,
+                  h->gate, h->d_builds, h->nerr,
                   h->hpos, h->hvel, h->hforce, h->he4, h->hw6};
     for (void* p : ps) if (p) cudaFree(p);
     for (int k = 0; k < 12; k++) if (h->ev[k]) cudaEventDestroy(h->ev[k]);
@@ -946,10 +982,11 @@ airebo_status airebo_neighbor(airebo_handle h, const double* d_pos, const int8_t
     return do_neighbor(h, d_pos);
 }
 
-airebo_status airebo_compute(airebo_handle h, const double* d_pos, double* d_force, double* d_energy4, double* d_virial6) {
+airebo_status airebo_compute(airebo_handle h, const double* d_pos, double* d_force, double* d_energy4, double* d_virial6,
+                             double* d_energy_per_atom) {
     if (!h) return AIREBO_ERR_ARG;
     if (h->n > 0 && (!d_pos || !d_force)) return fail(h, AIREBO_ERR_ARG, "null position or force pointer");
-    return compute_any(h, d_pos, d_force, d_energy4, d_virial6);
+    return compute_any(h, d_pos, d_force, d_energy4, d_virial6, nullptr, nullptr, false, nullptr, d_energy_per_atom);
 }
 
 airebo_status airebo_needs_rebuild(airebo_handle h, const double* d_pos, int* out_flag) {
@@ -969,7 +1006,8 @@ static airebo_status stage_host(airebo_handle h, int n) {
 }
 
 airebo_status airebo_compute_host(airebo_handle h, const double* h_pos, const int8_t* h_types, int64_t n,
-                                  const double* box, double* h_force, double* h_energy4, double* h_virial6) {
+                                  const double* box, double* h_force, double* h_energy4, double* h_virial6,
+                                  double* h_energy_per_atom) {
     if (!h) return AIREBO_ERR_ARG;
     if (n > 0 && (!h_pos || !h_types || !h_force)) return fail(h, AIREBO_ERR_ARG, "null host pointer");
     CK(cudaSetDevice(h->device));
@@ -988,19 +1026,29 @@ airebo_status airebo_compute_host(airebo_handle h, const double* h_pos, const in
         if (st) return st;
         if (flag) { st = do_neighbor(h, h->hpos); if (st) return st; }
     }
-    st = compute_any(h, h->hpos, h->hforce, h->he4, h_virial6 ? h->hw6 : nullptr);
+    if (h_energy_per_atom && (h->eatom_n < h->n || !h->eatom)) {
+        CK(realloc_dev(h->eatom, std::max(h->n, 1)));
+        h->eatom_n = h->n;
+    }
+    st = compute_any(h, h->hpos, h->hforce, h->he4, h_virial6 ? h->hw6 : nullptr, nullptr, nullptr, false, nullptr,
+                     h_energy_per_atom ? h->eatom : nullptr);
     if (st) return st;
     if (n) CK(cudaMemcpyAsync(h_force, h->hforce, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+    if (n && h_energy_per_atom)
+        CK(cudaMemcpyAsync(h_energy_per_atom, h->eatom, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
     if (h_energy4) CK(cudaMemcpyAsync(h_energy4, h->he4, sizeof(double) * 4, cudaMemcpyDeviceToHost, h->stream));
     if (h_virial6) CK(cudaMemcpyAsync(h_virial6, h->hw6, sizeof(double) * 6, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return AIREBO_OK;
 }
 
-__global__ void k_nve_energy(const double* acc, const double* ke, double* e4, long long rebuilds) {
+// potential, kinetic and total energy, and the list builds so far: those the
+// host ran plus those the device decided in asynchronous steps
+__global__ void k_nve_energy(const double* acc, const double* ke, double* e4, long long rebuilds,
+                             const long long* dev_builds) {
     if (threadIdx.x == 0) {
         double pe = acc[0] + acc[1] + acc[2];
-        e4[0] = pe; e4[1] = *ke; e4[2] = pe + *ke; e4[3] = (double)rebuilds;
+        e4[0] = pe; e4[1] = *ke; e4[2] = pe + *ke; e4[3] = (double)(rebuilds + *dev_builds);
     }
 }
 
@@ -1053,7 +1101,7 @@ airebo_status airebo_nve(airebo_handle h, double* d_pos, double* d_vel, double* 
         launch_nve_half(d_pos, d_vel, d_force, h->types, h->n, dt, false, nullptr, nullptr, last ? h->ke : nullptr, s);
         CK(cudaGetLastError());
         if (h->timing) { CK(cudaEventRecord(h->ev[11], s)); pending = true; }
-        if (last && d_energy4) k_nve_energy<<<1, 32, 0, s>>>(h->acc, h->ke, d_energy4, h->rebuilds);
+        if (last && d_energy4) k_nve_energy<<<1, 32, 0, s>>>(h->acc, h->ke, d_energy4, h->rebuilds, h->d_builds);
     }
     CK(cudaGetLastError());
     if (pending) {
@@ -1096,9 +1144,11 @@ airebo_status airebo_counters(airebo_handle h, int64_t* out8) {
     if (!h || !out8) return AIREBO_ERR_ARG;
     CK(cudaSetDevice(h->device));
     CK(cudaMemcpyAsync(h->h_u64, h->counters, sizeof(unsigned long long) * 8, cudaMemcpyDeviceToHost, h->stream));
+    long long dev_builds = 0;
+    CK(cudaMemcpyAsync(&dev_builds, h->d_builds, sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     for (int k = 0; k < 8; k++) out8[k] = (int64_t)h->h_u64[k];
-    out8[5] = h->rebuilds;
+    out8[5] = h->rebuilds + dev_builds;
     out8[6] = h->lj_cap;
     int mc = h->opt.precision == AIREBO_MIXED ? h->p32.b.map_cap : h->p64.b.map_cap;
     out8[4] = mc;
@@ -1158,15 +1208,130 @@ airebo_status airebo_check(airebo_handle h) {
     if (!h) return AIREBO_ERR_ARG;
     CK(cudaSetDevice(h->device));
     CK(cudaMemcpyAsync(h->h_err, h->derr, sizeof(int) * 8, cudaMemcpyDeviceToHost, h->stream));
+    int nerr[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(nerr, h->nerr, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    // read once: the flags of the asynchronous work so far start again from zero
+    CK(cudaMemsetAsync(h->derr, 0, sizeof(int) * 8, h->stream));
+    CK(cudaMemsetAsync(h->nerr, 0, sizeof(int) * 4, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    // the list builds the device decided on in asynchronous MD steps
+    if (nerr[2] == 1) return fail(h, AIREBO_ERR_NONFINITE, "non-finite position at a list build");
+    if (nerr[2] == 2) return fail(h, AIREBO_ERR_ARG, "position more than 120 box lengths outside the box at a list build");
+    if (nerr[3]) return fail(h, AIREBO_ERR_ARG, "atom type other than 0 (C) or 1 (H)");
+    if (airebo_status st = device_errors(h)) return st;
+    if (nerr[0] > h->lj_cap || nerr[1] > h->im_cap)
+        return fail(h, AIREBO_ERR_CAPACITY, "a neighbour-list capacity was exceeded at a list build; run airebo_neighbor and "
+                                            "airebo_compute once to grow it");
+    std::string cap;
+    if (h->h_err[ERR_SHORT] > h->stride) cap += " REBO neighbours per atom (" + std::to_string(h->h_err[ERR_SHORT]) + ")";
+    if (h->h_err[ERR_MAP]) cap += " connectivity-map entries per atom (" + std::to_string(h->h_err[ERR_MAP]) + ")";
+    if (h->h_err[ERR_QUEUE] > h->bq_cap) cap += " b* queue (" + std::to_string(h->h_err[ERR_QUEUE]) + ")";
+    if (!cap.empty())
+        return fail(h, AIREBO_ERR_CAPACITY, "a scratch capacity was exceeded:" + cap + "; run airebo_compute once to grow it");
+    return AIREBO_OK;
+}
+
+}  // extern "C"
+
+// Headroom for work that cannot grow a capacity while it runs (captured MD
+// steps): the full REBO slot stride, a quarter more connectivity-map entries
+// per atom, and a quarter more b* queue than the last evaluation needed.
+template <class R> static airebo_status reserve_headroom(airebo_handle h, Precision<R>& pr) {
+    if (h->stride < MAXN) {
+        h->stride = MAXN;
+        airebo_status st = alloc_step<R>(h, pr, h->n_alloc);
+        if (st) return st;
+    }
+    StepBuffers<R>& b = pr.b;
+    b.map_cap += b.map_cap / 4 + 4;
+    size_t mm = (size_t)h->n_alloc * b.map_cap;
+    CK(realloc_dev(b.map_key, mm)); CK(realloc_dev(b.map_wt, mm)); CK(realloc_dev(b.map_path, mm));
     CK(cudaMemcpyAsync(h->h_u64, h->counts, sizeof(int) * 8, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     const int* cn = (const int*)h->h_u64;
-    if (h->h_err[ERR_NONFINITE])
-        return fail(h, AIREBO_ERR_NONFINITE, h->h_err[ERR_NONFINITE] == 2 ? "two atoms closer than 1e-6 A (overlapping atoms)"
-                                                                           : "non-finite position");
-    if (h->h_err[ERR_SHORT] > h->stride || h->h_err[ERR_MAP] ||
-        std::max(cn[4], std::max(cn[5], cn[6])) > h->bq_cap)
-        return fail(h, AIREBO_ERR_CAPACITY, "a scratch capacity was exceeded; run airebo_compute once to grow it");
+    int nq = std::max(cn[4], std::max(cn[5], cn[6]));
+    if (nq + nq / 4 + 1024 > h->bq_cap) {
+        h->bq_cap = nq + nq / 4 + 1024;
+        CK(realloc_dev(h->bq, 3 * (size_t)h->bq_cap));
+        CK(realloc_dev(h->bq2, 3 * (size_t)h->bq_cap));
+    }
+    return AIREBO_OK;
+}
+
+extern "C" {
+
+// One velocity-Verlet step with no host work: the half kick and drift with the
+// displacement check, the device's rebuild decision, the list build behind it,
+// the evaluation, and the second half kick.
+static airebo_status nve_step_async(airebo_handle h, double* d_pos, double* d_vel, double* d_force, double dt,
+                                    bool last, double* d_energy4) {
+    cudaStream_t s = h->stream;
+    CK(cudaMemsetAsync(h->maxd2, 0, sizeof(unsigned long long), s));
+    launch_nve_half(d_pos, d_vel, d_force, h->types, h->n, dt, true, h->xref, h->maxd2, nullptr, s);
+    double half = 0.5 * h->opt.skin;
+    launch_rebuild_decide(h->maxd2, half * half, h->gate, h->d_builds, s);
+    NeighborArgs a = h->nargs;
+    a.pos = d_pos;
+    a.err = h->nerr;
+    a.gate = h->gate;
+    launch_neighbor_gated(a, s, h->nargs_ncell);
+    CK(cudaGetLastError());
+    airebo_status st = compute_any(h, d_pos, d_force, nullptr, nullptr, nullptr, nullptr, true);
+    if (st) return st;
+    if (last) CK(cudaMemsetAsync(h->ke, 0, sizeof(double), s));
+    launch_nve_half(d_pos, d_vel, d_force, h->types, h->n, dt, false, nullptr, nullptr, last ? h->ke : nullptr, s);
+    if (last && d_energy4) k_nve_energy<<<1, 32, 0, s>>>(h->acc, h->ke, d_energy4, h->rebuilds, h->d_builds);
+    CK(cudaGetLastError());
+    return AIREBO_OK;
+}
+
+airebo_status airebo_nve_async(airebo_handle h, double* d_pos, double* d_vel, double* d_force, double dt, int nsteps,
+                               double* d_energy4) {
+    if (!h) return AIREBO_ERR_ARG;
+    if (!h->built || !h->nargs_ok) return fail(h, AIREBO_ERR_STATE, "airebo_nve_async before airebo_neighbor");
+    if (nsteps < 0 || !(dt > 0)) return fail(h, AIREBO_ERR_ARG, "bad dt or step count");
+    if (h->n > 0 && (!d_pos || !d_vel || !d_force)) return fail(h, AIREBO_ERR_ARG, "null position, velocity or force pointer");
+    CK(cudaSetDevice(h->device));
+    for (int step = 0; step < nsteps; step++) {
+        airebo_status st = nve_step_async(h, d_pos, d_vel, d_force, dt, step == nsteps - 1, d_energy4);
+        if (st) return st;
+    }
+    return AIREBO_OK;
+}
+
+airebo_status airebo_graph_capture_nve(airebo_handle h, double* d_pos, double* d_vel, double* d_force, double dt,
+                                       int nsteps, double* d_energy4) {
+    if (!h) return AIREBO_ERR_ARG;
+    if (!h->stream) return fail(h, AIREBO_ERR_ARG, "graph capture needs a handle created on a non-default stream");
+    if (!h->built || !h->nargs_ok) return fail(h, AIREBO_ERR_STATE, "airebo_graph_capture_nve before airebo_neighbor");
+    if (nsteps < 1 || !(dt > 0)) return fail(h, AIREBO_ERR_ARG, "bad dt or step count");
+    if (h->n > 0 && (!d_pos || !d_vel || !d_force)) return fail(h, AIREBO_ERR_ARG, "null position, velocity or force pointer");
+    CK(cudaSetDevice(h->device));
+    // the lists are rebuilt at d_pos with a quarter more room per atom, a
+    // synchronous evaluation grows every scratch capacity, the scratch gets
+    // headroom for the steps ahead too, and a second evaluation leaves in
+    // d_force the forces the first step starts from
+    if (h->opt.enable_lj) h->lj_cap = ((int)(h->lj_cap * 1.25) + 31) / 32 * 32;
+    h->im_cap += h->im_cap / 4 + 4;
+    airebo_status st = do_neighbor(h, d_pos);
+    if (st) return st;
+    st = compute_any(h, d_pos, d_force, nullptr, nullptr);
+    if (st) return st;
+    st = h->opt.precision == AIREBO_MIXED ? reserve_headroom<float>(h, h->p32) : reserve_headroom<double>(h, h->p64);
+    if (st) return st;
+    st = compute_any(h, d_pos, d_force, nullptr, nullptr);
+    if (st) return st;
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    st = airebo_nve_async(h, d_pos, d_vel, d_force, dt, nsteps, d_energy4);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (st) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) return fail(h, AIREBO_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+    h->graph = g;
+    CK(cudaGraphInstantiate(&h->gexec, g, 0));
     return AIREBO_OK;
 }
 
@@ -1332,6 +1497,29 @@ airebo_status airebo_set_lj_params(airebo_handle h, const double* eps3, const do
     airebo_status st = upload_own_params(h);
     if (st) return st;
     if (sigma_changed) h->built = false;          // the LJ cut-off moved: the lists must be rebuilt
+    return AIREBO_OK;
+}
+
+airebo_status airebo_set_knots(airebo_handle h, const double* h_knots, int64_t count) {
+    if (!h || !h_knots) return AIREBO_ERR_ARG;
+    if (count != AIREBO_KNOT_COUNT) return fail(h, AIREBO_ERR_ARG, "knot data need AIREBO_KNOT_COUNT values");
+    for (int64_t k = 0; k < count; k++)
+        if (!std::isfinite(h_knots[k])) return fail(h, AIREBO_ERR_ARG, "non-finite knot datum");
+    Scalars s = h->sc;
+    // the parameter-file order of airebo_knot_grad
+    const double* q = h_knots;
+    auto take = [&](std::vector<double>& dst) { std::copy(q, q + dst.size(), dst.begin()); q += dst.size(); };
+    take(s.gC1d); take(s.gC2d); take(s.gHd);
+    for (int t = 0; t < 3; t++) take(s.P[t]);
+    for (int t = 0; t < 3; t++) take(s.F[t]);
+    take(s.T);
+    if (q - h_knots != count) return fail(h, AIREBO_ERR_ARG, "knot layout mismatch");
+    CK(cudaSetDevice(h->device));
+    CK(cudaStreamSynchronize(h->stream));
+    Scalars old = h->sc;
+    h->sc = s;
+    airebo_status st = upload_own_params(h);
+    if (st) { h->sc = old; upload_own_params(h); return st; }
     return AIREBO_OK;
 }
 

@@ -58,7 +58,7 @@ template <class R> struct StepArgs {
     int bstar_waves;                       // waves of resident blocks of the b* kernels (tuned)
     const int* sys;                        // batched systems: system of each atom (null: one system, box L)
     const double* Lsys;                    // batched systems: box of each system (3 per system)
-    double* eatom;                         // nullable: energy of each atom's anchored terms
+    double* eatom;                         // nullable: per-atom energies (each term split evenly between its i and j)
     double* f;
     double* acc;          // E_rebo, E_lj, E_tors, W[6]
     unsigned long long* counters;   // [8]
@@ -69,6 +69,10 @@ template <class R> struct StepArgs {
 };
 
 enum { ERR_SHORT = 0, ERR_MAP = 1, ERR_QUEUE = 2, ERR_NONFINITE = 3, ERR_DF = 4 };
+// bits of err[ERR_NONFINITE] and err[ERR_DF]: each condition has its own bit,
+// so that one evaluation can report several
+enum { NONFINITE_POS = 1, NONFINITE_OVERLAP = 2 };
+enum { DF_RANGE = 1, DF_FORCE = 2 };
 enum { CNT_BONDS = 0, CNT_BSTAR = 1, CNT_DSB = 2, CNT_LJ = 3, CNT_MAP = 4, CNT_BSTAR_FULL = 7 };
 
 // Half-width of the band around [b_min, b_max] inside which an FP32 b* does
@@ -104,8 +108,17 @@ struct NeighborArgs {
     const int* sreach;
     const double* scw;
     const int* scell0;
+    // device-decided rebuild (the asynchronous MD step): when set, every
+    // kernel of the build returns at once unless *gate is nonzero
+    const int* gate;
 };
 void launch_neighbor(NeighborArgs& a, cudaStream_t s, int ncell);
+// the same build behind a.gate, with the cell counts cleared and the
+// reference positions copied by gated kernels too (no host work at all)
+void launch_neighbor_gated(NeighborArgs& a, cudaStream_t s, int ncell);
+// *gate = max displacement^2 > half2, and the device build counter counts it
+void launch_rebuild_decide(const unsigned long long* maxd2_bits, double half2, int* gate, long long* builds,
+                           cudaStream_t s);
 // per-system sums of per-atom energies (one block per system)
 void launch_system_energy(const double* eatom, const long long* offsets, int nsys, double* out, cudaStream_t s);
 

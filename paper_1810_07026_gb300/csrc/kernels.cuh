@@ -86,6 +86,14 @@ __device__ __forceinline__ const double* box_of(const StepArgs<R>& a, int i) {
     return a.sys ? a.Lsys + 3 * a.sys[i] : a.L;
 }
 
+// Per-atom energies: each bond, torsion or pair term is split evenly between
+// the two atoms that define it (i and j of the bond or pair), so that the
+// per-atom energies do not depend on the atom numbering and sum to the total.
+__device__ __forceinline__ void eatom_pair(double* eatom, int i, int j, double e) {
+    atomicAdd(eatom + i, 0.5 * e);
+    atomicAdd(eatom + j, 0.5 * e);
+}
+
 __device__ __forceinline__ void load_disp(const double* pos, int n, const double* L, int i, int j, int img,
                                           double& dx, double& dy, double& dz) {
     if (img == 0) {
@@ -107,9 +115,9 @@ __global__ void __launch_bounds__(128) k_posf(StepArgs<R> a) {
     if (i >= a.n) return;
     int n = a.n;
     double xi = a.pos[i], yi = a.pos[n + i], zi = a.pos[2 * n + i];
-    if (!isfinite(xi) || !isfinite(yi) || !isfinite(zi)) atomicMax(a.err + ERR_NONFINITE, 1);
+    if (!isfinite(xi) || !isfinite(yi) || !isfinite(zi)) atomicOr(a.err + ERR_NONFINITE, NONFINITE_POS);
     if (a.fix) {
-        if (!(fabs(xi) < 2000.0 && fabs(yi) < 2000.0 && fabs(zi) < 2000.0)) atomicMax(a.err + ERR_DF, 1);
+        if (!(fabs(xi) < 2000.0 && fabs(yi) < 2000.0 && fabs(zi) < 2000.0)) atomicOr(a.err + ERR_DF, DF_RANGE);
         float4 h, l;
         df_split(xi, h.x, l.x); df_split(yi, h.y, l.y); df_split(zi, h.z, l.z);
         h.w = __int_as_float((int)a.G.type[i]);
@@ -182,7 +190,7 @@ __global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
         double dmax = (double)P.Dmax[p];
         if (!(r2 < dmax * dmax)) continue;
         // two atoms at (nearly) one point: every term diverges there
-        if (!(r2 > 1e-12)) { atomicMax(a.err + ERR_NONFINITE, 2); continue; }
+        if (!(r2 > 1e-12)) { atomicOr(a.err + ERR_NONFINITE, NONFINITE_OVERLAP); continue; }
         double ir = rsqrt_(r2);
         double r = r2 * ir;
         R dw, omw;
@@ -236,7 +244,7 @@ __global__ void __launch_bounds__(128, 4) k_rebo(StepArgs<R> a) {
         int2 bd = b < ncc ? a.ccbonds[b] : a.bonds[b - ncc];
         double e = rebo_bond<R>(P, a.G, bd.x, bd.y, sink);
         E += e;
-        if (a.eatom) atomicAdd(a.eatom + bd.x, e);
+        if (a.eatom) eatom_pair(a.eatom, bd.x, a.G.nj[bd.x * a.G.stride + bd.y], e);
     }
     block_accumulate<128>(E, sink.W, EXTRA && a.virial, a.acc + 0, a.acc + 3);
 }
@@ -253,7 +261,7 @@ __global__ void __launch_bounds__(128) k_torsion(StepArgs<R> a) {
         int2 bd = a.ccbonds[b];
         double e = torsion_bond<R>(P, a.G, bd.x, bd.y, sink);
         E += e;
-        if (a.eatom && e != 0.0) atomicAdd(a.eatom + bd.x, e);
+        if (a.eatom && e != 0.0) eatom_pair(a.eatom, bd.x, a.G.nj[bd.x * a.G.stride + bd.y], e);
     }
     block_accumulate<128>(E, sink.W, EXTRA && a.virial, a.acc + 2, a.acc + 3);
 }
@@ -273,7 +281,7 @@ __global__ void __launch_bounds__(128) k_torsion_dd(StepArgs<double> a) {
         int2 bd = a.ccbonds[b];
         double e = torsion_bond<dd>(P, G, bd.x, bd.y, sink);
         E += e;
-        if (a.eatom && e != 0.0) atomicAdd(a.eatom + bd.x, e);
+        if (a.eatom && e != 0.0) eatom_pair(a.eatom, bd.x, a.G.nj[bd.x * a.G.stride + bd.y], e);
     }
     block_accumulate<128>(E, sink.W, EXTRA && a.virial, a.acc + 2, a.acc + 3);
 }
@@ -357,7 +365,10 @@ __device__ __forceinline__ void lj_batch(const StepArgs<R>& a, const DevParams<R
         lj_eval_inner<R>(P, p, j, dx, dy, dz, r2, sink, acc.fx, acc.fy, acc.fz, E);
     else
         lj_eval_switch<R>(P, p, j, dx, dy, dz, r2, sink, acc.fx, acc.fy, acc.fz, E);
-    if (a.eatom) acc.e += E - E0;
+    if (a.eatom) {
+        acc.e += 0.5 * (E - E0);
+        atomicAdd(a.eatom + j, 0.5 * (E - E0));
+    }
 }
 
 // ---- double-float evaluation of the compacted pairs (precision AIREBO_DF64)
@@ -463,7 +474,10 @@ __device__ __noinline__ void lj_batch_df(const StepArgs<R>& a, const DfParams& D
         c = ff_add(ff_mul(dvr, so), ff_mul(ff_mul(vv, dso), ir));
     }
     E = ff_add(E, v);
-    if (a.eatom) acc.e = ff_add(acc.e, v);
+    if (a.eatom) {
+        acc.e = ff_add(acc.e, ff_mul_f(v, 0.5f));
+        atomicAdd(a.eatom + j, 0.5 * ff_to_double(v));
+    }
     ff gx = ff_mul(c, dx), gy = ff_mul(c, dy), gz = ff_mul(c, dz);
     if (fabsf(gx.hi) < FIX_LIMIT && fabsf(gy.hi) < FIX_LIMIT && fabsf(gz.hi) < FIX_LIMIT) {
         long long qx = ff_to_fixed(gx), qy = ff_to_fixed(gy), qz = ff_to_fixed(gz);
@@ -472,7 +486,7 @@ __device__ __noinline__ void lj_batch_df(const StepArgs<R>& a, const DfParams& D
         atomicAdd(a.fix + a.n + j, (unsigned long long)(-qy));
         atomicAdd(a.fix + 2 * a.n + j, (unsigned long long)(-qz));
     } else {
-        atomicMax(a.err + ERR_DF, 2);
+        atomicOr(a.err + ERR_DF, DF_FORCE);
     }
     if (EXTRA && a.virial) {
         W[0] = ff_sub(W[0], ff_mul(dx, gx)); W[1] = ff_sub(W[1], ff_mul(dy, gy)); W[2] = ff_sub(W[2], ff_mul(dz, gz));
@@ -529,7 +543,10 @@ __device__ __forceinline__ void lj_batch_mx(const StepArgs<R>& a, const DevParam
         c = dvr * so + vv * dso * ir;
     }
     E = ff_add_f(E, v);
-    if (a.eatom) acc.e = ff_add_f(acc.e, v);
+    if (a.eatom) {
+        acc.e = ff_add_f(acc.e, 0.5f * v);
+        atomicAdd(a.eatom + j, 0.5 * (double)v);
+    }
     float gx = c * rx, gy = c * ry, gz = c * rz;
     if (fabsf(gx) < FIX_LIMIT && fabsf(gy) < FIX_LIMIT && fabsf(gz) < FIX_LIMIT) {
         long long qx = f2fix(gx), qy = f2fix(gy), qz = f2fix(gz);
@@ -538,7 +555,7 @@ __device__ __forceinline__ void lj_batch_mx(const StepArgs<R>& a, const DevParam
         atomicAdd(a.fix + a.n + j, (unsigned long long)(-qy));
         atomicAdd(a.fix + 2 * a.n + j, (unsigned long long)(-qz));
     } else {
-        atomicMax(a.err + ERR_DF, 2);
+        atomicOr(a.err + ERR_DF, DF_FORCE);
     }
     if (EXTRA && a.virial) {
         W[0] = ff_add_f(W[0], -rx * gx); W[1] = ff_add_f(W[1], -ry * gy); W[2] = ff_add_f(W[2], -rz * gz);
@@ -691,7 +708,7 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
                     double gx = 0, gy = 0, gz = 0, E0 = E;
                     lj_eval<R>(P, a.G, i, p, j, dx, dy, dz, C, code, sink, gx, gy, gz, E);
                     atomicAdd(a.f + i, gx); atomicAdd(a.f + n + i, gy); atomicAdd(a.f + 2 * n + i, gz);
-                    if (a.eatom) atomicAdd(a.eatom + i, E - E0);
+                    if (a.eatom) eatom_pair(a.eatom, i, j, E - E0);
                 }
             }
 #pragma unroll
@@ -797,7 +814,7 @@ __global__ void __launch_bounds__(128, 8) k_bstar(StepArgs<R> a) {
         if (decided) {
             double e = bstar_finish<R>(P, a.G, i, j, rx, ry, rz, r2, C, code, Sb, R(0), sink);
             E += e;
-            if (a.eatom) atomicAdd(a.eatom + i, e);
+            if (a.eatom) eatom_pair(a.eatom, i, j, e);
         } else {
             int s = atomicAdd(a.nbq2, 1);
             if (s < 3 * a.bq_cap) a.bq2[s] = t;
@@ -828,7 +845,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 4) k_bstar_rev(StepA
         double e = bstar_full<R>(P, a.G, i, j, rx, ry, rz, r2, C, code, sink, dsb);
         dsb_count += dsb;
         E += e;
-        if (a.eatom) atomicAdd(a.eatom + i, e);
+        if (a.eatom) eatom_pair(a.eatom, i, j, e);
     }
     unsigned c = __reduce_add_sync(0xffffffffu, dsb_count);
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(a.counters + CNT_DSB, (unsigned long long)c);
@@ -842,6 +859,10 @@ __global__ void k_finish_counters(StepArgs<R> a) {
         a.counters[CNT_BONDS] = (unsigned long long)(*a.nbonds + *a.nccbonds);
         a.counters[CNT_BSTAR] = (unsigned long long)(a.nbq[0] + a.nbq[1] + a.nbq[2]);
         a.counters[CNT_BSTAR_FULL] = (unsigned long long)*a.nbq2;
+        // the longest b* queue, kept with the other flags (a capacity check
+        // after several asynchronous evaluations sees the largest of them)
+        int q = max(a.nbq[0], max(a.nbq[1], a.nbq[2]));
+        if (q > a.bq_cap) atomicMax(a.err + ERR_QUEUE, q);
     }
 }
 

@@ -36,7 +36,11 @@ __device__ __forceinline__ Grid grid_of(const NeighborArgs& a, int i) {
     return g;
 }
 
+// a gated build (a.gate set) runs only when the device decided to rebuild
+__device__ __forceinline__ bool gated_off(const int* gate) { return gate && *gate == 0; }
+
 __global__ void k_bin(NeighborArgs a) {
+    if (gated_off(a.gate)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     Grid g = grid_of(a, i);
@@ -60,7 +64,8 @@ __global__ void k_bin(NeighborArgs a) {
 // Exclusive scan of the cell counts into the cell starts (and the fill
 // cursors), by one block over tiles of 1024 cells: coalesced loads, a
 // shuffle scan in each warp, then over the warps' sums, and a running carry.
-__global__ void __launch_bounds__(1024) k_scan(const int* count, int* start, int* fill, int ncell) {
+__global__ void __launch_bounds__(1024) k_scan(const int* count, int* start, int* fill, int ncell, const int* gate) {
+    if (gated_off(gate)) return;
     __shared__ int wsum[32];
     int t = threadIdx.x, lane = t & 31, w = t >> 5;
     int carry = 0;
@@ -95,6 +100,7 @@ __global__ void __launch_bounds__(1024) k_scan(const int* count, int* start, int
 }
 
 __global__ void k_scatter(NeighborArgs a) {
+    if (gated_off(a.gate)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     int slot = atomicAdd(a.cell_fill + a.cell_of[i], 1);
@@ -116,6 +122,7 @@ __global__ void k_scatter(NeighborArgs a) {
 }
 
 __global__ void __launch_bounds__(128) k_build(NeighborArgs a, const int* cell_start) {
+    if (gated_off(a.gate)) return;
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= a.n) return;
     float4 pi = a.spos[s];
@@ -202,6 +209,7 @@ __global__ void __launch_bounds__(128) k_build(NeighborArgs a, const int* cell_s
 // kernel then meet the species of the neighbours k in the same slot order
 // and run the same branches.  (Two-pointer partition; rows are short.)
 __global__ void k_order_im(NeighborArgs a) {
+    if (gated_off(a.gate)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     int c = min(a.im_cnt[i], a.im_cap);
@@ -225,10 +233,45 @@ void launch_neighbor(NeighborArgs& a, cudaStream_t s, int ncell) {
     cudaMemsetAsync(a.cell_count, 0, sizeof(int) * ncell, s);
     int nb = (a.n + 127) / 128;
     k_bin<<<nb, 128, 0, s>>>(a);
-    k_scan<<<1, 1024, 0, s>>>(a.cell_count, a.cell_start, a.cell_fill, ncell);
+    k_scan<<<1, 1024, 0, s>>>(a.cell_count, a.cell_start, a.cell_fill, ncell, a.gate);
     k_scatter<<<nb, 128, 0, s>>>(a);
     k_build<<<nb, 128, 0, s>>>(a, a.cell_start);
     k_order_im<<<nb, 128, 0, s>>>(a);
+}
+
+__global__ void k_clear_cells(int* count, int ncell, const int* gate) {
+    if (gated_off(gate)) return;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) count[c] = 0;
+}
+
+// the positions of the build, for the next displacement check
+__global__ void k_copy_ref(const double* pos, double* xref, int n3, const int* gate) {
+    if (gated_off(gate)) return;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n3; k += gridDim.x * blockDim.x) xref[k] = pos[k];
+}
+
+void launch_neighbor_gated(NeighborArgs& a, cudaStream_t s, int ncell) {
+    if (a.n == 0) return;
+    int nb = (a.n + 127) / 128;
+    k_clear_cells<<<(ncell + 255) / 256, 256, 0, s>>>(a.cell_count, ncell, a.gate);
+    k_bin<<<nb, 128, 0, s>>>(a);
+    k_scan<<<1, 1024, 0, s>>>(a.cell_count, a.cell_start, a.cell_fill, ncell, a.gate);
+    k_scatter<<<nb, 128, 0, s>>>(a);
+    k_build<<<nb, 128, 0, s>>>(a, a.cell_start);
+    k_order_im<<<nb, 128, 0, s>>>(a);
+    k_copy_ref<<<(3 * a.n + 255) / 256, 256, 0, s>>>(a.pos, a.xref, 3 * a.n, a.gate);
+}
+
+__global__ void k_rebuild_decide(const unsigned long long* maxd2, double half2, int* gate, long long* builds) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int g = __longlong_as_double((long long)*maxd2) > half2 ? 1 : 0;
+        *gate = g;
+        if (g) *builds += 1;
+    }
+}
+
+void launch_rebuild_decide(const unsigned long long* maxd2, double half2, int* gate, long long* builds, cudaStream_t s) {
+    k_rebuild_decide<<<1, 32, 0, s>>>(maxd2, half2, gate, builds);
 }
 
 // per-system energy: sum of the per-atom energies of each system's atoms

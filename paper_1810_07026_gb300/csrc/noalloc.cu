@@ -15,6 +15,7 @@
 // must start at zero before each launch.  Calls whose kernels overlap on the
 // GPU (different streams, or different host threads on one device) race on
 // the array and must be serialised by the caller.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cmath>
 #include <mutex>
@@ -34,7 +35,10 @@ static __device__ __align__(256) double g_noalloc_scratch[NA_WORDS];
 
 constexpr int NA_MAX_DEVICES = 64;
 std::mutex g_setup_mutex;
+// per device: the array's device address and the id of the context it was
+// looked up in (a reset device gets a new context, and the array a new address)
 double* g_scratch_ptr[NA_MAX_DEVICES] = {};
+unsigned long long g_scratch_ctx[NA_MAX_DEVICES] = {};
 
 // One kernel: each block writes the maximum squared displacement of its atoms
 // to scratch[block]; the last block to finish reduces those into
@@ -64,8 +68,10 @@ __global__ void __launch_bounds__(NA_THREADS) k_max_disp_noalloc(const double* p
     __syncthreads();
     if (last) {
         __threadfence();
+        // the other blocks' maxima, read from L2 (where their writes went
+        // before their fences), not from this SM's L1
         double m = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) m = fmax(m, scratch[b]);
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) m = fmax(m, __ldcg(scratch + b));
         for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
         __syncthreads();
@@ -78,22 +84,53 @@ __global__ void __launch_bounds__(NA_THREADS) k_max_disp_noalloc(const double* p
     }
 }
 
-// Device address of the scratch array on the current device, looked up once
-// per device by the first call made with that device current (host code may
+// Id of the current context (0 if the driver cannot tell), from the driver
+// entry points the runtime hands out; the library does not link the driver.
+unsigned long long current_context_id() {
+    typedef CUresult (*get_current_t)(CUcontext*);
+    typedef CUresult (*get_id_t)(CUcontext, unsigned long long*);
+    static get_current_t get_current = nullptr;
+    static get_id_t get_id = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<get_current_t>(f1);
+            get_id = reinterpret_cast<get_id_t>(f2);
+        }
+        looked = true;
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&ctx) == CUDA_SUCCESS && ctx && get_id(ctx, &id) == CUDA_SUCCESS) return id;
+    return 0;
+}
+
+// Device address of the scratch array on the current device (host code may
 // not pass the array's name to a kernel: on the host it is only a stand-in
-// for the symbol).  That first call should therefore come before any stream
-// capture.
+// for the symbol).  Set-up: the first call made with a device current looks
+// the address up and keeps it with the id of the device's context; it is
+// looked up again only when that context has changed (after a
+// cudaDeviceReset).  That first call should come before any stream capture.
 cudaError_t scratch_address(double** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= NA_MAX_DEVICES) return cudaErrorInvalidDevice;
+    e = cudaSetDevice(dev);                    // makes the device's primary context current
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
+    unsigned long long ctx = current_context_id();
+    if (!g_scratch_ptr[dev] || ctx != g_scratch_ctx[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
         g_scratch_ptr[dev] = static_cast<double*>(p);
+        g_scratch_ctx[dev] = current_context_id();
     }
     *out = g_scratch_ptr[dev];
     return cudaSuccess;

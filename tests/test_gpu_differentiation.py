@@ -118,3 +118,47 @@ def test_fitting_loss_over_64_perturbed_copies(A):
                 vals.append(loss_of(e, s, False).item())
             fd = (vals[0] - vals[1]) / (2 * h)
             assert g[k].item() == pytest.approx(fd, rel=1e-4, abs=1e-6)
+
+
+def test_autograd_knots_and_set_knots(A):
+    """The spline knot data as a differentiable input of AireboEnergy: the
+    energy after set_knots equals the oracle's with the same knot data, and
+    the autograd gradient along a random direction in knot space equals
+    central differences of the oracle energy (1e-6 relative step)."""
+    params = inputs.make_params(0)
+    text = inputs.params_text(params)
+    pos, types, box = inputs.amorphous(300, 0.5, 0.9, seed=5)
+    ev = A.Airebo(text)
+    p = torch.tensor(pos, device="cuda")
+    ev.neighbor(p, torch.tensor(types, device="cuda"), box)
+    rng = np.random.default_rng(17)
+    k0 = A.knot_vector(params)
+    # perturbed knot data: the GPU energy follows the oracle's with the same data
+    k1 = k0 * (1.0 + 0.05 * rng.uniform(-1, 1, k0.size))
+    p1, o = dict(params), 0
+    for name, c in A.KNOT_BLOCKS:
+        p1[name] = k1[o:o + c].copy()
+        o += c
+    ev.set_knots(k1)
+    e1 = ev.compute(p)[1][0].item()
+    want = Oracle(inputs.params_text(p1)).energy(pos, types, box)
+    assert e1 == pytest.approx(want, rel=1e-10)
+    with pytest.raises(A.AireboError):
+        ev.set_knots(k1[:-1])
+    # gradient through autograd
+    eps = torch.tensor(params["lj.epsilon"], device="cuda")
+    sig = torch.tensor(params["lj.sigma"], device="cuda")
+    kt = torch.tensor(k0, device="cuda", requires_grad=True)
+    E = A.AireboEnergy.apply(p, eps, sig, ev, kt)
+    (gk,) = torch.autograd.grad(E, (kt,))
+    v = rng.normal(0.0, 1.0, k0.size) * np.maximum(np.abs(k0), 1e-3)
+    h = 1e-6
+    vals = []
+    for sgn in (1, -1):
+        q, o = dict(params), 0
+        for name, c in A.KNOT_BLOCKS:
+            q[name] = k0[o:o + c] + sgn * h * v[o:o + c]
+            o += c
+        vals.append(Oracle(inputs.params_text(q)).energy(pos, types, box))
+    fd = (vals[0] - vals[1]) / (2 * h)
+    assert float(gk.cpu().numpy() @ v) == pytest.approx(fd, rel=1e-5, abs=1e-7)

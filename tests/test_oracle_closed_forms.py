@@ -379,3 +379,21 @@ def test_angle_guard_in_torsion_and_dihedral(params):
     erebo = fR(p, CC, rcc) + bcc * fA(p, CC, rcc) + 2 * (fR(p, CH, rch) + bch * fA(p, CH, rch))
     assert knot_tri(p, "Tij.CC", 1, 1, 1) != 0.0
     assert e[1] == pytest.approx(erebo, rel=1e-11)
+
+
+def test_per_atom_energy_split(oracle, params):
+    """Per-atom energies split each term evenly between its two atoms: for two
+    H2 molecules 4 A apart, each H holds half its molecule's bond energy
+    (Alg. 1) and half of every LJ pair it is in (C = 1, S_r = 0 at 4 A)."""
+    p = params
+    a = [[0, 0, 0], [0.74, 0, 0], [0, 4.0, 0.3], [0.74, 4.0, 0.3]]
+    pos = np.ascontiguousarray(np.array(a, dtype=np.float64).T + 20.0)
+    e, _, _, _, ea = oracle.compute(pos, np.ones(4, dtype=np.int8), BOX, per_atom=True)
+    sg, eps = p["lj.sigma"][HH], p["lj.epsilon"][HH]
+    x = np.array(a)
+    ebond = fR(p, HH, 0.74) + (1.0 + knot_tri(p, "piRC.HH", 0, 0, 1)) * fA(p, HH, 0.74)
+    for i in range(4):
+        others = (2, 3) if i < 2 else (0, 1)
+        lj = sum(4 * eps * ((sg / r) ** 12 - (sg / r) ** 6) for r in (np.linalg.norm(x[i] - x[j]) for j in others))
+        assert ea[i] == pytest.approx(0.5 * ebond + 0.5 * lj, rel=1e-12)
+    assert ea.sum() == pytest.approx(e[0], rel=1e-13)

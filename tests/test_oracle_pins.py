@@ -315,3 +315,17 @@ def test_nve_energy_conservation_dt2(oracle):
     s2, _ = nve_energy_spread(oracle, pos, types, box, vel, 0.25, 10.0)
     assert s1 < 3e-4 * abs(tot[0])
     assert 2.5 < s1 / s2 < 6.0
+
+
+def test_per_atom_energies_sum_and_permute(oracle, hot):
+    """Per-atom energies sum to the total, per term, and follow a relabelling
+    of the atoms (the even split of each term does not depend on which atom
+    of a pair is i)."""
+    pos, types, box = hot
+    for flags, k in ((FLAG_ALL, 0), (FLAG_REBO, 1), (FLAG_LJ, 2), (FLAG_TORSION, 3)):
+        e, _, _, _, ea = oracle.compute(pos, types, box, flags, forces=False, per_atom=True)
+        assert ea.sum() == pytest.approx(e[k], rel=1e-12, abs=1e-12)
+    e, _, _, _, ea = oracle.compute(pos, types, box, per_atom=True)
+    perm = np.random.default_rng(7).permutation(len(types))
+    _, _, _, _, ea2 = oracle.compute(pos[:, perm], types[perm], box, per_atom=True)
+    assert np.abs(ea2 - ea[perm]).max() < 1e-11 * np.abs(ea).max()
