@@ -277,6 +277,22 @@ airebo_status airebo_param_grad(airebo_handle h, const double* d_pos, double* d_
                                 double* h_grad6);
 
 /*
+ * Parameter derivatives of the forces, for force matching: with a direction
+ * d_v (device double[3][n]), h_out6 (host double[6]) receives
+ * v . dF/d epsilon[CC, CH, HH] and v . dF/d sigma[CC, CH, HH] of the
+ * inter-molecular term (Sec. 2.1.2, the E^LJ of Alg. 3; epsilon is lj.epsilon
+ * or morse.epsilon), F the forces of airebo_compute -- e.g. v = 2 (F - F_ref)
+ * gives the gradient of sum |F - F_ref|^2.  The forces of the pair term are
+ * linear in epsilon, and dE/dsigma has the pair term's own form with the
+ * sigma-derivatives of its radial factors, so both come from one pass over
+ * the pairs (radial part, C_ij path, and the reverse b* in the S_b
+ * transition).  Also evaluates forces and energy like airebo_compute
+ * (d_energy4 nullable); every LJ pair takes the general path.  Synchronises.
+ */
+airebo_status airebo_force_param_grad(airebo_handle h, const double* d_pos, const double* d_v, double* d_force,
+                                      double* d_energy4, double* h_out6);
+
+/*
  * Replace epsilon[3] (lj.epsilon or morse.epsilon) and/or sigma[3] (lj.sigma)
  * of the inter-molecular term; either pointer may be NULL.  Changing sigma
  * moves the LJ cut-off, so the next call must be airebo_neighbor (compute

@@ -81,6 +81,7 @@ def lib():
             "airebo_set_launch_shape": (I, [P, I, I, I]),
             "airebo_set_knots": (I, [P, P, I64]),
             "airebo_nve_async": (I, [P, P, P, P, D, I, P]),
+            "airebo_force_param_grad": (I, [P, P, P, P, P, P]),
             "airebo_graph_capture_nve": (I, [P, P, P, P, D, I, P]),
         }
         for name, (res, args) in sig.items():
@@ -265,6 +266,18 @@ class Airebo:
         self._check(lib().airebo_param_grad(self._h, _ptr(pos), _ptr(force), _ptr(e4), _np(g)))
         return force, e4, g
 
+    def force_param_grad(self, pos, v, force=None):
+        """Forces, energies and v . dF/d(eps[3], sigma[3]) for a direction v (3, N) on the device."""
+        torch = self._torch
+        pos = self._dev(pos, torch.float64)
+        v = self._dev(v, torch.float64)
+        if force is None:
+            force = torch.empty_like(pos)
+        e4 = torch.empty(4, dtype=torch.float64, device=self.device)
+        g = np.zeros(6)
+        self._check(lib().airebo_force_param_grad(self._h, _ptr(pos), _ptr(v), _ptr(force), _ptr(e4), _np(g)))
+        return force, e4, g
+
     def knot_grad(self, pos, force=None):
         """Forces, energies and dE/d(spline knot data), KNOT_COUNT values in the parameter file's order."""
         torch = self._torch
@@ -413,6 +426,44 @@ class AireboEnergy:
 
             cls._fn = _F
         return cls._fn.apply(pos, eps, sigma, knots, evaluator)
+
+
+class AireboForces:
+    """Forces as a differentiable function of the inter-molecular parameters:
+    ``F = AireboForces.apply(pos, eps, sigma, evaluator)`` (3, N), for
+    force-matching losses such as sum |F - F_ref|^2.  The backward pass is the
+    library's hand-written v . dF/d(eps, sigma) (airebo_force_param_grad) with
+    v the incoming gradient of F; the gradient with respect to the positions
+    (a Hessian-vector product) is not provided and raises when asked for."""
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, pos, eps, sigma, evaluator):
+        if cls._fn is None:
+            import torch
+
+            class _F(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, pos, eps, sigma, ev):
+                    ev.set_lj_params(eps.detach().cpu().numpy(), sigma.detach().cpu().numpy())
+                    ev.neighbor(pos.detach(), ev._types, ev.box)
+                    f, _, _ = ev.compute(pos.detach())
+                    ctx.ev = ev
+                    ctx.save_for_backward(pos.detach())
+                    return f.clone()
+
+                @staticmethod
+                def backward(ctx, gF):
+                    if ctx.needs_input_grad[0]:
+                        raise NotImplementedError("AireboForces: no gradient with respect to the positions")
+                    (pos,) = ctx.saved_tensors
+                    _, _, g = ctx.ev.force_param_grad(pos, gF.contiguous())
+                    gt = torch.tensor(g, dtype=torch.float64, device=pos.device)
+                    return None, gt[:3], gt[3:], None
+
+            cls._fn = _F
+        return cls._fn.apply(pos, eps, sigma, evaluator)
 
 
 def knot_vector(params: dict):

@@ -735,6 +735,9 @@ template <class R> StepArgs<R> make_args(airebo_handle h, Precision<R>& pr, cons
     a.sys = h->nsys ? h->d_sys : nullptr;
     a.Lsys = h->nsys ? h->d_Lsys : nullptr;
     a.eatom = nullptr;
+    a.pgrad = nullptr;
+    a.jv = nullptr;
+    a.jout = nullptr;
     a.rebo = h->opt.enable_rebo != 0;
     a.lj_on = h->opt.enable_lj != 0;
     a.torsion = h->opt.enable_torsion != 0;
@@ -749,7 +752,8 @@ template <class R> StepArgs<R> make_args(airebo_handle h, Precision<R>& pr, cons
 template <class R>
 airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos, double* d_force, double* d_e4,
                          double* d_w6, double* d_pgrad = nullptr, double* d_esys = nullptr, bool async = false,
-                         double* d_kg = nullptr, double* d_eatom = nullptr) {
+                         double* d_kg = nullptr, double* d_eatom = nullptr, const double* d_jv = nullptr,
+                         double* d_jout = nullptr) {
     for (int attempt = 0; attempt < 4; attempt++) {
         cudaStream_t s = h->stream;
         if (h->n) CK(cudaMemsetAsync(d_force, 0, sizeof(double) * 3 * h->n, s));
@@ -763,6 +767,9 @@ airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos,
         if (a.fix && h->n) CK(cudaMemsetAsync(a.fix, 0, sizeof(unsigned long long) * 3 * h->n, s));
         a.pgrad = d_pgrad;
         if (d_pgrad) CK(cudaMemsetAsync(d_pgrad, 0, sizeof(double) * 6, s));
+        a.jv = d_jv;
+        a.jout = d_jv ? d_jout : nullptr;
+        if (d_jv) CK(cudaMemsetAsync(d_jout, 0, sizeof(double) * 6, s));
         if (d_kg) {
             // a second device copy of the parameters that carries the gradient buffer
             if (!pr.b.Pkg) CK(realloc_dev(pr.b.Pkg, 1));
@@ -826,7 +833,8 @@ airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos,
 
 airebo_status compute_any(airebo_handle h, const double* d_pos, double* d_force, double* d_e4, double* d_w6,
                           double* d_pgrad = nullptr, double* d_esys = nullptr, bool async = false,
-                          double* d_kg = nullptr, double* d_eatom = nullptr) {
+                          double* d_kg = nullptr, double* d_eatom = nullptr, const double* d_jv = nullptr,
+                          double* d_jout = nullptr) {
     if (!h->built) return fail(h, AIREBO_ERR_STATE, "airebo_compute before airebo_neighbor");
     CK(cudaSetDevice(h->device));
     if (d_esys && !d_eatom && (h->eatom_n < h->n || !h->eatom)) {
@@ -835,8 +843,10 @@ airebo_status compute_any(airebo_handle h, const double* d_pos, double* d_force,
         h->eatom_n = h->n;
     }
     if (h->opt.precision == AIREBO_MIXED)
-        return do_compute<float>(h, h->p32, d_pos, d_force, d_e4, d_w6, d_pgrad, d_esys, async, d_kg, d_eatom);
-    return do_compute<double>(h, h->p64, d_pos, d_force, d_e4, d_w6, d_pgrad, d_esys, async, d_kg, d_eatom);
+        return do_compute<float>(h, h->p32, d_pos, d_force, d_e4, d_w6, d_pgrad, d_esys, async, d_kg, d_eatom, d_jv,
+                                 d_jout);
+    return do_compute<double>(h, h->p64, d_pos, d_force, d_e4, d_w6, d_pgrad, d_esys, async, d_kg, d_eatom, d_jv,
+                              d_jout);
 }
 
 airebo_status check_rebuild(airebo_handle h, const double* d_pos, int* flag) {
@@ -1441,12 +1451,28 @@ airebo_status airebo_param_grad(airebo_handle h, const double* d_pos, double* d_
     if (h->n > 0 && (!d_pos || !d_force)) return fail(h, AIREBO_ERR_ARG, "null position or force pointer");
     if (!h->built) return fail(h, AIREBO_ERR_STATE, "airebo_param_grad before airebo_neighbor");
     CK(cudaSetDevice(h->device));
-    if (!h->pg) CK(realloc_dev(h->pg, 6));
+    if (!h->pg) CK(realloc_dev(h->pg, 12));
     airebo_status st = compute_any(h, d_pos, d_force, d_energy4, nullptr, h->pg);
     if (st) return st;
     CK(cudaMemcpyAsync(h->h_acc, h->pg, sizeof(double) * 6, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     for (int k = 0; k < 6; k++) h_grad6[k] = h->h_acc[k];
+    return AIREBO_OK;
+}
+
+airebo_status airebo_force_param_grad(airebo_handle h, const double* d_pos, const double* d_v, double* d_force,
+                                      double* d_energy4, double* h_out6) {
+    if (!h || !h_out6) return AIREBO_ERR_ARG;
+    if (h->n > 0 && (!d_pos || !d_force || !d_v)) return fail(h, AIREBO_ERR_ARG, "null position, direction or force pointer");
+    if (!h->built) return fail(h, AIREBO_ERR_STATE, "airebo_force_param_grad before airebo_neighbor");
+    CK(cudaSetDevice(h->device));
+    if (!h->pg) CK(realloc_dev(h->pg, 12));
+    airebo_status st = compute_any(h, d_pos, d_force, d_energy4, nullptr, nullptr, nullptr, false, nullptr, nullptr,
+                                   d_v, h->pg + 6);
+    if (st) return st;
+    CK(cudaMemcpyAsync(h->h_acc, h->pg + 6, sizeof(double) * 6, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < 6; k++) h_out6[k] = h->h_acc[k];
     return AIREBO_OK;
 }
 

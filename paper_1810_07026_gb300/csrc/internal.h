@@ -66,6 +66,8 @@ template <class R> struct StepArgs {
     bool virial;
     bool rebo, lj_on, torsion;
     double* pgrad;        // nullable: dE/d eps[3], dE/d sigma[3] of the inter-molecular term
+    const double* jv;     // nullable: a direction v (3 x n) for the parameter derivatives of the forces
+    double* jout;         // with jv: v . dF/d eps[3], v . dF/d sigma[3]
 };
 
 enum { ERR_SHORT = 0, ERR_MAP = 1, ERR_QUEUE = 2, ERR_NONFINITE = 3, ERR_DF = 4 };

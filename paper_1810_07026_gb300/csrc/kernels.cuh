@@ -18,7 +18,9 @@
 //                 two passes (pairs whose S_b is exactly 0 or 1, then the rest)
 //
 // Kernels with an EXTRA template flag have an instance without virial and
-// parameter-gradient accumulators, used whenever neither is asked for.
+// parameter-gradient accumulators, used whenever neither is asked for; the
+// LJ and b* kernels have a MODE instead (0 plain, 1 virial or parameter
+// gradient, 2 also the parameter derivatives of the forces).
 #pragma once
 
 #include <type_traits>
@@ -574,8 +576,10 @@ __device__ __forceinline__ void lj_batch_mx(const StepArgs<R>& a, const DevParam
 // EXTRA: the virial or the parameter gradient is wanted.  The instance without
 // them keeps no accumulators for them in registers (they cost the mixed
 // instance its spill-free register budget).
-template <class R, bool DF, bool EXTRA>
+template <class R, bool DF, int MODE>
 __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
+    constexpr bool EXTRA = MODE >= 1;      // virial or parameter gradient
+    constexpr bool JV = MODE == 2;         // the parameter derivatives of the forces too
     const DevParams<R>& P = *a.P;
     __shared__ double shift[3][9];                // image shifts S L for S in [-4, 4]
     __shared__ LjCuts<float> cutsf[3];            // thresholds in FP32, by species pair
@@ -602,7 +606,8 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
     LjBuf& B = bufs[threadIdx.x >> 5];
     unsigned lt = (1u << lane) - 1u;
     Sink sink{a.f, a.n, EXTRA && a.virial, {0, 0, 0, 0, 0, 0}, EXTRA && a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
-    bool general = EXTRA && a.pgrad != nullptr;
+    bool general = EXTRA && (a.pgrad != nullptr || a.jv != nullptr);
+    double J[6] = {0, 0, 0, 0, 0, 0};          // v . dF/d(eps, sigma) with a.jv
     LaneAcc acc;
     DfLaneAcc dacc;
     ff Edf{0.0f, 0.0f};
@@ -707,6 +712,11 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
                     lj_disp<R>(a, shift, i, j, img, dx, dy, dz);
                     double gx = 0, gy = 0, gz = 0, E0 = E;
                     lj_eval<R>(P, a.G, i, p, j, dx, dy, dz, C, code, sink, gx, gy, gz, E);
+                    if (JV && a.jv) {                 // S_r = 0 here: E = C V
+                        R qx = (R)dx, qy = (R)dy, qz = (R)dz;
+                        lj_pair_jvp<R>(P, a.G, i, j, qx, qy, qz, qx * qx + qy * qy + qz * qz, C, code, R(0), R(0),
+                                       a.jv, n, J);
+                    }
                     atomicAdd(a.f + i, gx); atomicAdd(a.f + n + i, gy); atomicAdd(a.f + 2 * n + i, gz);
                     if (a.eatom) eatom_pair(a.eatom, i, j, E - E0);
                 }
@@ -750,6 +760,7 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
     if (lane == 0 && ev) atomicAdd(a.counters + CNT_LJ, (unsigned long long)ev);
     block_accumulate<LJ_THREADS>(E, sink.W, EXTRA && a.virial, a.acc + 1, a.acc + 3);
     if (EXTRA && a.pgrad) block_accumulate_g<LJ_THREADS>(sink.G, a.pgrad);
+    if (JV && a.jv) block_accumulate_g<LJ_THREADS>(J, a.jout);
 }
 
 // ------------------------------------------------------------------ b* pairs
@@ -775,14 +786,16 @@ __device__ __forceinline__ void bstar_load(const StepArgs<R>& a, int t, int& i, 
     }
 }
 
-template <class R, bool EXTRA>
+template <class R, int MODE>
 // 64 registers (8 blocks of 128 per SM): this pass waits mostly on the
 // gathers of the FP32 screen, and twice the warps of the compiler's own
 // choice (80 registers) hide more of them (1.12 -> 1.03 ms at 1M PE, FP64)
 __global__ void __launch_bounds__(128, 8) k_bstar(StepArgs<R> a) {
+    constexpr bool EXTRA = MODE >= 1, JV = MODE == 2;
     const DevParams<R>& P = *a.P;
     Sink sink{a.f, a.n, EXTRA && a.virial, {0, 0, 0, 0, 0, 0}, EXTRA && a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
     double E = 0;
+    double J[6] = {0, 0, 0, 0, 0, 0};          // v . dF/d(eps, sigma) with a.jv
     int n0 = min(a.nbq[0], a.bq_cap), n1 = min(a.nbq[1], a.bq_cap), n2 = min(a.nbq[2], a.bq_cap);
     int nq = n0 + n1 + n2;
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nq; u += gridDim.x * blockDim.x) {
@@ -815,6 +828,7 @@ __global__ void __launch_bounds__(128, 8) k_bstar(StepArgs<R> a) {
             double e = bstar_finish<R>(P, a.G, i, j, rx, ry, rz, r2, C, code, Sb, R(0), sink);
             E += e;
             if (a.eatom) eatom_pair(a.eatom, i, j, e);
+            if (JV && a.jv) lj_pair_jvp<R>(P, a.G, i, j, rx, ry, rz, r2, C, code, Sb, R(0), a.jv, a.n, J);
         } else {
             int s = atomicAdd(a.nbq2, 1);
             if (s < 3 * a.bq_cap) a.bq2[s] = t;
@@ -822,16 +836,19 @@ __global__ void __launch_bounds__(128, 8) k_bstar(StepArgs<R> a) {
     }
     block_accumulate<128>(E, sink.W, EXTRA && a.virial, a.acc + 1, a.acc + 3);
     if (EXTRA && a.pgrad) block_accumulate_g<128>(sink.G, a.pgrad);
+    if (JV && a.jv) block_accumulate_g<128>(J, a.jout);
 }
 
 // Phase 2: the pairs of the second queue, b* and its gradient in one pass.
 // The FP32 (mixed) instance at 5 blocks per SM (0.655 -> 0.613 ms at 1M PE);
 // the FP64 one is best at 4 (3.0 ms; 3 and 5 blocks: 3.6 and 3.1 ms).
-template <class R, bool EXTRA>
+template <class R, int MODE>
 __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 4) k_bstar_rev(StepArgs<R> a) {
+    constexpr bool EXTRA = MODE >= 1, JV = MODE == 2;
     const DevParams<R>& P = *a.P;
     Sink sink{a.f, a.n, EXTRA && a.virial, {0, 0, 0, 0, 0, 0}, EXTRA && a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
     double E = 0;
+    double J[6] = {0, 0, 0, 0, 0, 0};          // v . dF/d(eps, sigma) with a.jv
     unsigned dsb_count = 0;
     int nq = min(*a.nbq2, 3 * a.bq_cap);
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nq; s += gridDim.x * blockDim.x) {
@@ -846,11 +863,17 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 4) k_bstar_rev(StepA
         dsb_count += dsb;
         E += e;
         if (a.eatom) eatom_pair(a.eatom, i, j, e);
+        if (JV && a.jv) {
+            R Sb;
+            R dotSb = bstar_jvp<R>(P, a.G, i, j, rx, ry, rz, r2, a.jv, a.n, Sb);
+            lj_pair_jvp<R>(P, a.G, i, j, rx, ry, rz, r2, C, code, Sb, dotSb, a.jv, a.n, J);
+        }
     }
     unsigned c = __reduce_add_sync(0xffffffffu, dsb_count);
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(a.counters + CNT_DSB, (unsigned long long)c);
     block_accumulate<128>(E, sink.W, EXTRA && a.virial, a.acc + 1, a.acc + 3);
     if (EXTRA && a.pgrad) block_accumulate_g<128>(sink.G, a.pgrad);
+    if (JV && a.jv) block_accumulate_g<128>(J, a.jout);
 }
 
 template <class R>
@@ -881,20 +904,29 @@ void launch_compute_impl(const StepArgs<R>& a, cudaStream_t s, int num_sms, cuda
     auto mark = [&](int k) { if (ev) cudaEventRecord(ev[k], s); };
     // grid-stride kernels launch whole waves: waves x resident blocks per SM x SMs
     // (the occupancies are asked once; nothing but stream work during graph capture)
-    bool extra = a.virial || a.pgrad != nullptr;
-    static int occ_all[2][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}};
-    int* occ = occ_all[extra];
+    // mode 0: plain evaluation; 1: with the virial or the parameter gradient;
+    // 2: with the parameter derivatives of the forces (LJ and b* kernels)
+    int mode = a.jv ? 2 : ((a.virial || a.pgrad != nullptr) ? 1 : 0);
+    bool extra = mode >= 1;
+    static int occ_all[3][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}, {-1, -1, -1, -1}};
+    int* occ = occ_all[mode];
     if (occ[0] < 0) {
         if (extra) {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_rebo<R, true>, 128, 0);
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_torsion<R, true>, 128, 0);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], k_bstar<R, true>, 128, 0);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[3], k_bstar_rev<R, true>, 128, 0);
         } else {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_rebo<R, false>, 128, 0);
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_torsion<R, false>, 128, 0);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], k_bstar<R, false>, 128, 0);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[3], k_bstar_rev<R, false>, 128, 0);
+        }
+        if (mode == 2) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], k_bstar<R, 2>, 128, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[3], k_bstar_rev<R, 2>, 128, 0);
+        } else if (mode == 1) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], k_bstar<R, 1>, 128, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[3], k_bstar_rev<R, 1>, 128, 0);
+        } else {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], k_bstar<R, 0>, 128, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[3], k_bstar_rev<R, 0>, 128, 0);
         }
     }
     auto grid_of = [&](int k, int waves) { return num_sms * (occ[k] > 0 ? occ[k] : 1) * waves; };
@@ -930,7 +962,7 @@ void launch_compute_impl(const StepArgs<R>& a, cudaStream_t s, int num_sms, cuda
     mark(4);
     if (a.lj_on) {
         // asked once: nothing but stream work during graph capture
-        static int per_sm[4] = {-1, -1, -1, -1};
+        static int per_sm[6] = {-1, -1, -1, -1, -1, -1};
         bool df = a.fix != nullptr;
         int need = (n + LJ_WARPS - 1) / LJ_WARPS;
         auto launch = [&](auto kernel, int slot) {
@@ -939,21 +971,29 @@ void launch_compute_impl(const StepArgs<R>& a, cudaStream_t s, int num_sms, cuda
             kernel<<<blocks < need ? blocks : need, LJ_THREADS, 0, s>>>(a);
         };
         if (df) {
-            if (extra) launch(k_lj<R, true, true>, 3); else launch(k_lj<R, true, false>, 2);
+            if (mode == 2) launch(k_lj<R, true, 2>, 5);
+            else if (mode == 1) launch(k_lj<R, true, 1>, 3);
+            else launch(k_lj<R, true, 0>, 2);
             k_fix_add<<<(n + 255) / 256, 256, 0, s>>>(a.fix, a.f, n);
         } else {
-            if (extra) launch(k_lj<R, false, true>, 1); else launch(k_lj<R, false, false>, 0);
+            if (mode == 2) launch(k_lj<R, false, 2>, 4);
+            else if (mode == 1) launch(k_lj<R, false, 1>, 1);
+            else launch(k_lj<R, false, 0>, 0);
         }
     }
     mark(5);
     if (a.lj_on) {
-        if (extra) k_bstar<R, true><<<grid_of(2, a.bstar_waves), 128, 0, s>>>(a);
-        else k_bstar<R, false><<<grid_of(2, a.bstar_waves), 128, 0, s>>>(a);
+        int g = grid_of(2, a.bstar_waves);
+        if (mode == 2) k_bstar<R, 2><<<g, 128, 0, s>>>(a);
+        else if (mode == 1) k_bstar<R, 1><<<g, 128, 0, s>>>(a);
+        else k_bstar<R, 0><<<g, 128, 0, s>>>(a);
     }
     mark(6);
     if (a.lj_on) {
-        if (extra) k_bstar_rev<R, true><<<grid_of(3, a.bstar_waves), 128, 0, s>>>(a);
-        else k_bstar_rev<R, false><<<grid_of(3, a.bstar_waves), 128, 0, s>>>(a);
+        int g = grid_of(3, a.bstar_waves);
+        if (mode == 2) k_bstar_rev<R, 2><<<g, 128, 0, s>>>(a);
+        else if (mode == 1) k_bstar_rev<R, 1><<<g, 128, 0, s>>>(a);
+        else k_bstar_rev<R, 0><<<g, 128, 0, s>>>(a);
     }
     mark(7);
     k_finish_counters<R><<<1, 32, 0, s>>>(a);

@@ -486,6 +486,32 @@ struct Sink {
     }
 };
 
+// The dot product of a direction v (3 x n, SoA) with the forces a term would
+// apply, in place of applying them: with the same calls as Sink, the forward
+// and reverse passes of a term give v . F of that term (a Jacobian-vector
+// product of the forces, used for parameter derivatives of the forces).
+struct JSink {
+    const double* v;
+    int n;
+    double jdot;
+    bool virial;        // never: the interface of Sink
+    double W[6];
+    HD double vdot(int a, double gx, double gy, double gz) const {
+        return v[a] * gx + v[n + a] * gy + v[2 * n + a] * gz;
+    }
+    // force +g on a, -g on b
+    HD void pair(int a, int b, double, double, double, double gx, double gy, double gz) {
+        jdot += vdot(a, gx, gy, gz) - vdot(b, gx, gy, gz);
+    }
+    // force -g on b; +g on a, kept by the caller (applied with add)
+    HD void half(int b, double, double, double, double gx, double gy, double gz,
+                 double& fax, double& fay, double& faz) {
+        jdot -= vdot(b, gx, gy, gz);
+        fax += gx; fay += gy; faz += gz;
+    }
+    HD void add(int a, double fx, double fy, double fz) { jdot += vdot(a, fx, fy, fz); }
+};
+
 // ------------------------------------------------------------------ bond order
 // One side of b_ij: centre c, partner o.  The forward pass fills it.
 template <class R> struct Side {
@@ -586,9 +612,9 @@ HD void side_forward(const DevParams<R>& P, const Graph<R>& G, int c, int o, R u
 // from pi^rc / pi^dh; dEdconj: adjoint of the conjugation sum.  Accumulates
 // the gradient with respect to the partner vector u (sign as given) and to
 // its length; applies the forces on the neighbours of c.
-template <class R>
+template <class R, class SinkT>
 HD void side_reverse(const DevParams<R>& P, const Graph<R>& G, int c, int o, R ux, R uy, R uz, R inv_u, R umag,
-                     const Side<R>& s, R dEdp, R dEdN_direct, R dEdconj, Sink& sink,
+                     const Side<R>& s, R dEdp, R dEdN_direct, R dEdconj, SinkT& sink,
                      R& gux, R& guy, R& guz, R& gumag, double& fcx, double& fcy, double& fcz) {
     int tc = G.type[c], to = G.type[o];
     int nc = G.cnt[c];
@@ -671,9 +697,9 @@ template <class R> HD R guardf(const DevParams<R>& P, R cs, R& dgd) {
 
 // sum over k in N(i)\j, l in N(j)\{i,k} of (1 - cos^2 w) w_ik w_jl s_i s_j, and
 // (reverse) its gradient times dEdD.  u = vector standing for r_ij.
-template <class R>
+template <class R, class SinkT>
 HD R dihedral_sum(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, R uy, R uz, R inv_u,
-                  bool reverse, R dEdD, Sink& sink, R& gux, R& guy, R& guz,
+                  bool reverse, R dEdD, SinkT& sink, R& gux, R& guy, R& guz,
                   double& fix, double& fiy, double& fiz, double& fjx, double& fjy, double& fjz) {
     R D = 0;
     int ni = G.cnt[i], nj = G.cnt[j];
@@ -760,9 +786,9 @@ template <class R> struct BstarSwitch {
 // gradient with respect to u and its length in gu*, gumag, and the forces on
 // i and j themselves in fi*, fj* (excluding the u gradient, which the caller
 // applies).
-template <class R, bool REV>
+template <class R, bool REV, class SinkT = Sink>
 HD R bond_order(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, R uy, R uz, R umag, R inv_u,
-                R eps, Sink& sink, R& gux, R& guy, R& guz, R& gumag,
+                R eps, SinkT& sink, R& gux, R& guy, R& guz, R& gumag,
                 double& fix, double& fiy, double& fiz, double& fjx, double& fjy, double& fjz,
                 BstarSwitch<R>* bsw = nullptr) {
     Side<R> si, sj;
@@ -1055,8 +1081,8 @@ HD int build_path_map(const Graph<R>& G, PathMap<R>& M, int i) {
 }
 
 // forces of dE/dwmax on the bonds of the path stored for atom i
-template <class R>
-HD void path_forces(const Graph<R>& G, int i, int code, R dEdw, Sink& sink, double& fix, double& fiy, double& fiz) {
+template <class R, class SinkT = Sink>
+HD void path_forces(const Graph<R>& G, int i, int code, R dEdw, SinkT& sink, double& fix, double& fiy, double& fiz) {
     int len = path_len(code);
     int q[3], from[3];
     q[0] = i * G.stride + path_a(code); from[0] = i;
@@ -1332,6 +1358,139 @@ HD double bstar_full(const DevParams<R>& P, const Graph<R>& G, int i, int j, R d
         }
     }
     return bstar_finish<R>(P, G, i, j, dx, dy, dz, r2, C, path_code, bsw.Sb, bsw.dSb, sink);
+}
+
+// ------------------------------------------------------------------ parameter derivatives of the forces
+// A factor of the LJ pair energy as a function of r and sigma: value, d/dr,
+// d/dsigma and d^2/(dr dsigma).
+template <class R> struct Rs { R v, r, s, rs; };
+
+// The product of three such factors.
+template <class R> HD Rs<R> rs_mul3(const Rs<R>& x, const Rs<R>& y, const Rs<R>& z) {
+    Rs<R> o;
+    o.v = x.v * y.v * z.v;
+    o.r = x.r * y.v * z.v + x.v * y.r * z.v + x.v * y.v * z.r;
+    o.s = x.s * y.v * z.v + x.v * y.s * z.v + x.v * y.v * z.s;
+    o.rs = x.rs * y.v * z.v + x.s * y.r * z.v + x.s * y.v * z.r + x.r * y.s * z.v + x.v * y.rs * z.v +
+           x.v * y.s * z.r + x.r * y.v * z.s + x.v * y.r * z.s + x.v * y.v * z.rs;
+    return o;
+}
+
+// A factor that depends on r and sigma through r/sigma only: from its first
+// and second r-derivatives, d/dsigma = -(r/sigma) d/dr and
+// d^2/(dr dsigma) = -(1/sigma) d/dr - (r/sigma) d^2/dr^2.
+template <class R> HD Rs<R> rs_scaled(R v, R dr, R drr, R r, R inv_sigma) {
+    return Rs<R>{v, dr, -r * inv_sigma * dr, -inv_sigma * dr - r * inv_sigma * drr};
+}
+
+// The radial factors of the LJ pair energy E = C (g1 + g2 S_b) (Alg. 3):
+// g1 = V S_out (1 - S_r), g2 = V S_out S_r, with their sigma-derivatives h1,
+// h2, and the r-derivatives of all four.  The Lennard-Jones core, the cut-off
+// switch S_out and S_r are functions of r/sigma; the Morse core does not
+// depend on sigma.
+template <class R>
+HD void lj_radial_sigma(const DevParams<R>& P, int p, R r, Rs<R>& g1, Rs<R>& g2) {
+    R isg = rcp_(P.sigma[p]);
+    Rs<R> A;
+    if (P.kind == 0) {
+        R ir = rcp_(r);
+        R u2 = P.sig2[p] * ir * ir;
+        R u6 = u2 * u2 * u2, u12 = u6 * u6;
+        R e4 = P.eps4[p];
+        A = rs_scaled<R>(e4 * (u12 - u6), -e4 * (R(12) * u12 - R(6) * u6) * ir,
+                         e4 * (R(156) * u12 - R(42) * u6) * ir * ir, r, isg);
+    } else {
+        R e = exp_(-P.malpha[p] * (r - P.mre[p]));
+        R a = P.malpha[p], em = P.meps[p];
+        A = Rs<R>{em * (e * e - R(2) * e), R(2) * a * em * (e - e * e), R(0), R(0)};   // no sigma in the core
+    }
+    // cut-off switch 1 - 3t^2 + 2t^3, t = (r - 2.7 sigma) / (0.3 sigma)
+    R t = (r - P.swlo[p]) * P.swinv[p];
+    Rs<R> B{R(1), R(0), R(0), R(0)};
+    if (gt_(t, R(0))) {
+        R w = P.swinv[p];
+        B = rs_scaled<R>(R(1) - t * t * (R(3) - R(2) * t), R(-6) * t * (R(1) - t) * w,
+                         R(-6) * (R(1) - R(2) * t) * w * w, r, isg);
+    }
+    // S_r = S((r - sigma) / ((2^(1/6) - 1) sigma)), and 1 - S_r
+    R ts = (r - P.Srlo[p]) * P.Srinv[p];
+    Rs<R> S{R(1), R(0), R(0), R(0)};
+    if (ge_(ts, R(1))) {
+        S = Rs<R>{R(0), R(0), R(0), R(0)};
+    } else if (gt_(ts, R(0))) {
+        R sn, cs;
+        sincospi_(ts, &sn, &cs);
+        R w = P.Srinv[p];
+        const R pi = R(3.14159265358979323846);
+        S = rs_scaled<R>(R(0.5) * (R(1) + cs), R(-0.5) * pi * sn * w, R(-0.5) * pi * pi * cs * w * w, r, isg);
+    }
+    Rs<R> Sm{R(1) - S.v, -S.r, -S.s, -S.rs};
+    g1 = rs_mul3<R>(A, B, Sm);
+    g2 = rs_mul3<R>(A, B, S);
+}
+
+// v . dF/d(eps_p) and v . dF/d(sigma_p) of one LJ pair i -> (j, image) with
+// displacement d, C and its path, S_b and dotSb = v . (-grad S_b) (zero where
+// dS_b = 0), added to J[p] and J[3 + p].  The forces of E = C (g1 + g2 S_b)
+// are linear in eps (so dF/deps = F / eps), and dE/dsigma = C (h1 + h2 S_b)
+// has the same form, so dF/dsigma = -grad(dE/dsigma) follows from the same
+// three parts: the radial force, the path forces of C (dotW = v . F of the
+// energy w_max, with C = 1 - w_max) and the b* forces.
+template <class R>
+HD void lj_pair_jvp(const DevParams<R>& P, const Graph<R>& G, int i, int j, R dx, R dy, R dz, R r2, R C, int code,
+                    R Sb, R dotSb, const double* v, int n, double* J) {
+    int p = pidx(G.type[i], G.type[j]);
+    R inv_r = rsqrt_(r2);
+    R r = r2 * inv_r;
+    Rs<R> g1, g2;
+    lj_radial_sigma<R>(P, p, r, g1, g2);
+    // (v_j - v_i) . r_hat
+    double vr = ((v[j] - v[i]) * (double)dx + (v[n + j] - v[n + i]) * (double)dy +
+                 (v[2 * n + j] - v[2 * n + i]) * (double)dz) * (double)inv_r;
+    double dotW = 0;
+    if (code >= 0) {
+        JSink js{v, n, 0.0, false, {0, 0, 0, 0, 0, 0}};
+        double fx = 0, fy = 0, fz = 0;
+        path_forces<R, JSink>(G, i, code, R(1), js, fx, fy, fz);
+        js.add(i, fx, fy, fz);
+        dotW = js.jdot;
+    }
+    // v . F for E = C (a1 + a2 S_b): the radial force -(dE/dr) r_hat on j (and
+    // its opposite on i), the path forces of C = 1 - w_max, and the b* forces
+    auto vdotF = [&](R a1, R a1r, R a2, R a2r) {
+        double c = (double)C;
+        return -c * (double)(a1r + a2r * Sb) * vr - (double)(a1 + a2 * Sb) * dotW + c * (double)a2 * (double)dotSb;
+    };
+    double eps = (double)(P.kind == 0 ? P.eps4[p] * R(0.25) : P.meps[p]);
+    J[p] += vdotF(g1.v, g1.r, g2.v, g2.r) / eps;
+    J[3 + p] += vdotF(g1.s, g1.rs, g2.s, g2.rs);
+}
+
+// dotSb = v . (-grad S_b) of a b* pair in its transition: the reverse bond
+// order with dE/db* = dS_b/db*, dotted with v instead of applied.
+template <class R>
+HD R bstar_jvp(const DevParams<R>& P, const Graph<R>& G, int i, int j, R dx, R dy, R dz, R r2, const double* v,
+               int n, R& Sb) {
+    int p = pidx(G.type[i], G.type[j]);
+    R inv_r = rsqrt_(r2);
+    R rs = P.rstar[p];
+    R ux = dx * inv_r * rs, uy = dy * inv_r * rs, uz = dz * inv_r * rs;
+    R gux = 0, guy = 0, guz = 0, gumag = 0;
+    double fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
+    JSink js{v, n, 0.0, false, {0, 0, 0, 0, 0, 0}};
+    BstarSwitch<R> bsw{P.bmin[p], P.binv[p], R(1), R(0), R(0)};
+    bond_order<R, true, JSink>(P, G, i, j, ux, uy, uz, rs, rcp_(rs), R(0), js, gux, guy, guz, gumag,
+                               fix, fiy, fiz, fjx, fjy, fjz, &bsw);
+    Sb = bsw.Sb;
+    if (is_zero(bsw.dSb)) return R(0);
+    R ud = (gux * dx + guy * dy + guz * dz) * inv_r;
+    R sc = rs * inv_r;
+    double gx = (double)(sc * (gux - ud * dx * inv_r));
+    double gy = (double)(sc * (guy - ud * dy * inv_r));
+    double gz = (double)(sc * (guz - ud * dz * inv_r));
+    js.add(i, fix + gx, fiy + gy, fiz + gz);
+    js.add(j, fjx - gx, fjy - gy, fjz - gz);
+    return (R)js.jdot;
 }
 
 }  // namespace airebo
