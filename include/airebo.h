@@ -79,16 +79,19 @@ typedef struct {
     int enable_lj;        /* 1: LJ term (Alg. 3) */
     int enable_torsion;   /* 1: torsion term (Alg. 2) */
     int max_lj_nbrs;      /* initial long-list capacity per atom; 0 = from the density */
-    int bstar_screen;     /* 0 (default): every b* in FP64 (AIREBO_FP64, AIREBO_DF64).  1: a
-                             faster FP64 path that is not strictly FP64: b* enters the LJ term only
-                             through S_b, which is exactly 0 or 1 outside [b_min, b_max], and an
-                             FP32 b* decides those pairs when it lies more than 1e-3 outside the
-                             transition; the rest are evaluated in FP64.  The margin rests on
-                             measured FP32 b* errors (below 1e-6 on the test systems), not on a
-                             proven bound.  Ignored by AIREBO_MIXED. */
+    int bstar_screen;     /* AIREBO_FP64 and AIREBO_DF64 (default 1): b* enters the LJ term only
+                             through S_b, which is exactly 1 below b_min and 0 above b_max; the
+                             first b* pass evaluates b* in FP32 together with a rigorous bound on
+                             its distance from the exact value of the same formula (each operation's
+                             rounding error and the FP32 roundings of the inputs and parameters,
+                             bounded upward), and decides S_b when the whole interval lies outside
+                             [b_min, b_max] by more than 1e-9 (room for the FP64 evaluation's own
+                             rounding); every other pair is evaluated in FP64.  The decided S_b are
+                             the FP64 ones.  0: every b* evaluated in FP64.  Ignored by
+                             AIREBO_MIXED. */
 } airebo_options;
 
-/* Fill opts with the defaults: skin 1.0 A, FP64, all three terms on, auto capacity, b* screen off. */
+/* Fill opts with the defaults: skin 1.0 A, FP64, all three terms on, auto capacity, b* screen on. */
 void airebo_default_options(airebo_options* opts);
 
 /*
@@ -388,6 +391,18 @@ airebo_status airebo_set_launch_shape(airebo_handle h, int lj_chunk, int bond_wa
 #define AIREBO_KNOT_COUNT 7548
 airebo_status airebo_knot_grad(airebo_handle h, const double* d_pos, double* d_force, double* d_energy4,
                                double* h_grad, int64_t count);
+
+/*
+ * Check of the b* screen's error bound (handles with bstar_screen = 1, FP64
+ * or DF64): one evaluation at d_pos (d_force receives the forces), then, for
+ * every pair queued for b* (Alg. 3, Sec. 2.1.3), the FP64 b* against the
+ * FP32 b* with its rigorous error bound.  h_out6 (host double[6]): pairs with
+ * a finite bound, pairs with an infinite one (sent to the FP64 pass), the
+ * largest |b*_32 - b*_64| / bound (at most 1 if the bound holds), the largest
+ * bound, the pairs whose difference exceeds their bound, and the largest
+ * difference.  A diagnostic.  AIREBO_ERR_STATE when the screen is off.
+ */
+airebo_status airebo_bstar_bound_check(airebo_handle h, const double* d_pos, double* d_force, double* h_out6);
 
 /*
  * Replace every spline knot datum of the handle's parameter set (the data

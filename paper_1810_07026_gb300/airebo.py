@@ -82,6 +82,7 @@ def lib():
             "airebo_set_knots": (I, [P, P, I64]),
             "airebo_nve_async": (I, [P, P, P, P, D, I, P]),
             "airebo_force_param_grad": (I, [P, P, P, P, P, P]),
+            "airebo_bstar_bound_check": (I, [P, P, P, P]),
             "airebo_graph_capture_nve": (I, [P, P, P, P, D, I, P]),
         }
         for name, (res, args) in sig.items():
@@ -137,7 +138,7 @@ class Airebo:
 
     def __init__(self, params: str | dict | None = None, precision: int = FP64, skin: float = 1.0,
                  rebo: bool = True, lj: bool = True, torsion: bool = True, max_lj_nbrs: int = 0, stream=None,
-                 bstar_screen: bool = False):
+                 bstar_screen: bool = True):
         import torch
         self._torch = torch
         if params is None:
@@ -294,6 +295,16 @@ class Airebo:
         e = None if eps is None else np.ascontiguousarray(np.asarray(eps, dtype=np.float64).reshape(3))
         sg = None if sigma is None else np.ascontiguousarray(np.asarray(sigma, dtype=np.float64).reshape(3))
         self._check(lib().airebo_set_lj_params(self._h, _np(e), _np(sg)))
+
+    def bstar_bound_check(self, pos):
+        """The b* screen's bound on every queued pair: (bounded pairs, unbounded pairs, largest
+        |b*_32 - b*_64| / bound, largest bound, pairs over their bound, largest difference)."""
+        torch = self._torch
+        pos = self._dev(pos, torch.float64)
+        force = torch.empty_like(pos)
+        out = np.zeros(6)
+        self._check(lib().airebo_bstar_bound_check(self._h, _ptr(pos), _ptr(force), _np(out)))
+        return dict(zip(("bounded", "unbounded", "max_ratio", "max_bound", "violations", "max_diff"), out.tolist()))
 
     def set_knots(self, knots):
         """Replace all KNOT_COUNT spline knot data (the order of knot_grad())."""

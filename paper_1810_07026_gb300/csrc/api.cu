@@ -337,6 +337,7 @@ struct airebo_ctx {
     Precision<double> p64;
     Precision<float> p32;
     Precision<dd> pdd;        // AIREBO_DF64: the parameters in double-float (torsion kernel)
+    Precision<ef> pef;        // the b* screen: the parameters in FP32 with their rounding errors
     // system
     int n = 0, n_alloc = 0;
     double L[3] = {0, 0, 0};
@@ -500,7 +501,7 @@ bool screen_on(airebo_handle h) {
 // b* screen, and for AIREBO_DF64 the double-float one of the torsion kernel
 airebo_status upload_own_params(airebo_handle h) {
     airebo_status st = h->opt.precision == AIREBO_MIXED ? upload_params<float>(h, h->p32) : upload_params<double>(h, h->p64);
-    if (!st && screen_on(h)) st = upload_params<float>(h, h->p32);
+    if (!st && screen_on(h)) st = upload_params<ef>(h, h->pef);
     if (!st && h->opt.precision == AIREBO_DF64) st = upload_params<dd>(h, h->pdd);
     return st;
 }
@@ -712,12 +713,12 @@ template <class R> StepArgs<R> make_args(airebo_handle h, Precision<R>& pr, cons
     a.bq = h->bq; a.nbq = h->counts + 4; a.bq_cap = h->bq_cap;
     a.bq2 = h->bq2; a.nbq2 = h->counts + 3;
     a.screen = false;
-    a.P32 = nullptr;
+    a.Pef = nullptr;
     a.G32 = Graph<float>{};
     a.s_dx = a.s_dy = a.s_dz = a.s_r = a.s_ir = a.s_w = a.s_nC = a.s_nH = nullptr;
     if (sizeof(R) == 8 && screen_on(h) && b.s_dx) {
         a.screen = true;
-        a.P32 = h->p32.b.P;
+        a.Pef = h->pef.b.P;
         a.s_dx = b.s_dx; a.s_dy = b.s_dy; a.s_dz = b.s_dz; a.s_r = b.s_r; a.s_ir = b.s_ir; a.s_w = b.s_w;
         a.s_nC = b.s_nC; a.s_nH = b.s_nH;
         a.G32.n = h->n; a.G32.stride = h->stride; a.G32.type = h->types; a.G32.cnt = b.cnt; a.G32.nj = b.nj;
@@ -914,7 +915,7 @@ void airebo_default_options(airebo_options* o) {
     o->enable_lj = 1;
     o->enable_torsion = 1;
     o->max_lj_nbrs = 0;
-    o->bstar_screen = 0;
+    o->bstar_screen = 1;
 }
 
 airebo_status airebo_create(const char* params, const airebo_options* opts, void* stream, airebo_handle* out) {
@@ -961,6 +962,7 @@ void airebo_destroy(airebo_handle h) {
     free_prec(h->p64);
     free_prec(h->p32);
     free_prec(h->pdd);
+    free_prec(h->pef);
     if (h->pg) cudaFree(h->pg);
     if (h->kg) cudaFree(h->kg);
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
@@ -1523,6 +1525,27 @@ airebo_status airebo_set_lj_params(airebo_handle h, const double* eps3, const do
     airebo_status st = upload_own_params(h);
     if (st) return st;
     if (sigma_changed) h->built = false;          // the LJ cut-off moved: the lists must be rebuilt
+    return AIREBO_OK;
+}
+
+airebo_status airebo_bstar_bound_check(airebo_handle h, const double* d_pos, double* d_force, double* h_out6) {
+    if (!h || !h_out6) return AIREBO_ERR_ARG;
+    if (h->n > 0 && (!d_pos || !d_force)) return fail(h, AIREBO_ERR_ARG, "null position or force pointer");
+    if (!h->built) return fail(h, AIREBO_ERR_STATE, "airebo_bstar_bound_check before airebo_neighbor");
+    if (!screen_on(h)) return fail(h, AIREBO_ERR_STATE, "the b* screen is off on this handle");
+    CK(cudaSetDevice(h->device));
+    airebo_status st = compute_any(h, d_pos, d_force, nullptr, nullptr);
+    if (st) return st;
+    double* out = nullptr;
+    CK(cudaMalloc((void**)&out, sizeof(double) * 6));
+    CK(cudaMemsetAsync(out, 0, sizeof(double) * 6, h->stream));
+    StepArgs<double> a = make_args<double>(h, h->p64, d_pos, d_force, false);
+    if (h->n) launch_bstar_bound_check(a, out, h->stream, h->num_sms);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_out6, out, sizeof(double) * 6, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(out);
+    if (e != cudaSuccess) return fail(h, AIREBO_ERR_CUDA, cudaGetErrorString(e));
     return AIREBO_OK;
 }
 

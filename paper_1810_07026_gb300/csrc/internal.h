@@ -47,9 +47,10 @@ template <class R> struct StepArgs {
     int2* ccbonds; int* nccbonds;             // C-C bonds i<j, same capacity
     int4* bq; int* nbq; int bq_cap;
     int* bq2; int* nbq2;                   // b* pairs left to the full-precision pass
-    // b* screen (FP64): an FP32 b* decides S_b where it is certain
+    // b* screen (FP64): an FP32 b* with a rigorous error bound decides S_b
+    // where the whole bound lies outside the transition
     bool screen;
-    const DevParams<float>* P32;
+    const DevParams<ef>* Pef;              // the parameters with their FP32 rounding errors
     Graph<float> G32;                      // reads the s_* arrays below
     float* s_dx; float* s_dy; float* s_dz; float* s_r; float* s_ir; float* s_w; float* s_nC; float* s_nH;
     int* lj_next;                          // work counter of the LJ kernel's warps
@@ -77,13 +78,16 @@ enum { NONFINITE_POS = 1, NONFINITE_OVERLAP = 2 };
 enum { DF_RANGE = 1, DF_FORCE = 2 };
 enum { CNT_BONDS = 0, CNT_BSTAR = 1, CNT_DSB = 2, CNT_LJ = 3, CNT_MAP = 4, CNT_BSTAR_FULL = 7 };
 
-// Half-width of the band around [b_min, b_max] inside which an FP32 b* does
-// not decide S_b.  Measured FP32-FP64 differences of b* stay below 1e-6.
-constexpr float BSTAR_SCREEN_MARGIN = 1e-3f;
+// The FP64 evaluation of b* differs from the exact value of its formula by
+// its own rounding (of order 1e-14 for these magnitudes); the screen's bound
+// is against the exact value, so a decision needs this much more room.
+constexpr double BSTAR_SCREEN_SLACK = 1e-9;
 
 // launchers, one instantiation per precision (kernels_f64.cu, kernels_f32.cu)
 // ev (nullable): 7 events recorded before each of the 6 stages and after the last
 template <class R> void launch_compute(const StepArgs<R>& a, cudaStream_t s, int num_sms, cudaEvent_t* ev);
+// check of the b* screen's error bound on every queued pair (kernels_f64.cu)
+void launch_bstar_bound_check(const StepArgs<double>& a, double* out, cudaStream_t s, int num_sms);
 
 // neighbour build (neighbor.cu)
 struct NeighborArgs {

@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
             a.g_r[q] = (R)r; a.g_ir[q] = (R)ir; a.g_w[q] = w; a.g_dw[q] = dw; a.g_omw[q] = omw;
             if (a.screen) {
                 a.s_dx[q] = (float)dx; a.s_dy[q] = (float)dy; a.s_dz[q] = (float)dz;
-                a.s_r[q] = (float)r; a.s_ir[q] = (float)ir; a.s_w[q] = (float)w;
+                a.s_r[q] = (float)r; a.s_ir[q] = (float)ir; a.s_w[q] = ef_mark_inexact((double)w);
             }
             // each bond once: i < j between like species, from the carbon for C-H,
             // so that the threads of a warp run the same code (species batches, Sec. 4.2)
@@ -227,8 +227,8 @@ __global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
     a.g_nC[i] = nC;
     a.g_nH[i] = nH;
     if (a.screen) {
-        a.s_nC[i] = (float)nC;
-        a.s_nH[i] = (float)nH;
+        a.s_nC[i] = ef_mark_inexact((double)nC);
+        a.s_nH[i] = ef_mark_inexact((double)nH);
     }
 }
 
@@ -809,17 +809,24 @@ __global__ void __launch_bounds__(128, 8) k_bstar(StepArgs<R> a) {
         R r2 = rx * rx + ry * ry + rz * rz;
         int p = pidx(a.G.type[i], a.G.type[j]);
         R Sb = R(0), dSb = R(1);
-        bool decided;
-        if (a.screen) {
-            const DevParams<float>& P32 = *a.P32;
-            float fx = (float)dx, fy = (float)dy, fz = (float)dz;
-            float bs = bstar_value<float>(P32, a.G32, i, j, fx, fy, fz, fx * fx + fy * fy + fz * fz, sink);
-            bool below = bs < P32.bmin[p] - BSTAR_SCREEN_MARGIN;
-            bool above = bs > P32.bmax[p] + BSTAR_SCREEN_MARGIN;
-            decided = below || above;
-            Sb = below ? R(1) : R(0);
-            dSb = R(0);
-        } else {
+        bool decided = false, screened = false;
+        if constexpr (sizeof(R) == 8) {
+            if (a.screen) {
+                // b* in FP32 with a bound e on its distance from the exact value:
+                // S_b is exactly 1 or 0 when [b* - e, b* + e] lies below b_min or
+                // above b_max (with room for the FP64 path's own rounding)
+                ef bs = bstar_value_ef(*a.Pef, GraphEf(a.G32), i, j, dx, dy, dz);
+                double lo = (double)bs.v - (double)bs.e - BSTAR_SCREEN_SLACK;
+                double hi = (double)bs.v + (double)bs.e + BSTAR_SCREEN_SLACK;
+                bool below = hi < (double)P.bmin[p];
+                bool above = lo > (double)P.bmax[p];
+                decided = below || above;
+                Sb = below ? R(1) : R(0);
+                dSb = R(0);
+                screened = true;
+            }
+        }
+        if (!screened) {
             R bs = bstar_value<R>(P, a.G, i, j, rx, ry, rz, r2, sink);
             Sb = bstar_switch<R>(P, p, bs, dSb);
             decided = dSb == R(0);
@@ -886,6 +893,34 @@ __global__ void k_finish_counters(StepArgs<R> a) {
         // after several asynchronous evaluations sees the largest of them)
         int q = max(a.nbq[0], max(a.nbq[1], a.nbq[2]));
         if (q > a.bq_cap) atomicMax(a.err + ERR_QUEUE, q);
+    }
+}
+
+// Check of the screen's bound on every queued b* pair: the FP64 b* against
+// the bounded FP32 one.  out (double[6], zeroed): pairs with a finite bound,
+// pairs with an infinite one, the largest |b*_32 - b*_64| / bound, the
+// largest bound, pairs where the difference exceeds the bound, and the
+// largest difference.
+static __global__ void __launch_bounds__(128) k_bstar_bound_check(StepArgs<double> a, double* out) {
+    const DevParams<double>& P = *a.P;
+    Sink none{nullptr, 0, false, {0, 0, 0, 0, 0, 0}, false, {0, 0, 0, 0, 0, 0}};
+    int n0 = min(a.nbq[0], a.bq_cap), n1 = min(a.nbq[1], a.bq_cap), n2 = min(a.nbq[2], a.bq_cap);
+    int nq = n0 + n1 + n2;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nq; u += gridDim.x * blockDim.x) {
+        int t = u < n0 ? u : (u < n0 + n1 ? a.bq_cap + (u - n0) : 2 * a.bq_cap + (u - n0 - n1));
+        int i, j, code;
+        double dx, dy, dz, C;
+        bstar_load<double>(a, t, i, j, dx, dy, dz, C, code);
+        double b64 = bstar_value<double>(P, a.G, i, j, dx, dy, dz, dx * dx + dy * dy + dz * dz, none);
+        ef bs = bstar_value_ef(*a.Pef, GraphEf(a.G32), i, j, dx, dy, dz);
+        double diff = fabs((double)bs.v - b64);
+        if (!(bs.e < EF_INF)) { atomicAdd(out + 1, 1.0); continue; }
+        atomicAdd(out + 0, 1.0);
+        double e = (double)bs.e;
+        atomicMax((unsigned long long*)(out + 2), (unsigned long long)__double_as_longlong(e > 0 ? diff / e : (diff > 0 ? 1e300 : 0.0)));
+        atomicMax((unsigned long long*)(out + 3), (unsigned long long)__double_as_longlong(e));
+        if (diff > e) atomicAdd(out + 4, 1.0);
+        atomicMax((unsigned long long*)(out + 5), (unsigned long long)__double_as_longlong(diff));
     }
 }
 

@@ -563,8 +563,8 @@ template <class R> HD R exp_lambda(const DevParams<R>& P, int tc, int tk, int to
     return exp_(P.lam * ((P.rhoH[tk] - rck) - (P.rhoH[to] - umag)));
 }
 
-template <class R, bool D>
-HD void side_forward(const DevParams<R>& P, const Graph<R>& G, int c, int o, R ux, R uy, R uz, R inv_u, R umag,
+template <class R, bool D, class GT = Graph<R>>
+HD void side_forward(const DevParams<R>& P, const GT& G, int c, int o, R ux, R uy, R uz, R inv_u, R umag,
                      Side<R>& s) {
     int tc = G.type[c], to = G.type[o];
     int nc = G.cnt[c];
@@ -697,9 +697,9 @@ template <class R> HD R guardf(const DevParams<R>& P, R cs, R& dgd) {
 
 // sum over k in N(i)\j, l in N(j)\{i,k} of (1 - cos^2 w) w_ik w_jl s_i s_j, and
 // (reverse) its gradient times dEdD.  u = vector standing for r_ij.
-template <class R, class SinkT>
-HD R dihedral_sum(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, R uy, R uz, R inv_u,
-                  bool reverse, R dEdD, SinkT& sink, R& gux, R& guy, R& guz,
+template <class R, bool REVD, class SinkT, class GT = Graph<R>>
+HD R dihedral_sum(const DevParams<R>& P, const GT& G, int i, int j, R ux, R uy, R uz, R inv_u,
+                  R dEdD, SinkT& sink, R& gux, R& guy, R& guz,
                   double& fix, double& fiy, double& fiz, double& fjx, double& fjy, double& fjz) {
     R D = 0;
     int ni = G.cnt[i], nj = G.cnt[j];
@@ -736,7 +736,7 @@ HD R dihedral_sum(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, 
             R cw = (n1x * n2x + n1y * n2y + n1z * n2z) * inv12;
             R one_m = R(1) - cw * cw;
             D += one_m * wik * wjl * si * sj;
-            if (!reverse) continue;
+            if constexpr (REVD) {
             R dwik = G.dw[qa], dwjl = G.dw[qb];     // the forward pass reads no dw/dr
             R in2s = rcp_(n2s);
             R dcw = dEdD * R(-2) * cw * wik * wjl * si * sj;
@@ -767,6 +767,7 @@ HD R dihedral_sum(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, 
             gux += -j1 * bx - j3 * ux; guy += -j1 * by - j3 * uy; guz += -j1 * bz - j3 * uz;
             sink.half(k, ax, ay, az, gax, gay, gaz, fix, fiy, fiz);
             sink.half(l, bx, by, bz, gbx, gby, gbz, fjx, fjy, fjz);
+            }
         }
     }
     return D;
@@ -786,14 +787,14 @@ template <class R> struct BstarSwitch {
 // gradient with respect to u and its length in gu*, gumag, and the forces on
 // i and j themselves in fi*, fj* (excluding the u gradient, which the caller
 // applies).
-template <class R, bool REV, class SinkT = Sink>
-HD R bond_order(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, R uy, R uz, R umag, R inv_u,
+template <class R, bool REV, class SinkT = Sink, class GT = Graph<R>>
+HD R bond_order(const DevParams<R>& P, const GT& G, int i, int j, R ux, R uy, R uz, R umag, R inv_u,
                 R eps, SinkT& sink, R& gux, R& guy, R& guz, R& gumag,
                 double& fix, double& fiy, double& fiz, double& fjx, double& fjy, double& fjz,
                 BstarSwitch<R>* bsw = nullptr) {
     Side<R> si, sj;
-    side_forward<R, REV>(P, G, i, j, ux, uy, uz, inv_u, umag, si);
-    side_forward<R, REV>(P, G, j, i, -ux, -uy, -uz, inv_u, umag, sj);
+    side_forward<R, REV, GT>(P, G, i, j, ux, uy, uz, inv_u, umag, si);
+    side_forward<R, REV, GT>(P, G, j, i, -ux, -uy, -uz, inv_u, umag, sj);
     int ti = G.type[i], tj = G.type[j];
     R Nconj = R(1) + si.conj * si.conj + sj.conj * sj.conj;
     // pi^rc: the carbon side's coordination first for a C-H bond
@@ -813,12 +814,14 @@ HD R bond_order(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, R 
     if (dih) {
         Tv = tricubic_cell<R, REV>(P.Ttab + cell * 64, tx, ty, tz, clx, cly, clz, Ta, Tb, Tc);
         R dummy = 0;
-        D = dihedral_sum<R>(P, G, i, j, ux, uy, uz, inv_u, false, R(0), sink, dummy, dummy, dummy,
-                            fix, fiy, fiz, fjx, fjy, fjz);
+        D = dihedral_sum<R, false, SinkT, GT>(P, G, i, j, ux, uy, uz, inv_u, R(0), sink, dummy, dummy, dummy,
+                                              fix, fiy, fiz, fjx, fjy, fjz);
         pidh = Tv * D;
     }
     R b = R(0.5) * (si.p + sj.p) + pirc + pidh;
-    if (!REV) return b;
+    if constexpr (!REV) {
+        return b;
+    } else {
     if (bsw) {
         R dS;
         bsw->Sb = Sw<R>((b - bsw->bmin) * bsw->binv, dS);
@@ -841,10 +844,11 @@ HD R bond_order(const DevParams<R>& P, const Graph<R>& G, int i, int j, R ux, R 
                     gvx, gvy, gvz, gumag, fjx, fjy, fjz);
     gux -= gvx; guy -= gvy; guz -= gvz;
     if (dih) {
-        dihedral_sum<R>(P, G, i, j, ux, uy, uz, inv_u, true, eps * Tv, sink, gux, guy, guz,
-                        fix, fiy, fiz, fjx, fjy, fjz);
+        dihedral_sum<R, true, SinkT, GT>(P, G, i, j, ux, uy, uz, inv_u, eps * Tv, sink, gux, guy, guz,
+                                         fix, fiy, fiz, fjx, fjy, fjz);
     }
     return b;
+    }
 }
 
 // ------------------------------------------------------------------ REBO bond (Alg. 1)
@@ -1494,3 +1498,7 @@ HD R bstar_jvp(const DevParams<R>& P, const Graph<R>& G, int i, int j, R dx, R d
 }
 
 }  // namespace airebo
+
+#ifdef __CUDACC__
+#include "ef.cuh"          // the FP32 value with an error bound (R = ef: the b* screen of the FP64 path)
+#endif

@@ -158,16 +158,26 @@ def test_counters_match_oracle(A, oracle, param_text):
     assert g["lj_in_cutoff"] == c["lj_in_cutoff"]
 
 
-@pytest.mark.parametrize("case", ["pe1152", "hot300", "hot1000", "pe32k"])
+@pytest.mark.parametrize("case", ["pe1152", "hot160", "hot300", "hot1000", "pe32k"])
 def test_bstar_screen(A, oracle, param_text, case):
-    """FP64 with the FP32 b* screen (an option, off by default) against FP64
-    without it and against the oracle: the same energies and forces (S_b is
-    exactly 0 or 1 wherever the screen decides), and the screen leaves fewer
-    pairs to the full pass; the 32,640-atom PE in full."""
+    """FP64 with the b* screen (FP32 b* with a rigorous error bound, the
+    default) against FP64 without it and against the oracle: the same
+    energies and forces (S_b is exactly 0 or 1 wherever the screen decides),
+    the bound holds on every queued pair (|b*_32 - b*_64| never exceeds it),
+    and the screen leaves fewer pairs to the full pass; the 32,640-atom PE in
+    full."""
     pos, types, box = CASES[case]() if case in CASES else inputs.workload(case)
     e, f, w, c = oracle.compute(pos, types, box)
     on, ev_on = gpu_eval(A, param_text, pos, types, box, bstar_screen=True)
     off, ev_off = gpu_eval(A, param_text, pos, types, box, bstar_screen=False)
+    chk = ev_on.bstar_bound_check(torch.tensor(pos, device="cuda"))
+    print(case, chk)
+    assert chk["violations"] == 0 and chk["max_ratio"] <= 1.0
+    assert chk["bounded"] + chk["unbounded"] == c["bstar"]
+    # crystals: every pair bounded; hot boxes: a spline argument within its
+    # bound of a knot (a bond just inside its switch) sends a pair to FP64
+    assert chk["bounded"] >= (0.999 if case.startswith("pe") else 0.75) * c["bstar"]
+    assert chk["max_bound"] < 1e-3
     assert_close(on, (e, f, w), 1e-10, 1e-8, 1e-8)
     assert_close(on, off, 1e-12, 1e-11, 1e-11)
     g_on, g_off = ev_on.counters(), ev_off.counters()
