@@ -117,7 +117,7 @@ const char* airebo_last_error(airebo_handle h);
  * intermediate list with r < Dmax_ij + skin for the REBO term, with explicit
  * periodic images.  d_pos: device double[3][n]; d_types: device int8[n]
  * (copied); box: host double[3].  Grows its capacities as needed (one stream
- * synchronisation).  n may be 0.
+ * synchronisation).  n may be 0 and must stay below 2^28 (268,435,456).
  */
 airebo_status airebo_neighbor(airebo_handle h, const double* d_pos, const int8_t* d_types, int64_t n,
                               const double* box);

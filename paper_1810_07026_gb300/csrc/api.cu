@@ -450,6 +450,18 @@ template <class R> airebo_status upload_params(airebo_handle h, Precision<R>& pr
 // the FP32 b* screen of the FP64 path (see k_bstar)
 bool screen_on(airebo_handle h);
 
+// the connectivity-map entries (map_cap per atom) and their hash tables (a
+// power of two of at least twice as many slots)
+template <class R> airebo_status alloc_map(airebo_handle h, StepBuffers<R>& b, int n) {
+    if (b.map_cap > (1 << MAP_IDX_BITS)) return fail(h, AIREBO_ERR_CAPACITY, "connectivity map beyond 4096 entries per atom");
+    b.map_hbits = 1;
+    while ((1 << b.map_hbits) < 2 * b.map_cap) b.map_hbits++;
+    size_t mm = (size_t)n * b.map_cap;
+    CK(realloc_dev(b.map_wt, mm)); CK(realloc_dev(b.map_path, mm));
+    CK(realloc_dev(b.map_ht, (size_t)n << b.map_hbits));
+    return AIREBO_OK;
+}
+
 template <class R> airebo_status alloc_step(airebo_handle h, Precision<R>& pr, int n) {
     StepBuffers<R>& b = pr.b;
     size_t m = (size_t)n * h->stride;
@@ -458,9 +470,9 @@ template <class R> airebo_status alloc_step(airebo_handle h, Precision<R>& pr, i
     CK(realloc_dev(b.r, m)); CK(realloc_dev(b.ir, m)); CK(realloc_dev(b.w, m)); CK(realloc_dev(b.dw, m)); CK(realloc_dev(b.omw, m));
     CK(realloc_dev(b.nC, n)); CK(realloc_dev(b.nH, n));
     if (b.map_cap == 0) b.map_cap = 32;
-    size_t mm = (size_t)n * b.map_cap;
-    CK(realloc_dev(b.map_cnt, n)); CK(realloc_dev(b.map_key, mm)); CK(realloc_dev(b.map_wt, mm)); CK(realloc_dev(b.map_path, mm));
-    CK(realloc_dev(b.map_mask, 4 * (size_t)n));
+    CK(realloc_dev(b.map_cnt, n));
+    airebo_status st = alloc_map<R>(h, b, n);
+    if (st) return st;
     if (sizeof(R) == 8 && screen_on(h)) {
         CK(realloc_dev(b.s_dx, m)); CK(realloc_dev(b.s_dy, m)); CK(realloc_dev(b.s_dz, m));
         CK(realloc_dev(b.s_r, m)); CK(realloc_dev(b.s_ir, m)); CK(realloc_dev(b.s_w, m));
@@ -472,15 +484,13 @@ template <class R> airebo_status alloc_step(airebo_handle h, Precision<R>& pr, i
 template <class R> airebo_status grow_map(airebo_handle h, Precision<R>& pr, int need) {
     StepBuffers<R>& b = pr.b;
     b.map_cap = std::max(need + 8, b.map_cap * 2);
-    size_t mm = (size_t)h->n_alloc * b.map_cap;
-    CK(realloc_dev(b.map_key, mm)); CK(realloc_dev(b.map_wt, mm)); CK(realloc_dev(b.map_path, mm));
-    return AIREBO_OK;
+    return alloc_map<R>(h, b, h->n_alloc);
 }
 
 template <class R> void free_prec(Precision<R>& pr) {
     StepBuffers<R>& b = pr.b;
     void* ps[] = {b.P, b.Pkg, b.tables, b.Tnz, b.cnt, b.nj, b.nimg, b.dx, b.dy, b.dz, b.r, b.ir, b.w, b.dw, b.omw, b.nC, b.nH,
-                  b.map_cnt, b.map_key, b.map_wt, b.map_path, b.map_mask,
+                  b.map_cnt, b.map_wt, b.map_path, b.map_ht,
                   b.s_dx, b.s_dy, b.s_dz, b.s_r, b.s_ir, b.s_w, b.s_nC, b.s_nH};
     for (void* p : ps) if (p) cudaFree(p);
     b = StepBuffers<R>();
@@ -697,8 +707,8 @@ template <class R> StepArgs<R> make_args(airebo_handle h, Precision<R>& pr, cons
     a.G.dx = b.dx; a.G.dy = b.dy; a.G.dz = b.dz; a.G.r = b.r; a.G.ir = b.ir; a.G.w = b.w; a.G.dw = b.dw; a.G.omw = b.omw; a.G.nC = b.nC; a.G.nH = b.nH;
     a.g_cnt = b.cnt; a.g_nj = b.nj; a.g_nimg = b.nimg; a.g_dx = b.dx; a.g_dy = b.dy; a.g_dz = b.dz;
     a.g_r = b.r; a.g_ir = b.ir; a.g_w = b.w; a.g_dw = b.dw; a.g_omw = b.omw; a.g_nC = b.nC; a.g_nH = b.nH;
-    a.M.cap = b.map_cap; a.M.cnt = b.map_cnt; a.M.key = b.map_key; a.M.wt = b.map_wt; a.M.path = b.map_path;
-    a.M.mask = b.map_mask;
+    a.M.cap = b.map_cap; a.M.cnt = b.map_cnt; a.M.wt = b.map_wt; a.M.path = b.map_path;
+    a.M.hbits = b.map_hbits; a.M.ht = b.map_ht;
     a.pos = d_pos;
     a.posf = h->posf;
     bool df = df_on(h);
@@ -883,7 +893,7 @@ airebo_status upload_Lhl(airebo_handle h, const double* boxes, int nsys) {
 }
 
 airebo_status set_system(airebo_handle h, const int8_t* d_types, int64_t n, const double* box, bool types_on_host) {
-    if (n < 0 || n > (1LL << 30)) return fail(h, AIREBO_ERR_ARG, "atom count out of range");
+    if (n < 0 || n >= MAP_MAX_ATOMS) return fail(h, AIREBO_ERR_ARG, "atom count out of range (at most 2^28 - 1)");
     if (!box) return fail(h, AIREBO_ERR_ARG, "box is null");
     double dm = max3(h->sc.Dmax);
     for (int d = 0; d < 3; d++)
@@ -1257,8 +1267,7 @@ template <class R> static airebo_status reserve_headroom(airebo_handle h, Precis
     }
     StepBuffers<R>& b = pr.b;
     b.map_cap += b.map_cap / 4 + 4;
-    size_t mm = (size_t)h->n_alloc * b.map_cap;
-    CK(realloc_dev(b.map_key, mm)); CK(realloc_dev(b.map_wt, mm)); CK(realloc_dev(b.map_path, mm));
+    if (airebo_status st2 = alloc_map<R>(h, b, h->n_alloc)) return st2;
     CK(cudaMemcpyAsync(h->h_u64, h->counts, sizeof(int) * 8, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     const int* cn = (const int*)h->h_u64;

@@ -17,10 +17,10 @@ template <class R> struct StepBuffers {
     int* cnt = nullptr; int* nj = nullptr; int* nimg = nullptr;
     R* dx = nullptr; R* dy = nullptr; R* dz = nullptr; R* r = nullptr; R* ir = nullptr; R* w = nullptr; R* dw = nullptr; R* omw = nullptr;
     R* nC = nullptr; R* nH = nullptr;
-    // connectivity map
-    int map_cap = 0;
-    int* map_cnt = nullptr; long long* map_key = nullptr; R* map_wt = nullptr; int* map_path = nullptr;
-    unsigned long long* map_mask = nullptr;   // 4 words per atom
+    // connectivity map: entries per atom and their hash table
+    int map_cap = 0, map_hbits = 0;
+    int* map_cnt = nullptr; R* map_wt = nullptr; int* map_path = nullptr;
+    unsigned long long* map_ht = nullptr;     // 2^map_hbits slots per atom
     // FP32 copy of the short-list geometry for the b* screen (FP64 only)
     float* s_dx = nullptr; float* s_dy = nullptr; float* s_dz = nullptr; float* s_r = nullptr; float* s_ir = nullptr;
     float* s_w = nullptr; float* s_nC = nullptr; float* s_nH = nullptr;

@@ -292,8 +292,20 @@ __global__ void __launch_bounds__(128) k_torsion_dd(StepArgs<double> a) {
 template <class R>
 __global__ void __launch_bounds__(128) k_path_map(StepArgs<R> a) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
     PathMap<R> M = a.M;
+    // the warp clears the hash tables of its atoms together: one contiguous
+    // run of 16-byte stores
+    {
+        int i0 = i - (threadIdx.x & 31);
+        int na = min(32, a.n - i0);
+        if (na > 0) {
+            uint4* T = reinterpret_cast<uint4*>(M.ht + ((size_t)i0 << M.hbits));
+            int words = (na << M.hbits) / 2;
+            for (int w = threadIdx.x & 31; w < words; w += 32) T[w] = make_uint4(0u, 0u, 0u, 0u);
+        }
+        __syncwarp();
+    }
+    if (i >= a.n) return;
     int ov = build_path_map<R>(a.G, M, i);
     if (ov) atomicMax(a.err + ERR_MAP, M.cnt[i] + ov);
 }
@@ -350,7 +362,8 @@ __device__ __forceinline__ void lj_disp(const StepArgs<R>& a, const double (*shi
 
 template <class R>
 __device__ __forceinline__ void lj_batch(const StepArgs<R>& a, const DevParams<R>& P, const double (*shift)[9],
-                                         LjBuf& B, int b, int lane, Sink& sink, LaneAcc& acc, double& E) {
+                                         const LjPow* K, LjBuf& B, int b, int lane, Sink& sink, LaneAcc& acc,
+                                         double& E) {
     int jp = B.jp[b][lane];
     int j = jp & 0x3fffffff, p = (unsigned)jp >> 30;
     int i = B.ia[b][lane];
@@ -364,9 +377,9 @@ __device__ __forceinline__ void lj_batch(const StepArgs<R>& a, const DevParams<R
     R r2 = rx * rx + ry * ry + rz * rz;
     double E0 = E;
     if (b == 0)
-        lj_eval_inner<R>(P, p, j, dx, dy, dz, r2, sink, acc.fx, acc.fy, acc.fz, E);
+        lj_eval_inner<R>(K[p], j, dx, dy, dz, r2, sink, acc.fx, acc.fy, acc.fz, E);
     else
-        lj_eval_switch<R>(P, p, j, dx, dy, dz, r2, sink, acc.fx, acc.fy, acc.fz, E);
+        lj_eval_switch<R>(P, K[p], p, j, dx, dy, dz, r2, sink, acc.fx, acc.fy, acc.fz, E);
     if (a.eatom) {
         acc.e += 0.5 * (E - E0);
         atomicAdd(a.eatom + j, 0.5 * (E - E0));
@@ -586,6 +599,7 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
     __shared__ LjBuf bufs[LJ_WARPS];
     __shared__ float shf[2][3][9];                // DF: split image shifts (hi, lo)
     __shared__ DfParams dfp;
+    __shared__ LjPow ljk[3];                       // the LJ pair in powers of 1/r^2, by species pair
     if (threadIdx.x < 27) {
         double v = (double)((int)(threadIdx.x % 9) - 4) * a.L[threadIdx.x / 9];
         shift[threadIdx.x / 9][threadIdx.x % 9] = v;
@@ -594,6 +608,7 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
     if (threadIdx.x < 3) {
         int q = threadIdx.x;
         cutsf[q] = LjCuts<float>{(float)P.rc2[q], (float)P.rpath2, (float)P.Srhi2[q], (float)P.swlo2[q]};
+        ljk[q] = lj_pow((double)P.eps4[q], (double)P.sig2[q]);
         if (DF) {
             dfp.sig2[q] = ff_from_double((double)P.sig2[q]);
             dfp.eps4[q] = ff_from_double((double)P.eps4[q]);
@@ -622,7 +637,7 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
             if constexpr (sizeof(R) == 8) lj_batch_df<R, EXTRA>(a, dfp, shf[0], shf[1], B, b, lane, dacc, Edf, Wdf);
             else lj_batch_mx<R, EXTRA>(a, P, shf[0], shf[1], B, b, lane, dacc, Edf, Wdf);
         } else {
-            lj_batch<R>(a, P, shift, B, b, lane, sink, acc, E);
+            lj_batch<R>(a, P, shift, ljk, B, b, lane, sink, acc, E);
         }
     };
     // warps take chunks of lj_chunk consecutive atoms from a global counter,

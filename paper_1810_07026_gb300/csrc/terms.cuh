@@ -1000,14 +1000,34 @@ HD int path_c(int p) { return (p >> 12) & 15; }
 template <class R> struct PathMap {
     int cap;
     int* cnt;            // entries per atom
-    long long* key;      // [n * cap]
-    R* wt;               // C = 1 - largest path weight
-    int* path;
-    unsigned long long* mask;   // [n * 4]: bit map_bit(atom) set for every atom in the map (a filter)
+    R* wt;               // [n * cap]: C = 1 - largest path weight
+    int* path;           // [n * cap]: the bonds of that path
+    int hbits;           // the hash table of atom i: 2^hbits slots from (i << hbits)
+    unsigned long long* ht;   // slot = ((key + 1) << MAP_IDX_BITS) | entry, 0 = empty
 };
 
-// 256-bit membership filter of a map: an atom whose bit is clear is not in it
-HD int map_bit(int atom) { return (int)(((unsigned)atom * 2654435761u) >> 24); }
+// The per-atom hash table of map keys (open addressing, linear probing): it
+// has at least twice as many slots as entries, so every probe sequence meets
+// an empty slot, after about 1.2 probes on average.  Keys are below 2^52
+// (atoms below 2^28), entries below 2^12.
+constexpr int MAP_IDX_BITS = 12;
+constexpr int MAP_MAX_ATOMS = 1 << 28;
+HD unsigned map_hash(long long key, int hbits) {
+    return (unsigned)(((unsigned long long)key * 0x9E3779B97F4A7C15ull) >> (64 - hbits));
+}
+// the entry of (atom, image) in the map of atom i, or -1
+template <class R> HD int map_find(const PathMap<R>& M, int i, long long key) {
+    const unsigned long long* T = M.ht + ((size_t)i << M.hbits);
+    unsigned mask = (1u << M.hbits) - 1, h = map_hash(key, M.hbits);
+    unsigned long long want = (unsigned long long)(key + 1);
+    for (unsigned probe = 0; probe <= mask; probe++) {
+        unsigned long long slot = T[h];
+        if (slot == 0ull) return -1;
+        if ((slot >> MAP_IDX_BITS) == want) return (int)(slot & ((1u << MAP_IDX_BITS) - 1));
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
 
 // Ties: larger weight (smaller C), then the shorter path, then the smaller k,
 // then the smaller l.  The map stores C = 1 - weight, formed from the 1 - w of
@@ -1020,18 +1040,32 @@ HD bool path_better(double c, int len, int k, int l, double c0, int len0, int k0
     return l < l0;
 }
 
+// 256-bit membership filter of the atoms already in a map (in registers
+// while the map is built): a clear bit means a new atom
+HD int map_bit(int atom) { return (int)(((unsigned)atom * 2654435761u) >> 24); }
+
 template <class R>
 HD int build_path_map(const Graph<R>& G, PathMap<R>& M, int i) {
     int base = i * M.cap;
     int count = 0, overflow = 0;
-    unsigned long long mask[4] = {0, 0, 0, 0};
+    unsigned long long* T = M.ht + ((size_t)i << M.hbits);      // cleared by the caller
+    unsigned mask = (1u << M.hbits) - 1;
+    // the filter, and for tables of up to 256 slots the occupied slots, in
+    // registers: a new atom (most atoms: bonds form trees) then takes an empty
+    // slot without reading the table back
+    unsigned long long filt[4] = {0, 0, 0, 0}, occ[4] = {0, 0, 0, 0};
+    bool occ_in_regs = M.hbits <= 8;
     auto insert = [&](int atom, int img, R c, int len, int k, int l, int code) {
         long long key = map_key(atom, img);
+        unsigned long long want = (unsigned long long)(key + 1);
+        unsigned h = map_hash(key, M.hbits);
         int bit = map_bit(atom);
-        // the filter rules out most repeats without a scan (chains reach each atom once)
-        bool seen = (mask[bit >> 6] >> (bit & 63)) & 1ull;
-        for (int e = 0; seen && e < count; e++) {
-            if (M.key[base + e] == key) {
+        bool seen = (filt[bit >> 6] >> (bit & 63)) & 1ull;
+        for (unsigned probe = 0; seen && probe <= mask; probe++) {
+            unsigned long long slot = T[h];
+            if (slot == 0ull) break;
+            if ((slot >> MAP_IDX_BITS) == want) {          // seen: keep the better path
+                int e = (int)(slot & ((1u << MAP_IDX_BITS) - 1));
                 int p0 = M.path[base + e];
                 int k0 = path_len(p0) >= 2 ? G.nj[i * G.stride + path_a(p0)] : -1;
                 int l0 = -1;
@@ -1042,13 +1076,21 @@ HD int build_path_map(const Graph<R>& G, PathMap<R>& M, int i) {
                 }
                 return;
             }
+            h = (h + 1) & mask;
         }
         if (count < M.cap) {
-            M.key[base + count] = key;
+            if (occ_in_regs) {
+                h = map_hash(key, M.hbits);
+                while ((occ[h >> 6] >> (h & 63)) & 1ull) h = (h + 1) & mask;     // at most half full
+                occ[h >> 6] |= 1ull << (h & 63);
+            } else if (!seen) {
+                for (unsigned probe = 0; probe <= mask && T[h] != 0ull; probe++) h = (h + 1) & mask;
+            }
+            T[h] = (want << MAP_IDX_BITS) | (unsigned long long)count;
             M.wt[base + count] = c;
             M.path[base + count] = code;
             count++;
-            mask[bit >> 6] |= 1ull << (bit & 63);
+            filt[bit >> 6] |= 1ull << (bit & 63);
         } else {
             overflow++;
         }
@@ -1080,7 +1122,6 @@ HD int build_path_map(const Graph<R>& G, PathMap<R>& M, int i) {
         }
     }
     M.cnt[i] = count;
-    for (int w = 0; w < 4; w++) M.mask[4 * i + w] = mask[w];
     return overflow;
 }
 
@@ -1179,33 +1220,42 @@ HD void lj_eval(const DevParams<R>& P, const Graph<R>& G, int i, int p, int j, d
     }
 }
 
+// The Lennard-Jones pair in powers of 1/r^2, with A = 4 eps sigma^6 and
+// B = 4 eps sigma^12 of one species pair: V = (1/r^6)(B/r^6 - A) and
+// (dV/dr)/r = (1/r^8)(6 A - 12 B/r^6).  Written so, V and (dV/dr)/r take the
+// fewest FP64 instructions (ten from 1/r^2 to both, with the energy sum).
+struct LjPow {
+    double A, B, A6, B12;        // A, B, 6 A, -12 B
+};
+HD LjPow lj_pow(double eps4, double sig2) {
+    double A = eps4 * sig2 * sig2 * sig2, B = A * sig2 * sig2 * sig2;
+    return LjPow{A, B, 6.0 * A, -12.0 * B};
+}
+
 // The common LJ pair: C = 1, no path, r inside 2.7 sigma (no cut-off switch):
 // V and (dV/dr)/r from 1/r^2 alone.
 template <class R>
-HD void lj_eval_inner(const DevParams<R>& P, int p, int j, double dx, double dy, double dz, R r2, Sink& sink,
+HD void lj_eval_inner(const LjPow& K, int j, double dx, double dy, double dz, R r2, Sink& sink,
                       double& fix, double& fiy, double& fiz, double& E) {
     R ir2 = rcp_(r2);
-    R s2 = P.sig2[p] * ir2;
-    R s6 = s2 * s2 * s2;
-    R e4 = P.eps4[p];
-    E += (double)(e4 * (s6 * s6 - s6));
-    double c = (double)(e4 * (R(6) * s6 - R(12) * s6 * s6) * ir2);
+    R ir6 = ir2 * ir2 * ir2;
+    E += (double)(ir6 * ((R)K.B * ir6 - (R)K.A));
+    double c = (double)(ir6 * ir2 * ((R)K.A6 + (R)K.B12 * ir6));
     sink.half(j, dx, dy, dz, c * dx, c * dy, c * dz, fix, fiy, fiz);
 }
 
 // C = 1, no path, r inside the cut-off switch (Lennard-Jones), or any
 // C = 1 pair without a path (Morse).
 template <class R>
-HD void lj_eval_switch(const DevParams<R>& P, int p, int j, double dx, double dy, double dz, R r2, Sink& sink,
-                       double& fix, double& fiy, double& fiz, double& E) {
+HD void lj_eval_switch(const DevParams<R>& P, const LjPow& K, int p, int j, double dx, double dy, double dz, R r2,
+                       Sink& sink, double& fix, double& fiy, double& fiz, double& E) {
     double c;
     if (P.kind == 0) {
         R ir = rsqrt_(r2);
         R ir2 = ir * ir;
-        R s2 = P.sig2[p] * ir2;
-        R s6 = s2 * s2 * s2;
-        R v = P.eps4[p] * (s6 * s6 - s6);
-        R dvr = P.eps4[p] * (R(-12) * s6 * s6 + R(6) * s6) * ir2;
+        R ir6 = ir2 * ir2 * ir2;
+        R v = ir6 * ((R)K.B * ir6 - (R)K.A);
+        R dvr = ir6 * ir2 * ((R)K.A6 + (R)K.B12 * ir6);
         R t = (r2 * ir - P.swlo[p]) * P.swinv[p];          // > 0 in this class
         R so = R(1) - t * t * (R(3) - R(2) * t);
         R dso = R(-6) * t * (R(1) - t) * P.swinv[p];
@@ -1239,15 +1289,7 @@ HD int lj_classify_c(const DevParams<R>& P, const PathMap<R>& M, int i, int j, i
     mi = -1; code = -1; C = R(1);
     if (!lt_nonneg(r2, k.rc2)) return 0;
     if (lt_nonneg(r2, k.rpath2)) {
-        // the filter rules most non-members out without touching the keys
-        int bit = map_bit(j);
-        if ((M.mask[4 * i + (bit >> 6)] >> (bit & 63)) & 1ull) {
-            long long key = map_key(j, img);
-            int c = M.cnt[i];
-            const long long* kk = M.key + (size_t)i * M.cap;
-            for (int e = 0; e < c; e++)
-                if (kk[e] == key) { mi = e; break; }
-        }
+        mi = map_find<R>(M, i, map_key(j, img));
         if (mi >= 0) {
             C = M.wt[(size_t)i * M.cap + mi];
             if (!gt_(C, R(0))) return 0;
