@@ -129,18 +129,24 @@ bool quintic_coeffs(const std::vector<double>& kn, const std::vector<double>& d,
     q.n = n;
     for (int m = 0; m <= n; m++) q.k[m] = (R)kn[m];
     for (int m = n + 1; m < 6; m++) q.k[m] = (R)kn[n];
-    for (int m = 0; m < 5; m++) { q.invh[m] = 0; for (int p = 0; p < 6; p++) q.a[m][p] = 0; }
+    for (int m = 0; m < 5; m++) {
+        q.invh[m] = 0;
+        for (int p = 0; p < 6; p++) q.a[m][p] = 0;
+        for (int p = 0; p < 5; p++) q.da[m][p] = 0;
+    }
     for (int m = 0; m < n; m++) {
         double h = kn[m + 1] - kn[m];
         if (!(h > 0)) { err = "angular spline knots not increasing"; return false; }
         q.invh[m] = (R)(1.0 / h);
         double w[6] = {d[3 * m], h * d[3 * m + 1], h * h * d[3 * m + 2],
                        h * h * d[3 * (m + 1) + 2], h * d[3 * (m + 1) + 1], d[3 * (m + 1)]};
+        double s[6];
         for (int p = 0; p < 6; p++) {
-            double s = 0;
-            for (int b = 0; b < 6; b++) s += w[b] * QB[b][p];
-            q.a[m][p] = (R)s;
+            s[p] = 0;
+            for (int b = 0; b < 6; b++) s[p] += w[b] * QB[b][p];
+            q.a[m][p] = (R)s[p];
         }
+        for (int p = 0; p < 5; p++) q.da[m][p] = (R)((p + 1) * s[p + 1] / h);
     }
     return true;
 }

@@ -239,12 +239,16 @@ template <class R, bool EXTRA>
 __global__ void __launch_bounds__(128, 4) k_rebo(StepArgs<R> a) {
     const DevParams<R>& P = *a.P;
     Sink sink{a.f, a.n, EXTRA && a.virial, {0, 0, 0, 0, 0, 0}, EXTRA && a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
+    // forward -> reverse angular terms (FP64: there they save FP64-pipe work;
+    // the FP32 instances do better with the shared memory left to L1)
+    __shared__ R scache[sizeof(R) == 8 ? side_cache_len<R>() * 128 : 1];
+    SideCache<R> sc{sizeof(R) == 8 ? scache + threadIdx.x : nullptr, 128};
     double E = 0;
     int ncc = min(*a.nccbonds, a.bond_cap);
     int nb = ncc + min(*a.nbonds, a.bond_cap);
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
         int2 bd = b < ncc ? a.ccbonds[b] : a.bonds[b - ncc];
-        double e = rebo_bond<R>(P, a.G, bd.x, bd.y, sink);
+        double e = rebo_bond<R>(P, a.G, bd.x, bd.y, sink, sc);
         E += e;
         if (a.eatom) eatom_pair(a.eatom, bd.x, a.G.nj[bd.x * a.G.stride + bd.y], e);
     }
@@ -872,6 +876,10 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 4) k_bstar_rev(StepA
     double E = 0;
     double J[6] = {0, 0, 0, 0, 0, 0};          // v . dF/d(eps, sigma) with a.jv
     unsigned dsb_count = 0;
+    // forward -> reverse angular terms (FP64: there they save FP64-pipe work;
+    // the FP32 instances do better with the shared memory left to L1)
+    __shared__ R scache[sizeof(R) == 8 ? side_cache_len<R>() * 128 : 1];
+    SideCache<R> sc{sizeof(R) == 8 ? scache + threadIdx.x : nullptr, 128};
     int nq = min(*a.nbq2, 3 * a.bq_cap);
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nq; s += gridDim.x * blockDim.x) {
         int i, j, code;
@@ -881,7 +889,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 4) k_bstar_rev(StepA
         R rx = (R)dx, ry = (R)dy, rz = (R)dz;
         R r2 = rx * rx + ry * ry + rz * rz;
         bool dsb;
-        double e = bstar_full<R>(P, a.G, i, j, rx, ry, rz, r2, C, code, sink, dsb);
+        double e = bstar_full<R>(P, a.G, i, j, rx, ry, rz, r2, C, code, sink, dsb, sc);
         dsb_count += dsb;
         E += e;
         if (a.eatom) eatom_pair(a.eatom, i, j, e);

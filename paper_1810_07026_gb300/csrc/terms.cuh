@@ -154,6 +154,7 @@ template <class R> struct Quintic {
     R k[6];            // knots
     R invh[5];         // 1 / interval width
     R a[5][6];         // power-basis coefficients in t = (x - k_m) / h_m
+    R da[5][5];        // those of the derivative in x: (p + 1) a[p + 1] / h_m
 };
 
 // Device copy of the parameter set; pair-indexed arrays use 0 = CC, 1 = CH, 2 = HH.
@@ -280,12 +281,13 @@ template <class R, bool D = true> HD R quintic(const Quintic<R>& q, R x, R& dfdx
     f = f * t + a[1];
     f = f * t + a[0];
     if (D) {
-        R d = R(5) * a[5];
-        d = d * t + R(4) * a[4];
-        d = d * t + R(3) * a[3];
-        d = d * t + R(2) * a[2];
-        d = d * t + a[1];
-        dfdx = cl ? R(0) : d * q.invh[m];
+        const R* b = q.da[m];
+        R d = b[4];
+        d = d * t + b[3];
+        d = d * t + b[2];
+        d = d * t + b[1];
+        d = d * t + b[0];
+        dfdx = cl ? R(0) : d;
     } else {
         dfdx = R(0);
     }
@@ -563,9 +565,25 @@ template <class R> HD R exp_lambda(const DevParams<R>& P, int tc, int tk, int to
     return exp_(P.lam * ((P.rhoH[tk] - rck) - (P.rhoH[to] - umag)));
 }
 
+// Per-thread store of the angular terms of a side's first SC_K neighbours
+// (the clamped cos, g, dg/dcos -- zero where cos was clamped -- and
+// e^lambda), written by the forward pass of a bond order and read back by its
+// reverse pass, which then skips their evaluation.  It lives in shared memory
+// as [value][slot][thread], so that a warp's accesses are consecutive;
+// p == nullptr: no store.
+constexpr int SC_K = 4;
+template <class R> struct SideCache {
+    R* p;
+    int stride;          // threads per block
+    HD R& at(int t, int v) const { return p[(t * 4 + v) * stride]; }
+    HD SideCache side(int s) const { return SideCache{p ? p + s * SC_K * 4 * stride : nullptr, stride}; }
+};
+// the store of both sides of one thread: 2 SC_K 4 values
+template <class R> constexpr int side_cache_len() { return 2 * SC_K * 4; }
+
 template <class R, bool D, class GT = Graph<R>>
 HD void side_forward(const DevParams<R>& P, const GT& G, int c, int o, R ux, R uy, R uz, R inv_u, R umag,
-                     Side<R>& s) {
+                     Side<R>& s, SideCache<R> sc = SideCache<R>{nullptr, 0}) {
     int tc = G.type[c], to = G.type[o];
     int nc = G.cnt[c];
     int so = slot_of(G, c, o);
@@ -598,7 +616,12 @@ HD void side_forward(const DevParams<R>& P, const GT& G, int c, int o, R ux, R u
         R g = gfun<R, D>(P, tc, cs, s.N, dgc, dgN);
         R e = exp_lambda<R>(P, tc, G.type[k], to, G.r[q], umag);
         s.sum += G.w[q] * g * e;
-        if (D) s.dsum_dN += G.w[q] * dgN * e;
+        if constexpr (D) {
+            s.dsum_dN += G.w[q] * dgN * e;
+            if (sc.p && t < SC_K) {
+                sc.at(t, 0) = cs; sc.at(t, 1) = g; sc.at(t, 2) = clc ? R(0) : dgc; sc.at(t, 3) = e;
+            }
+        }
     }
     s.P = 0; s.dPdNC = 0; s.dPdNH = 0;
     if (!(tc == 1 && to == 1)) {
@@ -615,7 +638,8 @@ HD void side_forward(const DevParams<R>& P, const GT& G, int c, int o, R ux, R u
 template <class R, class SinkT>
 HD void side_reverse(const DevParams<R>& P, const Graph<R>& G, int c, int o, R ux, R uy, R uz, R inv_u, R umag,
                      const Side<R>& s, R dEdp, R dEdN_direct, R dEdconj, SinkT& sink,
-                     R& gux, R& guy, R& guz, R& gumag, double& fcx, double& fcy, double& fcz) {
+                     R& gux, R& guy, R& guz, R& gumag, double& fcx, double& fcy, double& fcz,
+                     SideCache<R> sc = SideCache<R>{nullptr, 0}) {
     int tc = G.type[c], to = G.type[o];
     int nc = G.cnt[c];
     R ac = R(-0.5) * s.p * s.p * s.p * dEdp;       // dE/dsum = dE/dP
@@ -635,12 +659,18 @@ HD void side_reverse(const DevParams<R>& P, const Graph<R>& G, int c, int o, R u
         int tk = G.type[k];
         R dxk = G.dx[q], dyk = G.dy[q], dzk = G.dz[q];
         R rck = G.r[q], inv_r = G.ir[q], w = G.w[q], dw = G.dw[q];
-        R cs_raw = (ux * dxk + uy * dyk + uz * dzk) * inv_u * inv_r;
-        bool cl;
-        R cs = clamp_<R>(cs_raw, R(-1), R(1), cl);
-        R dgc, dgN;
-        R g = gfun<R, true>(P, tc, cs, s.N, dgc, dgN);
-        R e = exp_lambda<R>(P, tc, tk, to, rck, umag);
+        R cs, g, dgc, e;          // dgc: zero where cos was clamped
+        if (sc.p && t < SC_K) {   // from the forward pass
+            cs = sc.at(t, 0); g = sc.at(t, 1); dgc = sc.at(t, 2); e = sc.at(t, 3);
+        } else {
+            R cs_raw = (ux * dxk + uy * dyk + uz * dzk) * inv_u * inv_r;
+            bool cl;
+            cs = clamp_<R>(cs_raw, R(-1), R(1), cl);
+            R dgN;
+            g = gfun<R, true>(P, tc, cs, s.N, dgc, dgN);
+            if (cl) dgc = R(0);
+            e = exp_lambda<R>(P, tc, tk, to, rck, umag);
+        }
         if (P.kg) kg_gfun<R>(P, tc, cs, s.N, (double)(ac * w * e));
         // d E / d w_ck
         R dEdw = (tk == 0 ? dEdNC : dEdNH) + ac * g * e;
@@ -657,7 +687,7 @@ HD void side_reverse(const DevParams<R>& P, const Graph<R>& G, int c, int o, R u
             dEdr -= t;
             gumag += t;
         }
-        R dEdcs = cl ? R(0) : ac * w * e * dgc;
+        R dEdcs = ac * w * e * dgc;
         // cos = u.d / (|u| |d|)
         R a1 = dEdcs * inv_u * inv_r, a2 = dEdcs * cs * inv_r * inv_r, a3 = dEdcs * cs * inv_u * inv_u;
         R er = dEdr * inv_r;
@@ -791,10 +821,10 @@ template <class R, bool REV, class SinkT = Sink, class GT = Graph<R>>
 HD R bond_order(const DevParams<R>& P, const GT& G, int i, int j, R ux, R uy, R uz, R umag, R inv_u,
                 R eps, SinkT& sink, R& gux, R& guy, R& guz, R& gumag,
                 double& fix, double& fiy, double& fiz, double& fjx, double& fjy, double& fjz,
-                BstarSwitch<R>* bsw = nullptr) {
+                BstarSwitch<R>* bsw = nullptr, SideCache<R> sc = SideCache<R>{nullptr, 0}) {
     Side<R> si, sj;
-    side_forward<R, REV, GT>(P, G, i, j, ux, uy, uz, inv_u, umag, si);
-    side_forward<R, REV, GT>(P, G, j, i, -ux, -uy, -uz, inv_u, umag, sj);
+    side_forward<R, REV, GT>(P, G, i, j, ux, uy, uz, inv_u, umag, si, sc.side(0));
+    side_forward<R, REV, GT>(P, G, j, i, -ux, -uy, -uz, inv_u, umag, sj, sc.side(1));
     int ti = G.type[i], tj = G.type[j];
     R Nconj = R(1) + si.conj * si.conj + sj.conj * sj.conj;
     // pi^rc: the carbon side's coordination first for a C-H bond
@@ -839,9 +869,9 @@ HD R bond_order(const DevParams<R>& P, const GT& G, int i, int j, R ux, R uy, R 
     R half = R(0.5) * eps;
     R gvx = 0, gvy = 0, gvz = 0;     // side j works on -u
     side_reverse<R>(P, G, i, j, ux, uy, uz, inv_u, umag, si, half, dEdNi, dEdNconj * R(2) * si.conj, sink,
-                    gux, guy, guz, gumag, fix, fiy, fiz);
+                    gux, guy, guz, gumag, fix, fiy, fiz, sc.side(0));
     side_reverse<R>(P, G, j, i, -ux, -uy, -uz, inv_u, umag, sj, half, dEdNj, dEdNconj * R(2) * sj.conj, sink,
-                    gvx, gvy, gvz, gumag, fjx, fjy, fjz);
+                    gvx, gvy, gvz, gumag, fjx, fjy, fjz, sc.side(1));
     gux -= gvx; guy -= gvy; guz -= gvz;
     if (dih) {
         dihedral_sum<R, true, SinkT, GT>(P, G, i, j, ux, uy, uz, inv_u, eps * Tv, sink, gux, guy, guz,
@@ -853,7 +883,8 @@ HD R bond_order(const DevParams<R>& P, const GT& G, int i, int j, R ux, R uy, R 
 
 // ------------------------------------------------------------------ REBO bond (Alg. 1)
 template <class R>
-HD double rebo_bond(const DevParams<R>& P, const Graph<R>& G, int i, int slot, Sink& sink) {
+HD double rebo_bond(const DevParams<R>& P, const Graph<R>& G, int i, int slot, Sink& sink,
+                    SideCache<R> sc = SideCache<R>{nullptr, 0}) {
     int q = i * G.stride + slot;
     int j = G.nj[q];
     int p = pidx(G.type[i], G.type[j]);
@@ -875,7 +906,7 @@ HD double rebo_bond(const DevParams<R>& P, const Graph<R>& G, int i, int slot, S
     R gux = 0, guy = 0, guz = 0, gumag = 0;
     double fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
     R b = bond_order<R, true>(P, G, i, j, ux, uy, uz, r, ir, fA, sink, gux, guy, guz, gumag,
-                              fix, fiy, fiz, fjx, fjy, fjz);
+                              fix, fiy, fiz, fjx, fjy, fjz, nullptr, sc);
     R dEdr = dfR + b * dfA + gumag;
     R e = dEdr * ir;
     gux += e * ux; guy += e * uy; guz += e * uz;
@@ -1151,16 +1182,17 @@ HD void path_forces(const Graph<R>& G, int i, int code, R dEdw, SinkT& sink, dou
 // V^LJ = 4 eps [(s/r)^12 - (s/r)^6] times the C^1 cubic cut-off, from r^2;
 // dVr = (dV/dr)/r.  The cut-off switch is evaluated without a branch (t is
 // clamped at 0, where it is the identity), so lanes of a warp never diverge.
-template <class R> HD R vlj(const DevParams<R>& P, int p, R r2, R& dVr) {
-    R ir = rsqrt_(r2);
+// ir = 1/r is given.
+template <class R> HD R vlj(const DevParams<R>& P, int p, R r2, R ir, R& dVr) {
     R r = r2 * ir;
     R v, dvr;
     if (P.kind == 0) {
         R ir2 = ir * ir;
         R s2 = P.sig2[p] * ir2;
         R s6 = s2 * s2 * s2;
-        v = P.eps4[p] * (s6 * s6 - s6);
-        dvr = P.eps4[p] * (R(-12) * s6 * s6 + R(6) * s6) * ir2;
+        R t6 = P.eps4[p] * s6;
+        v = t6 * s6 - t6;
+        dvr = t6 * ir2 * (R(6) - R(12) * s6);
     } else {                         // Morse (AIREBO-M): eps (e^2 - 2 e), e = exp(-alpha (r - r_e))
         R e = exp_(-P.malpha[p] * (r - P.mre[p]));
         v = P.meps[p] * (e * e - R(2) * e);
@@ -1173,6 +1205,7 @@ template <class R> HD R vlj(const DevParams<R>& P, int p, R r2, R& dVr) {
     dVr = dvr * so + v * dso * ir;
     return v * so;
 }
+template <class R> HD R vlj(const DevParams<R>& P, int p, R r2, R& dVr) { return vlj<R>(P, p, r2, rsqrt_(r2), dVr); }
 
 // dV/d(eps) and dV/d(sigma) of the inter-molecular pair term (with its cut-off
 // switch) at r; eps is lj.epsilon (Lennard-Jones) or morse.epsilon (Morse).
@@ -1311,15 +1344,13 @@ HD int lj_classify(const DevParams<R>& P, const PathMap<R>& M, int i, int p, int
 // b* pair: (S_r S_b + 1 - S_r) C V for the pair i -> (j, image) with
 // displacement d; C and its path given, and S_b(b*) with its derivative
 // already known.  Applies every force except the one through db*, which the
-// reverse bond order applies where dS_b != 0.
+// reverse bond order applies where dS_b != 0.  1/r, V and (dV/dr)/r of the
+// pair are given.
 template <class R>
-HD double bstar_finish(const DevParams<R>& P, const Graph<R>& G, int i, int j, R dx, R dy, R dz, R r2,
-                       R C, int path_code, R Sb, R dSb, Sink& sink) {
+HD double bstar_finish_v(const DevParams<R>& P, const Graph<R>& G, int i, int j, R dx, R dy, R dz, R r2,
+                         R inv_r, R V, R dVr, R C, int path_code, R Sb, R dSb, Sink& sink) {
     int p = pidx(G.type[i], G.type[j]);
-    R inv_r = rsqrt_(r2);
     R r = r2 * inv_r;
-    R dVr;
-    R V = vlj<R>(P, p, r2, dVr);
     R dSr;
     R Sr = Sw<R>((r - P.Srlo[p]) * P.Srinv[p], dSr);
     dSr *= P.Srinv[p];
@@ -1344,6 +1375,16 @@ HD double bstar_finish(const DevParams<R>& P, const Graph<R>& G, int i, int j, R
         sink.W[3] -= (double)dx * gy; sink.W[4] -= (double)dx * gz; sink.W[5] -= (double)dy * gz;
     }
     return (double)E;
+}
+
+// the same, with 1/r, V and (dV/dr)/r evaluated here
+template <class R>
+HD double bstar_finish(const DevParams<R>& P, const Graph<R>& G, int i, int j, R dx, R dy, R dz, R r2,
+                       R C, int path_code, R Sb, R dSb, Sink& sink) {
+    R inv_r = rsqrt_(r2);
+    R dVr;
+    R V = vlj<R>(P, pidx(G.type[i], G.type[j]), r2, inv_r, dVr);
+    return bstar_finish_v<R>(P, G, i, j, dx, dy, dz, r2, inv_r, V, dVr, C, path_code, Sb, dSb, sink);
 }
 
 // b* of the pair i -> (j, image) with displacement d: the bond order of
@@ -1373,12 +1414,12 @@ template <class R> HD R bstar_switch(const DevParams<R>& P, int p, R bs, R& dSb)
 // when dS_b != 0.
 template <class R>
 HD double bstar_full(const DevParams<R>& P, const Graph<R>& G, int i, int j, R dx, R dy, R dz, R r2,
-                     R C, int path_code, Sink& sink, bool& dsb) {
+                     R C, int path_code, Sink& sink, bool& dsb, SideCache<R> sc = SideCache<R>{nullptr, 0}) {
     int p = pidx(G.type[i], G.type[j]);
     R inv_r = rsqrt_(r2);
     R r = r2 * inv_r;
     R dVr;
-    R V = vlj<R>(P, p, r2, dVr);
+    R V = vlj<R>(P, p, r2, inv_r, dVr);
     R dSr;
     R Sr = Sw<R>((r - P.Srlo[p]) * P.Srinv[p], dSr);
     R rs = P.rstar[p];
@@ -1387,7 +1428,7 @@ HD double bstar_full(const DevParams<R>& P, const Graph<R>& G, int i, int j, R d
     double fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
     BstarSwitch<R> bsw{P.bmin[p], P.binv[p], Sr * C * V, R(0), R(0)};
     bond_order<R, true>(P, G, i, j, ux, uy, uz, rs, rcp_(rs), R(0), sink, gux, guy, guz, gumag,
-                        fix, fiy, fiz, fjx, fjy, fjz, &bsw);
+                        fix, fiy, fiz, fjx, fjy, fjz, &bsw, sc);
     dsb = !is_zero(bsw.dSb);
     if (dsb) {
         // u = r* d/|d|: only the direction of d carries a gradient
@@ -1403,7 +1444,7 @@ HD double bstar_full(const DevParams<R>& P, const Graph<R>& G, int i, int j, R d
             sink.W[3] -= (double)dx * gy; sink.W[4] -= (double)dx * gz; sink.W[5] -= (double)dy * gz;
         }
     }
-    return bstar_finish<R>(P, G, i, j, dx, dy, dz, r2, C, path_code, bsw.Sb, bsw.dSb, sink);
+    return bstar_finish_v<R>(P, G, i, j, dx, dy, dz, r2, inv_r, V, dVr, C, path_code, bsw.Sb, bsw.dSb, sink);
 }
 
 // ------------------------------------------------------------------ parameter derivatives of the forces
