@@ -268,6 +268,10 @@ bool load_scalars(const HostParams& hp, Scalars& s, std::string& err) {
     return true;
 }
 
+// the device tables of one precision: spline coefficients, then knot data
+constexpr int PKNOT_OFF = 3 * 256 + 4 * NTRI_CELLS * 64;
+constexpr int TABLES_LEN = PKNOT_OFF + 3 * 25 * 3 + 4 * 225 * 4;
+
 template <class R>
 bool fill_params(const Scalars& s, DevParams<R>& P, std::vector<R>& tables, std::vector<unsigned char>& Tnz, std::string& err) {
     for (int p = 0; p < 3; p++) {
@@ -312,12 +316,20 @@ bool fill_params(const Scalars& s, DevParams<R>& P, std::vector<R>& tables, std:
     if (!quintic_coeffs<R>(s.gC1k, s.gC1d, P.gC1, err) || !quintic_coeffs<R>(s.gC2k, s.gC2d, P.gC2, err) ||
         !quintic_coeffs<R>(s.gHk, s.gHd, P.gH, err))
         return false;
-    // tables: P (3 x 256), pi^rc (3 x 8192), T (8192)
-    std::vector<double> buf(3 * 256 + 4 * NTRI_CELLS * 64);
+    // tables: P (3 x 256), pi^rc (3 x 8192), T (8192) coefficients, then the
+    // knot data: P (3 x 25 x 3), pi^rc (3 x 225 x 4), T (225 x 4)
+    std::vector<double> buf(TABLES_LEN);
     for (int t = 0; t < 3; t++) bicubic_coeffs(s.P[t], buf.data() + t * 256);
     for (int t = 0; t < 3; t++) tricubic_coeffs(s.F[t], buf.data() + 3 * 256 + t * NTRI_CELLS * 64, nullptr);
     Tnz.assign(NTRI_CELLS, 0);
     tricubic_coeffs(s.T, buf.data() + 3 * 256 + 3 * NTRI_CELLS * 64, Tnz.data());
+    double* kp = buf.data() + PKNOT_OFF;
+    for (int t = 0; t < 3; t++)
+        for (int k = 0; k < 25; k++)
+            for (int c = 0; c < 3; c++) *kp++ = s.P[t][k * 4 + c];          // f, fx, fy
+    for (int t = 0; t < 4; t++)                                            // pi^rc CC, CH, HH, then T_CC
+        for (int k = 0; k < 225; k++)
+            for (int c = 0; c < 4; c++) *kp++ = (t < 3 ? s.F[t] : s.T)[k * 8 + c];   // f, fx, fy, fz
     tables.resize(buf.size());
     for (size_t k = 0; k < buf.size(); k++) tables[k] = (R)buf[k];
     return true;
@@ -448,6 +460,9 @@ template <class R> airebo_status upload_params(airebo_handle h, Precision<R>& pr
     pr.hp.Ftab = pr.b.tables + 3 * 256;
     pr.hp.Ttab = pr.b.tables + 3 * 256 + 3 * NTRI_CELLS * 64;
     pr.hp.Tnz = pr.b.Tnz;
+    pr.hp.Pknot = pr.b.tables + PKNOT_OFF;
+    pr.hp.Fknot = pr.hp.Pknot + 3 * 25 * 3;
+    pr.hp.Tknot = pr.hp.Fknot + 3 * 225 * 4;
     pr.hp.kg = nullptr;
     CK(cudaMemcpy(pr.b.P, &pr.hp, sizeof(DevParams<R>), cudaMemcpyHostToDevice));
     return AIREBO_OK;
@@ -727,7 +742,7 @@ template <class R> StepArgs<R> make_args(airebo_handle h, Precision<R>& pr, cons
     a.bonds = h->bonds; a.nbonds = h->counts; a.bond_cap = h->bond_cap;
     a.ccbonds = h->ccbonds; a.nccbonds = h->counts + 2;
     a.bq = h->bq; a.nbq = h->counts + 4; a.bq_cap = h->bq_cap;
-    a.bq2 = h->bq2; a.nbq2 = h->counts + 3;
+    a.bq2 = h->bq2; a.nbq2 = h->counts + 8;
     a.screen = false;
     a.Pef = nullptr;
     a.G32 = Graph<float>{};
@@ -776,7 +791,7 @@ airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos,
         if (h->n) CK(cudaMemsetAsync(d_force, 0, sizeof(double) * 3 * h->n, s));
         CK(cudaMemsetAsync(h->acc, 0, sizeof(double) * 9, s));
         CK(cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * 8, s));
-        CK(cudaMemsetAsync(h->counts, 0, sizeof(int) * 8, s));
+        CK(cudaMemsetAsync(h->counts, 0, sizeof(int) * 12, s));
         // an asynchronous evaluation keeps the flags of earlier ones: they stay
         // set until airebo_check reads and clears them
         if (!async) CK(cudaMemsetAsync(h->derr, 0, sizeof(int) * 8, s));
@@ -957,7 +972,7 @@ airebo_status airebo_create(const char* params, const airebo_options* opts, void
     if (ce != cudaSuccess) { delete h; return AIREBO_ERR_CUDA; }
     st = upload_own_params(h);
     if (!st) {
-        if (realloc_dev(h->counts, 8) || realloc_dev(h->acc, 9) || realloc_dev(h->counters, 8) ||
+        if (realloc_dev(h->counts, 12) || realloc_dev(h->acc, 9) || realloc_dev(h->counters, 8) ||
             realloc_dev(h->derr, 8) || realloc_dev(h->maxd2, 1) || realloc_dev(h->ke, 1) ||
             realloc_dev(h->gate, 1) || realloc_dev(h->d_builds, 1) || realloc_dev(h->nerr, 4) ||
             cudaMemset(h->derr, 0, sizeof(int) * 8) || cudaMemset(h->d_builds, 0, sizeof(long long)) ||

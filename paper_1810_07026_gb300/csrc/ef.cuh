@@ -325,7 +325,7 @@ HD ef bstar_value_ef(const DevParams<ef>& P, const GT& G, int i, int j, double d
     ef gux(0.0f), guy(0.0f), guz(0.0f), gumag(0.0f);
     double fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
     Sink none{nullptr, 0, false, {0, 0, 0, 0, 0, 0}, false, {0, 0, 0, 0, 0, 0}};
-    return bond_order<ef, false, Sink, GT>(P, G, i, j, ux, uy, uz, rs, rcp_(rs), ef(0.0f), none, gux, guy, guz, gumag,
+    return bond_order_c<ef, false, Sink, GT>(P, G, i, j, ux, uy, uz, rs, rcp_(rs), ef(0.0f), none, gux, guy, guz, gumag,
                                            fix, fiy, fiz, fjx, fjy, fjz);
 }
 

@@ -46,7 +46,7 @@ template <class R> struct StepArgs {
     int2* bonds; int* nbonds; int bond_cap;   // bonds i<j that are not C-C
     int2* ccbonds; int* nccbonds;             // C-C bonds i<j, same capacity
     int4* bq; int* nbq; int bq_cap;
-    int* bq2; int* nbq2;                   // b* pairs left to the full-precision pass
+    int* bq2; int* nbq2;                   // b* pairs left to the full-precision pass, by species pair (3 x bq_cap)
     // b* screen (FP64): an FP32 b* with a rigorous error bound decides S_b
     // where the whole bound lies outside the transition
     bool screen;

@@ -314,6 +314,21 @@ __global__ void __launch_bounds__(128) k_path_map(StepArgs<R> a) {
     if (ov) atomicMax(a.err + ERR_MAP, M.cnt[i] + ov);
 }
 
+// A slot in queue k (counter ctr[k]) for each lane of the warp that calls
+// this: one atomic per distinct k among the calling lanes, which share it in
+// lane order.  (An atomic on a per-lane address is not combined across the
+// warp by the compiler, and 32 of them on one counter serialise.)
+__device__ __forceinline__ int queue_slot(int* ctr, int k) {
+    unsigned act = __activemask();
+    unsigned peers = __match_any_sync(act, k);
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(ctr + k, __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    return base + __popc(peers & ((1u << lane) - 1));
+}
+
 // ------------------------------------------------------------------ LJ
 // Persistent warps stride over atoms i.  For each chunk of 32 entries of i's
 // half list, every lane forms the FP64 displacement and tests its pair (cut-off,
@@ -724,7 +739,7 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
                     st = lj_classify_c<R, float>(P, a.M, i, j, img, r2f, kf, C, code, mi, general);
                 }
                 if (st == 2) {
-                    int q = atomicAdd(a.nbq + p, 1);
+                    int q = queue_slot(a.nbq, p);
                     if (q < a.bq_cap) a.bq[(size_t)p * a.bq_cap + q] = make_int4(i, e, mi, 0);
                 } else if (st == 4) {     // rare: 0 < C < 1 along a path
                     double dx, dy, dz;
@@ -856,8 +871,8 @@ __global__ void __launch_bounds__(128, 8) k_bstar(StepArgs<R> a) {
             if (a.eatom) eatom_pair(a.eatom, i, j, e);
             if (JV && a.jv) lj_pair_jvp<R>(P, a.G, i, j, rx, ry, rz, r2, C, code, Sb, R(0), a.jv, a.n, J);
         } else {
-            int s = atomicAdd(a.nbq2, 1);
-            if (s < 3 * a.bq_cap) a.bq2[s] = t;
+            int s = queue_slot(a.nbq2, p);            // kept by species pair, as the first queue
+            if (s < a.bq_cap) a.bq2[(size_t)p * a.bq_cap + s] = t;
         }
     }
     block_accumulate<128>(E, sink.W, EXTRA && a.virial, a.acc + 1, a.acc + 3);
@@ -880,8 +895,11 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 4) k_bstar_rev(StepA
     // the FP32 instances do better with the shared memory left to L1)
     __shared__ R scache[sizeof(R) == 8 ? side_cache_len<R>() * 128 : 1];
     SideCache<R> sc{sizeof(R) == 8 ? scache + threadIdx.x : nullptr, 128};
-    int nq = min(*a.nbq2, 3 * a.bq_cap);
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nq; s += gridDim.x * blockDim.x) {
+    int n0 = min(a.nbq2[0], a.bq_cap), n1 = min(a.nbq2[1], a.bq_cap), n2 = min(a.nbq2[2], a.bq_cap);
+    int nq = n0 + n1 + n2;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nq; u += gridDim.x * blockDim.x) {
+        // species pair by species pair (CC, CH, HH), so that warps are uniform
+        int s = u < n0 ? u : (u < n0 + n1 ? a.bq_cap + (u - n0) : 2 * a.bq_cap + (u - n0 - n1));
         int i, j, code;
         double dx, dy, dz;
         R C;
@@ -911,7 +929,7 @@ __global__ void k_finish_counters(StepArgs<R> a) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         a.counters[CNT_BONDS] = (unsigned long long)(*a.nbonds + *a.nccbonds);
         a.counters[CNT_BSTAR] = (unsigned long long)(a.nbq[0] + a.nbq[1] + a.nbq[2]);
-        a.counters[CNT_BSTAR_FULL] = (unsigned long long)*a.nbq2;
+        a.counters[CNT_BSTAR_FULL] = (unsigned long long)(a.nbq2[0] + a.nbq2[1] + a.nbq2[2]);
         // the longest b* queue, kept with the other flags (a capacity check
         // after several asynchronous evaluations sees the largest of them)
         int q = max(a.nbq[0], max(a.nbq[1], a.nbq[2]));

@@ -23,6 +23,7 @@
 #include <cstdint>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #ifdef __CUDACC__
 #define HD __host__ __device__ __forceinline__
@@ -177,6 +178,12 @@ template <class R> struct DevParams {
     const R* Ftab;                   // 3 tables (CC, CH, HH) x 128 cells x 64 coefficients
     const R* Ttab;                   // T_CC: 128 cells x 64 coefficients
     const unsigned char* Tnz;        // 1 where a T_CC cell has a nonzero coefficient
+    // the knot data (value and first derivatives) of the same splines, for
+    // arguments that lie on knots: P 3 x 25 x (f, fx, fy); pi^rc 3 x 225 x
+    // (f, fx, fy, fz); T_CC 225 x (f, fx, fy, fz)
+    const R* Pknot;
+    const R* Fknot;
+    const R* Tknot;
     double* kg;                      // dE/d(power-basis coefficient) of every spline, or null (layout KG_*)
 };
 
@@ -292,6 +299,42 @@ template <class R, bool D = true> HD R quintic(const Quintic<R>& q, R x, R& dfdx
         dfdx = R(0);
     }
     return f;
+}
+
+// The knot, an integer in [lo, hi] (0 <= lo < hi <= 15), that a spline
+// argument x lies on after the clamp to [lo, hi], or -1 when it lies between
+// two knots; cl: x was clamped.  For FP64 by integer operations on the bit
+// pattern (no FP64-pipe issue): x in (lo, hi) is an integer when the
+// mantissa bits below its binary point are zero.
+HD int knot_of(double x, int lo, int hi, bool& cl) {
+    long long k = okey(x), klo = okey((double)lo), khi = okey((double)hi);
+    cl = false;
+    if (k <= klo) { cl = k < klo; return lo; }
+    if (k >= khi) { cl = k > khi; return hi; }
+    long long b = k;                             // x > lo >= 0: the key is the bit pattern
+    int e = (int)(b >> 52) - 1023;               // 0 <= e <= 3 for 1 <= x < 16
+    if (e < 0) return -1;
+    long long m = b & 0xFFFFFFFFFFFFFLL;
+    if (m & ((1LL << (52 - e)) - 1)) return -1;
+    return (int)((1LL << e) | (m >> (52 - e)));
+}
+HD int knot_of(float x, int lo, int hi, bool& cl) {
+    cl = false;
+    if (!(x > (float)lo)) { cl = x < (float)lo || !(x == x); return lo; }
+    if (x >= (float)hi) { cl = x > (float)hi; return hi; }
+    int k = (int)x;
+    return (float)k == x ? k : -1;
+}
+// value and first derivatives of a knot all zero
+template <class R> HD bool knot_zero(const R* t) {
+    if constexpr (std::is_floating_point<R>::value) return is_zero(t[0]) && is_zero(t[1]) && is_zero(t[2]) && is_zero(t[3]);
+    else return false;
+}
+// the knot of the tricubic grid (N_ij, N_ji in [0, 4], N^conj in [1, 9]) that
+// (x, y, z) lies on, as (x * 5 + y) * 9 + z - 1, or -1
+template <class R> HD int tri_knot(R x, R y, R z, bool& clx, bool& cly, bool& clz) {
+    int kx = knot_of(x, 0, 4, clx), ky = knot_of(y, 0, 4, cly), kz = knot_of(z, 1, 9, clz);
+    return (kx < 0 || ky < 0 || kz < 0) ? -1 : (kx * 5 + ky) * 9 + (kz - 1);
 }
 
 // clamp a spline argument (a NaN too: every table index stays in range)
@@ -626,7 +669,20 @@ HD void side_forward(const DevParams<R>& P, const GT& G, int c, int o, R ux, R u
     s.P = 0; s.dPdNC = 0; s.dPdNH = 0;
     if (!(tc == 1 && to == 1)) {
         int tab = (tc == 0 && to == 0) ? 0 : (tc == 0 ? 1 : 2);
-        s.P = bicubic<R, D>(P.Ptab + tab * 256, s.NC, s.NH, s.dPdNC, s.dPdNH);
+        bool knot = false;
+        if constexpr (std::is_floating_point<R>::value) {
+            // integer N^C and N^H (every bond fully on): the knot data, which
+            // the bicubic interpolates exactly, instead of its polynomial
+            bool cx, cy;
+            int kx = knot_of(s.NC, 0, 4, cx), ky = knot_of(s.NH, 0, 4, cy);
+            if (kx >= 0 && ky >= 0) {
+                const R* k = P.Pknot + (tab * 25 + kx * 5 + ky) * 3;
+                s.P = k[0];
+                if (D) { s.dPdNC = cx ? R(0) : k[1]; s.dPdNH = cy ? R(0) : k[2]; }
+                knot = true;
+            }
+        }
+        if (!knot) s.P = bicubic<R, D>(P.Ptab + tab * 256, s.NC, s.NH, s.dPdNC, s.dPdNH);
     }
     s.p = rsqrt_(R(1) + s.sum + s.P);
 }
@@ -831,18 +887,39 @@ HD R bond_order(const DevParams<R>& P, const GT& G, int i, int j, R ux, R uy, R 
     int tab = (ti == tj) ? (ti == 0 ? 0 : 2) : 1;
     bool swap = (ti == 1 && tj == 0);
     R xa = swap ? sj.N : si.N, xb = swap ? si.N : sj.N, xc = Nconj;
-    bool clx, cly, clz;
-    R tx, ty, tz;
-    int cell = tri_cell_index<R>(xa, xb, xc, clx, cly, clz, tx, ty, tz);
-    R Fa, Fb, Fc;
-    R pirc = tricubic_cell<R, REV>(P.Ftab + (tab * NTRI_CELLS + cell) * 64, tx, ty, tz, clx, cly, clz, Fa, Fb, Fc);
-    R dFdNi = swap ? Fb : Fa, dFdNj = swap ? Fa : Fb;
-    // pi^dh (C-C only), skipped where the T_CC cell is identically zero
-    // (unless its coefficients' gradient is wanted)
+    bool clx = false, cly = false, clz = false;
+    R tx = 0, ty = 0, tz = 0;
+    R Fa, Fb, Fc, pirc;
     R pidh = 0, D = 0, Tv = 0, Ta = 0, Tb = 0, Tc = 0;
-    bool dih = (ti == 0 && tj == 0) && (P.Tnz[cell] || (REV && P.kg));
+    int cell = 0;
+    bool dih;
+    // all three arguments on knots (integer coordinations, the common case of
+    // saturated bonds): the knot data of pi^rc and T, which the tricubics
+    // interpolate exactly; not with the coefficient gradient, which wants the cell
+    int kn = -1;
+    if constexpr (std::is_floating_point<R>::value) {
+        if (!(REV && P.kg)) kn = tri_knot<R>(xa, xb, xc, clx, cly, clz);
+    }
+    if (kn >= 0) {
+        const R* k = P.Fknot + (tab * 225 + kn) * 4;
+        pirc = k[0];
+        Fa = (REV && !clx) ? k[1] : R(0); Fb = (REV && !cly) ? k[2] : R(0); Fc = (REV && !clz) ? k[3] : R(0);
+        const R* t = P.Tknot + kn * 4;
+        dih = (ti == 0 && tj == 0) && !knot_zero<R>(t);
+        if (dih) {
+            Tv = t[0];
+            Ta = (REV && !clx) ? t[1] : R(0); Tb = (REV && !cly) ? t[2] : R(0); Tc = (REV && !clz) ? t[3] : R(0);
+        }
+    } else {
+        cell = tri_cell_index<R>(xa, xb, xc, clx, cly, clz, tx, ty, tz);
+        pirc = tricubic_cell<R, REV>(P.Ftab + (tab * NTRI_CELLS + cell) * 64, tx, ty, tz, clx, cly, clz, Fa, Fb, Fc);
+        // pi^dh (C-C only), skipped where the T_CC cell is identically zero
+        // (unless its coefficients' gradient is wanted)
+        dih = (ti == 0 && tj == 0) && (P.Tnz[cell] || (REV && P.kg));
+        if (dih) Tv = tricubic_cell<R, REV>(P.Ttab + cell * 64, tx, ty, tz, clx, cly, clz, Ta, Tb, Tc);
+    }
+    R dFdNi = swap ? Fb : Fa, dFdNj = swap ? Fa : Fb;
     if (dih) {
-        Tv = tricubic_cell<R, REV>(P.Ttab + cell * 64, tx, ty, tz, clx, cly, clz, Ta, Tb, Tc);
         R dummy = 0;
         D = dihedral_sum<R, false, SinkT, GT>(P, G, i, j, ux, uy, uz, inv_u, R(0), sink, dummy, dummy, dummy,
                                               fix, fiy, fiz, fjx, fjy, fjz);
@@ -879,6 +956,30 @@ HD R bond_order(const DevParams<R>& P, const GT& G, int i, int j, R ux, R uy, R 
     }
     return b;
     }
+}
+
+// bond_order of an unbonded pair with the carbon first for a C-H pair:
+// b_ij = b_ji with u -> -u, so the lanes of a warp of C-H pairs (taken from
+// the half list in either order) walk the carbon's neighbours in the same
+// side pass.  The swap is made on the arguments and undone on the results.
+template <class R, bool REV, class SinkT = Sink, class GT = Graph<R>>
+HD R bond_order_c(const DevParams<R>& P, const GT& G, int i, int j, R ux, R uy, R uz, R umag, R inv_u,
+                  R eps, SinkT& sink, R& gux, R& guy, R& guz, R& gumag,
+                  double& fix, double& fiy, double& fiz, double& fjx, double& fjy, double& fjz,
+                  BstarSwitch<R>* bsw = nullptr, SideCache<R> sc = SideCache<R>{nullptr, 0}) {
+    bool sw = G.type[i] == 1 && G.type[j] == 0;
+    int a = sw ? j : i, b = sw ? i : j;
+    R vx = sw ? -ux : ux, vy = sw ? -uy : uy, vz = sw ? -uz : uz;
+    R gvx = R(0), gvy = R(0), gvz = R(0);
+    double fax = 0, fay = 0, faz = 0, fbx = 0, fby = 0, fbz = 0;
+    R bo = bond_order<R, REV, SinkT, GT>(P, G, a, b, vx, vy, vz, umag, inv_u, eps, sink, gvx, gvy, gvz, gumag,
+                                         fax, fay, faz, fbx, fby, fbz, bsw, sc);
+    if constexpr (REV) {
+        gux += sw ? -gvx : gvx; guy += sw ? -gvy : gvy; guz += sw ? -gvz : gvz;
+        fix += sw ? fbx : fax; fiy += sw ? fby : fay; fiz += sw ? fbz : faz;
+        fjx += sw ? fax : fbx; fjy += sw ? fay : fby; fjz += sw ? faz : fbz;
+    }
+    return bo;
 }
 
 // ------------------------------------------------------------------ REBO bond (Alg. 1)
@@ -1397,7 +1498,7 @@ HD R bstar_value(const DevParams<R>& P, const Graph<R>& G, int i, int j, R dx, R
     R ux = dx * inv_r * rs, uy = dy * inv_r * rs, uz = dz * inv_r * rs;
     R gux = 0, guy = 0, guz = 0, gumag = 0;
     double fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
-    return bond_order<R, false>(P, G, i, j, ux, uy, uz, rs, rcp_(rs), R(0), sink, gux, guy, guz, gumag,
+    return bond_order_c<R, false>(P, G, i, j, ux, uy, uz, rs, rcp_(rs), R(0), sink, gux, guy, guz, gumag,
                                 fix, fiy, fiz, fjx, fjy, fjz);
 }
 
@@ -1427,8 +1528,8 @@ HD double bstar_full(const DevParams<R>& P, const Graph<R>& G, int i, int j, R d
     R gux = 0, guy = 0, guz = 0, gumag = 0;
     double fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
     BstarSwitch<R> bsw{P.bmin[p], P.binv[p], Sr * C * V, R(0), R(0)};
-    bond_order<R, true>(P, G, i, j, ux, uy, uz, rs, rcp_(rs), R(0), sink, gux, guy, guz, gumag,
-                        fix, fiy, fiz, fjx, fjy, fjz, &bsw, sc);
+    bond_order_c<R, true>(P, G, i, j, ux, uy, uz, rs, rcp_(rs), R(0), sink, gux, guy, guz, gumag,
+                          fix, fiy, fiz, fjx, fjy, fjz, &bsw, sc);
     dsb = !is_zero(bsw.dSb);
     if (dsb) {
         // u = r* d/|d|: only the direction of d carries a gradient
@@ -1566,8 +1667,8 @@ HD R bstar_jvp(const DevParams<R>& P, const Graph<R>& G, int i, int j, R dx, R d
     double fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
     JSink js{v, n, 0.0, false, {0, 0, 0, 0, 0, 0}};
     BstarSwitch<R> bsw{P.bmin[p], P.binv[p], R(1), R(0), R(0)};
-    bond_order<R, true, JSink>(P, G, i, j, ux, uy, uz, rs, rcp_(rs), R(0), js, gux, guy, guz, gumag,
-                               fix, fiy, fiz, fjx, fjy, fjz, &bsw);
+    bond_order_c<R, true, JSink>(P, G, i, j, ux, uy, uz, rs, rcp_(rs), R(0), js, gux, guy, guz, gumag,
+                                 fix, fiy, fiz, fjx, fjy, fjz, &bsw);
     Sb = bsw.Sb;
     if (is_zero(bsw.dSb)) return R(0);
     R ud = (gux * dx + guy * dy + guz * dz) * inv_r;
