@@ -260,12 +260,14 @@ template <class R, bool EXTRA>
 __global__ void __launch_bounds__(128) k_torsion(StepArgs<R> a) {
     const DevParams<R>& P = *a.P;
     Sink sink{a.f, a.n, EXTRA && a.virial, {0, 0, 0, 0, 0, 0}, EXTRA && a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
+    __shared__ R tstore[TORS_L * TORS_V * 128];        // the l-side values and sums of each thread
+    TorsStore<R> S{tstore + threadIdx.x, 128};
     double E = 0;
     int nb = *a.nccbonds;
     if (nb > a.bond_cap) nb = a.bond_cap;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
         int2 bd = a.ccbonds[b];
-        double e = torsion_bond<R>(P, a.G, bd.x, bd.y, sink);
+        double e = torsion_bond_f<R>(P, a.G, bd.x, bd.y, sink, S);
         E += e;
         if (a.eatom && e != 0.0) eatom_pair(a.eatom, bd.x, a.G.nj[bd.x * a.G.stride + bd.y], e);
     }

@@ -1118,6 +1118,139 @@ HD double torsion_bond(const DevParams<R>& P, const GT& G, int i, int slot, Sink
     return E;
 }
 
+// The same torsion of one bond with its double sum factored.  Every term of
+// the gradient is linear in its (k, l) pieces: the gradient with respect to
+// n1 = u x a_k, summed over l, is wij [sum_l q n2_l - |n1|^-2 (sum_l dcw cos w) n1]
+// (q = dcw / (|n1| |n2|)), and likewise for n2 summed over k; the guard and
+// weight derivatives collect sum_l w_jl s_j V and sum_k w_ik s_i V.  So each
+// (k, l) pair forms only cos w, V, dV/dcos w and those sums; the cross
+// products with u and the forces on k (on l) are applied once per
+// neighbour.  The l-side values and sums of up to TORS_L neighbours of j sit
+// in a per-thread store in shared memory ([value][slot][thread]); a j with
+// more neighbours takes torsion_bond.
+constexpr int TORS_L = 3, TORS_V = 12;      // slots, values per slot
+template <class R> struct TorsStore {
+    R* p;
+    int stride;
+    HD R& at(int t, int v) const { return p[(t * TORS_V + v) * stride]; }
+};
+template <class R>
+HD double torsion_bond_f(const DevParams<R>& P, const Graph<R>& G, int i, int slot, Sink& sink, TorsStore<R> S) {
+    int q = i * G.stride + slot;
+    int j = G.nj[q];
+    int ni = G.cnt[i], nj = G.cnt[j];
+    int sj_ = slot_of(G, i, j), si_ = slot_of(G, j, i);
+    int mi = ni - (sj_ < MAXN), mj = nj - (si_ < MAXN);
+    if (mj > TORS_L) return torsion_bond<R>(P, G, i, slot, sink);
+    R ux = G.dx[q], uy = G.dy[q], uz = G.dz[q];
+    R wij = G.w[q], dwij = G.dw[q];
+    R inv_u = G.ir[q];
+    // the l side: n2 = u x b_l (0-2) and 1/|n2| (3), w_jl s_j (4), s_j (5) and
+    // ds_j (6); then the sums over k: q n1_k (7-9), dcw cos w (10), w_ik s_i V (11)
+    for (int tb = 0; tb < mj; tb++) {
+        int qb = j * G.stride + tb + (tb >= si_);
+        R bx = G.dx[qb], by = G.dy[qb], bz = G.dz[qb];
+        R csj = -(ux * bx + uy * by + uz * bz) * inv_u * G.ir[qb];
+        R dsj;
+        R sj = guardf<R>(P, csj, dsj);
+        R n2x = uy * bz - uz * by, n2y = uz * bx - ux * bz, n2z = ux * by - uy * bx;
+        S.at(tb, 0) = n2x; S.at(tb, 1) = n2y; S.at(tb, 2) = n2z;
+        S.at(tb, 3) = is_zero(sj) ? R(0) : rsqrt_(n2x * n2x + n2y * n2y + n2z * n2z);
+        S.at(tb, 4) = G.w[qb] * sj; S.at(tb, 5) = sj; S.at(tb, 6) = dsj;
+        for (int v = 7; v < TORS_V; v++) S.at(tb, v) = R(0);
+    }
+    bool any = false;
+    double Ssum = 0;                 // sum over (k, l) of w_ik s_i w_jl s_j V
+    R gux = 0, guy = 0, guz = 0;
+    double fix = 0, fiy = 0, fiz = 0, fjx = 0, fjy = 0, fjz = 0;
+    for (int ta = 0; ta < mi; ta++) {
+        int qa = i * G.stride + ta + (ta >= sj_);
+        int k = G.nj[qa];
+        R ax = G.dx[qa], ay = G.dy[qa], az = G.dz[qa];
+        R wik = G.w[qa], inv_ra = G.ir[qa];
+        R csi = (ux * ax + uy * ay + uz * az) * inv_u * inv_ra;
+        R dsi;
+        R si = guardf<R>(P, csi, dsi);
+        if (is_zero(si)) continue;
+        R n1x = uy * az - uz * ay, n1y = uz * ax - ux * az, n1z = ux * ay - uy * ax;
+        R rn1 = rsqrt_(n1x * n1x + n1y * n1y + n1z * n1z);
+        R wsi = wik * si;
+        int tk = G.type[k] == 1;
+        R Ax = 0, Ay = 0, Az = 0, Bk = 0, Ik = 0;     // sum_l q n2_l, sum_l dcw cos w, sum_l w_jl s_j V
+        bool kany = false;
+        for (int tb = 0; tb < mj; tb++) {
+            int l = G.nj[j * G.stride + tb + (tb >= si_)];
+            if (l == k) continue;              // a three-ring
+            if (is_zero(S.at(tb, 5))) continue;
+            R n2x = S.at(tb, 0), n2y = S.at(tb, 1), n2z = S.at(tb, 2);
+            R inv12 = rn1 * S.at(tb, 3);
+            R cw = (n1x * n2x + n1y * n2y + n1z * n2z) * inv12;
+            R h = R(0.5) * (R(1) + cw);
+            R h2 = h * h, h4 = h2 * h2;
+            R eps = P.teps[tk + (G.type[l] == 1)];
+            R Vt = eps * (R(256.0 / 405.0) * h4 * h - R(0.1));
+            R dVdcw = eps * R(256.0 / 405.0) * R(2.5) * h4;
+            R wsj = S.at(tb, 4);
+            R wkl = wsi * wsj;
+            Ssum += (double)(wkl * Vt);
+            Ik += wsj * Vt;
+            S.at(tb, 11) += wsi * Vt;
+            R dcw = wkl * dVdcw;             // times w_ij below
+            R qq = dcw * inv12, dd = dcw * cw;
+            Ax += qq * n2x; Ay += qq * n2y; Az += qq * n2z; Bk += dd;
+            S.at(tb, 7) += qq * n1x; S.at(tb, 8) += qq * n1y; S.at(tb, 9) += qq * n1z; S.at(tb, 10) += dd;
+            kany = true;
+        }
+        if (!kany) continue;
+        any = true;
+        // the gradient with respect to n1, then to a_k and u through n1 = u x a_k
+        R c1 = rn1 * rn1 * Bk;
+        R g1x = wij * (Ax - c1 * n1x), g1y = wij * (Ay - c1 * n1y), g1z = wij * (Az - c1 * n1z);
+        R gax = g1y * uz - g1z * uy, gay = g1z * ux - g1x * uz, gaz = g1x * uy - g1y * ux;
+        gux += ay * g1z - az * g1y; guy += az * g1x - ax * g1z; guz += ax * g1y - ay * g1x;
+        // the weight w_ik and the guard s_i
+        R ea = G.dw[qa] * wij * si * Ik * inv_ra;
+        gax += ea * ax; gay += ea * ay; gaz += ea * az;
+        R dci = wik * wij * dsi * Ik;
+        R i1 = dci * inv_u * inv_ra, i2 = dci * csi * inv_ra * inv_ra, i3 = dci * csi * inv_u * inv_u;
+        gax += i1 * ux - i2 * ax; gay += i1 * uy - i2 * ay; gaz += i1 * uz - i2 * az;
+        gux += i1 * ax - i3 * ux; guy += i1 * ay - i3 * uy; guz += i1 * az - i3 * uz;
+        sink.half(k, ax, ay, az, gax, gay, gaz, fix, fiy, fiz);
+    }
+    if (!any) return 0.0;
+    for (int tb = 0; tb < mj; tb++) {
+        R sj = S.at(tb, 5);
+        if (is_zero(sj)) continue;
+        int qb = j * G.stride + tb + (tb >= si_);
+        R bx = G.dx[qb], by = G.dy[qb], bz = G.dz[qb];
+        R inv_rb = G.ir[qb];
+        R n2x = S.at(tb, 0), n2y = S.at(tb, 1), n2z = S.at(tb, 2), rn2 = S.at(tb, 3);
+        R c2 = rn2 * rn2 * S.at(tb, 10), Jl = S.at(tb, 11);
+        R g2x = wij * (S.at(tb, 7) - c2 * n2x), g2y = wij * (S.at(tb, 8) - c2 * n2y), g2z = wij * (S.at(tb, 9) - c2 * n2z);
+        R gbx = g2y * uz - g2z * uy, gby = g2z * ux - g2x * uz, gbz = g2x * uy - g2y * ux;
+        gux += by * g2z - bz * g2y; guy += bz * g2x - bx * g2z; guz += bx * g2y - by * g2x;
+        R eb = wij * G.dw[qb] * sj * Jl * inv_rb;
+        gbx += eb * bx; gby += eb * by; gbz += eb * bz;
+        R csj = -(ux * bx + uy * by + uz * bz) * inv_u * inv_rb;
+        R dcj = wij * G.w[qb] * S.at(tb, 6) * Jl;
+        R j1 = dcj * inv_u * inv_rb, j2 = dcj * csj * inv_rb * inv_rb, j3 = dcj * csj * inv_u * inv_u;
+        gbx += -j1 * ux - j2 * bx; gby += -j1 * uy - j2 * by; gbz += -j1 * uz - j2 * bz;
+        gux += -j1 * bx - j3 * ux; guy += -j1 * by - j3 * uy; guz += -j1 * bz - j3 * uz;
+        sink.half(G.nj[qb], bx, by, bz, gbx, gby, gbz, fjx, fjy, fjz);
+    }
+    // the bond weight w_ij
+    R em = dwij * (R)Ssum * inv_u;
+    gux += em * ux; guy += em * uy; guz += em * uz;
+    double gx = (double)gux, gy = (double)guy, gz = (double)guz;
+    atomic_add(sink.f + i, fix + gx); atomic_add(sink.f + sink.n + i, fiy + gy); atomic_add(sink.f + 2 * sink.n + i, fiz + gz);
+    atomic_add(sink.f + j, fjx - gx); atomic_add(sink.f + sink.n + j, fjy - gy); atomic_add(sink.f + 2 * sink.n + j, fjz - gz);
+    if (sink.virial) {
+        sink.W[0] -= (double)ux * gx; sink.W[1] -= (double)uy * gy; sink.W[2] -= (double)uz * gz;
+        sink.W[3] -= (double)ux * gy; sink.W[4] -= (double)ux * gz; sink.W[5] -= (double)uy * gz;
+    }
+    return (double)wij * Ssum;
+}
+
 // ------------------------------------------------------------------ C_ij paths (Sec. 2.1.2, 4.3)
 // A connectivity map of atom i holds, for every atom reachable over at most
 // three REBO bonds (keyed by atom and periodic image), the largest path
