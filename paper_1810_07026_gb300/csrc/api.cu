@@ -739,7 +739,7 @@ template <class R> StepArgs<R> make_args(airebo_handle h, Precision<R>& pr, cons
     for (int d = 0; d < 3; d++) a.L[d] = h->L[d];
     a.lj = h->lj; a.lj_cnt = h->lj_cnt; a.lj_cap = h->lj_cap;
     a.im = h->im; a.im_cnt = h->im_cnt; a.im_cap = h->im_cap;
-    a.bonds = h->bonds; a.nbonds = h->counts; a.bond_cap = h->bond_cap;
+    a.bonds = h->bonds; a.nbonds = h->counts; a.bond_cap = h->bond_cap; a.nhhbonds = h->counts + 1;
     a.ccbonds = h->ccbonds; a.nccbonds = h->counts + 2;
     a.bq = h->bq; a.nbq = h->counts + 4; a.bq_cap = h->bq_cap;
     a.bq2 = h->bq2; a.nbq2 = h->counts + 8;

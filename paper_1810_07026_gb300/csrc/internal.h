@@ -43,7 +43,8 @@ template <class R> struct StepArgs {
     double L[3];
     const int2* lj; const int* lj_cnt; int lj_cap;
     const int2* im; const int* im_cnt; int im_cap;
-    int2* bonds; int* nbonds; int bond_cap;   // bonds i<j that are not C-C
+    int2* bonds; int* nbonds; int bond_cap;   // C-H bonds from the carbon, from the front
+    int* nhhbonds;                            // H-H bonds i<j, in the same array from its far end
     int2* ccbonds; int* nccbonds;             // C-C bonds i<j, same capacity
     int4* bq; int* nbq; int bq_cap;
     int* bq2; int* nbq2;                   // b* pairs left to the full-precision pass, by species pair (3 x bq_cap)

@@ -213,6 +213,9 @@ __global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
                 if (ti == 0 && tj == 0) {
                     int c = atomicAdd(a.nccbonds, 1);
                     if (c < a.bond_cap) a.ccbonds[c] = make_int2(i, cnt);
+                } else if (ti == 1 && tj == 1) {   // H-H bonds from the far end of the same array
+                    int b = atomicAdd(a.nhhbonds, 1);
+                    if (b < a.bond_cap) a.bonds[a.bond_cap - 1 - b] = make_int2(i, cnt);
                 } else {
                     int b = atomicAdd(a.nbonds, 1);
                     if (b < a.bond_cap) a.bonds[b] = make_int2(i, cnt);
@@ -244,10 +247,12 @@ __global__ void __launch_bounds__(128, 4) k_rebo(StepArgs<R> a) {
     __shared__ R scache[sizeof(R) == 8 ? side_cache_len<R>() * 128 : 1];
     SideCache<R> sc{sizeof(R) == 8 ? scache + threadIdx.x : nullptr, 128};
     double E = 0;
-    int ncc = min(*a.nccbonds, a.bond_cap);
-    int nb = ncc + min(*a.nbonds, a.bond_cap);
+    // C-C, C-H, then H-H bonds (from the far end of a.bonds): warps of one species pair
+    int ncc = min(*a.nccbonds, a.bond_cap), nch = min(*a.nbonds, a.bond_cap);
+    int nhh = min(*a.nhhbonds, a.bond_cap - nch);
+    int nb = ncc + nch + nhh;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
-        int2 bd = b < ncc ? a.ccbonds[b] : a.bonds[b - ncc];
+        int2 bd = b < ncc ? a.ccbonds[b] : (b < ncc + nch ? a.bonds[b - ncc] : a.bonds[a.bond_cap - 1 - (b - ncc - nch)]);
         double e = rebo_bond<R>(P, a.G, bd.x, bd.y, sink, sc);
         E += e;
         if (a.eatom) eatom_pair(a.eatom, bd.x, a.G.nj[bd.x * a.G.stride + bd.y], e);
@@ -341,11 +346,17 @@ __device__ __forceinline__ int queue_slot(int* ctr, int k) {
 constexpr int LJ_THREADS = 256;
 constexpr int LJ_WARPS = LJ_THREADS / 32;
 
-// two compaction buffers per warp: 0 = inner pairs, 1 = pairs in the cut-off switch
+// three compaction buffers per warp: 0 = inner pairs, 1 = pairs in the
+// cut-off switch, 2 = pairs with 0 < C_ij < 1 along a path (and, with the
+// parameter derivatives, every pair), whose C_ij and path code sit in LjPathBuf
 struct LjBuf {
-    int jp[2][64];          // j | species pair << 30
-    int ia[2][64];          // the list's atom i
-    int im[2][64];          // packed image of j
+    int jp[3][64];          // j | species pair << 30
+    int ia[3][64];          // the list's atom i
+    int im[3][64];          // packed image of j
+};
+template <class R> struct LjPathBuf {
+    R C[64];
+    int code[64];
 };
 
 // Per-lane force (and energy) accumulator of the atom whose pairs the lane
@@ -379,6 +390,31 @@ __device__ __forceinline__ void lj_disp(const StepArgs<R>& a, const double (*shi
             dx += shift[0][sx + 4]; dy += shift[1][sy + 4]; dz += shift[2][sz + 4];
         }
     }
+}
+
+// The compacted pairs along a path (buffer 2): the general pair term with
+// C_ij and the path's forces, in FP64 in every instance (their number is
+// small; with the parameter derivatives every pair takes this batch)
+template <class R, bool JV>
+__device__ __forceinline__ void lj_batch_path(const StepArgs<R>& a, const DevParams<R>& P, const double (*shift)[9],
+                                           const LjBuf& B, const LjPathBuf<R>& PB, int lane, Sink& sink,
+                                           double& E, double* J) {
+    int jp = B.jp[2][lane];
+    int j = jp & 0x3fffffff, p = (unsigned)jp >> 30;
+    int i = B.ia[2][lane];
+    R C = PB.C[lane];
+    int code = PB.code[lane];
+    int n = a.n;
+    double dx, dy, dz;
+    lj_disp<R>(a, shift, i, j, B.im[2][lane], dx, dy, dz);
+    double gx = 0, gy = 0, gz = 0, E0 = E;
+    lj_eval<R>(P, a.G, i, p, j, dx, dy, dz, C, code, sink, gx, gy, gz, E);
+    if (JV && a.jv) {                 // S_r = 0 here: E = C V
+        R qx = (R)dx, qy = (R)dy, qz = (R)dz;
+        lj_pair_jvp<R>(P, a.G, i, j, qx, qy, qz, qx * qx + qy * qy + qz * qz, C, code, R(0), R(0), a.jv, n, J);
+    }
+    atomicAdd(a.f + i, gx); atomicAdd(a.f + n + i, gy); atomicAdd(a.f + 2 * n + i, gz);
+    if (a.eatom) eatom_pair(a.eatom, i, j, E - E0);
 }
 
 template <class R>
@@ -614,10 +650,15 @@ template <class R, bool DF, int MODE>
 __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
     constexpr bool EXTRA = MODE >= 1;      // virial or parameter gradient
     constexpr bool JV = MODE == 2;         // the parameter derivatives of the forces too
+    // path pairs (FP64 arithmetic) batched where the FP64 pipe bounds the
+    // kernel; the FP32 instance evaluates them where they are found
+    constexpr bool PATHBUF = sizeof(R) == 8;
+    constexpr int NBUF = PATHBUF ? 3 : 2;
     const DevParams<R>& P = *a.P;
     __shared__ double shift[3][9];                // image shifts S L for S in [-4, 4]
     __shared__ LjCuts<float> cutsf[3];            // thresholds in FP32, by species pair
     __shared__ LjBuf bufs[LJ_WARPS];
+    __shared__ LjPathBuf<R> pbufs[PATHBUF ? LJ_WARPS : 1];
     __shared__ float shf[2][3][9];                // DF: split image shifts (hi, lo)
     __shared__ DfParams dfp;
     __shared__ LjPow ljk[3];                       // the LJ pair in powers of 1/r^2, by species pair
@@ -640,6 +681,7 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
     __syncthreads();
     int lane = threadIdx.x & 31;
     LjBuf& B = bufs[threadIdx.x >> 5];
+    LjPathBuf<R>& PB = pbufs[PATHBUF ? threadIdx.x >> 5 : 0];
     unsigned lt = (1u << lane) - 1u;
     Sink sink{a.f, a.n, EXTRA && a.virial, {0, 0, 0, 0, 0, 0}, EXTRA && a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
     bool general = EXTRA && (a.pgrad != nullptr || a.jv != nullptr);
@@ -651,9 +693,13 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
     double E = 0;
     unsigned evaluated = 0;
     int n = a.n;
-    int cnt[2] = {0, 0};
+    int cnt[3] = {0, 0, 0};
     // the pair arithmetic of one full (or, at the end, partial) batch
     auto batch = [&](int b) {
+        if (PATHBUF && b == 2) {
+            lj_batch_path<R, JV>(a, P, shift, B, PB, lane, sink, E, J);
+            return;
+        }
         if constexpr (DF) {
             if constexpr (sizeof(R) == 8) lj_batch_df<R, EXTRA>(a, dfp, shf[0], shf[1], B, b, lane, dacc, Edf, Wdf);
             else lj_batch_mx<R, EXTRA>(a, P, shf[0], shf[1], B, b, lane, dacc, Edf, Wdf);
@@ -686,6 +732,8 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
         for (int base = 0; base < ne; base += 32) {
             int e = base + lane;
             int st = 0, j = 0, p = 0, img = 0;
+            R Cq = R(1);
+            int codeq = -1;                // C_ij and path of a pair for buffer 2
             if (e < ne) {
                 int2 ent = row[e];
                 j = ent.x;
@@ -743,27 +791,33 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
                 if (st == 2) {
                     int q = queue_slot(a.nbq, p);
                     if (q < a.bq_cap) a.bq[(size_t)p * a.bq_cap + q] = make_int4(i, e, mi, 0);
-                } else if (st == 4) {     // rare: 0 < C < 1 along a path
-                    double dx, dy, dz;
-                    lj_disp<R>(a, shift, i, j, img, dx, dy, dz);
-                    double gx = 0, gy = 0, gz = 0, E0 = E;
-                    lj_eval<R>(P, a.G, i, p, j, dx, dy, dz, C, code, sink, gx, gy, gz, E);
-                    if (JV && a.jv) {                 // S_r = 0 here: E = C V
-                        R qx = (R)dx, qy = (R)dy, qz = (R)dz;
-                        lj_pair_jvp<R>(P, a.G, i, j, qx, qy, qz, qx * qx + qy * qy + qz * qz, C, code, R(0), R(0),
-                                       a.jv, n, J);
+                } else if (st == 4) {     // 0 < C < 1 along a path
+                    if constexpr (PATHBUF) {      // to buffer 2
+                        Cq = C;
+                        codeq = code;
+                    } else {
+                        double dx, dy, dz;
+                        lj_disp<R>(a, shift, i, j, img, dx, dy, dz);
+                        double gx = 0, gy = 0, gz = 0, E0 = E;
+                        lj_eval<R>(P, a.G, i, p, j, dx, dy, dz, C, code, sink, gx, gy, gz, E);
+                        if (JV && a.jv) {                 // S_r = 0 here: E = C V
+                            R qx = (R)dx, qy = (R)dy, qz = (R)dz;
+                            lj_pair_jvp<R>(P, a.G, i, j, qx, qy, qz, qx * qx + qy * qy + qz * qz, C, code, R(0),
+                                           R(0), a.jv, n, J);
+                        }
+                        atomicAdd(a.f + i, gx); atomicAdd(a.f + n + i, gy); atomicAdd(a.f + 2 * n + i, gz);
+                        if (a.eatom) eatom_pair(a.eatom, i, j, E - E0);
                     }
-                    atomicAdd(a.f + i, gx); atomicAdd(a.f + n + i, gy); atomicAdd(a.f + 2 * n + i, gz);
-                    if (a.eatom) eatom_pair(a.eatom, i, j, E - E0);
                 }
             }
 #pragma unroll
-            for (int b = 0; b < 2; b++) {
-                int want = b == 0 ? 1 : 3;
+            for (int b = 0; b < NBUF; b++) {
+                int want = b == 0 ? 1 : (b == 1 ? 3 : 4);
                 unsigned m = __ballot_sync(0xffffffffu, st == want);
                 if (st == want) {
                     int s = cnt[b] + __popc(m & lt);
                     B.jp[b][s] = j | (p << 30); B.ia[b][s] = i; B.im[b][s] = img;
+                    if (PATHBUF && b == 2) { PB.C[s] = Cq; PB.code[s] = codeq; }
                 }
                 cnt[b] += __popc(m);
                 __syncwarp();
@@ -773,6 +827,7 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
                     if (lane < cnt[b] - 32) {
                         int s = 32 + lane;
                         B.jp[b][lane] = B.jp[b][s]; B.ia[b][lane] = B.ia[b][s]; B.im[b][lane] = B.im[b][s];
+                        if (PATHBUF && b == 2) { PB.C[lane] = PB.C[s]; PB.code[lane] = PB.code[s]; }
                     }
                     cnt[b] -= 32;
                     __syncwarp();
@@ -782,7 +837,7 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
     }
     // the warp's last, partly filled batches
 #pragma unroll
-    for (int b = 0; b < 2; b++)
+    for (int b = 0; b < NBUF; b++)
         if (lane < cnt[b]) batch(b);
     if (DF) {
         dacc.flush(a.fix, n, a.eatom);
@@ -929,7 +984,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 4) k_bstar_rev(StepA
 template <class R>
 __global__ void k_finish_counters(StepArgs<R> a) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
-        a.counters[CNT_BONDS] = (unsigned long long)(*a.nbonds + *a.nccbonds);
+        a.counters[CNT_BONDS] = (unsigned long long)(*a.nbonds + *a.nccbonds + *a.nhhbonds);
         a.counters[CNT_BSTAR] = (unsigned long long)(a.nbq[0] + a.nbq[1] + a.nbq[2]);
         a.counters[CNT_BSTAR_FULL] = (unsigned long long)(a.nbq2[0] + a.nbq2[1] + a.nbq2[2]);
         // the longest b* queue, kept with the other flags (a capacity check

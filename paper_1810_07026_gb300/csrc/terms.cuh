@@ -355,12 +355,18 @@ template <class R, bool D = true> HD R bicubic(const R* tab, R x, R y, R& fx, R&
         fy = (D && !cy) ? a[1] : R(0);
         return a[0];
     }
+    // at t = 0 in a dimension only its powers 0 and 1 (0 without derivatives)
+    // contribute: the loops stop there, with the same sums as the full ones
+    int pt = is_zero(tx) ? (D ? 1 : 0) : 3;
+    bool ty0 = is_zero(ty);
     R f = 0, dx = 0, dy = 0;
+#pragma unroll
     for (int p = 3; p >= 0; p--) {
+        if (p > pt) continue;
         const R* c = a + p * 4;
-        R cp = ((c[3] * ty + c[2]) * ty + c[1]) * ty + c[0];
+        R cp = ty0 ? c[0] : ((c[3] * ty + c[2]) * ty + c[1]) * ty + c[0];
         if (D) {
-            R dcp = (R(3) * c[3] * ty + R(2) * c[2]) * ty + c[1];
+            R dcp = ty0 ? c[1] : (R(3) * c[3] * ty + R(2) * c[2]) * ty + c[1];
             dx = dx * tx + f;
             dy = dy * tx + dcp;
         }
@@ -390,14 +396,22 @@ HD R tricubic_cell(const R* a, R tx, R ty, R tz, bool clx, bool cly, bool clz, R
         fz = (D && !clz) ? a[1] : R(0);
         return a[0];
     }
+    // at t = 0 in a dimension only its powers 0 and 1 (0 without derivatives)
+    // contribute: the loops stop there, with the same sums as the full ones
+    int pt = is_zero(tx) ? (D ? 1 : 0) : 3, qt = is_zero(ty) ? (D ? 1 : 0) : 3;
+    bool tz0 = is_zero(tz);
     R f = 0, dx = 0, dy = 0, dz = 0;
+#pragma unroll
     for (int p = 3; p >= 0; p--) {
+        if (p > pt) continue;
         R cp = 0, cpy = 0, cpz = 0;
+#pragma unroll
         for (int q = 3; q >= 0; q--) {
+            if (q > qt) continue;
             const R* c = a + (p * 4 + q) * 4;
-            R cq = ((c[3] * tz + c[2]) * tz + c[1]) * tz + c[0];
+            R cq = tz0 ? c[0] : ((c[3] * tz + c[2]) * tz + c[1]) * tz + c[0];
             if (D) {
-                R dcq = (R(3) * c[3] * tz + R(2) * c[2]) * tz + c[1];
+                R dcq = tz0 ? c[1] : (R(3) * c[3] * tz + R(2) * c[2]) * tz + c[1];
                 cpy = cpy * ty + cp;
                 cpz = cpz * ty + dcq;
             }
