@@ -81,8 +81,9 @@ enum { CNT_BONDS = 0, CNT_BSTAR = 1, CNT_DSB = 2, CNT_LJ = 3, CNT_MAP = 4, CNT_B
 
 // The FP64 evaluation of b* differs from the exact value of its formula by
 // its own rounding (of order 1e-14 for these magnitudes); the screen's bound
-// is against the exact value, so a decision needs this much more room.
-constexpr double BSTAR_SCREEN_SLACK = 1e-9;
+// is against the exact value, so a decision needs this much more room (an
+// FP32 constant of at least 1e-9).
+constexpr float BSTAR_SCREEN_SLACK = 1.1e-9f;
 
 // launchers, one instantiation per precision (kernels_f64.cu, kernels_f32.cu)
 // ev (nullable): 7 events recorded before each of the 6 stages and after the last

@@ -235,6 +235,44 @@ __global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
     }
 }
 
+// Groups the items of one pass of a block of NT threads (one item per
+// thread, or none) by a small key, so that the threads of a warp take items
+// with equal keys -- for the bond-order kernels the neighbour counts of the
+// two atoms, i.e. equal loop trip counts: a counting sort in shared memory.
+// key in [0, 64) for an item, -1 for none; returns the item this thread
+// takes, or -1.  Every thread of the block calls it.
+template <int NT>
+__device__ int block_group(int key, int item, int* s_cnt /* 65 */, int* s_item /* NT */) {
+    int t = threadIdx.x;
+    for (int k = t; k <= 64; k += NT) s_cnt[k] = 0;
+    __syncthreads();
+    int kk = key < 0 ? 64 : key;
+    int rank = atomicAdd(s_cnt + kk, 1);
+    __syncthreads();
+    if (t < 32) {                     // exclusive scan of the 64 key counts (the empty bucket last)
+        int v0 = s_cnt[2 * t], v1 = s_cnt[2 * t + 1], x = v0 + v1;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (t >= o) x += y;
+        }
+        int ex = x - v0 - v1;
+        __syncwarp();
+        s_cnt[2 * t] = ex;
+        s_cnt[2 * t + 1] = ex + v0;
+        if (t == 31) s_cnt[64] = x;
+    }
+    __syncthreads();
+    s_item[s_cnt[kk] + rank] = key < 0 ? -1 : item;
+    __syncthreads();
+    int r = s_item[t];
+    __syncthreads();                  // the arrays are rewritten by the next pass
+    return r;
+}
+// the grouping key of a pair of atoms: their neighbour counts (up to 7)
+__device__ __forceinline__ int count_key(const int* cnt, int i, int j) {
+    return (min(cnt[i], 7) << 3) | min(cnt[j], 7);
+}
+
 // ------------------------------------------------------------------ REBO bonds
 // EXTRA (here and in the torsion and b* kernels): the virial or the parameter
 // gradient is wanted; the instances without them hold no accumulators for them.
@@ -251,8 +289,19 @@ __global__ void __launch_bounds__(128, 4) k_rebo(StepArgs<R> a) {
     int ncc = min(*a.nccbonds, a.bond_cap), nch = min(*a.nbonds, a.bond_cap);
     int nhh = min(*a.nhhbonds, a.bond_cap - nch);
     int nb = ncc + nch + nhh;
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
-        int2 bd = b < ncc ? a.ccbonds[b] : (b < ncc + nch ? a.bonds[b - ncc] : a.bonds[a.bond_cap - 1 - (b - ncc - nch)]);
+    __shared__ int s_cnt[65], s_item[128];
+    auto bond = [&](int b) {
+        return b < ncc ? a.ccbonds[b] : (b < ncc + nch ? a.bonds[b - ncc] : a.bonds[a.bond_cap - 1 - (b - ncc - nch)]);
+    };
+    for (int base = blockIdx.x * 128; base < nb; base += gridDim.x * 128) {
+        int b = base + threadIdx.x, key = -1;
+        if (b < nb) {
+            int2 bd = bond(b);
+            key = count_key(a.G.cnt, bd.x, a.G.nj[bd.x * a.G.stride + bd.y]);
+        }
+        b = block_group<128>(key, b, s_cnt, s_item);
+        if (b < 0) continue;
+        int2 bd = bond(b);
         double e = rebo_bond<R>(P, a.G, bd.x, bd.y, sink, sc);
         E += e;
         if (a.eatom) eatom_pair(a.eatom, bd.x, a.G.nj[bd.x * a.G.stride + bd.y], e);
@@ -887,6 +936,13 @@ __global__ void __launch_bounds__(128, 8) k_bstar(StepArgs<R> a) {
     Sink sink{a.f, a.n, EXTRA && a.virial, {0, 0, 0, 0, 0, 0}, EXTRA && a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
     double E = 0;
     double J[6] = {0, 0, 0, 0, 0, 0};          // v . dF/d(eps, sigma) with a.jv
+    // the screen's thresholds in FP32: b_min rounded down, b_max rounded up
+    __shared__ float bcut[2][3];
+    if (threadIdx.x < 3) {
+        bcut[0][threadIdx.x] = __double2float_rd((double)P.bmin[threadIdx.x]);
+        bcut[1][threadIdx.x] = __double2float_ru((double)P.bmax[threadIdx.x]);
+    }
+    __syncthreads();
     int n0 = min(a.nbq[0], a.bq_cap), n1 = min(a.nbq[1], a.bq_cap), n2 = min(a.nbq[2], a.bq_cap);
     int nq = n0 + n1 + n2;
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nq; u += gridDim.x * blockDim.x) {
@@ -905,12 +961,14 @@ __global__ void __launch_bounds__(128, 8) k_bstar(StepArgs<R> a) {
             if (a.screen) {
                 // b* in FP32 with a bound e on its distance from the exact value:
                 // S_b is exactly 1 or 0 when [b* - e, b* + e] lies below b_min or
-                // above b_max (with room for the FP64 path's own rounding)
+                // above b_max (with room for the FP64 path's own rounding); the
+                // interval's ends are rounded outwards, the thresholds inwards,
+                // so the FP32 comparisons decide only what the exact ones would
                 ef bs = bstar_value_ef(*a.Pef, GraphEf(a.G32), i, j, dx, dy, dz);
-                double lo = (double)bs.v - (double)bs.e - BSTAR_SCREEN_SLACK;
-                double hi = (double)bs.v + (double)bs.e + BSTAR_SCREEN_SLACK;
-                bool below = hi < (double)P.bmin[p];
-                bool above = lo > (double)P.bmax[p];
+                float lo = __fsub_rd(__fsub_rd(bs.v, bs.e), BSTAR_SCREEN_SLACK);
+                float hi = __fadd_ru(__fadd_ru(bs.v, bs.e), BSTAR_SCREEN_SLACK);
+                bool below = hi < bcut[0][p];
+                bool above = lo > bcut[1][p];
                 decided = below || above;
                 Sb = below ? R(1) : R(0);
                 dSb = R(0);

@@ -1593,15 +1593,12 @@ HD int lj_classify(const DevParams<R>& P, const PathMap<R>& M, int i, int p, int
 // displacement d; C and its path given, and S_b(b*) with its derivative
 // already known.  Applies every force except the one through db*, which the
 // reverse bond order applies where dS_b != 0.  1/r, V and (dV/dr)/r of the
-// pair are given.
+// pair are given, and S_r with dS_r/dr.
 template <class R>
 HD double bstar_finish_v(const DevParams<R>& P, const Graph<R>& G, int i, int j, R dx, R dy, R dz, R r2,
-                         R inv_r, R V, R dVr, R C, int path_code, R Sb, R dSb, Sink& sink) {
+                         R inv_r, R V, R dVr, R Sr, R dSr, R C, int path_code, R Sb, R dSb, Sink& sink) {
     int p = pidx(G.type[i], G.type[j]);
     R r = r2 * inv_r;
-    R dSr;
-    R Sr = Sw<R>((r - P.Srlo[p]) * P.Srinv[p], dSr);
-    dSr *= P.Srinv[p];
     R factor = Sr * Sb + R(1) - Sr;
     R E = factor * C * V;
     R dEdr_r = (dSr * (Sb - R(1))) * C * V * inv_r + factor * C * dVr;   // (dE/dr)/r
@@ -1625,14 +1622,18 @@ HD double bstar_finish_v(const DevParams<R>& P, const Graph<R>& G, int i, int j,
     return (double)E;
 }
 
-// the same, with 1/r, V and (dV/dr)/r evaluated here
+// the same, with 1/r, V, (dV/dr)/r and S_r evaluated here
 template <class R>
 HD double bstar_finish(const DevParams<R>& P, const Graph<R>& G, int i, int j, R dx, R dy, R dz, R r2,
                        R C, int path_code, R Sb, R dSb, Sink& sink) {
+    int p = pidx(G.type[i], G.type[j]);
     R inv_r = rsqrt_(r2);
     R dVr;
-    R V = vlj<R>(P, pidx(G.type[i], G.type[j]), r2, inv_r, dVr);
-    return bstar_finish_v<R>(P, G, i, j, dx, dy, dz, r2, inv_r, V, dVr, C, path_code, Sb, dSb, sink);
+    R V = vlj<R>(P, p, r2, inv_r, dVr);
+    R dSr;
+    R Sr = Sw<R>((r2 * inv_r - P.Srlo[p]) * P.Srinv[p], dSr);
+    return bstar_finish_v<R>(P, G, i, j, dx, dy, dz, r2, inv_r, V, dVr, Sr, dSr * P.Srinv[p], C, path_code, Sb, dSb,
+                             sink);
 }
 
 // b* of the pair i -> (j, image) with displacement d: the bond order of
@@ -1692,7 +1693,8 @@ HD double bstar_full(const DevParams<R>& P, const Graph<R>& G, int i, int j, R d
             sink.W[3] -= (double)dx * gy; sink.W[4] -= (double)dx * gz; sink.W[5] -= (double)dy * gz;
         }
     }
-    return bstar_finish_v<R>(P, G, i, j, dx, dy, dz, r2, inv_r, V, dVr, C, path_code, bsw.Sb, bsw.dSb, sink);
+    return bstar_finish_v<R>(P, G, i, j, dx, dy, dz, r2, inv_r, V, dVr, Sr, dSr * P.Srinv[p], C, path_code, bsw.Sb,
+                             bsw.dSb, sink);
 }
 
 // ------------------------------------------------------------------ parameter derivatives of the forces
