@@ -144,29 +144,117 @@ __global__ void __launch_bounds__(128) k_posf(StepArgs<R> a) {
 // test.
 template <class R>
 __global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
     const DevParams<R>& P = *a.P;
+    // D_max^2 by species pair: in FP32 with the pre-test's factor, and in FP64
+    __shared__ float dm2f[3];
+    __shared__ double dm2[3];
+    // per warp: the entries that passed the FP32 pre-test, as (owner lane,
+    // entry), evaluated in FP64 32 at a time; and each lane's slot count
+    __shared__ int q_e[4][64];
+    __shared__ int q_l[4][64];
+    __shared__ int s_cnt[4][32];
+    if (threadIdx.x < 3) {
+        double d = (double)P.Dmax[threadIdx.x];
+        float df = (float)d;
+        dm2f[threadIdx.x] = df * df * 1.000001f;
+        dm2[threadIdx.x] = d * d;
+    }
+    int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    s_cnt[wib][lane] = 0;
+    __syncthreads();
     int n = a.n;
-    double xi = a.pos[i], yi = a.pos[n + i], zi = a.pos[2 * n + i];
-    float4 pfi = a.posf[i];
+    int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31);     // the warp's first atom
+    int i = i0 + lane;
+    bool act = i < n;
+    int ne = 0;
+    float4 pfi = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    int ti = 0;
+    if (act) {
+        ne = a.im_cnt[i];
+        pfi = a.posf[i];
+        ti = a.G.type[i];
+    }
     float err0 = 2.3841858e-7f * (2.0f * fmaxf(fabsf(pfi.x), fmaxf(fabsf(pfi.y), fabsf(pfi.z))) + 8.0f) +
                  (a.fix ? 4.8828125e-4f : 0.0f);
-    int ti = a.G.type[i];
-    int cnt = 0;
-    R nC = 0, nH = 0;
-    int ne = a.im_cnt[i];
-    const int2* row = a.im + (size_t)i * a.im_cap;
-    const double* L = box_of(a, i);
+    const int2* row = a.im + (size_t)(act ? i : 0) * a.im_cap;
+    const double* L = box_of(a, act ? i : 0);
     float Lf[3] = {(float)L[0], (float)L[1], (float)L[2]};
     float Lmax = fmaxf(Lf[0], fmaxf(Lf[1], Lf[2]));
-    for (int e = 0; e < ne; e++) {
-        int2 ent = row[e];
-        int j = ent.x, img = ent.y;
-        float4 pj = a.posf[j];
-        int tj = __float_as_int(pj.w);
-        int p = pidx(ti, tj);
-        {
+    unsigned lt = (1u << lane) - 1u;
+    int qn = 0;
+    // the FP64 test and the slot of queued entry k (this lane's), for the whole warp
+    auto batch = [&](int k) {
+        bool have = lane < k;
+        int ol = have ? q_l[wib][lane] : 0, e = have ? q_e[wib][lane] : 0;
+        int io = i0 + ol;
+        bool pass = false;
+        int j = 0, img = 0, to = 0, tj = 0, p = 0;
+        double dx = 0, dy = 0, dz = 0, r2 = 1;
+        if (have) {
+            int2 ent = a.im[(size_t)io * a.im_cap + e];
+            j = ent.x; img = ent.y;
+            to = a.G.type[io]; tj = a.G.type[j];
+            p = pidx(to, tj);
+            if (img == 0) {               // most entries: no image, three FP64 operations
+                dx = a.pos[j] - a.pos[io]; dy = a.pos[n + j] - a.pos[n + io]; dz = a.pos[2 * n + j] - a.pos[2 * n + io];
+            } else {
+                const double* Lo = box_of(a, io);
+                dx = a.pos[j] + img_x(img) * Lo[0] - a.pos[io];
+                dy = a.pos[n + j] + img_y(img) * Lo[1] - a.pos[n + io];
+                dz = a.pos[2 * n + j] + img_z(img) * Lo[2] - a.pos[2 * n + io];
+            }
+            r2 = dx * dx + dy * dy + dz * dz;
+            pass = lt_nonneg(r2, dm2[p]);            // r2 >= 0; a NaN is not below
+            // two atoms at (nearly) one point: every term diverges there
+            if (pass && !(r2 > 1e-12)) { atomicOr(a.err + ERR_NONFINITE, NONFINITE_OVERLAP); pass = false; }
+        }
+        // slots in entry order: the entries of one atom sit in the queue in
+        // the order of its row, and take consecutive slots after its count
+        unsigned mp = __ballot_sync(0xffffffffu, pass);
+        unsigned peers = __match_any_sync(0xffffffffu, pass ? ol : 32 + lane) & mp;
+        int rank = __popc(peers & lt);
+        int slot = pass ? s_cnt[wib][ol] + rank : 0;
+        __syncwarp();
+        if (pass && rank == __popc(peers) - 1) s_cnt[wib][ol] = slot + 1;
+        __syncwarp();
+        if (pass && slot < a.G.stride) {
+            double ir = rsqrt_(r2);
+            double r = r2 * ir;
+            R dw, omw;
+            R w = wfun_c<R>(P, p, (R)r, dw, omw);
+            int q = io * a.G.stride + slot;
+            a.g_nj[q] = j; a.g_nimg[q] = img;
+            a.g_dx[q] = (R)dx; a.g_dy[q] = (R)dy; a.g_dz[q] = (R)dz;
+            a.g_r[q] = (R)r; a.g_ir[q] = (R)ir; a.g_w[q] = w; a.g_dw[q] = dw; a.g_omw[q] = omw;
+            if (a.screen) {
+                a.s_dx[q] = (float)dx; a.s_dy[q] = (float)dy; a.s_dz[q] = (float)dz;
+                a.s_r[q] = (float)r; a.s_ir[q] = (float)ir; a.s_w[q] = ef_mark_inexact((double)w);
+            }
+            // each bond once: i < j between like species, from the carbon for C-H,
+            // so that the threads of a warp run the same code (species batches, Sec. 4.2)
+            bool mine = (to == tj) ? (j > io) : (to == 0);
+            if (mine) {
+                if (to == 0 && tj == 0) {
+                    int c = atomicAdd(a.nccbonds, 1);
+                    if (c < a.bond_cap) a.ccbonds[c] = make_int2(io, slot);
+                } else if (to == 1 && tj == 1) {   // H-H bonds from the far end of the same array
+                    int b = atomicAdd(a.nhhbonds, 1);
+                    if (b < a.bond_cap) a.bonds[a.bond_cap - 1 - b] = make_int2(io, slot);
+                } else {
+                    int b = atomicAdd(a.nbonds, 1);
+                    if (b < a.bond_cap) a.bonds[b] = make_int2(io, slot);
+                }
+            }
+        }
+    };
+    int nmax = __reduce_max_sync(0xffffffffu, ne);
+    for (int e = 0; e < nmax; e++) {
+        bool keep = false;
+        if (e < ne) {
+            int2 ent = row[e];
+            int j = ent.x, img = ent.y;
+            float4 pj = a.posf[j];
+            int p = pidx(ti, __float_as_int(pj.w));
             float fx = pj.x - pfi.x, fy = pj.y - pfi.y, fz = pj.z - pfi.z;
             float err = err0;
             if (img != 0) {
@@ -177,56 +265,39 @@ __global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
             // |r2f - r2| <= sum_c |f_c - d_c| (2 |f_c| + |f_c - d_c|) + rounding
             float r2f = fx * fx + fy * fy + fz * fz;
             float band = err * (2.0f * (fabsf(fx) + fabsf(fy) + fabsf(fz)) + 3.0f * err) + 1e-6f * r2f;
-            float dmf = (float)P.Dmax[p];
-            if (r2f > dmf * dmf * 1.000001f + band) continue;
+            keep = !(r2f > dm2f[p] + band);
         }
-        double dx, dy, dz;
-        if (img == 0) {               // most entries: no image, three FP64 operations
-            dx = a.pos[j] - xi; dy = a.pos[n + j] - yi; dz = a.pos[2 * n + j] - zi;
-        } else {
-            dx = a.pos[j] + img_x(img) * L[0] - xi;
-            dy = a.pos[n + j] + img_y(img) * L[1] - yi;
-            dz = a.pos[2 * n + j] + img_z(img) * L[2] - zi;
+        unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+            int s = qn + __popc(m & lt);
+            q_l[wib][s] = lane; q_e[wib][s] = e;
         }
-        double r2 = dx * dx + dy * dy + dz * dz;
-        double dmax = (double)P.Dmax[p];
-        if (!(r2 < dmax * dmax)) continue;
-        // two atoms at (nearly) one point: every term diverges there
-        if (!(r2 > 1e-12)) { atomicOr(a.err + ERR_NONFINITE, NONFINITE_OVERLAP); continue; }
-        double ir = rsqrt_(r2);
-        double r = r2 * ir;
-        R dw, omw;
-        R w = wfun_c<R>(P, p, (R)r, dw, omw);
-        if (cnt < a.G.stride) {
-            int q = i * a.G.stride + cnt;
-            a.g_nj[q] = j; a.g_nimg[q] = img;
-            a.g_dx[q] = (R)dx; a.g_dy[q] = (R)dy; a.g_dz[q] = (R)dz;
-            a.g_r[q] = (R)r; a.g_ir[q] = (R)ir; a.g_w[q] = w; a.g_dw[q] = dw; a.g_omw[q] = omw;
-            if (a.screen) {
-                a.s_dx[q] = (float)dx; a.s_dy[q] = (float)dy; a.s_dz[q] = (float)dz;
-                a.s_r[q] = (float)r; a.s_ir[q] = (float)ir; a.s_w[q] = ef_mark_inexact((double)w);
+        qn += __popc(m);
+        __syncwarp();
+        if (qn >= 32) {
+            batch(32);
+            __syncwarp();
+            if (lane < qn - 32) {
+                q_l[wib][lane] = q_l[wib][32 + lane]; q_e[wib][lane] = q_e[wib][32 + lane];
             }
-            // each bond once: i < j between like species, from the carbon for C-H,
-            // so that the threads of a warp run the same code (species batches, Sec. 4.2)
-            bool mine = (ti == tj) ? (j > i) : (ti == 0);
-            if (mine) {
-                if (ti == 0 && tj == 0) {
-                    int c = atomicAdd(a.nccbonds, 1);
-                    if (c < a.bond_cap) a.ccbonds[c] = make_int2(i, cnt);
-                } else if (ti == 1 && tj == 1) {   // H-H bonds from the far end of the same array
-                    int b = atomicAdd(a.nhhbonds, 1);
-                    if (b < a.bond_cap) a.bonds[a.bond_cap - 1 - b] = make_int2(i, cnt);
-                } else {
-                    int b = atomicAdd(a.nbonds, 1);
-                    if (b < a.bond_cap) a.bonds[b] = make_int2(i, cnt);
-                }
-            }
+            qn -= 32;
+            __syncwarp();
         }
-        cnt++;
-        if (tj == 0) nC += w; else nH += w;
     }
+    if (qn > 0) batch(qn);
+    __syncwarp();
+    if (!act) return;
+    int cnt = s_cnt[wib][lane];
+    int c = cnt < a.G.stride ? cnt : a.G.stride;
     if (cnt > a.G.stride) atomicMax(a.err + ERR_SHORT, cnt);
-    a.g_cnt[i] = cnt < a.G.stride ? cnt : a.G.stride;
+    // the coordinations, summed over the slots in row order
+    R nC = 0, nH = 0;
+    for (int s = 0; s < c; s++) {
+        int q = i * a.G.stride + s;
+        R w = a.g_w[q];
+        if (a.G.type[a.g_nj[q]] == 0) nC += w; else nH += w;
+    }
+    a.g_cnt[i] = c;
     a.g_nC[i] = nC;
     a.g_nH[i] = nH;
     if (a.screen) {
