@@ -56,9 +56,10 @@ FLOPS_LJ_PAIR = 44        # displacement with image (9), r^2 (5), sqrt, 1/r, (s/
 FLOPS_LJ_TEST = 14        # displacement and r^2 of a pair that is tested but not evaluated (C = 0, or queued for b*)
 # DRAM bytes (read + write) per atom of one k_lj<double> launch, measured by ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum) on the 261,120-atom PE with
-# the same kernel: 687.1 MB per launch.  The traffic is the list read, whose
-# length per atom the density fixes, so it scales with the atom count.
-LJ_DRAM_BYTES_PER_ATOM = 687.1e6 / 261120
+# the same kernel: 736.1 + 40.5 MB per launch.  The traffic is the list read
+# and the connectivity-map probes, whose size per atom the density fixes, so
+# it scales with the atom count.
+LJ_DRAM_BYTES_PER_ATOM = (736.137728e6 + 40.517632e6) / 261120
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 FP64_FMA_PER_SM_CLK = 2   # 1.25 TFLOP/s nominal FP64 = 152 SMs x 2 FMA x 2 flop x 2.07 GHz
