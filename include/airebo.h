@@ -216,7 +216,8 @@ airebo_status airebo_counters(airebo_handle h, int64_t* out8);
 
 /*
  * Copy a neighbour list to the host (for checks).  which: 0 = LJ half list
- * (pairs i<j, or i==j with a positive image, r < 3 sigma + skin), 1 = REBO
+ * (each pair once, in the row of the atom that sorts first by cell at the
+ * last build; i==j with a positive image; r < 3 sigma + skin), 1 = REBO
  * intermediate list (r < Dmax + skin, full), 2 = exact REBO list of the last
  * compute (r < Dmax, full, at most 8 per atom).  h_cnt: int32[n];
  * h_j: int32[n * cap]; h_img: int8[n * cap * 3] (image S, x_j + S L - x_i).

@@ -140,6 +140,7 @@ __global__ void __launch_bounds__(128) k_build(NeighborArgs a, const int* cell_s
     // cells farther than the largest cut-off from this atom are skipped: the
     // squared distance from the atom to a stencil cell's box, per dimension
     float rmax2 = fmaxf(fmaxf(lj2[0], lj2[1]), fmaxf(im2[0], im2[1]));
+    float rim2 = fmaxf(im2[0], im2[1]);
     float Lf[3] = {(float)g.L[0], (float)g.L[1], (float)g.L[2]};
     float cwf[3] = {(float)g.cw[0], (float)g.cw[1], (float)g.cw[2]};
     int nlj = 0, nim = 0;
@@ -166,13 +167,18 @@ __global__ void __launch_bounds__(128) k_build(NeighborArgs a, const int* cell_s
             int cy = qy - sy * g.nc[1];
             for (int oz = -g.reach[2]; oz <= g.reach[2]; oz++) {
                 int qz = ci[2] + oz;
-                if (ey + slab(qz, 2, pi.z) >= rmax2) continue;
+                float ez = ey + slab(qz, 2, pi.z);
+                if (ez >= rmax2) continue;
                 int sz = qz >= 0 ? qz / g.nc[2] : -((-qz + g.nc[2] - 1) / g.nc[2]);
                 int cz = qz - sz * g.nc[2];
                 int c = g.cell0 + (cx * g.nc[1] + cy) * g.nc[2] + cz;
                 float shx = sx * Lf[0] - pi.x, shy = sy * Lf[1] - pi.y, shz = sz * Lf[2] - pi.z;
+                // the LJ half list keeps a pair in the row of the atom that
+                // sorts first (cell order): beyond the REBO range only the
+                // candidates sorted from this atom on can enter a list
                 int e1 = cell_start[c + 1];
-                for (int t = cell_start[c]; t < e1; t++) {
+                int t0 = ez < rim2 ? cell_start[c] : max(cell_start[c], s);
+                for (int t = t0; t < e1; t++) {
                     float4 pj = a.spos[t];
                     float dx = pj.x + shx, dy = pj.y + shy, dz = pj.z + shz;
                     float r2 = dx * dx + dy * dy + dz * dz;
@@ -190,7 +196,7 @@ __global__ void __launch_bounds__(128) k_build(NeighborArgs a, const int* cell_s
                         nim++;
                     }
                     bool pos = Sx > 0 || (Sx == 0 && (Sy > 0 || (Sy == 0 && Sz > 0)));
-                    if (a.with_lj && (j > i || (self && pos))) {
+                    if (a.with_lj && (t > s || (self && pos))) {
                         if (nlj < a.lj_cap) ljrow[nlj] = make_int2(j, img);
                         nlj++;
                     }

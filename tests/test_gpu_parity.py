@@ -222,8 +222,9 @@ def as_set(cnt, j, img):
 @pytest.mark.parametrize("case", ["diamond216", "hot300", "pe1152"])
 def test_lists(A, oracle, params, param_text, case):
     """Index work: the exact REBO list equals the oracle's set bit for bit; the
-    skin lists contain every pair within cut-off + skin, and nothing beyond it
-    by more than the FP32 margin."""
+    skin lists contain every pair within cut-off + skin (the LJ half list once,
+    in one of the pair's two rows), and nothing beyond it by more than the
+    FP32 margin."""
     pos, types, box = CASES[case]()
     _, ev = gpu_eval(A, param_text, pos, types, box)
     off, jj, img = oracle.rebo_neighbors(pos, types, box)
@@ -235,8 +236,9 @@ def test_lists(A, oracle, params, param_text, case):
         for (i, j, S) in got:
             d = pos[:, j] + np.array(S) * box - pos[:, i]
             assert np.sqrt(d @ d) < cut(types[i], types[j]) + skin + 3e-3
-            if which == 0:
-                assert j > i or (j == i and S > (0, 0, 0))
+            if which == 0:                  # each pair once: never also in j's row
+                assert (j, i, tuple(-s for s in S)) not in got or (j == i and S > (0, 0, 0))
+                assert j != i or S > (0, 0, 0)
         # every pair within cut + skin - margin is present
         rc = np.array([[cut(a, b) for b in (0, 1)] for a in (0, 1)])
         for i in range(0, len(types), 7):
@@ -249,8 +251,10 @@ def test_lists(A, oracle, params, param_text, case):
                     j = int(j)
                     if j == i and S == (0, 0, 0):
                         continue
-                    if which == 1 or j > i or (j == i and S > (0, 0, 0)):
+                    if which == 1:
                         assert (i, j, S) in got
+                    elif j != i or S > (0, 0, 0):      # the half list holds it in one of the two rows
+                        assert (i, j, S) in got or (j, i, tuple(-s for s in S)) in got
 
 
 def test_pe32k_full_parity(A, oracle, param_text):
