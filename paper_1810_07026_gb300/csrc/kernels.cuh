@@ -407,12 +407,14 @@ __global__ void __launch_bounds__(128) k_torsion_dd(StepArgs<double> a) {
     const DevParams<dd>& P = *a.Pdd;
     GraphAs<dd, double> G(a.G);
     Sink sink{a.f, a.n, EXTRA && a.virial, {0, 0, 0, 0, 0, 0}, false, {0, 0, 0, 0, 0, 0}};
+    __shared__ dd tstore[TORS_L * TORS_V * 128];       // the l-side values and sums of each thread
+    TorsStore<dd> S{tstore + threadIdx.x, 128};
     double E = 0;
     int nb = *a.nccbonds;
     if (nb > a.bond_cap) nb = a.bond_cap;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
         int2 bd = a.ccbonds[b];
-        double e = torsion_bond<dd>(P, G, bd.x, bd.y, sink);
+        double e = torsion_bond_f<dd>(P, G, bd.x, bd.y, sink, S);
         E += e;
         if (a.eatom && e != 0.0) eatom_pair(a.eatom, bd.x, a.G.nj[bd.x * a.G.stride + bd.y], e);
     }

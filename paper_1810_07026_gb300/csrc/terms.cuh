@@ -1141,15 +1141,16 @@ HD double torsion_bond(const DevParams<R>& P, const GT& G, int i, int slot, Sink
 // products with u and the forces on k (on l) are applied once per
 // neighbour.  The l-side values and sums of up to TORS_L neighbours of j sit
 // in a per-thread store in shared memory ([value][slot][thread]); a j with
-// more neighbours takes torsion_bond.
+// more neighbours takes torsion_bond.  GT: the graph view (the FP64 short
+// list read as double-float in the DF64 kernel).
 constexpr int TORS_L = 3, TORS_V = 12;      // slots, values per slot
 template <class R> struct TorsStore {
     R* p;
     int stride;
     HD R& at(int t, int v) const { return p[(t * TORS_V + v) * stride]; }
 };
-template <class R>
-HD double torsion_bond_f(const DevParams<R>& P, const Graph<R>& G, int i, int slot, Sink& sink, TorsStore<R> S) {
+template <class R, class GT = Graph<R>>
+HD double torsion_bond_f(const DevParams<R>& P, const GT& G, int i, int slot, Sink& sink, TorsStore<R> S) {
     int q = i * G.stride + slot;
     int j = G.nj[q];
     int ni = G.cnt[i], nj = G.cnt[j];
