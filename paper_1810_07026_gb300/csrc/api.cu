@@ -378,6 +378,7 @@ struct airebo_ctx {
     int2* bonds = nullptr; int2* ccbonds = nullptr; int bond_cap = 0;
     int4* bq = nullptr; int bq_cap = 0;
     int* bq2 = nullptr;
+    int4* pq = nullptr;             // LJ pairs along a path (0 < C_ij < 1), FP64 arithmetic
     int* counts = nullptr;               // [0] non-C-C bonds [2] C-C bonds [3] b* reverse queue [4..6] b* queue per species pair [7] LJ work counter
     double* acc = nullptr;               // 9 doubles
     unsigned long long* counters = nullptr;   // 8
@@ -565,6 +566,7 @@ airebo_status alloc_atoms(airebo_handle h, int n) {
     h->bq_cap = std::max(h->bq_cap, na * 4 + 1024);
     CK(realloc_dev(h->bq, 3 * (size_t)h->bq_cap));
     CK(realloc_dev(h->bq2, 3 * (size_t)h->bq_cap));
+    CK(realloc_dev(h->pq, (size_t)h->bq_cap));
     h->n_alloc = na;
     airebo_status st = h->opt.precision == AIREBO_MIXED ? alloc_step<float>(h, h->p32, na) : alloc_step<double>(h, h->p64, na);
     if (st) return st;
@@ -743,6 +745,7 @@ template <class R> StepArgs<R> make_args(airebo_handle h, Precision<R>& pr, cons
     a.ccbonds = h->ccbonds; a.nccbonds = h->counts + 2;
     a.bq = h->bq; a.nbq = h->counts + 4; a.bq_cap = h->bq_cap;
     a.bq2 = h->bq2; a.nbq2 = h->counts + 8;
+    a.pq = h->pq; a.npq = h->counts + 3;
     a.screen = false;
     a.Pef = nullptr;
     a.G32 = Graph<float>{};
@@ -851,11 +854,12 @@ airebo_status do_compute(airebo_handle h, Precision<R>& pr, const double* d_pos,
             again = true;
         }
         const int* cn = (const int*)h->h_u64;
-        int nq = std::max(cn[4], std::max(cn[5], cn[6]));
+        int nq = std::max(std::max(cn[3], cn[4]), std::max(cn[5], cn[6]));    // path queue, b* queues
         if (nq > h->bq_cap) {
             h->bq_cap = nq + nq / 4 + 1024;
             CK(realloc_dev(h->bq, 3 * (size_t)h->bq_cap));
             CK(realloc_dev(h->bq2, 3 * (size_t)h->bq_cap));
+            CK(realloc_dev(h->pq, (size_t)h->bq_cap));
             again = true;
         }
         if (!again) return AIREBO_OK;
@@ -1003,7 +1007,7 @@ void airebo_destroy(airebo_handle h) {
         for (void* p : bs) if (p) cudaFree(p);
     }
     void* ps[] = {h->types, h->cell_of, h->cell_count, h->cell_start, h->cell_fill, h->spos, h->posf, h->pq_lo, h->fix, h->swrap, h->lj, h->lj_cnt,
-                  h->im, h->im_cnt, h->xref, h->bonds, h->ccbonds, h->bq, h->bq2, h->counts, h->acc, h->counters, h->derr, h->maxd2, h->ke,
+                  h->im, h->im_cnt, h->xref, h->bonds, h->ccbonds, h->bq, h->bq2, h->pq, h->counts, h->acc, h->counters, h->derr, h->maxd2, h->ke,
                   h->gate, h->d_builds, h->nerr,
                   h->hpos, h->hvel, h->hforce, h->he4, h->hw6};
     for (void* p : ps) if (p) cudaFree(p);
@@ -1269,7 +1273,7 @@ airebo_status airebo_check(airebo_handle h) {
     std::string cap;
     if (h->h_err[ERR_SHORT] > h->stride) cap += " REBO neighbours per atom (" + std::to_string(h->h_err[ERR_SHORT]) + ")";
     if (h->h_err[ERR_MAP]) cap += " connectivity-map entries per atom (" + std::to_string(h->h_err[ERR_MAP]) + ")";
-    if (h->h_err[ERR_QUEUE] > h->bq_cap) cap += " b* queue (" + std::to_string(h->h_err[ERR_QUEUE]) + ")";
+    if (h->h_err[ERR_QUEUE] > h->bq_cap) cap += " b* or path queue (" + std::to_string(h->h_err[ERR_QUEUE]) + ")";
     if (!cap.empty())
         return fail(h, AIREBO_ERR_CAPACITY, "a scratch capacity was exceeded:" + cap + "; run airebo_compute once to grow it");
     return AIREBO_OK;
@@ -1292,11 +1296,12 @@ template <class R> static airebo_status reserve_headroom(airebo_handle h, Precis
     CK(cudaMemcpyAsync(h->h_u64, h->counts, sizeof(int) * 8, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     const int* cn = (const int*)h->h_u64;
-    int nq = std::max(cn[4], std::max(cn[5], cn[6]));
+    int nq = std::max(std::max(cn[3], cn[4]), std::max(cn[5], cn[6]));
     if (nq + nq / 4 + 1024 > h->bq_cap) {
         h->bq_cap = nq + nq / 4 + 1024;
         CK(realloc_dev(h->bq, 3 * (size_t)h->bq_cap));
         CK(realloc_dev(h->bq2, 3 * (size_t)h->bq_cap));
+        CK(realloc_dev(h->pq, (size_t)h->bq_cap));
     }
     return AIREBO_OK;
 }

@@ -48,6 +48,7 @@ template <class R> struct StepArgs {
     int2* ccbonds; int* nccbonds;             // C-C bonds i<j, same capacity
     int4* bq; int* nbq; int bq_cap;
     int* bq2; int* nbq2;                   // b* pairs left to the full-precision pass, by species pair (3 x bq_cap)
+    int4* pq; int* npq;                    // LJ pairs along a path for k_lj_path (FP64 arithmetic; bq_cap)
     // b* screen (FP64): an FP32 b* with a rigorous error bound decides S_b
     // where the whole bound lies outside the transition
     bool screen;

@@ -468,17 +468,11 @@ __device__ __forceinline__ int queue_slot(int* ctr, int k) {
 constexpr int LJ_THREADS = 256;
 constexpr int LJ_WARPS = LJ_THREADS / 32;
 
-// three compaction buffers per warp: 0 = inner pairs, 1 = pairs in the
-// cut-off switch, 2 = pairs with 0 < C_ij < 1 along a path (and, with the
-// parameter derivatives, every pair), whose C_ij and path code sit in LjPathBuf
+// two compaction buffers per warp: 0 = inner pairs, 1 = pairs in the cut-off switch
 struct LjBuf {
-    int jp[3][64];          // j | species pair << 30
-    int ia[3][64];          // the list's atom i
-    int im[3][64];          // packed image of j
-};
-template <class R> struct LjPathBuf {
-    R C[64];
-    int code[64];
+    int jp[2][64];          // j | species pair << 30
+    int ia[2][64];          // the list's atom i
+    int im[2][64];          // packed image of j
 };
 
 // Per-lane force (and energy) accumulator of the atom whose pairs the lane
@@ -512,31 +506,6 @@ __device__ __forceinline__ void lj_disp(const StepArgs<R>& a, const double (*shi
             dx += shift[0][sx + 4]; dy += shift[1][sy + 4]; dz += shift[2][sz + 4];
         }
     }
-}
-
-// The compacted pairs along a path (buffer 2): the general pair term with
-// C_ij and the path's forces, in FP64 in every instance (their number is
-// small; with the parameter derivatives every pair takes this batch)
-template <class R, bool JV>
-__device__ __forceinline__ void lj_batch_path(const StepArgs<R>& a, const DevParams<R>& P, const double (*shift)[9],
-                                           const LjBuf& B, const LjPathBuf<R>& PB, int lane, Sink& sink,
-                                           double& E, double* J) {
-    int jp = B.jp[2][lane];
-    int j = jp & 0x3fffffff, p = (unsigned)jp >> 30;
-    int i = B.ia[2][lane];
-    R C = PB.C[lane];
-    int code = PB.code[lane];
-    int n = a.n;
-    double dx, dy, dz;
-    lj_disp<R>(a, shift, i, j, B.im[2][lane], dx, dy, dz);
-    double gx = 0, gy = 0, gz = 0, E0 = E;
-    lj_eval<R>(P, a.G, i, p, j, dx, dy, dz, C, code, sink, gx, gy, gz, E);
-    if (JV && a.jv) {                 // S_r = 0 here: E = C V
-        R qx = (R)dx, qy = (R)dy, qz = (R)dz;
-        lj_pair_jvp<R>(P, a.G, i, j, qx, qy, qz, qx * qx + qy * qy + qz * qz, C, code, R(0), R(0), a.jv, n, J);
-    }
-    atomicAdd(a.f + i, gx); atomicAdd(a.f + n + i, gy); atomicAdd(a.f + 2 * n + i, gz);
-    if (a.eatom) eatom_pair(a.eatom, i, j, E - E0);
 }
 
 template <class R>
@@ -772,15 +741,13 @@ template <class R, bool DF, int MODE>
 __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
     constexpr bool EXTRA = MODE >= 1;      // virial or parameter gradient
     constexpr bool JV = MODE == 2;         // the parameter derivatives of the forces too
-    // path pairs (FP64 arithmetic) batched where the FP64 pipe bounds the
-    // kernel; the FP32 instance evaluates them where they are found
-    constexpr bool PATHBUF = sizeof(R) == 8;
-    constexpr int NBUF = PATHBUF ? 3 : 2;
+    // path pairs (FP64 arithmetic) go to k_lj_path where the FP64 pipe bounds
+    // the kernel; the FP32 instance evaluates them where they are found
+    constexpr bool PATHQ = sizeof(R) == 8;
     const DevParams<R>& P = *a.P;
     __shared__ double shift[3][9];                // image shifts S L for S in [-4, 4]
     __shared__ LjCuts<float> cutsf[3];            // thresholds in FP32, by species pair
     __shared__ LjBuf bufs[LJ_WARPS];
-    __shared__ LjPathBuf<R> pbufs[PATHBUF ? LJ_WARPS : 1];
     __shared__ float shf[2][3][9];                // DF: split image shifts (hi, lo)
     __shared__ DfParams dfp;
     __shared__ LjPow ljk[3];                       // the LJ pair in powers of 1/r^2, by species pair
@@ -803,7 +770,6 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
     __syncthreads();
     int lane = threadIdx.x & 31;
     LjBuf& B = bufs[threadIdx.x >> 5];
-    LjPathBuf<R>& PB = pbufs[PATHBUF ? threadIdx.x >> 5 : 0];
     unsigned lt = (1u << lane) - 1u;
     Sink sink{a.f, a.n, EXTRA && a.virial, {0, 0, 0, 0, 0, 0}, EXTRA && a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
     bool general = EXTRA && (a.pgrad != nullptr || a.jv != nullptr);
@@ -815,13 +781,9 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
     double E = 0;
     unsigned evaluated = 0;
     int n = a.n;
-    int cnt[3] = {0, 0, 0};
+    int cnt[2] = {0, 0};
     // the pair arithmetic of one full (or, at the end, partial) batch
     auto batch = [&](int b) {
-        if (PATHBUF && b == 2) {
-            lj_batch_path<R, JV>(a, P, shift, B, PB, lane, sink, E, J);
-            return;
-        }
         if constexpr (DF) {
             if constexpr (sizeof(R) == 8) lj_batch_df<R, EXTRA>(a, dfp, shf[0], shf[1], B, b, lane, dacc, Edf, Wdf);
             else lj_batch_mx<R, EXTRA>(a, P, shf[0], shf[1], B, b, lane, dacc, Edf, Wdf);
@@ -854,8 +816,6 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
         for (int base = 0; base < ne; base += 32) {
             int e = base + lane;
             int st = 0, j = 0, p = 0, img = 0;
-            R Cq = R(1);
-            int codeq = -1;                // C_ij and path of a pair for buffer 2
             if (e < ne) {
                 int2 ent = row[e];
                 j = ent.x;
@@ -914,9 +874,9 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
                     int q = queue_slot(a.nbq, p);
                     if (q < a.bq_cap) a.bq[(size_t)p * a.bq_cap + q] = make_int4(i, e, mi, 0);
                 } else if (st == 4) {     // 0 < C < 1 along a path
-                    if constexpr (PATHBUF) {      // to buffer 2
-                        Cq = C;
-                        codeq = code;
+                    if constexpr (PATHQ) {        // to k_lj_path, a thread per pair
+                        int q = queue_slot(a.npq, 0);
+                        if (q < a.bq_cap) a.pq[q] = make_int4(i, e, mi, 0);
                     } else {
                         double dx, dy, dz;
                         lj_disp<R>(a, shift, i, j, img, dx, dy, dz);
@@ -933,13 +893,12 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
                 }
             }
 #pragma unroll
-            for (int b = 0; b < NBUF; b++) {
-                int want = b == 0 ? 1 : (b == 1 ? 3 : 4);
+            for (int b = 0; b < 2; b++) {
+                int want = b == 0 ? 1 : 3;
                 unsigned m = __ballot_sync(0xffffffffu, st == want);
                 if (st == want) {
                     int s = cnt[b] + __popc(m & lt);
                     B.jp[b][s] = j | (p << 30); B.ia[b][s] = i; B.im[b][s] = img;
-                    if (PATHBUF && b == 2) { PB.C[s] = Cq; PB.code[s] = codeq; }
                 }
                 cnt[b] += __popc(m);
                 __syncwarp();
@@ -949,7 +908,6 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
                     if (lane < cnt[b] - 32) {
                         int s = 32 + lane;
                         B.jp[b][lane] = B.jp[b][s]; B.ia[b][lane] = B.ia[b][s]; B.im[b][lane] = B.im[b][s];
-                        if (PATHBUF && b == 2) { PB.C[lane] = PB.C[s]; PB.code[lane] = PB.code[s]; }
                     }
                     cnt[b] -= 32;
                     __syncwarp();
@@ -959,7 +917,7 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
     }
     // the warp's last, partly filled batches
 #pragma unroll
-    for (int b = 0; b < NBUF; b++)
+    for (int b = 0; b < 2; b++)
         if (lane < cnt[b]) batch(b);
     if (DF) {
         dacc.flush(a.fix, n, a.eatom);
@@ -974,6 +932,54 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
     block_accumulate<LJ_THREADS>(E, sink.W, EXTRA && a.virial, a.acc + 1, a.acc + 3);
     if (EXTRA && a.pgrad) block_accumulate_g<LJ_THREADS>(sink.G, a.pgrad);
     if (JV && a.jv) block_accumulate_g<LJ_THREADS>(J, a.jout);
+}
+
+// The LJ pairs along a path (0 < C_ij < 1, or with the parameter derivatives
+// every pair with C_ij > 0 that the FP64 path evaluates in full), queued by
+// the FP64 and DF64 instances of k_lj: a thread per pair, the general pair
+// term with C_ij and the path's forces.  There are about one per atom once
+// thermal motion makes partial bonds; evaluated inside k_lj, by the few lanes
+// whose entries they were or in per-warp batches, they left most lanes of
+// their FP64 instructions idle.
+template <class R, int MODE>
+__global__ void __launch_bounds__(128) k_lj_path(StepArgs<R> a) {
+    constexpr bool EXTRA = MODE >= 1, JV = MODE == 2;
+    const DevParams<R>& P = *a.P;
+    __shared__ double shift[3][9];                // image shifts S L for S in [-4, 4]
+    if (threadIdx.x < 27)
+        shift[threadIdx.x / 9][threadIdx.x % 9] = (double)((int)(threadIdx.x % 9) - 4) * a.L[threadIdx.x / 9];
+    __syncthreads();
+    Sink sink{a.f, a.n, EXTRA && a.virial, {0, 0, 0, 0, 0, 0}, EXTRA && a.pgrad != nullptr, {0, 0, 0, 0, 0, 0}};
+    double E = 0;
+    double J[6] = {0, 0, 0, 0, 0, 0};          // v . dF/d(eps, sigma) with a.jv
+    int n = a.n;
+    int nq = min(*a.npq, a.bq_cap);
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nq; u += gridDim.x * blockDim.x) {
+        int4 q = a.pq[u];
+        int i = q.x;
+        int2 ent = a.lj[(size_t)i * a.lj_cap + q.y];
+        int j = ent.x;
+        int p = pidx(a.G.type[i], a.G.type[j]);
+        R C = R(1);
+        int code = -1;
+        if (q.z >= 0) {
+            C = a.M.wt[(size_t)i * a.M.cap + q.z];
+            code = a.M.path[(size_t)i * a.M.cap + q.z];
+        }
+        double dx, dy, dz;
+        lj_disp<R>(a, shift, i, j, ent.y, dx, dy, dz);
+        double gx = 0, gy = 0, gz = 0, E0 = E;
+        lj_eval<R>(P, a.G, i, p, j, dx, dy, dz, C, code, sink, gx, gy, gz, E);
+        if (JV && a.jv) {                 // S_r = 0 here: E = C V
+            R qx = (R)dx, qy = (R)dy, qz = (R)dz;
+            lj_pair_jvp<R>(P, a.G, i, j, qx, qy, qz, qx * qx + qy * qy + qz * qz, C, code, R(0), R(0), a.jv, n, J);
+        }
+        atomicAdd(a.f + i, gx); atomicAdd(a.f + n + i, gy); atomicAdd(a.f + 2 * n + i, gz);
+        if (a.eatom) eatom_pair(a.eatom, i, j, E - E0);
+    }
+    block_accumulate<128>(E, sink.W, EXTRA && a.virial, a.acc + 1, a.acc + 3);
+    if (EXTRA && a.pgrad) block_accumulate_g<128>(sink.G, a.pgrad);
+    if (JV && a.jv) block_accumulate_g<128>(J, a.jout);
 }
 
 // ------------------------------------------------------------------ b* pairs
@@ -1120,7 +1126,7 @@ __global__ void k_finish_counters(StepArgs<R> a) {
         a.counters[CNT_BSTAR_FULL] = (unsigned long long)(a.nbq2[0] + a.nbq2[1] + a.nbq2[2]);
         // the longest b* queue, kept with the other flags (a capacity check
         // after several asynchronous evaluations sees the largest of them)
-        int q = max(a.nbq[0], max(a.nbq[1], a.nbq[2]));
+        int q = max(max(a.nbq[0], a.nbq[1]), max(a.nbq[2], *a.npq));
         if (q > a.bq_cap) atomicMax(a.err + ERR_QUEUE, q);
     }
 }
@@ -1243,6 +1249,12 @@ void launch_compute_impl(const StepArgs<R>& a, cudaStream_t s, int num_sms, cuda
             if (mode == 2) launch(k_lj<R, false, 2>, 4);
             else if (mode == 1) launch(k_lj<R, false, 1>, 1);
             else launch(k_lj<R, false, 0>, 0);
+        }
+        if (sizeof(R) == 8) {             // the path pairs the FP64-arithmetic instances queued
+            int g = num_sms * 16;
+            if (mode == 2) k_lj_path<R, 2><<<g, 128, 0, s>>>(a);
+            else if (mode == 1) k_lj_path<R, 1><<<g, 128, 0, s>>>(a);
+            else k_lj_path<R, 0><<<g, 128, 0, s>>>(a);
         }
     }
     mark(5);

@@ -972,16 +972,20 @@ HD R bond_order(const DevParams<R>& P, const GT& G, int i, int j, R ux, R uy, R 
     }
 }
 
-// bond_order of an unbonded pair with the carbon first for a C-H pair:
-// b_ij = b_ji with u -> -u, so the lanes of a warp of C-H pairs (taken from
-// the half list in either order) walk the carbon's neighbours in the same
-// side pass.  The swap is made on the arguments and undone on the results.
+// bond_order of an unbonded pair in a canonical orientation: the carbon
+// first for a C-H pair, the lower index first for a like pair.  b_ij = b_ji
+// with u -> -u for the symmetric tables of the potential, but not for a
+// perturbed (asymmetric) pi^rc or T table, so the orientation must not depend
+// on which atom's list row holds the pair; and the lanes of a warp of C-H
+// pairs then walk the carbon's neighbours in the same side pass.  The swap is
+// made on the arguments and undone on the results.
 template <class R, bool REV, class SinkT = Sink, class GT = Graph<R>>
 HD R bond_order_c(const DevParams<R>& P, const GT& G, int i, int j, R ux, R uy, R uz, R umag, R inv_u,
                   R eps, SinkT& sink, R& gux, R& guy, R& guz, R& gumag,
                   double& fix, double& fiy, double& fiz, double& fjx, double& fjy, double& fjz,
                   BstarSwitch<R>* bsw = nullptr, SideCache<R> sc = SideCache<R>{nullptr, 0}) {
-    bool sw = G.type[i] == 1 && G.type[j] == 0;
+    int ti = G.type[i], tj = G.type[j];
+    bool sw = (ti == 1 && tj == 0) || (ti == tj && j < i);
     int a = sw ? j : i, b = sw ? i : j;
     R vx = sw ? -ux : ux, vy = sw ? -uy : uy, vz = sw ? -uz : uz;
     R gvx = R(0), gvy = R(0), gvz = R(0);
