@@ -501,12 +501,12 @@ def run_ours(args):
             hbm, hbm_kind = hbm_peak()
             gbs = roof["traffic"] / lj_avg_s / 1e9
             roof["hbm"] = {"achieved_gbs": gbs, "peak_gbs": hbm, "peak_kind": hbm_kind, "frac": gbs / hbm}
-        # kernels of one NVE step: 2 half kicks, short list, REBO, torsion, map,
-        # per timed step (one airebo_nve call): two half-step kernels, the nine
+        # per timed step (one airebo_nve call): two half-step kernels, the ten
         # kernels of an evaluation (FP32 positions, short list, REBO, torsion,
-        # map, LJ, two b* passes, counters) and the energy write; five more per
-        # list rebuild (bin, scan, scatter, build, order)
-        launches = 12 * args.steps + 5 * r64["builds"]
+        # map, LJ, LJ pairs along a path, two b* passes, counters) and the
+        # energy write; five more per list rebuild (bin, scan, scatter, build,
+        # order)
+        launches = 13 * args.steps + 5 * r64["builds"]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r64["ms"] / args.steps, "higher_is_better": True,

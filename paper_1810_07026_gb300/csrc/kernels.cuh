@@ -464,7 +464,8 @@ __device__ __forceinline__ int queue_slot(int* ctr, int k) {
 // C_ij lookup, S_r); the pairs that need the full pair term are compacted with
 // a ballot into a per-warp buffer in shared memory (the "compress" of Sec. 4.3),
 // and the FP64 pair arithmetic runs only on full batches of 32 compacted pairs,
-// so no lane idles through it.  Pairs with S_r != 0 go to the b* queue.
+// so no lane idles through it.  Pairs with S_r != 0 go to the b* queue, pairs
+// along a path (0 < C_ij < 1) to the queue of k_lj_path.
 constexpr int LJ_THREADS = 256;
 constexpr int LJ_WARPS = LJ_THREADS / 32;
 
@@ -741,9 +742,6 @@ template <class R, bool DF, int MODE>
 __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
     constexpr bool EXTRA = MODE >= 1;      // virial or parameter gradient
     constexpr bool JV = MODE == 2;         // the parameter derivatives of the forces too
-    // path pairs (FP64 arithmetic) go to k_lj_path where the FP64 pipe bounds
-    // the kernel; the FP32 instance evaluates them where they are found
-    constexpr bool PATHQ = sizeof(R) == 8;
     const DevParams<R>& P = *a.P;
     __shared__ double shift[3][9];                // image shifts S L for S in [-4, 4]
     __shared__ LjCuts<float> cutsf[3];            // thresholds in FP32, by species pair
@@ -873,23 +871,9 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
                 if (st == 2) {
                     int q = queue_slot(a.nbq, p);
                     if (q < a.bq_cap) a.bq[(size_t)p * a.bq_cap + q] = make_int4(i, e, mi, 0);
-                } else if (st == 4) {     // 0 < C < 1 along a path
-                    if constexpr (PATHQ) {        // to k_lj_path, a thread per pair
-                        int q = queue_slot(a.npq, 0);
-                        if (q < a.bq_cap) a.pq[q] = make_int4(i, e, mi, 0);
-                    } else {
-                        double dx, dy, dz;
-                        lj_disp<R>(a, shift, i, j, img, dx, dy, dz);
-                        double gx = 0, gy = 0, gz = 0, E0 = E;
-                        lj_eval<R>(P, a.G, i, p, j, dx, dy, dz, C, code, sink, gx, gy, gz, E);
-                        if (JV && a.jv) {                 // S_r = 0 here: E = C V
-                            R qx = (R)dx, qy = (R)dy, qz = (R)dz;
-                            lj_pair_jvp<R>(P, a.G, i, j, qx, qy, qz, qx * qx + qy * qy + qz * qz, C, code, R(0),
-                                           R(0), a.jv, n, J);
-                        }
-                        atomicAdd(a.f + i, gx); atomicAdd(a.f + n + i, gy); atomicAdd(a.f + 2 * n + i, gz);
-                        if (a.eatom) eatom_pair(a.eatom, i, j, E - E0);
-                    }
+                } else if (st == 4) {     // 0 < C < 1 along a path: to k_lj_path, a thread per pair
+                    int q = queue_slot(a.npq, 0);
+                    if (q < a.bq_cap) a.pq[q] = make_int4(i, e, mi, 0);
                 }
             }
 #pragma unroll
@@ -935,9 +919,8 @@ __global__ void __launch_bounds__(LJ_THREADS, 4) k_lj(StepArgs<R> a) {
 }
 
 // The LJ pairs along a path (0 < C_ij < 1, or with the parameter derivatives
-// every pair with C_ij > 0 that the FP64 path evaluates in full), queued by
-// the FP64 and DF64 instances of k_lj: a thread per pair, the general pair
-// term with C_ij and the path's forces.  There are about one per atom once
+// every pair with C_ij > 0 outside the b* queue), queued by k_lj: a thread per
+// pair, the general pair term with C_ij and the path's forces.  There are about one per atom once
 // thermal motion makes partial bonds; evaluated inside k_lj, by the few lanes
 // whose entries they were or in per-warp batches, they left most lanes of
 // their FP64 instructions idle.
@@ -1250,7 +1233,7 @@ void launch_compute_impl(const StepArgs<R>& a, cudaStream_t s, int num_sms, cuda
             else if (mode == 1) launch(k_lj<R, false, 1>, 1);
             else launch(k_lj<R, false, 0>, 0);
         }
-        if (sizeof(R) == 8) {             // the path pairs the FP64-arithmetic instances queued
+        {                                 // the pairs along a path that k_lj queued
             int g = num_sms * 16;
             if (mode == 2) k_lj_path<R, 2><<<g, 128, 0, s>>>(a);
             else if (mode == 1) k_lj_path<R, 1><<<g, 128, 0, s>>>(a);
