@@ -54,12 +54,13 @@ DRIFT_STEPS = 200         # NVE steps after the timed region whose total energy 
 # Algorithmic FP64 work per unit, in flops (FMA = 2).
 FLOPS_LJ_PAIR = 44        # displacement with image (9), r^2 (5), sqrt, 1/r, (s/r)^6, V, dV/dr, force, sums (30)
 FLOPS_LJ_TEST = 14        # displacement and r^2 of a pair that is tested but not evaluated (C = 0, or queued for b*)
-# DRAM bytes (read + write) per atom of one k_lj<double> launch, measured by ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum) on the 261,120-atom PE with
-# the same kernel: 736.1 + 40.5 MB per launch.  The traffic is the list read
-# and the connectivity-map probes, whose size per atom the density fixes, so
-# it scales with the atom count.
-LJ_DRAM_BYTES_PER_ATOM = (736.137728e6 + 40.517632e6) / 261120
+# DRAM bytes (read + write) per atom of one k_lj<double> launch and the
+# k_lj_path launch that follows it (the LJ stage the bench times), measured by
+# ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the 261,120-atom PE
+# with the same kernels: 724.4 + 21.6 MB and 9.0 + 0.1 MB per launch.  The
+# traffic is the list read and the connectivity-map probes, whose size per
+# atom the density fixes, so it scales with the atom count.
+LJ_DRAM_BYTES_PER_ATOM = (724.409856e6 + 21.606144e6 + 8.958208e6 + 0.11776e6) / 261120
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 FP64_FMA_PER_SM_CLK = 2   # 1.25 TFLOP/s nominal FP64 = 152 SMs x 2 FMA x 2 flop x 2.07 GHz
@@ -492,7 +493,7 @@ def run_ours(args):
         roof = {"kernel": "k_lj<double>", "bound": "alu", "achieved": achieved, "peak": peak64_nom,
                 "unit": "TFLOP/s", "frac": (achieved / peak64_nom) if achieved else None,
                 "traffic": LJ_DRAM_BYTES_PER_ATOM * n if args.workload.startswith("pe") else None,
-                "traffic_unit": "bytes per launch (ncu, 261,120-atom PE, scaled by atoms)",
+                "traffic_unit": "bytes per k_lj + k_lj_path launch pair (ncu, 261,120-atom PE, scaled by atoms)",
                 "peak_kind": "FP64 nominal from SM count x FMA units x max clock; measured FMA probe beside it",
                 "peak_measured": peak64_meas,
                 "flops_per_launch": flops_lj, "avg_launch_ms": lj_avg_s * 1e3,
