@@ -230,8 +230,9 @@ airebo_status airebo_export_lists(airebo_handle h, int which, int32_t* h_cnt, in
  * each launch.  airebo_set_timing(h, 1) starts (and zeroes) the record;
  * airebo_kernel_times fills ms[k] (total milliseconds) and launches[k] for
  * k = 0 FP32 positions and short list, 1 REBO bonds, 2 torsion, 3
- * connectivity map, 4 LJ pairs (with the merge of the fixed-point LJ sums in
- * the mixed and DF64 paths), 5 b* pairs (first pass), 6 neighbour build, 7 NVE
+ * connectivity map, 4 LJ pairs (the pair kernel, the kernel of the pairs
+ * along a path, and the merge of the fixed-point LJ sums in the mixed and DF64
+ * paths), 5 b* pairs (first pass), 6 neighbour build, 7 NVE
  * half steps, 8 b* pairs (second pass).  out arrays: 9 entries.
  */
 airebo_status airebo_set_timing(airebo_handle h, int on);
