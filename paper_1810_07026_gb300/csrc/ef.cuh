@@ -312,12 +312,23 @@ struct GraphEf {
           r{g.r}, ir{g.ir}, w{g.w}, nC{g.nC}, nH{g.nH} {}
 };
 
+// A displacement component rounded to FP32, with a bound on the rounding
+// from the rounded value alone: |x - RN(x)| <= 2^-24 |RN(x)| for a normal
+// result, plus the smallest subnormal for one below the normal range.  One
+// conversion and FP32 work (the exact error, x - (double)RN(x), would take
+// three more FP64-pipe instructions); the bound is the worst case of the
+// rounding at this magnitude, at most twice the largest error it can make.
+HD ef ef_round(double x) {
+    float v = (float)x;
+    return ef::raw(v, ru_add(ru_mul(fabsf(v), 5.9604645e-8f), 1.4e-45f));
+}
+
 // b* of the pair i -> (j, image) (the bond order at the fixed length r* along
 // the FP64 displacement d), with its bound
 template <class GT>
 HD ef bstar_value_ef(const DevParams<ef>& P, const GT& G, int i, int j, double dx, double dy, double dz) {
     int p = pidx(G.type[i], G.type[j]);
-    ef x(dx), y(dy), z(dz);
+    ef x = ef_round(dx), y = ef_round(dy), z = ef_round(dz);
     ef r2 = x * x + y * y + z * z;
     ef inv_r = rsqrt_(r2);
     ef rs = P.rstar[p];
