@@ -970,8 +970,9 @@ __global__ void __launch_bounds__(128) k_lj_path(StepArgs<R> a) {
 // exactly 1 below b_min and 0 above b_max.  Where b* is clear of that
 // transition, phase 1 finishes the pair; the others go to a second queue, and
 // phase 2 evaluates them in one bond-order pass with its reverse.  In FP64 the
-// phase-1 b* is an FP32 evaluation, trusted only outside a band of
-// BSTAR_SCREEN_MARGIN around the transition (the screen).
+// phase-1 b* is an FP32 evaluation that carries a rigorous bound on its
+// distance from the exact value, trusted only where that interval, widened by
+// BSTAR_SCREEN_SLACK, lies clear of the transition (the screen).
 template <class R>
 __device__ __forceinline__ void bstar_load(const StepArgs<R>& a, int t, int& i, int& j, double& dx, double& dy,
                                            double& dz, R& C, int& code) {
