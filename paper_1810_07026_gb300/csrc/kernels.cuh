@@ -1075,9 +1075,31 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 4) k_bstar_rev(StepA
     SideCache<R> sc{sizeof(R) == 8 ? scache + threadIdx.x : nullptr, 128};
     int n0 = min(a.nbq2[0], a.bq_cap), n1 = min(a.nbq2[1], a.bq_cap), n2 = min(a.nbq2[2], a.bq_cap);
     int nq = n0 + n1 + n2;
-    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nq; u += gridDim.x * blockDim.x) {
-        // species pair by species pair (CC, CH, HH), so that warps are uniform
-        int s = u < n0 ? u : (u < n0 + n1 ? a.bq_cap + (u - n0) : 2 * a.bq_cap + (u - n0 - n1));
+    // species pair by species pair (CC, CH, HH); in FP64 each block's pairs are
+    // further grouped by the two atoms' neighbour counts and whether their
+    // coordinations are integers (the spline knot paths), so that the lanes of
+    // a warp run like bond orders (the FP32 instance is faster without)
+    __shared__ int s_cnt[65], s_item[128];
+    auto seg = [&](int u) { return u < n0 ? u : (u < n0 + n1 ? a.bq_cap + (u - n0) : 2 * a.bq_cap + (u - n0 - n1)); };
+    auto int_n = [&](int x) { R N = a.G.nC[x] + a.G.nH[x]; return N == floor_(N) ? 1 : 0; };
+    constexpr bool GROUP = sizeof(R) == 8;
+    int step = GROUP ? gridDim.x * 128 : gridDim.x * blockDim.x;
+    for (int base = blockIdx.x * (GROUP ? 128 : blockDim.x); base < nq; base += step) {
+        int u = base + (GROUP ? threadIdx.x : 0);
+        if constexpr (GROUP) {
+            int key = -1;
+            if (u < nq) {
+                int4 q = a.bq[a.bq2[seg(u)]];
+                int ii = q.x, jj = a.lj[(size_t)q.x * a.lj_cap + q.y].x;
+                key = (min(a.G.cnt[ii] + a.G.cnt[jj], 15) << 2) | (int_n(ii) << 1) | int_n(jj);
+            }
+            u = block_group<128>(key, u, s_cnt, s_item);
+            if (u < 0) continue;
+        } else {
+            u = base + threadIdx.x;
+            if (u >= nq) break;
+        }
+        int s = seg(u);
         int i, j, code;
         double dx, dy, dz;
         R C;
