@@ -308,8 +308,8 @@ __global__ void __launch_bounds__(128) k_short_list(StepArgs<R> a) {
 
 // Groups the items of one pass of a block of NT threads (one item per
 // thread, or none) by a small key, so that the threads of a warp take items
-// with equal keys -- for the bond-order kernels the neighbour counts of the
-// two atoms, i.e. equal loop trip counts: a counting sort in shared memory.
+// with equal keys -- for the bond-order kernels bond_key, i.e. equal loop trip
+// counts and spline paths: a counting sort in shared memory.
 // key in [0, 64) for an item, -1 for none; returns the item this thread
 // takes, or -1.  Every thread of the block calls it.
 template <int NT>
@@ -339,9 +339,12 @@ __device__ int block_group(int key, int item, int* s_cnt /* 65 */, int* s_item /
     __syncthreads();                  // the arrays are rewritten by the next pass
     return r;
 }
-// the grouping key of a pair of atoms: their neighbour counts (up to 7)
-__device__ __forceinline__ int count_key(const int* cnt, int i, int j) {
-    return (min(cnt[i], 7) << 3) | min(cnt[j], 7);
+// the grouping key of a pair of atoms for their bond order: the sum of their
+// neighbour counts (loop trip counts) and whether each coordination is an
+// integer (the spline knot paths)
+template <class R> __device__ __forceinline__ int bond_key(const Graph<R>& G, int i, int j) {
+    R Ni = G.nC[i] + G.nH[i], Nj = G.nC[j] + G.nH[j];
+    return (min(G.cnt[i] + G.cnt[j], 15) << 2) | ((Ni == floor_(Ni) ? 1 : 0) << 1) | (Nj == floor_(Nj) ? 1 : 0);
 }
 
 // ------------------------------------------------------------------ REBO bonds
@@ -368,7 +371,7 @@ __global__ void __launch_bounds__(128, 4) k_rebo(StepArgs<R> a) {
         int b = base + threadIdx.x, key = -1;
         if (b < nb) {
             int2 bd = bond(b);
-            key = count_key(a.G.cnt, bd.x, a.G.nj[bd.x * a.G.stride + bd.y]);
+            key = bond_key<R>(a.G, bd.x, a.G.nj[bd.x * a.G.stride + bd.y]);
         }
         b = block_group<128>(key, b, s_cnt, s_item);
         if (b < 0) continue;
@@ -1081,7 +1084,6 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 4) k_bstar_rev(StepA
     // a warp run like bond orders (the FP32 instance is faster without)
     __shared__ int s_cnt[65], s_item[128];
     auto seg = [&](int u) { return u < n0 ? u : (u < n0 + n1 ? a.bq_cap + (u - n0) : 2 * a.bq_cap + (u - n0 - n1)); };
-    auto int_n = [&](int x) { R N = a.G.nC[x] + a.G.nH[x]; return N == floor_(N) ? 1 : 0; };
     constexpr bool GROUP = sizeof(R) == 8;
     int step = GROUP ? gridDim.x * 128 : gridDim.x * blockDim.x;
     for (int base = blockIdx.x * (GROUP ? 128 : blockDim.x); base < nq; base += step) {
@@ -1090,8 +1092,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 4) k_bstar_rev(StepA
             int key = -1;
             if (u < nq) {
                 int4 q = a.bq[a.bq2[seg(u)]];
-                int ii = q.x, jj = a.lj[(size_t)q.x * a.lj_cap + q.y].x;
-                key = (min(a.G.cnt[ii] + a.G.cnt[jj], 15) << 2) | (int_n(ii) << 1) | int_n(jj);
+                key = bond_key<R>(a.G, q.x, a.lj[(size_t)q.x * a.lj_cap + q.y].x);
             }
             u = block_group<128>(key, u, s_cnt, s_item);
             if (u < 0) continue;
